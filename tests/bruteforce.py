@@ -1,0 +1,120 @@
+"""Brute-force geometry used to pin the oracle (test helper, pure numpy).
+
+Nothing here follows the oracle's or the GPU library's algorithms: it samples
+points densely along a ray and classifies each point by direct point location
+in the pin lattice, then run-length encodes the region sequence.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def region_ids(prob, x, y):
+    """Radial region of points (x, y): cell by cell, inner circle then moderator."""
+    cx = np.clip(np.floor(x / prob.pitch).astype(np.int64), 0, prob.ncx - 1)
+    cy = np.clip(np.floor(y / prob.pitch).astype(np.int64), 0, prob.ncy - 1)
+    c = cy * prob.ncx + cx
+    nreg = np.where(prob.has_pin != 0, 2, 1)
+    base = np.concatenate([[0], np.cumsum(nreg)[:-1]])
+    px = (cx + 0.5) * prob.pitch
+    py = (cy + 0.5) * prob.pitch
+    inside = (x - px) ** 2 + (y - py) ** 2 < prob.fuel_radius ** 2
+    pin = prob.has_pin[c] != 0
+    return np.where(pin & ~inside, base[c] + 1, base[c])
+
+
+def laydown(prob, m):
+    """Closed-form cyclic laydown of first-quadrant azimuth m."""
+    W_x = prob.ncx * prob.pitch
+    W_y = prob.ncy * prob.pitch
+    phi = 2 * math.pi * (m + 0.5) / prob.n_azim
+    nx = math.ceil(W_x * abs(math.sin(phi)) / prob.radial_spacing)
+    ny = math.ceil(W_y * abs(math.cos(phi)) / prob.radial_spacing)
+    phi_eff = math.atan2(W_y * nx, W_x * ny)
+    return dict(nx=nx, ny=ny, phi_eff=phi_eff, W_x=W_x, W_y=W_y,
+                delta_eff=(W_x / nx) * math.sin(phi_eff))
+
+
+def track_start_dir(prob, tr):
+    """Start point and unit direction of a 2D track from its face/index."""
+    A = prob.n_azim
+    a = tr["azim"]
+    nq = A // 4
+    m = a if a < nq else A // 2 - 1 - a
+    ld = laydown(prob, m)
+    nx, ny, W_x, W_y = ld["nx"], ld["ny"], ld["W_x"], ld["W_y"]
+    k = tr["sk"]
+    face = tr["sface"]
+    if face == 2:      # ymin
+        x0, y0 = (k + 0.5) * W_x / nx, 0.0
+    elif face == 0:    # xmin
+        x0, y0 = 0.0, (k + 0.5) * W_y / ny
+    else:              # xmax
+        x0, y0 = W_x, (k + 0.5) * W_y / ny
+    phi = ld["phi_eff"] if a < nq else math.pi - ld["phi_eff"]
+    return x0, y0, math.cos(phi), math.sin(phi), ld
+
+
+def exit_length(prob, x0, y0, dx, dy):
+    W_x = prob.ncx * prob.pitch
+    W_y = prob.ncy * prob.pitch
+    ts = []
+    if dx > 0:
+        ts.append((W_x - x0) / dx)
+    if dx < 0:
+        ts.append(-x0 / dx)
+    if dy > 0:
+        ts.append((W_y - y0) / dy)
+    return min(ts)
+
+
+def rle(ids, step):
+    """Run-length encode a sampled id sequence: (ids, lengths)."""
+    ids = np.asarray(ids)
+    if ids.size == 0:
+        return np.zeros(0, dtype=np.int64), np.zeros(0)
+    change = np.flatnonzero(np.diff(ids)) + 1
+    starts = np.concatenate([[0], change])
+    ends = np.concatenate([change, [ids.size]])
+    return ids[starts], (ends - starts) * step
+
+
+def drop_short(ids, lens, min_len):
+    """Remove runs shorter than min_len and merge equal neighbours."""
+    keep = lens >= min_len
+    ids, lens = ids[keep], lens[keep]
+    if ids.size == 0:
+        return ids, lens
+    out_i, out_l = [ids[0]], [lens[0]]
+    for i, l in zip(ids[1:], lens[1:]):
+        if i == out_i[-1]:
+            out_l[-1] += l
+        else:
+            out_i.append(i)
+            out_l.append(l)
+    return np.array(out_i), np.array(out_l)
+
+
+def ray_regions(prob, x0, y0, dx, dy, L, n_samples=200000):
+    h = L / n_samples
+    s = (np.arange(n_samples) + 0.5) * h
+    ids = region_ids(prob, x0 + s * dx, y0 + s * dy)
+    return rle(ids, h) + (h,)
+
+
+def ray_fsrs_3d(prob, x0, y0, dx, dy, L, z_start, cot, n_samples=200000):
+    """FSR sequence and 3D lengths of the 3D line z(s) = z_start + s cot over the
+    2D track, sampled densely, keeping only the part inside 0 < z < H."""
+    h = L / n_samples
+    s = (np.arange(n_samples) + 0.5) * h
+    z = z_start + s * cot
+    inside = (z > 0) & (z < prob.height)
+    s, z = s[inside], z[inside]
+    reg = region_ids(prob, x0 + s * dx, y0 + s * dy)
+    layer = np.floor(z / (prob.height / prob.n_layers)).astype(np.int64)
+    fsr = reg * prob.n_layers + layer
+    sin = 1.0 / math.sqrt(1.0 + cot * cot)
+    ids, lens = rle(fsr, h / sin)
+    return ids, lens, h / sin
