@@ -1,0 +1,246 @@
+/*
+ * moc.h -- C ABI of the GB300 3D method-of-characteristics transport sweep.
+ *
+ * The library solves the multigroup neutron transport equation (Eq. 1 of
+ * "Neutron particle transport 3D method of characteristic Multi GPU platform
+ * Parallel Computing", arXiv 2503.17743) on an axially extruded pin lattice
+ * with the method of characteristics: 2D cyclic tracks are expanded on the
+ * GPU into axially stacked 3D tracks (Sec. 2.2, Eqs. 5-11), every segment is
+ * attenuated per group and polar angle with the flat-source solution (Eq. 3)
+ * and tallied into flat-source-region (FSR) scalar fluxes (Eq. 4), inside a
+ * power iteration for k-eff (Sec. 3.1, "iterative solving").
+ *
+ * Conventions for every entry point:
+ *   - Every call returns MOC_OK (0) or one of the MOC_ERR_* codes below;
+ *     moc_last_error() returns a thread-local message for the last failure.
+ *   - All pointers in descriptors are HOST pointers; the library copies what
+ *     it needs during the call and never keeps a caller pointer.
+ *   - Handles are opaque and owned by the library; each create/generate has
+ *     a destroy.  Device memory is allocated by the library with cudaMalloc
+ *     on the device named in moc_track_params.device.
+ *   - `stream` arguments are cudaStream_t values passed as void*; NULL means
+ *     the handle's own stream.  Calls that return results to host memory
+ *     synchronise that stream before returning.
+ *   - Arrays indexed by FSR use the FSR numbering of the geometry: radial
+ *     regions numbered cell by cell (cell c = cy*ncx + cx; a pin cell has the
+ *     region inside the circle then the moderator around it, any other cell
+ *     one region), FSR = region * n_layers + layer.  Group index is fastest:
+ *     phi[fsr * G + g].
+ */
+#ifndef MOC3D_MOC_H
+#define MOC3D_MOC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define MOC_OK 0
+#define MOC_ERR_INVALID_ARG 1
+#define MOC_ERR_OUT_OF_MEMORY 2
+#define MOC_ERR_CUDA 3
+#define MOC_ERR_NOT_CONVERGED 4
+#define MOC_ERR_TIMEOUT 5
+#define MOC_ERR_UNSUPPORTED 6
+
+/* arithmetic of the sweep */
+#define MOC_FP32 0
+#define MOC_FP64 1
+
+/* FSR tally strategy of the sweep kernel */
+#define MOC_TALLY_AUTO 0   /* shared-memory tile when it fits, else global */
+#define MOC_TALLY_SHARED 1 /* per-stack tile privatised in shared memory, flushed in FP64 */
+#define MOC_TALLY_GLOBAL 2 /* atomics straight into the FP64 global tally */
+
+typedef struct moc_geometry moc_geometry;
+typedef struct moc_tracks moc_tracks;
+
+/* Axially extruded pin lattice (Sec. 2.2: every axial plane has the same
+ * radial geometry; materials may change from layer to layer).
+ *   ncx, ncy      cells along x and y, square cells of side `pitch` (cm)
+ *   fuel_radius   radius (cm) of the circle of a pin cell, < pitch/2
+ *   height        axial extent (cm), split into n_layers equal layers
+ *   has_pin       [ncy*ncx] 1 = cell holds a circle (two regions), 0 = one region
+ *   mat_in        [ncy*ncx*n_layers] material inside the circle, per layer
+ *   mat_out       [ncy*ncx*n_layers] material outside the circle (whole cell
+ *                 for has_pin = 0), per layer
+ *   bc            faces xmin, xmax, ymin, ymax, zmin, zmax: 1 reflective, 0 vacuum */
+typedef struct {
+    int32_t ncx, ncy;
+    double pitch, fuel_radius, height;
+    int32_t n_layers;
+    const int32_t *has_pin;
+    const int32_t *mat_in;
+    const int32_t *mat_out;
+    int32_t bc[6];
+} moc_geometry_desc;
+
+/* Multigroup macroscopic cross sections (1/cm), host arrays:
+ *   sigma_t     [M*G]     total
+ *   sigma_s     [M*G*G]   scattering from group g into group h at [m][g][h]
+ *   nu_sigma_f  [M*G]     nu times fission
+ *   chi         [M*G]     fission spectrum
+ *   ext_source  [M*G]     isotropic volumetric source density, or NULL */
+typedef struct {
+    int32_t num_materials, num_groups;
+    const double *sigma_t;
+    const double *sigma_s;
+    const double *nu_sigma_f;
+    const double *chi;
+    const double *ext_source;
+} moc_materials;
+
+/* Track layout and sweep configuration.
+ *   n_azim             azimuthal angles over [0, 2 pi), multiple of 4
+ *   n_polar            polar angles over (0, pi), even (Gauss-Legendre in
+ *                      cos(theta), n_polar/2 per hemisphere)
+ *   radial_spacing     desired 2D track spacing (cm); corrected for cycles
+ *   axial_spacing      desired z-stack spacing dz (cm, Eq. 5); the layer
+ *                      height must be a whole number of spacings
+ *   precision          MOC_FP32 or MOC_FP64 sweep arithmetic
+ *   preload_budget_bytes  device bytes for stored (EXP) segments, Sec. 4.2:
+ *                      < 0 store every segment, 0 generate every segment on
+ *                      the fly (OTF), > 0 store the largest stacks first
+ *                      until the budget is used
+ *   tally_mode         MOC_TALLY_*
+ *   block_threads      threads per block of the sweep (0 = tuned default)
+ *   blocks_per_sm      resident sweep blocks per SM (0 = occupancy maximum)
+ *   device             CUDA device ordinal */
+typedef struct {
+    int32_t n_azim, n_polar;
+    double radial_spacing, axial_spacing;
+    int32_t precision;
+    int64_t preload_budget_bytes;
+    int32_t tally_mode;
+    int32_t block_threads;
+    int32_t blocks_per_sm;
+    int32_t device;
+} moc_track_params;
+
+/* Stopping rule of a solve: |k_n - k_(n-1)| < tol_k (eigenvalue problems
+ * only) and residual < tol_src, or max_iter iterations.  tol_src <= 0 runs
+ * exactly max_iter iterations.  use_graph = 1 captures one outer iteration
+ * as a CUDA graph and replays it. */
+typedef struct {
+    double tol_k, tol_src;
+    int32_t max_iter;
+    int32_t use_graph;
+} moc_solve_params;
+
+/* Result of a solve or of moc_iterate. */
+typedef struct {
+    double k;               /* k-eff (1 for fixed-source problems) */
+    double residual;        /* RMS relative change of the fission source (eigen) or flux (fixed) */
+    double dk;              /* k change over the last iteration */
+    double production;      /* sum V nu-Sigma_f phi of the normalised flux */
+    double absorption;      /* sum V Sigma_a phi */
+    double leakage;         /* outgoing weighted flux at vacuum faces, last sweep */
+    double seconds;         /* device time of the iterations */
+    double integrations;    /* segment-group integrations performed */
+    int32_t iterations;
+    int32_t converged;
+} moc_result;
+
+/* thread-local message of the last error */
+const char *moc_last_error(void);
+
+/* Create a geometry from a lattice and cross sections (host only, no GPU
+ * work).  Errors: MOC_ERR_INVALID_ARG for NULL arrays, non-positive or NaN
+ * Sigma_t, negative cross sections, scattering row sums >= Sigma_t, material
+ * indices out of range, a circle that does not fit its cell. */
+int moc_create_geometry(const moc_geometry_desc *desc, const moc_materials *mat,
+                        moc_geometry **out);
+void moc_destroy_geometry(moc_geometry *geom);
+
+/* Device bytes moc_generate_tracks would allocate for this layout, without
+ * allocating (host work only): `resident` excludes stored segments,
+ * `preload_all` is the extra for storing every segment. */
+int moc_query_footprint(const moc_geometry *geom, const moc_track_params *params,
+                        int64_t *resident, int64_t *preload_all);
+
+/* 2D cyclic tracking on the host (Sec. 3.1 keeps it on the CPU), z-stack
+ * tables (Sec. 3.2 Z-STACK), then on the device: per-track segment counts,
+ * the preload plan (Sec. 4.2) and the stored segments, tracked FSR volumes,
+ * and the initial state (phi = 1, boundary fluxes 0, k = 1).  Errors:
+ * MOC_ERR_UNSUPPORTED when the layer height is not a whole number of axial
+ * spacings, MOC_ERR_OUT_OF_MEMORY when the device cannot hold the state,
+ * MOC_ERR_CUDA on a CUDA failure. */
+int moc_generate_tracks(const moc_geometry *geom, const moc_track_params *params,
+                        moc_tracks **out);
+void moc_destroy_tracks(moc_tracks *tracks);
+
+/* One transport sweep (Eq. 3 on every segment, both directions, all groups
+ * and polar angles; tallies of Eq. 4) from the current source, followed by
+ * the scalar-flux update phi = (4 pi Q + tally / V) / Sigma_t.  Boundary
+ * fluxes advance by one Jacobi step. */
+int moc_sweep(moc_tracks *tracks, void *stream);
+
+/* Isotropic source from the current flux:
+ * Q = (sum_h Sigma_s[h->g] phi_h + chi_g / k * sum_h nuSigma_f,h phi_h + S_g) / (4 pi). */
+int moc_update_source(moc_tracks *tracks, double k, void *stream);
+
+/* Power iteration to convergence (eigenvalue problem; the geometry must have
+ * no external source).  Returns MOC_ERR_NOT_CONVERGED (with `res` filled)
+ * when max_iter is reached first. */
+int moc_solve_eigen(moc_tracks *tracks, const moc_solve_params *params, moc_result *res);
+
+/* Source iteration to convergence of a fixed-source problem (the geometry
+ * must have an external source). */
+int moc_solve_fixed_source(moc_tracks *tracks, const moc_solve_params *params,
+                           moc_result *res);
+
+/* Reset the state to phi = 1, zero boundary fluxes, k = 1. */
+int moc_reset(moc_tracks *tracks);
+
+/* Run exactly n outer iterations (source, sweep, flux update, k update) from
+ * the current state; eigenvalue or fixed-source by the geometry. */
+int moc_iterate(moc_tracks *tracks, int32_t n, int32_t use_graph, moc_result *res);
+
+/* Copy the normalised scalar flux [n_fsr*G] (FP64, host) and k. */
+int moc_get_flux(moc_tracks *tracks, double *phi, double *k);
+
+/* Set the scalar flux [n_fsr*G] and k (host FP64 input). */
+int moc_set_flux(moc_tracks *tracks, const double *phi, double k);
+
+/* Tracked FSR volumes [n_fsr] (FP64, host). */
+int moc_get_volumes(moc_tracks *tracks, double *volumes);
+
+/* Layout counts, int64 values written to out[0..n-1]:
+ *   0 n_fsr, 1 groups, 2 2D tracks, 3 z-stacks (both hemispheres), 4 3D tracks,
+ *   5 3D segments, 6 segment-group integrations per sweep, 7 stored segments,
+ *   8 preloaded stacks, 9 device bytes held, 10 axial lattice cells Nz,
+ *   11 lattice cells per layer, 12 sweep blocks, 13 sweep threads per block,
+ *   14 tally mode in use, 15 precision, 16 sweep shared memory bytes per block,
+ *   17 shared tile entries, 18 lanes per track (groups, padded), 19 most
+ *   segments on one track */
+int moc_tracks_info(const moc_tracks *tracks, int64_t *out, int32_t n);
+
+/* 3D segments of z-stack (t, p) as the device generator produces them
+ * (lengths in the sweep's precision, returned as FP64):
+ * t = 2D track, p = polar index in [0, n_polar) (p < n_polar/2 upward, p - n_polar/2
+ * the downward mirror).  Tracks are listed by their lattice index i (the
+ * track whose height at the start of t is z_0 + i dz with 0 <= z_0 < dz), in
+ * increasing i; segments in traversal order along t.  Capacities are in
+ * elements; on return *n_tracks and *n_segments hold the sizes (also when a
+ * capacity was too small, with MOC_ERR_INVALID_ARG). */
+int moc_get_stack_segments(moc_tracks *tracks, int32_t t, int32_t p, int64_t cap_tracks,
+                           int64_t cap_segments, int64_t *track_index, int32_t *n_seg,
+                           int32_t *fsr, double *length, int64_t *n_tracks,
+                           int64_t *n_segments);
+
+/* Incoming boundary flux of one track direction (t, p, i, sense = 0 along t,
+ * 1 against it) for the next sweep, get (set = 0) or set (set = 1), G values. */
+int moc_track_psi(moc_tracks *tracks, int32_t t, int32_t p, int64_t i, int32_t sense,
+                  double *values, int32_t set);
+
+/* Sweep from a caller-given source Q [n_fsr*G] (per steradian, host FP64) with
+ * the current boundary fluxes; returns the FSR tally [n_fsr*G] and leakage. */
+int moc_sweep_from_source(moc_tracks *tracks, const double *Q, double *tally, double *leakage);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MOC3D_MOC_H */

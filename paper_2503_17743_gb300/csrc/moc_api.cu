@@ -1,0 +1,815 @@
+// C ABI of the GB300 3D MOC library (include/moc.h): device memory, the
+// track generation pipeline and the outer iteration.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "moc_kernels.h"
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t n = 0;
+    ~DevBuf() { if (p) cudaFree(p); }
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+};
+
+}  // namespace
+
+struct moc_tracks {
+    moc_geometry geom;
+    Layout L;
+    int precision = MOC_FP32;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sms = 0;
+    // device buffers
+    DevBuf d_desc, d_zn, d_zf, d_zf64, d_reg2d, d_len2d, d_len2d64, d_segs, d_fsr_mat, d_order;
+    DevBuf d_tpl_off, d_tpl_loff, d_tpl_lmin, d_tpl_lidx;
+    DevBuf d_dst;
+    DevBuf d_phi, d_qr, d_tally, d_vol, d_psi[2], d_fiss, d_fiss_old, d_partial, d_scal, d_counter;
+    DevBuf d_sigt, d_sigt64, d_sigs64, d_nsf64, d_chi64, d_src64;
+    double *h_scal = nullptr;  // pinned mirror of the device scalars
+    int cur = 0;               // psi buffer holding the next incoming fluxes
+    bool has_psi = false;
+    // layout numbers
+    std::vector<int64_t> stack_nseg;
+    std::vector<int32_t> order;
+    int64_t n_segments3d = 0;   // both frames
+    int64_t n_stored = 0;
+    int64_t n_exp_stacks = 0;
+    int32_t max_nseg = 0;
+    int nb_max = 0;
+    double integrations = 0;    // per sweep
+    size_t bytes = 0;
+    // sweep launch
+    int tally_smem = 0;
+    int tile_cap = 0;
+    int block = 256;
+    int grid = 0;
+    size_t smem = 0;
+    int red_grid = 0;
+    // host copies
+    std::vector<double> vol;
+    // graphs, one per psi parity
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    DevLayout dl{};
+    DevState ds{};
+    ~moc_tracks() {
+        for (auto &g : graph) if (g) cudaGraphExecDestroy(g);
+        if (h_scal) cudaFreeHost(h_scal);
+        if (stream) cudaStreamDestroy(stream);
+    }
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e, const char *what) {
+    moc_set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) return MOC_ERR_OUT_OF_MEMORY;
+    return MOC_ERR_CUDA;
+}
+
+#define TRY(x, what)                                      \
+    do {                                                  \
+        cudaError_t e_ = (x);                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+cudaError_t dalloc(moc_tracks *h, DevBuf &b, size_t bytes) {
+    b.n = bytes;
+    if (bytes == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e == cudaSuccess) h->bytes += bytes;
+    return e;
+}
+
+template <typename T>
+cudaError_t upload(moc_tracks *h, DevBuf &b, const std::vector<T> &v) {
+    cudaError_t e = dalloc(h, b, v.size() * sizeof(T));
+    if (e != cudaSuccess || v.empty()) return e;
+    return cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream);
+}
+
+size_t real_size(int precision) { return precision == MOC_FP64 ? 8 : 4; }
+
+void fill_views(moc_tracks *h) {
+    DevLayout &dl = h->dl;
+    dl.desc = (const StackDesc *)h->d_desc.p;
+    dl.zn = (const int32_t *)h->d_zn.p;
+    dl.zf = (const float *)h->d_zf.p;
+    dl.zf64 = (const double *)h->d_zf64.p;
+    dl.reg2d = (const int32_t *)h->d_reg2d.p;
+    dl.len2d = (const float *)h->d_len2d.p;
+    dl.len2d64 = (const double *)h->d_len2d64.p;
+    dl.tpl_off = (const int64_t *)h->d_tpl_off.p;
+    dl.tpl_loff = (const int64_t *)h->d_tpl_loff.p;
+    dl.tpl_lmin = (const int32_t *)h->d_tpl_lmin.p;
+    dl.tpl_lidx = (const int32_t *)h->d_tpl_lidx.p;
+    dl.segs = h->d_segs.p;
+    dl.fsr_mat = (const int32_t *)h->d_fsr_mat.p;
+    dl.dst = (const int64_t *)h->d_dst.p;
+    dl.Ph = h->L.Ph;
+    dl.Nz = h->L.Nz;
+    dl.cpl = h->L.cpl;
+    dl.NL = h->geom.nl;
+    dl.G = h->geom.G;
+    dl.M = h->geom.M;
+    dl.bc_zmin = h->geom.bc[FACE_ZMIN];
+    dl.bc_zmax = h->geom.bc[FACE_ZMAX];
+    dl.n_slots = h->L.n_gtrk * 4;
+    DevState &s = h->ds;
+    s.phi = (double *)h->d_phi.p;
+    s.qr = h->d_qr.p;
+    s.tally = (double *)h->d_tally.p;
+    s.vol = (double *)h->d_vol.p;
+    s.psi_a = h->d_psi[0].p;
+    s.psi_b = h->d_psi[1].p;
+    s.fiss = (double *)h->d_fiss.p;
+    s.fiss_old = (double *)h->d_fiss_old.p;
+    s.partial = (double *)h->d_partial.p;
+    s.scal = (double *)h->d_scal.p;
+    s.counter = (int32_t *)h->d_counter.p;
+    s.sig_t = h->d_sigt.p;
+    s.sig_t64 = (const double *)h->d_sigt64.p;
+    s.sig_s64 = (const double *)h->d_sigs64.p;
+    s.nsf64 = (const double *)h->d_nsf64.p;
+    s.chi64 = (const double *)h->d_chi64.p;
+    s.src64 = (const double *)h->d_src64.p;
+}
+
+cudaError_t set_scalar(moc_tracks *h, int slot, double v) {
+    return cudaMemcpyAsync((double *)h->d_scal.p + slot, &v, sizeof(double), cudaMemcpyHostToDevice,
+                           h->stream);
+}
+
+// one sweep into the other psi buffer (no source update, no finalize)
+cudaError_t enqueue_sweep(moc_tracks *h, cudaStream_t s, int cur) {
+    cudaError_t e = cudaMemsetAsync(h->d_counter.p, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    const void *pin = h->has_psi ? h->d_psi[cur].p : nullptr;
+    void *pout = h->has_psi ? h->d_psi[1 - cur].p : nullptr;
+    return launch_sweep(h->precision, h->tally_smem, h->dl, h->ds, (const int32_t *)h->d_order.p,
+                        (int32_t)h->order.size(), h->tile_cap, pin, pout, h->grid, h->block, h->smem, s);
+}
+
+cudaError_t enqueue_finalize(moc_tracks *h, cudaStream_t s) {
+    const int nfsr = h->geom.nfsr;
+    if (h->geom.src.empty())
+        return launch_finalize(h->precision, h->dl, h->ds, nfsr, h->red_grid, h->integrations, s);
+    return launch_finalize_fixed(h->precision, h->dl, h->ds, nfsr, h->red_grid, h->integrations, s);
+}
+
+// one outer iteration: source, sweep, flux update, k / residual; the scalars
+// are copied to the pinned host mirror at the end
+cudaError_t enqueue_iteration(moc_tracks *h, cudaStream_t s, int cur) {
+    cudaError_t e = launch_source(h->precision, h->dl, h->ds, h->geom.nfsr, h->red_grid, s);
+    if (e != cudaSuccess) return e;
+    e = enqueue_sweep(h, s, cur);
+    if (e != cudaSuccess) return e;
+    e = enqueue_finalize(h, s);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(h->h_scal, h->d_scal.p, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s);
+}
+
+cudaError_t build_graphs(moc_tracks *h) {
+    for (int c = 0; c < 2; ++c) {
+        if (h->graph[c]) continue;
+        cudaGraph_t g;
+        cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        e = enqueue_iteration(h, h->stream, c);
+        cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+        if (e != cudaSuccess) return e;
+        if (e2 != cudaSuccess) return e2;
+        e = cudaGraphInstantiate(&h->graph[c], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+void fill_result(moc_tracks *h, moc_result *r, double seconds, int iters) {
+    if (!r) return;
+    const double *s = h->h_scal;
+    const bool eig = h->geom.src.empty();
+    r->k = eig ? s[SC_K] : 1.0;
+    r->residual = s[SC_RES];
+    r->dk = s[SC_DK];
+    r->production = eig ? 1.0 : s[SC_PROD];
+    r->absorption = eig ? s[SC_ABS] * s[SC_SCALE] : s[SC_ABS];
+    r->leakage = s[SC_LEAK_PREV];
+    r->seconds = seconds;
+    r->integrations = (double)iters * h->integrations;
+    r->iterations = iters;
+    r->converged = s[SC_CONV] != 0.0 ? 1 : 0;
+}
+
+int run_iterations(moc_tracks *h, int n, bool stop_on_conv, bool graph, moc_result *res) {
+    TRY(cudaSetDevice(h->device), "cudaSetDevice");
+    if (graph) TRY(build_graphs(h), "graph capture");
+    cudaEvent_t e0, e1;
+    TRY(cudaEventCreate(&e0), "event");
+    TRY(cudaEventCreate(&e1), "event");
+    TRY(cudaEventRecord(e0, h->stream), "event");
+    int it = 0;
+    double seconds_total = 0.0;
+    for (; it < n;) {
+        if (graph) TRY(cudaGraphLaunch(h->graph[h->cur], h->stream), "graph launch");
+        else TRY(enqueue_iteration(h, h->stream, h->cur), "iteration");
+        if (h->has_psi) h->cur = 1 - h->cur;
+        ++it;
+        TRY(cudaStreamSynchronize(h->stream), "iteration");
+        if (stop_on_conv && h->h_scal[SC_CONV] != 0.0) break;
+    }
+    TRY(cudaEventRecord(e1, h->stream), "event");
+    TRY(cudaEventSynchronize(e1), "event");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    seconds_total = ms * 1e-3;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    fill_result(h, res, seconds_total, it);
+    return MOC_OK;
+}
+
+int init_state(moc_tracks *h) {
+    TRY(cudaMemsetAsync(h->d_tally.p, 0, h->d_tally.n, h->stream), "memset");
+    for (int c = 0; c < 2; ++c)
+        if (h->d_psi[c].p) TRY(cudaMemsetAsync(h->d_psi[c].p, 0, h->d_psi[c].n, h->stream), "memset");
+    h->cur = 0;
+    TRY(set_scalar(h, SC_INTEG, 0.0), "scalar");
+    TRY(set_scalar(h, SC_LEAK_PREV, 0.0), "scalar");
+    TRY(launch_init_state(h->dl, h->ds, h->geom.nfsr, h->red_grid, h->stream), "init state");
+    TRY(cudaMemcpyAsync(h->h_scal, h->d_scal.p, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
+                        h->stream), "scalars");
+    TRY(cudaStreamSynchronize(h->stream), "init state");
+    return MOC_OK;
+}
+
+// map (2D track t, polar p over both hemispheres, lattice index i) to the
+// stored stack, frame and stored index
+bool map_track(const moc_tracks *h, int t, int p, int64_t i, int64_t &stack, int &frame, int64_t &j) {
+    const Layout &L = h->L;
+    if (t < 0 || t >= L.nt || p < 0 || p >= L.P) return false;
+    stack = (int64_t)t * L.Ph + (p % L.Ph);
+    frame = p < L.Ph ? 0 : 1;
+    if (frame == 0) j = i;
+    else {
+        // mirrored: height at the start of t is H - dz (j + zeta0) = z_0' + i dz
+        const bool zero = L.zf[L.zoff[stack]] == 0.0f && L.zn[L.zoff[stack]] == 0;
+        j = (int64_t)L.Nz - i - (zero ? 0 : 1);
+    }
+    const StackDesc &d = L.desc[stack];
+    return j >= d.i_lo && j < (int64_t)d.i_lo + d.n_trk;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+
+extern "C" int moc_query_footprint(const moc_geometry *g, const moc_track_params *p,
+                                   int64_t *resident, int64_t *preload_all) {
+    if (!g || !p) { moc_set_error("NULL argument"); return MOC_ERR_INVALID_ARG; }
+    Layout L;
+    std::string err;
+    int rc = moc_build_layout(*g, *p, L, err);
+    if (rc) { moc_set_error(err); return rc; }
+    const size_t rs = real_size(p->precision);
+    const int64_t G = g->G;
+    int64_t b = 0;
+    b += (int64_t)L.desc.size() * sizeof(StackDesc) + (int64_t)L.zn.size() * 8;
+    b += (int64_t)L.seg_reg.size() * 8 + (int64_t)g->nfsr * 4 + (int64_t)L.desc.size() * 4;
+    b += (int64_t)g->nfsr * G * (8 + rs + 8) + (int64_t)g->nfsr * 8 * 3;
+    bool refl = false;
+    for (int f = 0; f < 6; ++f) refl |= g->bc[f] != 0;
+    if (refl) b += 2 * L.n_gtrk * 4 * G * (int64_t)rs;
+    if (resident) *resident = b;
+    if (preload_all) {
+        // an upper estimate from the 2D segments: each 3D track crosses its 2D
+        // segments plus the layer planes it passes
+        double segs = 0;
+        for (int64_t s = 0; s < L.n_stacks; ++s) {
+            const StackDesc &d = L.desc[s];
+            const double planes = (double)(L.zn[d.zoff + d.nb] - L.zn[d.zoff] + 1) / L.cpl + 1;
+            segs += (double)d.n_trk * (d.nb + planes);
+        }
+        *preload_all = (int64_t)(segs * 8 + (double)L.n_gtrk * 8);
+    }
+    return MOC_OK;
+}
+
+extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params *prm,
+                                   moc_tracks **out) {
+    if (!g || !prm || !out) { moc_set_error("NULL argument"); return MOC_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (prm->precision != MOC_FP32 && prm->precision != MOC_FP64) {
+        moc_set_error("precision must be MOC_FP32 or MOC_FP64");
+        return MOC_ERR_INVALID_ARG;
+    }
+    std::unique_ptr<moc_tracks> h(new moc_tracks());
+    h->geom = *g;
+    h->precision = prm->precision;
+    h->device = prm->device;
+    std::string err;
+    int rc = moc_build_layout(h->geom, *prm, h->L, err);
+    if (rc) { moc_set_error(err); return rc; }
+    Layout &L = h->L;
+    const moc_geometry &geo = h->geom;
+    const int G = geo.G;
+    if ((int64_t)geo.nfsr * G > 0x7fffffffLL) { moc_set_error("too many FSR-groups"); return MOC_ERR_UNSUPPORTED; }
+    for (int t = 0; t < L.nt; ++t) h->nb_max = std::max(h->nb_max, L.seg_off[t + 1] - L.seg_off[t]);
+    if (h->nb_max >= 65536) { moc_set_error("a 2D track has too many segments"); return MOC_ERR_UNSUPPORTED; }
+    if (L.n_gtrk * 4 >= (int64_t)1 << 40) { moc_set_error("too many 3D tracks"); return MOC_ERR_UNSUPPORTED; }
+    if (L.Ph > 16) { moc_set_error("at most 32 polar angles"); return MOC_ERR_UNSUPPORTED; }
+    // tally mode: a shared tile of every (2D segment, layer) row of one unit
+    // when it fits
+    h->tile_cap = h->nb_max * geo.nl;
+    {
+        int mode = prm->tally_mode;
+        const size_t smem_tile = sweep_smem_bytes(h->precision, 1, geo.M, G, h->tile_cap);
+        const bool fits = smem_tile <= 200 * 1024;
+        if (mode == MOC_TALLY_AUTO) mode = (fits && smem_tile <= 100 * 1024) ? MOC_TALLY_SHARED : MOC_TALLY_GLOBAL;
+        if (mode == MOC_TALLY_SHARED && !fits) mode = MOC_TALLY_GLOBAL;
+        h->tally_smem = mode == MOC_TALLY_SHARED ? 1 : 0;
+    }
+    TRY(cudaSetDevice(h->device), "cudaSetDevice");
+    TRY(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "stream");
+    TRY(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device), "attribute");
+    TRY(cudaMallocHost(&h->h_scal, SC_COUNT * sizeof(double)), "pinned scalars");
+    // layout tables
+    std::vector<int32_t> reg2d(L.seg_reg.begin(), L.seg_reg.end());
+    std::vector<float> len2d(L.seg_len.begin(), L.seg_len.end());
+    TRY(upload(h.get(), h->d_zn, L.zn), "upload");
+    TRY(upload(h.get(), h->d_zf, L.zf), "upload");
+    TRY(upload(h.get(), h->d_reg2d, reg2d), "upload");
+    TRY(upload(h.get(), h->d_len2d, len2d), "upload");
+    TRY(upload(h.get(), h->d_fsr_mat, geo.fsr_mat), "upload");
+    if (h->precision == MOC_FP64) {
+        TRY(upload(h.get(), h->d_zf64, L.zf64), "upload");
+        TRY(upload(h.get(), h->d_len2d64, L.seg_len), "upload");
+    }
+    TRY(upload(h.get(), h->d_desc, L.desc), "upload");
+    fill_views(h.get());
+    // segment counts per stack
+    const int64_t ns = L.n_stacks;
+    DevBuf d_nseg, d_max;
+    TRY(dalloc(h.get(), d_nseg, ns * sizeof(int64_t)), "alloc");
+    TRY(dalloc(h.get(), d_max, sizeof(int32_t)), "alloc");
+    TRY(cudaMemsetAsync(d_max.p, 0, sizeof(int32_t), h->stream), "memset");
+    const int lgrid = (int)std::max<int64_t>(1, std::min<int64_t>(ns, (int64_t)h->sms * 16));
+    TRY(launch_count_stacks(h->dl, ns, (int64_t *)d_nseg.p, (int32_t *)d_max.p, lgrid, h->stream), "count");
+    h->stack_nseg.resize(ns);
+    TRY(cudaMemcpyAsync(h->stack_nseg.data(), d_nseg.p, ns * sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream), "copy");
+    TRY(cudaMemcpyAsync(&h->max_nseg, d_max.p, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream), "copy");
+    TRY(cudaStreamSynchronize(h->stream), "count");
+    h->bytes -= d_nseg.n + d_max.n;
+    int64_t segs_up = 0;
+    for (auto v : h->stack_nseg) segs_up += v;
+    h->n_segments3d = 2 * segs_up;
+    h->integrations = (double)h->n_segments3d * 2.0 * G;
+    // Stored segments (EXP, Sec. 4.2).  What is stored is one template per
+    // class r < cpl of a stack (the tracks r, r + cpl, ... are one-layer shifts
+    // of each other); the work unit of the sweep is a 2D track with all its
+    // polar stacks.  Template sizes first, for every stack:
+    const int Ph = L.Ph;
+    const int cpl = L.cpl;
+    std::vector<int64_t> tpl_first(ns, 0);
+    int64_t n_tpl_all = 0;
+    for (int64_t s = 0; s < ns; ++s) {
+        tpl_first[s] = n_tpl_all;
+        L.desc[s].exp_base = n_tpl_all;
+        n_tpl_all += std::min(cpl, L.desc[s].n_trk);
+    }
+    std::vector<int64_t> tcnt(n_tpl_all);
+    std::vector<int32_t> tlmin(n_tpl_all), tnlay(n_tpl_all);
+    if (n_tpl_all > 0) {
+        DevBuf d_all, d_cnt, d_lmin, d_nlay;
+        std::vector<int32_t> all(ns);
+        std::iota(all.begin(), all.end(), 0);
+        TRY(cudaMemcpyAsync(h->d_desc.p, L.desc.data(), ns * sizeof(StackDesc), cudaMemcpyHostToDevice, h->stream), "upload");
+        TRY(upload(h.get(), d_all, all), "upload");
+        TRY(dalloc(h.get(), d_cnt, n_tpl_all * 8), "alloc");
+        TRY(dalloc(h.get(), d_lmin, n_tpl_all * 4), "alloc");
+        TRY(dalloc(h.get(), d_nlay, n_tpl_all * 4), "alloc");
+        TRY(launch_tpl_count(h->dl, (const int32_t *)d_all.p, ns, (int64_t *)d_cnt.p, (int32_t *)d_lmin.p,
+                             (int32_t *)d_nlay.p, lgrid, h->stream), "template sizes");
+        TRY(cudaMemcpyAsync(tcnt.data(), d_cnt.p, n_tpl_all * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
+        TRY(cudaMemcpyAsync(tlmin.data(), d_lmin.p, n_tpl_all * 4, cudaMemcpyDeviceToHost, h->stream), "copy");
+        TRY(cudaMemcpyAsync(tnlay.data(), d_nlay.p, n_tpl_all * 4, cudaMemcpyDeviceToHost, h->stream), "copy");
+        TRY(cudaStreamSynchronize(h->stream), "template sizes");
+        h->bytes -= d_all.n + d_cnt.n + d_lmin.n + d_nlay.n;
+    }
+    // plan: units (2D tracks) by decreasing work; store a unit's templates
+    // while the budget lasts (largest first), generate the rest on the fly
+    std::vector<int64_t> unit_nseg(L.nt, 0);
+    for (int t = 0; t < L.nt; ++t)
+        for (int ph = 0; ph < Ph; ++ph) unit_nseg[t] += h->stack_nseg[(int64_t)t * Ph + ph];
+    std::vector<int32_t> by_size(L.nt);
+    std::iota(by_size.begin(), by_size.end(), 0);
+    std::stable_sort(by_size.begin(), by_size.end(),
+                     [&](int32_t a, int32_t b) { return unit_nseg[a] > unit_nseg[b]; });
+    const int64_t rec_bytes = (int64_t)segrec_size(h->precision);
+    const int64_t budget = prm->preload_budget_bytes;
+    int64_t used = 0;
+    std::vector<int32_t> exp_stacks;
+    std::vector<int64_t> off_h(1, 0), loff_h(1, 0);
+    std::vector<int32_t> lmin_h;
+    for (int32_t t : by_size) {
+        int64_t need = 0;
+        bool ok = true;
+        for (int ph = 0; ph < Ph; ++ph) {
+            const int64_t s = (int64_t)t * Ph + ph;
+            for (int r = 0; r < std::min(cpl, L.desc[s].n_trk); ++r) {
+                const int64_t q = tpl_first[s] + r;
+                need += tcnt[q] * rec_bytes + (int64_t)(tnlay[q] + 1) * 4 + 20;
+                ok = ok && tlmin[q] > -30000 && tlmin[q] + tnlay[q] < 30000;
+            }
+        }
+        if (!ok || (budget >= 0 && used + need > budget)) {
+            for (int ph = 0; ph < Ph; ++ph) L.desc[(int64_t)t * Ph + ph].exp_base = -1;
+            continue;
+        }
+        used += need;
+        for (int ph = 0; ph < Ph; ++ph) {
+            const int64_t s = (int64_t)t * Ph + ph;
+            L.desc[s].exp_base = (int64_t)lmin_h.size();
+            for (int r = 0; r < std::min(cpl, L.desc[s].n_trk); ++r) {
+                const int64_t q = tpl_first[s] + r;
+                off_h.push_back(off_h.back() + tcnt[q]);
+                loff_h.push_back(loff_h.back() + tnlay[q] + 1);
+                lmin_h.push_back(tlmin[q]);
+            }
+            exp_stacks.push_back((int32_t)s);
+        }
+    }
+    h->n_exp_stacks = (int64_t)exp_stacks.size();
+    TRY(cudaMemcpyAsync(h->d_desc.p, L.desc.data(), ns * sizeof(StackDesc), cudaMemcpyHostToDevice, h->stream), "upload");
+    if (!exp_stacks.empty()) {
+        DevBuf d_exp_stacks;
+        TRY(upload(h.get(), d_exp_stacks, exp_stacks), "upload");
+        TRY(upload(h.get(), h->d_tpl_off, off_h), "upload");
+        TRY(upload(h.get(), h->d_tpl_loff, loff_h), "upload");
+        TRY(upload(h.get(), h->d_tpl_lmin, lmin_h), "upload");
+        h->n_stored = off_h.back();
+        TRY(dalloc(h.get(), h->d_segs, (size_t)std::max<int64_t>(h->n_stored, 1) * rec_bytes), "alloc templates");
+        TRY(dalloc(h.get(), h->d_tpl_lidx, (size_t)loff_h.back() * 4), "alloc template index");
+        fill_views(h.get());
+        const int egrid = (int)std::max<int64_t>(1, std::min<int64_t>(h->n_exp_stacks, (int64_t)h->sms * 16));
+        TRY(launch_tpl_write(h->precision, h->dl, (const int32_t *)d_exp_stacks.p, h->n_exp_stacks,
+                             h->d_segs.p, (int32_t *)h->d_tpl_lidx.p, egrid, h->stream), "templates");
+        TRY(cudaStreamSynchronize(h->stream), "templates");
+        h->bytes -= d_exp_stacks.n;
+    }
+    fill_views(h.get());
+    // cross sections
+    if (geo.M > 65535) { moc_set_error("too many materials"); return MOC_ERR_UNSUPPORTED; }
+    if (h->precision == MOC_FP64) {
+        TRY(upload(h.get(), h->d_sigt, geo.sigt), "upload");
+    } else {
+        std::vector<float> s32(geo.sigt.begin(), geo.sigt.end());
+        TRY(upload(h.get(), h->d_sigt, s32), "upload");
+    }
+    TRY(upload(h.get(), h->d_sigt64, geo.sigt), "upload");
+    TRY(upload(h.get(), h->d_sigs64, geo.sigs), "upload");
+    TRY(upload(h.get(), h->d_nsf64, geo.nsf), "upload");
+    TRY(upload(h.get(), h->d_chi64, geo.chi), "upload");
+    if (!geo.src.empty()) TRY(upload(h.get(), h->d_src64, geo.src), "upload");
+    // state
+    const size_t nfg = (size_t)geo.nfsr * G;
+    const size_t rs = real_size(h->precision);
+    TRY(dalloc(h.get(), h->d_phi, nfg * 8), "alloc flux");
+    TRY(dalloc(h.get(), h->d_qr, nfg * rs), "alloc source");
+    TRY(dalloc(h.get(), h->d_tally, nfg * 8), "alloc tally");
+    TRY(dalloc(h.get(), h->d_vol, (size_t)geo.nfsr * 8), "alloc volumes");
+    TRY(dalloc(h.get(), h->d_fiss, (size_t)geo.nfsr * 8), "alloc");
+    TRY(dalloc(h.get(), h->d_fiss_old, (size_t)geo.nfsr * 8), "alloc");
+    h->red_grid = (int)std::max<int64_t>(1, std::min<int64_t>((geo.nfsr + 255) / 256, (int64_t)h->sms * 4));
+    TRY(dalloc(h.get(), h->d_partial, (size_t)h->red_grid * 4 * 8), "alloc");
+    TRY(dalloc(h.get(), h->d_scal, SC_COUNT * 8), "alloc");
+    TRY(dalloc(h.get(), h->d_counter, 64), "alloc");
+    bool refl = false;
+    for (int f = 0; f < 6; ++f) refl |= geo.bc[f] != 0;
+    h->has_psi = refl;
+    if (refl) {
+        // every reflective link must land on a track direction, and no
+        // direction may be fed twice; a failure here is an internal error
+        std::vector<uint8_t> hit((size_t)L.n_gtrk * 4, 0);
+        for (int64_t s = 0; s < ns; ++s) {
+            const StackDesc &d = L.desc[s];
+            for (int k = 0; k < d.n_trk; ++k)
+                for (int v = 0; v < 4; ++v) {
+                    const int64_t dst = moc_layout_link(geo, L, s, (int64_t)d.i_lo + k, v);
+                    if (dst == -1) continue;
+                    if (dst < 0 || dst >= (int64_t)hit.size() || hit[dst]) {
+                        moc_set_error("internal: 3D link outside the track set or not one-to-one");
+                        return MOC_ERR_INVALID_ARG;
+                    }
+                    hit[dst] = 1;
+                }
+        }
+        TRY(dalloc(h.get(), h->d_dst, (size_t)L.n_gtrk * 4 * sizeof(int64_t)), "alloc links");
+        fill_views(h.get());
+        TRY(launch_links(h->dl, ns, (int64_t *)h->d_dst.p, lgrid, h->stream), "links");
+        const size_t pb = (size_t)L.n_gtrk * 4 * G * rs;
+        TRY(dalloc(h.get(), h->d_psi[0], pb), "alloc boundary fluxes");
+        TRY(dalloc(h.get(), h->d_psi[1], pb), "alloc boundary fluxes");
+    }
+    fill_views(h.get());
+    std::vector<double> init(SC_COUNT, 0.0);
+    init[SC_EIGEN] = geo.src.empty() ? 1.0 : 0.0;
+    init[SC_SCALE] = 1.0;
+    init[SC_K] = 1.0;
+    TRY(cudaMemcpyAsync(h->d_scal.p, init.data(), SC_COUNT * 8, cudaMemcpyHostToDevice, h->stream), "upload");
+    TRY(cudaMemsetAsync(h->d_vol.p, 0, h->d_vol.n, h->stream), "memset");
+    TRY(launch_volumes(h->precision, h->dl, ns, (double *)h->d_vol.p, lgrid, h->stream), "volumes");
+    h->vol.resize(geo.nfsr);
+    TRY(cudaMemcpyAsync(h->vol.data(), h->d_vol.p, geo.nfsr * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
+    // schedule: work units (2D tracks) in decreasing work, largest first
+    h->order = by_size;
+    TRY(upload(h.get(), h->d_order, h->order), "upload");
+    fill_views(h.get());
+    // sweep launch shape (tally mode chosen above)
+    h->smem = sweep_smem_bytes(h->precision, h->tally_smem, geo.M, G, h->tile_cap);
+    h->block = prm->block_threads > 0 ? std::max(32, std::min(prm->block_threads, 256) / 32 * 32) : 256;
+    int bps = 0;
+    TRY(sweep_occupancy(h->precision, h->tally_smem, G, h->block, h->smem, &bps), "occupancy");
+    if (bps < 1) { moc_set_error("sweep kernel does not fit on an SM"); return MOC_ERR_UNSUPPORTED; }
+    if (prm->blocks_per_sm > 0) bps = std::min(bps, prm->blocks_per_sm);
+    h->grid = std::max(1, std::min<int>(h->sms * bps, (int)std::min<int64_t>(ns, 1 << 30)));
+    rc = init_state(h.get());
+    if (rc) return rc;
+    *out = h.release();
+    return MOC_OK;
+}
+
+extern "C" void moc_destroy_tracks(moc_tracks *h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    delete h;
+}
+
+extern "C" int moc_reset(moc_tracks *h) {
+    if (!h) { moc_set_error("NULL handle"); return MOC_ERR_INVALID_ARG; }
+    TRY(cudaSetDevice(h->device), "cudaSetDevice");
+    return init_state(h);
+}
+
+extern "C" int moc_update_source(moc_tracks *h, double k, void *stream) {
+    if (!h) { moc_set_error("NULL handle"); return MOC_ERR_INVALID_ARG; }
+    TRY(cudaSetDevice(h->device), "cudaSetDevice");
+    cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+    double kk = k;
+    TRY(cudaMemcpyAsync((double *)h->d_scal.p + SC_K, &kk, 8, cudaMemcpyHostToDevice, s), "scalar");
+    TRY(launch_source(h->precision, h->dl, h->ds, h->geom.nfsr, h->red_grid, s), "source");
+    TRY(cudaStreamSynchronize(s), "source");
+    return MOC_OK;
+}
+
+extern "C" int moc_sweep(moc_tracks *h, void *stream) {
+    if (!h) { moc_set_error("NULL handle"); return MOC_ERR_INVALID_ARG; }
+    TRY(cudaSetDevice(h->device), "cudaSetDevice");
+    cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+    TRY(enqueue_sweep(h, s, h->cur), "sweep");
+    if (h->has_psi) h->cur = 1 - h->cur;
+    TRY(enqueue_finalize(h, s), "finalize");
+    TRY(cudaMemcpyAsync(h->h_scal, h->d_scal.p, SC_COUNT * 8, cudaMemcpyDeviceToHost, s), "scalars");
+    TRY(cudaStreamSynchronize(s), "sweep");
+    return MOC_OK;
+}
+
+extern "C" int moc_iterate(moc_tracks *h, int32_t n, int32_t use_graph, moc_result *res) {
+    if (!h || n < 0) { moc_set_error("bad arguments"); return MOC_ERR_INVALID_ARG; }
+    return run_iterations(h, n, false, use_graph != 0, res);
+}
+
+static int solve(moc_tracks *h, const moc_solve_params *p, moc_result *res, bool eigen) {
+    if (!h || !p || p->max_iter < 1) { moc_set_error("bad arguments"); return MOC_ERR_INVALID_ARG; }
+    if (eigen != h->geom.src.empty()) {
+        moc_set_error(eigen ? "moc_solve_eigen: the geometry has an external source"
+                            : "moc_solve_fixed_source: the geometry has no external source");
+        return MOC_ERR_INVALID_ARG;
+    }
+    int rc = init_state(h);
+    if (rc) return rc;
+    TRY(set_scalar(h, SC_TOLK, p->tol_k), "scalar");
+    TRY(set_scalar(h, SC_TOLS, p->tol_src), "scalar");
+    rc = run_iterations(h, p->max_iter, p->tol_src > 0, p->use_graph != 0, res);
+    if (rc) return rc;
+    if (p->tol_src > 0 && h->h_scal[SC_CONV] == 0.0) {
+        moc_set_error("not converged within max_iter");
+        return MOC_ERR_NOT_CONVERGED;
+    }
+    return MOC_OK;
+}
+
+extern "C" int moc_solve_eigen(moc_tracks *h, const moc_solve_params *p, moc_result *res) {
+    return solve(h, p, res, true);
+}
+
+extern "C" int moc_solve_fixed_source(moc_tracks *h, const moc_solve_params *p, moc_result *res) {
+    return solve(h, p, res, false);
+}
+
+extern "C" int moc_get_flux(moc_tracks *h, double *phi, double *k) {
+    if (!h) { moc_set_error("NULL handle"); return MOC_ERR_INVALID_ARG; }
+    TRY(cudaSetDevice(h->device), "cudaSetDevice");
+    TRY(cudaMemcpyAsync(h->h_scal, h->d_scal.p, SC_COUNT * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
+    const size_t n = (size_t)h->geom.nfsr * h->geom.G;
+    if (phi) TRY(cudaMemcpyAsync(phi, h->d_phi.p, n * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
+    TRY(cudaStreamSynchronize(h->stream), "copy");
+    const double sc = h->h_scal[SC_SCALE];
+    if (phi && sc != 1.0)
+        for (size_t q = 0; q < n; ++q) phi[q] *= sc;
+    if (k) *k = h->geom.src.empty() ? h->h_scal[SC_K] : 1.0;
+    return MOC_OK;
+}
+
+extern "C" int moc_set_flux(moc_tracks *h, const double *phi, double k) {
+    if (!h || !phi) { moc_set_error("NULL argument"); return MOC_ERR_INVALID_ARG; }
+    TRY(cudaSetDevice(h->device), "cudaSetDevice");
+    const moc_geometry &g = h->geom;
+    const size_t n = (size_t)g.nfsr * g.G;
+    std::vector<double> fiss(g.nfsr, 0.0);
+    double P = 0;
+    for (int i = 0; i < g.nfsr; ++i) {
+        const int m = g.fsr_mat[i];
+        for (int gr = 0; gr < g.G; ++gr) fiss[i] += g.nsf[(size_t)m * g.G + gr] * phi[(size_t)i * g.G + gr];
+        P += h->vol[i] * fiss[i];
+    }
+    const bool eig = g.src.empty();
+    const double scale = (eig && P > 0) ? 1.0 / P : 1.0;
+    for (auto &f : fiss) f *= scale;
+    TRY(cudaMemcpyAsync(h->d_phi.p, phi, n * 8, cudaMemcpyHostToDevice, h->stream), "upload");
+    TRY(cudaMemcpyAsync(h->d_fiss_old.p, fiss.data(), g.nfsr * 8, cudaMemcpyHostToDevice, h->stream), "upload");
+    TRY(set_scalar(h, SC_SCALE, scale), "scalar");
+    TRY(set_scalar(h, SC_K, k), "scalar");
+    TRY(cudaStreamSynchronize(h->stream), "upload");
+    return MOC_OK;
+}
+
+extern "C" int moc_get_volumes(moc_tracks *h, double *v) {
+    if (!h || !v) { moc_set_error("NULL argument"); return MOC_ERR_INVALID_ARG; }
+    std::memcpy(v, h->vol.data(), h->vol.size() * 8);
+    return MOC_OK;
+}
+
+extern "C" int moc_tracks_info(const moc_tracks *h, int64_t *out, int32_t n) {
+    if (!h || !out) { moc_set_error("NULL argument"); return MOC_ERR_INVALID_ARG; }
+    const int64_t v[20] = {h->geom.nfsr, h->geom.G, h->L.nt, 2 * h->L.n_stacks, 2 * h->L.n_gtrk,
+                           h->n_segments3d, (int64_t)h->integrations, h->n_stored, h->n_exp_stacks,
+                           (int64_t)h->bytes, h->L.Nz, h->L.cpl, h->grid, h->block,
+                           h->tally_smem ? MOC_TALLY_SHARED : MOC_TALLY_GLOBAL, h->precision,
+                           (int64_t)h->smem, h->tile_cap, sweep_lanes_per_track(h->geom.G),
+                           h->max_nseg};
+    for (int i = 0; i < n && i < 20; ++i) out[i] = v[i];
+    return MOC_OK;
+}
+
+extern "C" int moc_get_stack_segments(moc_tracks *h, int32_t t, int32_t p, int64_t cap_tracks,
+                                      int64_t cap_segments, int64_t *track_index, int32_t *n_seg,
+                                      int32_t *fsr, double *length, int64_t *n_tracks,
+                                      int64_t *n_segments) {
+    if (!h) { moc_set_error("NULL handle"); return MOC_ERR_INVALID_ARG; }
+    const Layout &L = h->L;
+    if (t < 0 || t >= L.nt || p < 0 || p >= L.P) { moc_set_error("stack out of range"); return MOC_ERR_INVALID_ARG; }
+    TRY(cudaSetDevice(h->device), "cudaSetDevice");
+    const int64_t s = (int64_t)t * L.Ph + (p % L.Ph);
+    const int frame = p < L.Ph ? 0 : 1;
+    const StackDesc &d = L.desc[s];
+    // per-track counts by the device generator
+    DevBuf d_cnt;
+    TRY(dalloc(h, d_cnt, (size_t)(d.n_trk + 1) * sizeof(int64_t)), "alloc");
+    TRY(cudaMemsetAsync(d_cnt.p, 0, d_cnt.n, h->stream), "memset");
+    TRY(launch_track_counts(h->dl, s, (int64_t *)d_cnt.p, h->stream), "count");
+    std::vector<int64_t> cnt(d.n_trk + 1, 0);
+    TRY(cudaMemcpyAsync(cnt.data(), d_cnt.p, cnt.size() * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
+    TRY(cudaStreamSynchronize(h->stream), "count");
+    h->bytes -= d_cnt.n;
+    std::vector<int64_t> offs(d.n_trk + 1, 0);
+    for (int k = 0; k < d.n_trk; ++k) offs[k + 1] = offs[k] + cnt[k + 1];
+    const int64_t tot = offs[d.n_trk];
+    *n_tracks = d.n_trk;
+    *n_segments = tot;
+    if (cap_tracks < d.n_trk || cap_segments < tot) {
+        moc_set_error("capacity too small");
+        return MOC_ERR_INVALID_ARG;
+    }
+    DevBuf d_offs, d_f, d_l;
+    TRY(upload(h, d_offs, offs), "upload");
+    TRY(dalloc(h, d_f, (size_t)std::max<int64_t>(tot, 1) * 4), "alloc");
+    TRY(dalloc(h, d_l, (size_t)std::max<int64_t>(tot, 1) * 8), "alloc");
+    TRY(launch_stack_segments(h->precision, h->dl, s, (const int64_t *)d_offs.p, (int32_t *)d_f.p,
+                              (double *)d_l.p, h->stream), "segments");
+    std::vector<int32_t> f(tot);
+    std::vector<double> l(tot);
+    if (tot) {
+        TRY(cudaMemcpyAsync(f.data(), d_f.p, tot * 4, cudaMemcpyDeviceToHost, h->stream), "copy");
+        TRY(cudaMemcpyAsync(l.data(), d_l.p, tot * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
+    }
+    TRY(cudaStreamSynchronize(h->stream), "copy");
+    h->bytes -= d_offs.n + d_f.n + d_l.n;
+    const int NL = h->geom.nl;
+    const bool zero = L.zf[d.zoff] == 0.0f && L.zn[d.zoff] == 0;
+    int64_t q = 0;
+    for (int kk = 0; kk < d.n_trk; ++kk) {
+        // frame D: list by increasing physical index = decreasing stored index
+        const int k = frame == 0 ? kk : d.n_trk - 1 - kk;
+        const int64_t j = d.i_lo + k;
+        track_index[kk] = frame == 0 ? j : (int64_t)L.Nz - j - (zero ? 0 : 1);
+        n_seg[kk] = (int32_t)(offs[k + 1] - offs[k]);
+        for (int64_t a = offs[k]; a < offs[k + 1]; ++a, ++q) {
+            int32_t ff = f[a];
+            if (frame == 1) {
+                const int reg = ff / NL, Lr = ff % NL;
+                ff = reg * NL + (NL - 1 - Lr);
+            }
+            fsr[q] = ff;
+            length[q] = l[a];
+        }
+    }
+    return MOC_OK;
+}
+
+extern "C" int moc_track_psi(moc_tracks *h, int32_t t, int32_t p, int64_t i, int32_t sense,
+                             double *values, int32_t set) {
+    if (!h || !values || sense < 0 || sense > 1) { moc_set_error("bad arguments"); return MOC_ERR_INVALID_ARG; }
+    if (!h->has_psi) { moc_set_error("all faces are vacuum: no boundary fluxes are stored"); return MOC_ERR_UNSUPPORTED; }
+    int64_t s, j;
+    int frame;
+    if (!map_track(h, t, p, i, s, frame, j)) { moc_set_error("track out of range"); return MOC_ERR_INVALID_ARG; }
+    TRY(cudaSetDevice(h->device), "cudaSetDevice");
+    const StackDesc &d = h->L.desc[s];
+    const int G = h->geom.G;
+    const int64_t gid = d.trk_off + (j - d.i_lo);
+    const int v = frame * 2 + sense;
+    const size_t rs = real_size(h->precision);
+    char *base = (char *)h->d_psi[h->cur].p + ((size_t)(gid * 4 + v) * G) * rs;
+    TRY(cudaMemcpyAsync(h->h_scal, h->d_scal.p, SC_COUNT * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
+    TRY(cudaStreamSynchronize(h->stream), "copy");
+    const double sc = h->h_scal[SC_SCALE];
+    if (set) {
+        if (rs == 8) {
+            std::vector<double> tmp(G);
+            for (int g = 0; g < G; ++g) tmp[g] = values[g] / sc;
+            TRY(cudaMemcpy(base, tmp.data(), G * 8, cudaMemcpyHostToDevice), "copy");
+        } else {
+            std::vector<float> tmp(G);
+            for (int g = 0; g < G; ++g) tmp[g] = (float)(values[g] / sc);
+            TRY(cudaMemcpy(base, tmp.data(), G * 4, cudaMemcpyHostToDevice), "copy");
+        }
+    } else {
+        if (rs == 8) {
+            TRY(cudaMemcpy(values, base, G * 8, cudaMemcpyDeviceToHost), "copy");
+            for (int g = 0; g < G; ++g) values[g] *= sc;
+        } else {
+            std::vector<float> tmp(G);
+            TRY(cudaMemcpy(tmp.data(), base, G * 4, cudaMemcpyDeviceToHost), "copy");
+            for (int g = 0; g < G; ++g) values[g] = tmp[g] * sc;
+        }
+    }
+    return MOC_OK;
+}
+
+extern "C" int moc_sweep_from_source(moc_tracks *h, const double *Q, double *tally, double *leakage) {
+    if (!h || !Q) { moc_set_error("NULL argument"); return MOC_ERR_INVALID_ARG; }
+    TRY(cudaSetDevice(h->device), "cudaSetDevice");
+    const moc_geometry &g = h->geom;
+    const size_t n = (size_t)g.nfsr * g.G;
+    const size_t rs = real_size(h->precision);
+    std::vector<double> qr(n);
+    for (int i = 0; i < g.nfsr; ++i)
+        for (int gr = 0; gr < g.G; ++gr)
+            qr[(size_t)i * g.G + gr] = Q[(size_t)i * g.G + gr] / g.sigt[(size_t)g.fsr_mat[i] * g.G + gr];
+    if (rs == 8) {
+        TRY(cudaMemcpyAsync(h->d_qr.p, qr.data(), n * 8, cudaMemcpyHostToDevice, h->stream), "upload");
+        TRY(cudaStreamSynchronize(h->stream), "upload");
+    } else {
+        std::vector<float> q32(qr.begin(), qr.end());
+        TRY(cudaMemcpyAsync(h->d_qr.p, q32.data(), n * 4, cudaMemcpyHostToDevice, h->stream), "upload");
+        TRY(cudaStreamSynchronize(h->stream), "upload");
+    }
+    TRY(cudaMemsetAsync(h->d_tally.p, 0, n * 8, h->stream), "memset");
+    TRY(set_scalar(h, SC_LEAK, 0.0), "scalar");
+    TRY(enqueue_sweep(h, h->stream, h->cur), "sweep");
+    if (h->has_psi) h->cur = 1 - h->cur;
+    if (tally) TRY(cudaMemcpyAsync(tally, h->d_tally.p, n * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
+    TRY(cudaMemcpyAsync(h->h_scal, h->d_scal.p, SC_COUNT * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
+    TRY(cudaStreamSynchronize(h->stream), "sweep");
+    if (leakage) *leakage = h->h_scal[SC_LEAK];
+    TRY(cudaMemsetAsync(h->d_tally.p, 0, n * 8, h->stream), "memset");
+    TRY(set_scalar(h, SC_LEAK, 0.0), "scalar");
+    // the outgoing fluxes are physical values: the next sweep reads them as is
+    TRY(set_scalar(h, SC_SCALE, 1.0), "scalar");
+    TRY(cudaStreamSynchronize(h->stream), "sweep");
+    return MOC_OK;
+}

@@ -1,0 +1,288 @@
+// Device-side data structures and the on-the-fly 3D segment generator.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "moc_internal.h"
+
+#define MOC_PI 3.14159265358979323846
+
+// Read-only problem data of one track layout, all device pointers.
+struct DevLayout {
+    const StackDesc *desc;   // [n_stacks] upward stacks
+    const int32_t *zn;       // lattice boundary integer parts
+    const float *zf;         // lattice boundary fractions (topology decisions, FP32 lengths)
+    const double *zf64;      // the same fractions in FP64 (FP64 sweeps only)
+    const int32_t *reg2d;    // radial region of each 2D segment
+    const float *len2d;      // length of each 2D segment (cm)
+    const double *len2d64;   // the same in FP64 (FP64 sweeps only)
+    const int64_t *tpl_off;  // stored templates: record offsets [n_tpl + 1]
+    const int64_t *tpl_loff; // offsets into tpl_lidx [n_tpl + 1]
+    const int32_t *tpl_lmin; // lowest template layer of each template
+    const int32_t *tpl_lidx; // first record of each template layer (relative), + count
+    const void *segs;        // template records, SegRec<real>
+    const int32_t *fsr_mat;  // material of each FSR
+    const int64_t *dst;      // [n_gtrk*4] link destination of every track direction, or null (all vacuum)
+    int32_t Nz, cpl, NL, G, M, Ph;
+    int32_t bc_zmin, bc_zmax;
+    int64_t n_slots;         // geometric tracks * 4 variants (bound of every link)
+};
+
+// State buffers of one solve.
+struct DevState {
+    double *phi;        // [nfsr*G] scalar flux (unnormalised after a sweep)
+    void *qr;           // [nfsr*G] Q / Sigma_t per steradian, real
+    double *tally;      // [nfsr*G] FP64 tally accumulator
+    double *vol;        // [nfsr] tracked volumes
+    void *psi_a;        // boundary fluxes, [n_gtrk*4*G] real (may be null: all vacuum)
+    void *psi_b;
+    double *fiss;       // [nfsr] raw fission rate of the latest flux
+    double *fiss_old;   // [nfsr] normalised fission rate of the previous flux
+    double *partial;    // per-block partial sums
+    double *scal;       // device scalars (see ScalarSlot)
+    int32_t *counter;   // work counter of the persistent sweep
+    const void *sig_t;  // [M*G] real
+    const double *sig_t64, *sig_s64, *nsf64, *chi64, *src64;  // [M*G(*G)] FP64 cross sections
+};
+
+// slots of DevState::scal
+enum ScalarSlot {
+    SC_K = 0,      // current k
+    SC_DK,         // last k change
+    SC_SCALE,      // 1 / production of the latest flux (eigen) or 1
+    SC_PROD,       // production of the latest flux (raw)
+    SC_ABS,        // absorption of the latest flux (raw)
+    SC_LEAK,       // leakage accumulated by the latest sweep (raw)
+    SC_RES,        // residual
+    SC_ITER,       // iterations done
+    SC_CONV,       // 1 when converged
+    SC_TOLK, SC_TOLS,
+    SC_EIGEN,      // 1 for an eigenvalue problem
+    SC_INTEG,      // integrations performed
+    SC_LEAK_PREV,  // leakage of the latest completed sweep, normalised
+    SC_COUNT = 16
+};
+
+// ---------------------------------------------------------------------------
+// On-the-fly generation of the 3D segments of one track of an upward z-stack
+// (Eqs. 5-11, Alg. 1 "traceSegmentsOTF").
+//
+// In lattice units u = z / dz the track i of the stack is u(s) = i + zeta(s)
+// (Eq. 5).  With zeta at the 2D boundaries stored as integer + fraction, the
+// layer crossed inside a 2D segment and the FSR sequence follow from integer
+// arithmetic only; lengths are Eq. 8 (full 2D length / sin), Eq. 11 (full
+// layer, cpl * dz / cos) or a partial lattice interval times dz / cos.
+// `visit(b, layer, len)` is called for every segment in traversal order:
+// along the 2D track for sense 0, against it for sense 1.
+
+// A stored segment: key = (2D segment b << 16) | layer, and its length.
+template <typename real>
+struct SegRec;
+template <>
+struct __align__(8) SegRec<float> {
+    uint32_t key;
+    float len;
+};
+template <>
+struct __align__(16) SegRec<double> {
+    uint32_t key;
+    uint32_t pad;
+    double len;
+};
+
+template <typename real>
+__device__ __forceinline__ real lat_frac(const DevLayout &dl, int idx);
+template <>
+__device__ __forceinline__ float lat_frac<float>(const DevLayout &dl, int idx) { return __ldg(dl.zf + idx); }
+template <>
+__device__ __forceinline__ double lat_frac<double>(const DevLayout &dl, int idx) { return __ldg(dl.zf64 + idx); }
+template <typename real>
+__device__ __forceinline__ real len_2d(const DevLayout &dl, int idx);
+template <>
+__device__ __forceinline__ float len_2d<float>(const DevLayout &dl, int idx) { return __ldg(dl.len2d + idx); }
+template <>
+__device__ __forceinline__ double len_2d<double>(const DevLayout &dl, int idx) { return __ldg(dl.len2d64 + idx); }
+__device__ __forceinline__ float lam_of(const StackDesc &d, float) { return d.lam; }
+__device__ __forceinline__ double lam_of(const StackDesc &d, double) { return d.lam64; }
+__device__ __forceinline__ float isin_of(const StackDesc &d, float) { return d.inv_sin; }
+__device__ __forceinline__ double isin_of(const StackDesc &d, double) { return d.inv_sin64; }
+
+template <typename real>
+struct SegRange {
+    int32_t ua, ub;   // integer lattice coordinate at the piece ends (clipped to [0, Nz])
+    real fa, fb;      // fractions at the ends
+    bool full;        // spans the whole 2D segment (Eq. 8 applies)
+    int32_t La, Le;   // first and last layer crossed
+};
+
+// Topology (integers and the sign of the FP32 fraction) is the same for both
+// precisions; only the fractions that enter the lengths change type.
+template <typename real>
+__device__ __forceinline__ void seg_range(const DevLayout &dl, const StackDesc &d, int i, int b,
+                                          SegRange<real> &r) {
+    int32_t ua = i + __ldg(dl.zn + d.zoff + b);
+    real fa = lat_frac<real>(dl, d.zoff + b);
+    int32_t ub = i + __ldg(dl.zn + d.zoff + b + 1);
+    const bool fb_pos = __ldg(dl.zf + d.zoff + b + 1) > 0.0f;
+    real fb = lat_frac<real>(dl, d.zoff + b + 1);
+    bool full = true;
+    if (ua < 0) { ua = 0; fa = (real)0; full = false; }
+    bool end_pos = fb_pos;
+    if (ub > dl.Nz || (ub == dl.Nz && fb_pos)) { ub = dl.Nz; fb = (real)0; end_pos = false; full = false; }
+    r.ua = ua; r.fa = fa; r.ub = ub; r.fb = fb; r.full = full;
+    r.La = min(ua / dl.cpl, dl.NL - 1);
+    r.Le = min((end_pos ? ub : ub - 1) / dl.cpl, dl.NL - 1);
+}
+
+template <typename real>
+__device__ __forceinline__ real piece_len(const DevLayout &dl, const StackDesc &d, int b,
+                                          const SegRange<real> &r, int L) {
+    const real lam = lam_of(d, (real)0);
+    if (r.La == r.Le) {
+        if (r.full) return len_2d<real>(dl, d.seg2d_off + b) * isin_of(d, (real)0);   // Eq. 8
+        return ((real)(r.ub - r.ua) + (r.fb - r.fa)) * lam;
+    }
+    if (L == r.La) return ((real)((r.La + 1) * dl.cpl - r.ua) - r.fa) * lam;
+    if (L == r.Le) return ((real)(r.ub - r.Le * dl.cpl) + r.fb) * lam;
+    return (real)dl.cpl * lam;                                                      // Eq. 11
+}
+
+// first 2D segment whose end lies above the bottom: i + zeta(b+1) > 0
+__device__ __forceinline__ int first_seg(const DevLayout &dl, const StackDesc &d, int i) {
+    if (i + __ldg(dl.zn + d.zoff) >= 0) return 0;
+    int lo = 0, hi = d.nb - 1;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        int u = i + __ldg(dl.zn + d.zoff + mid + 1);
+        bool above = u > 0 || (u == 0 && __ldg(dl.zf + d.zoff + mid + 1) > 0.0f);
+        if (above) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+// last 2D segment: the first whose end reaches the top, i + zeta(b+1) >= Nz
+__device__ __forceinline__ int last_seg(const DevLayout &dl, const StackDesc &d, int i) {
+    if (i + __ldg(dl.zn + d.zoff + d.nb) < dl.Nz) return d.nb - 1;
+    int lo = 0, hi = d.nb - 1;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (i + __ldg(dl.zn + d.zoff + mid + 1) >= dl.Nz) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+template <typename real, class Visit>
+__device__ __forceinline__ void walk_otf(const DevLayout &dl, const StackDesc &d, int i, int sense,
+                                         Visit &visit) {
+    const int b0 = first_seg(dl, d, i), b1 = last_seg(dl, d, i);
+    SegRange<real> r;
+    if (sense == 0) {
+        for (int b = b0; b <= b1; ++b) {
+            seg_range(dl, d, i, b, r);
+            for (int L = r.La; L <= r.Le; ++L) visit(b, L, piece_len(dl, d, b, r, L));
+        }
+    } else {
+        for (int b = b1; b >= b0; --b) {
+            seg_range(dl, d, i, b, r);
+            for (int L = r.Le; L >= r.La; --L) visit(b, L, piece_len(dl, d, b, r, L));
+        }
+    }
+}
+
+// number of segments of track i (no lengths)
+__device__ __forceinline__ int count_otf(const DevLayout &dl, const StackDesc &d, int i) {
+    const int b0 = first_seg(dl, d, i), b1 = last_seg(dl, d, i);
+    int n = 0;
+    SegRange<float> r;
+    for (int b = b0; b <= b1; ++b) {
+        seg_range(dl, d, i, b, r);
+        n += r.Le - r.La + 1;
+    }
+    return n;
+}
+
+// Exit of track i of a stack in variant v (frame = v >> 1, sense = v & 1):
+// returns the destination geometric track * 4 + variant, -1 for a vacuum
+// face.  Exit type from the integer lattice at the exit end: radial (per-stack
+// rule), axial (same stack, other frame, index -/+ Nz) or an edge shared with
+// an axial face (both reflective: the track reverses).
+__device__ __forceinline__ int64_t exit_dest(const DevLayout &dl, const StackDesc *descs,
+                                             const StackDesc &d, const StackDesc *dg, int i, int v) {
+    const int frame = v >> 1, sense = v & 1;
+    const int z = d.zoff + (sense == 0 ? d.nb : 0);
+    const int32_t ui = i + __ldg(dl.zn + z);
+    const float uf = __ldg(dl.zf + z);
+    int kind;
+    int abc;
+    if (sense == 0) {
+        kind = ui < dl.Nz ? 0 : ((ui == dl.Nz && uf == 0.0f) ? 2 : 1);
+        abc = frame == 0 ? dl.bc_zmax : dl.bc_zmin;
+    } else {
+        kind = (ui > 0 || (ui == 0 && uf > 0.0f)) ? 0 : ((ui == 0 && uf == 0.0f) ? 2 : 1);
+        abc = frame == 0 ? dl.bc_zmin : dl.bc_zmax;
+    }
+    const int64_t gid = d.trk_off + (i - d.i_lo);
+    // per-variant link fields are read from global memory (dg) so that the
+    // register copy `d` is never indexed dynamically
+    const int rbc = dg->rad_bc[v];
+    if (kind == 2) return (abc && rbc) ? gid * 4 + (frame * 2 + (1 - sense)) : -1;
+    if (kind == 1) {
+        if (!abc) return -1;
+        const int j = sense == 0 ? i - dl.Nz : i + dl.Nz;
+        return (d.trk_off + (j - d.i_lo)) * 4 + ((1 - frame) * 2 + sense);
+    }
+    if (!rbc) return -1;
+    const int dst = dg->rad_dst[v];
+    const int j = (int)dg->rad_sign[v] * i + dg->rad_shift[v];
+    return (descs[dst].trk_off + (j - descs[dst].i_lo)) * 4 + dg->rad_var[v];
+}
+
+__device__ __forceinline__ float fast_exp2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ---------------------------------------------------------------------------
+// Segment templates.  Because the layer planes lie on the axial lattice, track
+// i + cpl of a z-stack is track i shifted up by exactly one layer (Eq. 5 with
+// i -> i + cpl): same 2D segments, same lengths, layer + 1.  The unclipped line
+// u(s) = i0 + zeta(s) of a stack therefore serves as a template for every
+// track i0 + m cpl: that track's segments are the template pieces whose layer
+// L_t + m lies in [0, NL).  The domain faces z = 0 and z = H are layer planes,
+// so clipping a track to the domain never cuts a template piece.
+
+__device__ __forceinline__ int floor_div(int a, int c) { return a >= 0 ? a / c : -((-a + c - 1) / c); }
+
+// pieces of the unclipped line u = i0 + zeta(s) inside 2D segment b
+template <typename real>
+struct TplRange {
+    int32_t ua, ub;
+    real fa, fb;
+    int32_t La, Le;
+};
+
+template <typename real>
+__device__ __forceinline__ void tpl_range(const DevLayout &dl, const StackDesc &d, int i0, int b,
+                                          TplRange<real> &r) {
+    r.ua = i0 + __ldg(dl.zn + d.zoff + b);
+    r.fa = lat_frac<real>(dl, d.zoff + b);
+    r.ub = i0 + __ldg(dl.zn + d.zoff + b + 1);
+    r.fb = lat_frac<real>(dl, d.zoff + b + 1);
+    const bool fb_pos = __ldg(dl.zf + d.zoff + b + 1) > 0.0f;
+    r.La = floor_div(r.ua, dl.cpl);
+    r.Le = floor_div(fb_pos ? r.ub : r.ub - 1, dl.cpl);
+}
+
+template <typename real>
+__device__ __forceinline__ real tpl_len(const DevLayout &dl, const StackDesc &d, int b,
+                                        const TplRange<real> &r, int L) {
+    const real lam = lam_of(d, (real)0);
+    if (r.La == r.Le) return len_2d<real>(dl, d.seg2d_off + b) * isin_of(d, (real)0);      // Eq. 8
+    if (L == r.La) return ((real)((r.La + 1) * dl.cpl - r.ua) - r.fa) * lam;
+    if (L == r.Le) return ((real)(r.ub - r.Le * dl.cpl) + r.fb) * lam;
+    return (real)dl.cpl * lam;                                                              // Eq. 11
+}
+
+constexpr int kTplLayerBias = 32768;  // template layers are stored as L + bias in 16 bits

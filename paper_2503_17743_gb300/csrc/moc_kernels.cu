@@ -1,0 +1,454 @@
+// CUDA kernels of the GB300 3D MOC transport sweep (sm_103a).
+//
+//   k_count_stacks  segments per z-stack (preload planning, Sec. 4.2)
+//   k_tpl_count     sizes of the stored segment templates (EXP, Sec. 4.2)
+//   k_tpl_write     writes the stored templates
+//   k_links         link destination of every track direction
+//   k_volumes       tracked FSR volumes
+//   k_source        isotropic source update, FP64
+//   k_finalize      scalar flux from the tallies + FP64 block partials
+//   k_reduce_k      FP64 production / absorption / k / normalisation
+//   k_residual      FP64 fission-source residual partials
+//   k_reduce_res    FP64 residual + convergence flag
+#include <cstdio>
+
+#include "moc_device.cuh"
+#include "moc_kernels.h"
+
+namespace {
+
+constexpr float kLog2e = 1.4426950408889634f;
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+    }
+    return r;  // valid in thread 0
+}
+
+// ---------------------------------------------------------------------------
+// layout kernels
+
+__global__ void k_count_stacks(DevLayout dl, int64_t n_stacks, int64_t *stack_nseg,
+                               int32_t *max_nseg) {
+    __shared__ double sh[32];
+    for (int64_t s = blockIdx.x; s < n_stacks; s += gridDim.x) {
+        const StackDesc d = dl.desc[s];
+        double acc = 0;
+        int mx = 0;
+        for (int k = threadIdx.x; k < d.n_trk; k += blockDim.x) {
+            int n = count_otf(dl, d, d.i_lo + k);
+            acc += n;
+            mx = max(mx, n);
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(max_nseg, mx);
+        double tot = block_sum(acc, sh);
+        if (threadIdx.x == 0) stack_nseg[s] = (int64_t)(tot + 0.5);
+        __syncthreads();
+    }
+}
+
+// Stored templates (one per class r < cpl of each stored stack, template
+// index desc.exp_base + r): piece count, lowest layer and layer span.
+__global__ void k_tpl_count(DevLayout dl, const int32_t *exp_stacks, int64_t n_exp, int64_t *cnt,
+                            int32_t *lmin, int32_t *nlay) {
+    for (int64_t q = blockIdx.x; q < n_exp; q += gridDim.x) {
+        const StackDesc d = dl.desc[exp_stacks[q]];
+        const int ntpl = min(dl.cpl, d.n_trk);
+        for (int r = threadIdx.x; r < ntpl; r += blockDim.x) {
+            const int i0 = d.i_lo + r;
+            int n = 0, lo = 0, hi = 0;
+            TplRange<float> tr;
+            for (int b = 0; b < d.nb; ++b) {
+                tpl_range(dl, d, i0, b, tr);
+                if (b == 0) lo = tr.La;
+                if (tr.Le >= tr.La) n += tr.Le - tr.La + 1;
+                hi = max(hi, tr.Le);
+            }
+            const int64_t t = d.exp_base + r;
+            cnt[t] = n;
+            lmin[t] = lo;
+            nlay[t] = max(hi - lo + 1, 1);
+        }
+    }
+}
+
+template <typename real>
+__global__ void k_tpl_write(DevLayout dl, const int32_t *exp_stacks, int64_t n_exp,
+                            SegRec<real> *recs, int32_t *lidx) {
+    for (int64_t q = blockIdx.x; q < n_exp; q += gridDim.x) {
+        const StackDesc d = dl.desc[exp_stacks[q]];
+        const int ntpl = min(dl.cpl, d.n_trk);
+        for (int r = threadIdx.x; r < ntpl; r += blockDim.x) {
+            const int64_t t = d.exp_base + r;
+            const int i0 = d.i_lo + r;
+            const int Lmin = dl.tpl_lmin[t];
+            const int64_t lb = dl.tpl_loff[t];
+            const int nL = (int)(dl.tpl_loff[t + 1] - lb) - 1;
+            SegRec<real> *out = recs + dl.tpl_off[t];
+            int pos = 0, x = 0;
+            TplRange<real> tr;
+            for (int b = 0; b < d.nb; ++b) {
+                tpl_range(dl, d, i0, b, tr);
+                for (int L = tr.La; L <= tr.Le; ++L) {
+                    while (x <= L - Lmin && x <= nL) lidx[lb + x++] = pos;
+                    SegRec<real> rec{};
+                    rec.key = ((uint32_t)b << 16) | (uint32_t)(L + kTplLayerBias);
+                    rec.len = tpl_len(dl, d, b, tr, L);
+                    out[pos++] = rec;
+                }
+            }
+            while (x <= nL) lidx[lb + x++] = pos;
+        }
+    }
+}
+
+// destination of the outgoing flux of every stored track direction (slot
+// gid*4+v of the next sweep's incoming flux, -1 at a vacuum face)
+__global__ void k_links(DevLayout dl, int64_t n_stacks, int64_t *dst) {
+    for (int64_t s = blockIdx.x; s < n_stacks; s += gridDim.x) {
+        const StackDesc d = dl.desc[s];
+        for (int k = threadIdx.x; k < d.n_trk; k += blockDim.x) {
+            const int i = d.i_lo + k;
+            const int64_t gid = d.trk_off + k;
+            for (int v = 0; v < 4; ++v) {
+                int64_t t = exit_dest(dl, dl.desc, d, dl.desc + s, i, v);
+                if (t >= dl.n_slots) t = -1;
+                dst[gid * 4 + v] = t;
+            }
+        }
+    }
+}
+
+template <typename real>
+struct VolVisit {
+    const int32_t *reg2d;
+    int NL;
+    double *vol;
+    double c;
+    __device__ void operator()(int b, int L, real len) {
+        const int reg = __ldg(reg2d + b);
+        atomicAdd(vol + (size_t)reg * NL + L, c * (double)len);
+        atomicAdd(vol + (size_t)reg * NL + (NL - 1 - L), c * (double)len);
+    }
+};
+
+template <typename real>
+__global__ void k_volumes(DevLayout dl, int64_t n_stacks, double *vol) {
+    for (int64_t s = blockIdx.x; s < n_stacks; s += gridDim.x) {
+        const StackDesc d = dl.desc[s];
+        // each stored track carries two directions of equal weight, in two frames
+        VolVisit<real> v{dl.reg2d + d.seg2d_off, dl.NL, vol, 2.0 * d.W / (4.0 * MOC_PI)};
+        for (int k = threadIdx.x; k < d.n_trk; k += blockDim.x) walk_otf<real>(dl, d, d.i_lo + k, 0, v);
+    }
+}
+
+// segments of the stack's tracks for introspection (frame U order)
+template <typename real>
+struct ListVisit {
+    const int32_t *reg2d;
+    int NL;
+    int32_t *f;
+    double *l;
+    __device__ void operator()(int b, int L, real ln) {
+        *f++ = __ldg(reg2d + b) * NL + L;
+        *l++ = (double)ln;
+    }
+};
+
+template <typename real>
+__global__ void k_stack_segments(DevLayout dl, int64_t s, const int64_t *offs, int32_t *fsr_u,
+                                 double *len) {
+    const StackDesc d = dl.desc[s];
+    for (int k = threadIdx.x; k < d.n_trk; k += blockDim.x) {
+        ListVisit<real> v{dl.reg2d + d.seg2d_off, dl.NL, fsr_u + offs[k], len + offs[k]};
+        walk_otf<real>(dl, d, d.i_lo + k, 0, v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FSR-sized FP64 kernels
+
+// Q = (sum_h Sigma_s[h->g] phi_h + chi_g / k sum_h nuSigma_f,h phi_h + S_g) / 4pi, with
+// phi normalised on the fly by the latest scale; qr = Q / Sigma_t.
+template <typename real>
+__global__ void k_source(DevLayout dl, DevState st, int32_t nfsr) {
+    const int G = dl.G;
+    const double scale = st.scal[SC_SCALE];
+    const double k = st.scal[SC_K];
+    const bool eig = st.scal[SC_EIGEN] != 0.0;
+    real *qr = reinterpret_cast<real *>(st.qr);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nfsr; i += gridDim.x * blockDim.x) {
+        const int m = dl.fsr_mat[i];
+        const double *ph = st.phi + (size_t)i * G;
+        double fis = 0.0;
+        if (eig)
+            for (int h = 0; h < G; ++h) fis += st.nsf64[m * G + h] * ph[h] * scale;
+        for (int g = 0; g < G; ++g) {
+            double sc = 0.0;
+            for (int h = 0; h < G; ++h) sc += st.sig_s64[((size_t)m * G + h) * G + g] * ph[h] * scale;
+            double q = sc;
+            if (eig) q += st.chi64[m * G + g] * fis / k;
+            if (st.src64) q += st.src64[m * G + g];
+            q /= 4.0 * MOC_PI;
+            qr[(size_t)i * G + g] = (real)(q / st.sig_t64[m * G + g]);
+        }
+    }
+}
+
+// phi = 4 pi Qr + tally / (V Sigma_t); tally cleared; block partials of
+// production, absorption and (fixed source) the flux residual.
+template <typename real>
+__global__ void k_finalize(DevLayout dl, DevState st, int32_t nfsr) {
+    __shared__ double sh[32];
+    const int G = dl.G;
+    const bool eig = st.scal[SC_EIGEN] != 0.0;
+    const real *qr = reinterpret_cast<const real *>(st.qr);
+    double P = 0, Ab = 0, r2 = 0, cnt = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nfsr; i += gridDim.x * blockDim.x) {
+        const int m = dl.fsr_mat[i];
+        const double V = st.vol[i];
+        double fis = 0.0;
+        for (int g = 0; g < G; ++g) {
+            const size_t q = (size_t)i * G + g;
+            const double sg = st.sig_t64[m * G + g];
+            double phi = 4.0 * MOC_PI * (double)qr[q];
+            if (V > 0.0) phi += st.tally[q] / (V * sg);
+            st.tally[q] = 0.0;
+            if (!eig && phi > 0.0) {
+                double rr = (phi - st.phi[q]) / phi;
+                r2 += rr * rr;
+                cnt += 1.0;
+            }
+            st.phi[q] = phi;
+            fis += st.nsf64[m * G + g] * phi;
+            double sa = sg;
+            for (int h = 0; h < G; ++h) sa -= st.sig_s64[((size_t)m * G + g) * G + h];
+            Ab += V * sa * phi;
+        }
+        P += V * fis;
+        st.fiss[i] = fis;
+    }
+    double v;
+    v = block_sum(P, sh); if (threadIdx.x == 0) st.partial[blockIdx.x * 4 + 0] = v;
+    v = block_sum(Ab, sh); if (threadIdx.x == 0) st.partial[blockIdx.x * 4 + 1] = v;
+    v = block_sum(r2, sh); if (threadIdx.x == 0) st.partial[blockIdx.x * 4 + 2] = v;
+    v = block_sum(cnt, sh); if (threadIdx.x == 0) st.partial[blockIdx.x * 4 + 3] = v;
+}
+
+// single block: production, absorption, k update and normalisation scale
+__global__ void k_reduce_k(DevState st, int nblocks, double integrations) {
+    if (threadIdx.x != 0) return;
+    double P = 0, Ab = 0, r2 = 0, cnt = 0;
+    for (int b = 0; b < nblocks; ++b) {
+        P += st.partial[b * 4 + 0];
+        Ab += st.partial[b * 4 + 1];
+        r2 += st.partial[b * 4 + 2];
+        cnt += st.partial[b * 4 + 3];
+    }
+    double *s = st.scal;
+    const bool eig = s[SC_EIGEN] != 0.0;
+    s[SC_PROD] = P;
+    s[SC_ABS] = Ab;
+    s[SC_INTEG] += integrations;
+    s[SC_ITER] += 1.0;
+    if (eig) {
+        const double kn = s[SC_K] * P;  // the swept flux was normalised to production 1
+        s[SC_DK] = kn - s[SC_K];
+        s[SC_K] = kn;
+        s[SC_SCALE] = P > 0.0 ? 1.0 / P : 1.0;
+        s[SC_LEAK_PREV] = s[SC_LEAK] * s[SC_SCALE];
+    } else {
+        s[SC_DK] = 0.0;
+        s[SC_SCALE] = 1.0;
+        s[SC_RES] = cnt > 0 ? sqrt(r2 / cnt) : 0.0;
+        s[SC_LEAK_PREV] = s[SC_LEAK];
+        s[SC_CONV] = (s[SC_TOLS] > 0 && s[SC_RES] < s[SC_TOLS]) ? 1.0 : 0.0;
+    }
+    s[SC_LEAK] = 0.0;
+}
+
+// eigenvalue residual: RMS relative change of the normalised fission rate
+__global__ void k_residual(DevState st, int32_t nfsr) {
+    __shared__ double sh[32];
+    const double scale = st.scal[SC_SCALE];
+    double r2 = 0, cnt = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nfsr; i += gridDim.x * blockDim.x) {
+        const double f = st.fiss[i] * scale;
+        if (f > 0.0) {
+            const double r = (f - st.fiss_old[i]) / f;
+            r2 += r * r;
+            cnt += 1.0;
+        }
+        st.fiss_old[i] = f;
+    }
+    double v;
+    v = block_sum(r2, sh); if (threadIdx.x == 0) st.partial[blockIdx.x * 4 + 2] = v;
+    v = block_sum(cnt, sh); if (threadIdx.x == 0) st.partial[blockIdx.x * 4 + 3] = v;
+}
+
+__global__ void k_reduce_res(DevState st, int nblocks) {
+    if (threadIdx.x != 0) return;
+    double r2 = 0, cnt = 0;
+    for (int b = 0; b < nblocks; ++b) {
+        r2 += st.partial[b * 4 + 2];
+        cnt += st.partial[b * 4 + 3];
+    }
+    double *s = st.scal;
+    s[SC_RES] = cnt > 0 ? sqrt(r2 / cnt) : 0.0;
+    s[SC_CONV] = (s[SC_TOLS] > 0 && s[SC_RES] < s[SC_TOLS] && fabs(s[SC_DK]) < s[SC_TOLK]) ? 1.0 : 0.0;
+}
+
+// initial state: phi = 1; production of it -> scale; fission rate reference
+__global__ void k_init_state(DevLayout dl, DevState st, int32_t nfsr) {
+    __shared__ double sh[32];
+    const int G = dl.G;
+    double P = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nfsr; i += gridDim.x * blockDim.x) {
+        const int m = dl.fsr_mat[i];
+        double fis = 0.0;
+        for (int g = 0; g < G; ++g) {
+            st.phi[(size_t)i * G + g] = 1.0;
+            st.tally[(size_t)i * G + g] = 0.0;
+            fis += st.nsf64[m * G + g];
+        }
+        st.fiss[i] = fis;
+        P += st.vol[i] * fis;
+    }
+    double v = block_sum(P, sh);
+    if (threadIdx.x == 0) st.partial[blockIdx.x * 4 + 0] = v;
+}
+
+__global__ void k_init_finish(DevState st, int nblocks, int32_t nfsr) {
+    __shared__ double s_scale;
+    if (threadIdx.x == 0) {
+        double P = 0;
+        for (int b = 0; b < nblocks; ++b) P += st.partial[b * 4 + 0];
+        double *s = st.scal;
+        const bool eig = s[SC_EIGEN] != 0.0;
+        s[SC_K] = 1.0;
+        s[SC_DK] = 0.0;
+        s[SC_SCALE] = (eig && P > 0.0) ? 1.0 / P : 1.0;
+        s[SC_PROD] = P;
+        s[SC_LEAK] = 0.0;
+        s[SC_RES] = 0.0;
+        s[SC_ITER] = 0.0;
+        s[SC_CONV] = 0.0;
+        s_scale = s[SC_SCALE];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nfsr; i += blockDim.x) st.fiss_old[i] = st.fiss[i] * s_scale;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+
+#define CK(x)                                            \
+    do {                                                 \
+        cudaError_t e_ = (x);                            \
+        if (e_ != cudaSuccess) return e_;                \
+    } while (0)
+
+cudaError_t launch_count_stacks(const DevLayout &dl, int64_t n_stacks, int64_t *stack_nseg,
+                                int32_t *max_nseg, int grid, cudaStream_t s) {
+    k_count_stacks<<<grid, 128, 0, s>>>(dl, n_stacks, stack_nseg, max_nseg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tpl_count(const DevLayout &dl, const int32_t *exp_stacks, int64_t n_exp,
+                             int64_t *cnt, int32_t *lmin, int32_t *nlay, int grid, cudaStream_t s) {
+    if (n_exp == 0) return cudaSuccess;
+    k_tpl_count<<<grid, 32, 0, s>>>(dl, exp_stacks, n_exp, cnt, lmin, nlay);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tpl_write(int precision, const DevLayout &dl, const int32_t *exp_stacks,
+                             int64_t n_exp, void *recs, int32_t *lidx, int grid, cudaStream_t s) {
+    if (n_exp == 0) return cudaSuccess;
+    if (precision == MOC_FP64)
+        k_tpl_write<double><<<grid, 32, 0, s>>>(dl, exp_stacks, n_exp, (SegRec<double> *)recs, lidx);
+    else
+        k_tpl_write<float><<<grid, 32, 0, s>>>(dl, exp_stacks, n_exp, (SegRec<float> *)recs, lidx);
+    return cudaGetLastError();
+}
+
+size_t segrec_size(int precision) {
+    return precision == MOC_FP64 ? sizeof(SegRec<double>) : sizeof(SegRec<float>);
+}
+
+// per-track segment counts of one stack (introspection)
+__global__ void k_track_counts(DevLayout dl, int64_t s, int64_t *cnt) {
+    const StackDesc d = dl.desc[s];
+    for (int k = threadIdx.x; k < d.n_trk; k += blockDim.x) cnt[k + 1] = count_otf(dl, d, d.i_lo + k);
+}
+
+cudaError_t launch_track_counts(const DevLayout &dl, int64_t stack, int64_t *cnt, cudaStream_t s) {
+    k_track_counts<<<1, 128, 0, s>>>(dl, stack, cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_links(const DevLayout &dl, int64_t n_stacks, int64_t *dst, int grid,
+                         cudaStream_t s) {
+    k_links<<<grid, 128, 0, s>>>(dl, n_stacks, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_volumes(int precision, const DevLayout &dl, int64_t n_stacks, double *vol,
+                           int grid, cudaStream_t s) {
+    if (precision == MOC_FP64) k_volumes<double><<<grid, 128, 0, s>>>(dl, n_stacks, vol);
+    else k_volumes<float><<<grid, 128, 0, s>>>(dl, n_stacks, vol);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stack_segments(int precision, const DevLayout &dl, int64_t stack,
+                                  const int64_t *offs, int32_t *fsr, double *len, cudaStream_t s) {
+    if (precision == MOC_FP64) k_stack_segments<double><<<1, 128, 0, s>>>(dl, stack, offs, fsr, len);
+    else k_stack_segments<float><<<1, 128, 0, s>>>(dl, stack, offs, fsr, len);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_source(int precision, const DevLayout &dl, const DevState &st, int32_t nfsr,
+                          int grid, cudaStream_t s) {
+    if (precision == MOC_FP64) k_source<double><<<grid, 256, 0, s>>>(dl, st, nfsr);
+    else k_source<float><<<grid, 256, 0, s>>>(dl, st, nfsr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(int precision, const DevLayout &dl, const DevState &st, int32_t nfsr,
+                            int grid, double integrations, cudaStream_t s) {
+    if (precision == MOC_FP64) k_finalize<double><<<grid, 256, 0, s>>>(dl, st, nfsr);
+    else k_finalize<float><<<grid, 256, 0, s>>>(dl, st, nfsr);
+    CK(cudaGetLastError());
+    k_reduce_k<<<1, 32, 0, s>>>(st, grid, integrations);
+    CK(cudaGetLastError());
+    k_residual<<<grid, 256, 0, s>>>(st, nfsr);
+    CK(cudaGetLastError());
+    k_reduce_res<<<1, 32, 0, s>>>(st, grid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_fixed(int precision, const DevLayout &dl, const DevState &st,
+                                  int32_t nfsr, int grid, double integrations, cudaStream_t s) {
+    if (precision == MOC_FP64) k_finalize<double><<<grid, 256, 0, s>>>(dl, st, nfsr);
+    else k_finalize<float><<<grid, 256, 0, s>>>(dl, st, nfsr);
+    CK(cudaGetLastError());
+    k_reduce_k<<<1, 32, 0, s>>>(st, grid, integrations);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_state(const DevLayout &dl, const DevState &st, int32_t nfsr, int grid,
+                              cudaStream_t s) {
+    k_init_state<<<grid, 256, 0, s>>>(dl, st, nfsr);
+    CK(cudaGetLastError());
+    k_init_finish<<<1, 256, 0, s>>>(st, grid, nfsr);
+    return cudaGetLastError();
+}

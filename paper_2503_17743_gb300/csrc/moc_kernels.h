@@ -1,0 +1,37 @@
+// Launchers of the CUDA kernels (moc_kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "moc_device.cuh"
+
+cudaError_t launch_count_stacks(const DevLayout &dl, int64_t n_stacks, int64_t *stack_nseg,
+                                int32_t *max_nseg, int grid, cudaStream_t s);
+cudaError_t launch_tpl_count(const DevLayout &dl, const int32_t *exp_stacks, int64_t n_exp,
+                             int64_t *cnt, int32_t *lmin, int32_t *nlay, int grid, cudaStream_t s);
+cudaError_t launch_tpl_write(int precision, const DevLayout &dl, const int32_t *exp_stacks,
+                             int64_t n_exp, void *recs, int32_t *lidx, int grid, cudaStream_t s);
+size_t segrec_size(int precision);
+cudaError_t launch_track_counts(const DevLayout &dl, int64_t stack, int64_t *cnt, cudaStream_t s);
+cudaError_t launch_links(const DevLayout &dl, int64_t n_stacks, int64_t *dst, int grid,
+                         cudaStream_t s);
+cudaError_t launch_volumes(int precision, const DevLayout &dl, int64_t n_stacks, double *vol,
+                           int grid, cudaStream_t s);
+cudaError_t launch_stack_segments(int precision, const DevLayout &dl, int64_t stack,
+                                  const int64_t *offs, int32_t *fsr, double *len, cudaStream_t s);
+// the sweep (moc_sweep.cu)
+int sweep_lanes_per_track(int G);
+size_t sweep_smem_bytes(int precision, int tally_smem, int M, int G, int cap);
+cudaError_t launch_sweep(int precision, int tally_smem, const DevLayout &dl, const DevState &st,
+                         const int32_t *order, int32_t n_work, int32_t cap, const void *psi_in,
+                         void *psi_out, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t sweep_occupancy(int precision, int tally_smem, int G, int block, size_t smem,
+                            int *blocks_per_sm);
+cudaError_t launch_source(int precision, const DevLayout &dl, const DevState &st, int32_t nfsr,
+                          int grid, cudaStream_t s);
+cudaError_t launch_finalize(int precision, const DevLayout &dl, const DevState &st, int32_t nfsr,
+                            int grid, double integrations, cudaStream_t s);
+cudaError_t launch_finalize_fixed(int precision, const DevLayout &dl, const DevState &st,
+                                  int32_t nfsr, int grid, double integrations, cudaStream_t s);
+cudaError_t launch_init_state(const DevLayout &dl, const DevState &st, int32_t nfsr, int grid,
+                              cudaStream_t s);

@@ -1,0 +1,237 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Bars: FSR-id sequences and segment counts bit-exact; FP32 segment lengths
+within 1e-6 (relative) + 1e-6 cm; tallies, fluxes and k within the stated
+tolerances (FP64 sweeps ~1e-10, FP32 sweeps: flux 1e-4 max relative, k 1e-5
+absolute).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_2503_17743_gb300 import (MOC_FP32, MOC_FP64, MOC_TALLY_GLOBAL, MOC_TALLY_SHARED,
+                                    Geometry, Tracks, track_params)
+
+pytestmark = pytest.mark.gpu
+
+NTH = os.cpu_count() or 4
+
+
+def _lat3(bc=(1, 1, 1, 1, 1, 1), seed=3):
+    return synth.lattice(seed, n=3, G=3, height=4.0, n_layers=4, n_azim=8, n_polar=4,
+                         radial_spacing=0.15, axial_spacing=0.5, bc=bc, n_gt=2, name="lat3")
+
+
+PROBLEMS = {
+    "pin": lambda: synth.pin_cell(1),
+    "lat3": lambda: _lat3(),
+    "lat3_mixed": lambda: _lat3(bc=(1, 0, 1, 1, 0, 1), seed=4),
+    "lattice5": lambda: synth.workload("lattice5"),
+    "l17_small": lambda: synth.workload("lattice17_small"),
+}
+
+_cache = {}
+
+
+def get(name):
+    if name not in _cache:
+        p = PROBLEMS[name]()
+        _cache[name] = (p, oracle.Oracle(p, n_threads=NTH), Geometry(p))
+    return _cache[name]
+
+
+def make(name, **kw):
+    p, o, g = get(name)
+    return p, o, Tracks(g, track_params(p, **kw))
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_segments_bit_exact(name):
+    p, o, tr = make(name)
+    step = max(1, o.n_tracks2d // 60)
+    for t in range(0, o.n_tracks2d, step):
+        for pp in range(p.n_polar):
+            oi, on, of, ol = o.stack(t, pp)
+            gi, gn, gf, gl = tr.stack_segments(t, pp)
+            np.testing.assert_array_equal(gi, oi, err_msg=f"track indices t={t} p={pp}")
+            np.testing.assert_array_equal(gn, on, err_msg=f"segment counts t={t} p={pp}")
+            np.testing.assert_array_equal(gf, of, err_msg=f"fsr ids t={t} p={pp}")
+            assert np.all(np.abs(gl - ol) <= 1e-6 * ol + 1e-6), (t, pp, np.abs(gl - ol).max())
+    tr.close()
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_volumes(name):
+    p, o, tr = make(name)
+    np.testing.assert_allclose(tr.volumes(), o.volumes(), rtol=1e-6)
+    info = tr.info
+    assert info["tracks3d"] == o.n_tracks3d
+    tr.close()
+
+
+@pytest.mark.parametrize("prec,rtol", [(MOC_FP64, 1e-11), (MOC_FP32, 2e-5)])
+@pytest.mark.parametrize("name", ["pin", "lat3", "lat3_mixed", "l17_small"])
+def test_two_sweeps_from_source(name, prec, rtol):
+    """Seeded source, zero incoming fluxes, two sweeps: the second one runs on
+    the boundary fluxes the first one passed through the links."""
+    p, o, tr = make(name, precision=prec)
+    rng = np.random.default_rng(11)
+    Q = rng.uniform(0.2, 1.0, size=(o.n_fsr, p.num_groups))
+    o.reset()
+    for sweep in range(2):
+        ot, ol = o.sweep_once(Q)
+        gt, gl = tr.sweep_from_source(Q)
+        scale = np.abs(ot).max()
+        assert np.abs(gt - ot).max() <= rtol * scale, (sweep, np.abs(gt - ot).max() / scale)
+        assert abs(gl - ol) <= rtol * max(abs(ol), 1e-300) + 1e-300
+    o.reset()
+    tr.close()
+
+
+@pytest.mark.parametrize("name", ["lat3", "lat3_mixed"])
+def test_single_track_links(name):
+    """Q = 0 and one incoming flux: the flux arrives attenuated at exactly the
+    track direction the oracle's geometric link names."""
+    p, o, tr = make(name, precision=MOC_FP64)
+    rng = np.random.default_rng(5)
+    G = p.num_groups
+    zero = np.zeros((o.n_fsr, G))
+    for _ in range(12):
+        t = int(rng.integers(o.n_tracks2d))
+        pp = int(rng.integers(p.n_polar))
+        imin, n = o.stack_range(t, pp)
+        i = imin + int(rng.integers(n))
+        s = int(rng.integers(2))
+        val = rng.uniform(0.5, 2.0, size=G)
+        o.reset(); o.clear_psi()
+        tr.reset()
+        o.psi(t, pp, i, s, val)
+        tr.psi(t, pp, i, s, val)
+        ot, _ = o.sweep_once(zero)
+        gt, _ = tr.sweep_from_source(zero)
+        np.testing.assert_allclose(gt, ot, rtol=1e-12, atol=1e-14)
+        d = o.link(t, pp, i, s)
+        if d[0] >= 0:
+            np.testing.assert_allclose(tr.psi(*d), o.psi(*d), rtol=1e-12)
+            assert np.all(o.psi(*d) > 0)
+    o.reset()
+    tr.close()
+
+
+@pytest.mark.parametrize("prec,ktol,ftol", [(MOC_FP64, 1e-11, 1e-10), (MOC_FP32, 1e-5, 1e-4)])
+@pytest.mark.parametrize("name", ["pin", "lat3_mixed", "lattice5", "l17_small"])
+def test_power_iterations(name, prec, ktol, ftol):
+    p, o, tr = make(name, precision=prec)
+    n = 15
+    o.reset()
+    ref = o.iterate(n)
+    res = tr.iterate(n, use_graph=True)
+    phi, k = tr.flux()
+    assert res["iterations"] == n
+    assert abs(k - ref["k"]) < ktol, (k, ref["k"])
+    np.testing.assert_allclose(phi, o.flux(), rtol=ftol)
+    tr.close()
+
+
+def test_converged_pin_cell_fp64():
+    p, o, tr = make("pin", precision=MOC_FP64)
+    ref = o.solve(tol_k=1e-10, tol_src=1e-9, max_iter=5000)
+    res = tr.solve_eigen(tol_k=1e-10, tol_src=1e-9, max_iter=5000)
+    assert ref["converged"] and res["converged"]
+    assert abs(res["k"] - ref["k"]) < 1e-10
+    assert abs(res["iterations"] - ref["iterations"]) <= 1
+    phi, _ = tr.flux()
+    np.testing.assert_allclose(phi, o.flux(), rtol=1e-9)
+    # balance: production / k = absorption (all faces reflective), to the
+    # convergence level of the solve
+    assert abs(1.0 / res["k"] - res["absorption"]) < 1e-7
+    tr.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(MOC_FP64, 1e-9), (MOC_FP32, 1e-5)])
+def test_infinite_medium_closed_form(prec, tol):
+    p = synth.pin_cell(1, homogeneous=True)
+    tr = Tracks(Geometry(p), track_params(p, precision=prec))
+    res = tr.solve_eigen(tol_k=1e-12 if prec == MOC_FP64 else 1e-8,
+                         tol_src=1e-11 if prec == MOC_FP64 else 1e-6, max_iter=20000)
+    st, ss, nsf, chi = p.sigma_t[0], p.sigma_s[0], p.nu_sigma_f[0], p.chi[0]
+    kinf = nsf @ np.linalg.solve(np.diag(st) - ss.T, chi)
+    assert abs(res["k"] - kinf) < tol
+    tr.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(MOC_FP64, 1e-9), (MOC_FP32, 1e-5)])
+def test_fixed_source(prec, tol):
+    p = synth.pin_cell(5, G=3, homogeneous=True)
+    p = p.with_tracks(nu_sigma_f=np.zeros_like(p.nu_sigma_f),
+                      ext_source=np.tile([[1.0, 0.4, 0.2]], (p.num_materials, 1)))
+    tr = Tracks(Geometry(p), track_params(p, precision=prec))
+    res = tr.solve_fixed_source(tol_src=1e-11 if prec == MOC_FP64 else 1e-6, max_iter=20000)
+    ref = np.linalg.solve(np.diag(p.sigma_t[0]) - p.sigma_s[0].T, p.ext_source[0])
+    phi, _ = tr.flux()
+    np.testing.assert_allclose(phi, np.tile(ref, (phi.shape[0], 1)), rtol=tol)
+    tr.close()
+    # heterogeneous fixed-source lattice vs the oracle after n iterations
+    q = synth.lattice(8, n=3, G=4, height=4.0, n_layers=2, n_azim=8, n_polar=4,
+                      radial_spacing=0.2, axial_spacing=0.5, fixed_source=True)
+    o = oracle.Oracle(q, n_threads=NTH)
+    o.reset()
+    o.iterate(12)
+    tr = Tracks(Geometry(q), track_params(q, precision=prec))
+    tr.iterate(12)
+    phi, _ = tr.flux()
+    np.testing.assert_allclose(phi, o.flux(), rtol=1e-9 if prec == MOC_FP64 else 1e-4)
+    tr.close()
+
+
+@pytest.mark.parametrize("name", ["lat3_mixed", "l17_small"])
+def test_stored_and_generated_segments_agree(name):
+    """Preload budgets: everything stored (EXP), nothing stored (OTF), and a
+    partial budget give the same sweep (Sec. 4.2)."""
+    p, o, _ = get(name)
+    Q = np.random.default_rng(2).uniform(0.2, 1.0, size=(o.n_fsr, p.num_groups))
+    outs, infos = [], []
+    full = Tracks(get(name)[2], track_params(p, preload_budget_bytes=-1))
+    half_budget = full.info["stored_segments"] * 8 // 2
+    full.close()
+    for budget in (-1, 0, half_budget):
+        tr = Tracks(get(name)[2], track_params(p, preload_budget_bytes=budget))
+        infos.append(tr.info)
+        outs.append([tr.sweep_from_source(Q)[0], tr.sweep_from_source(Q)[0]])
+        tr.close()
+    # stored templates: one per class of each stack, far fewer pieces than segments
+    assert 0 < infos[0]["stored_segments"] * 2 < infos[0]["segments3d"]
+    assert infos[0]["preloaded_stacks"] == infos[0]["stacks"] // 2
+    assert infos[1]["stored_segments"] == 0
+    assert 0 < infos[2]["preloaded_stacks"] < infos[0]["preloaded_stacks"]
+    for run in outs[1:]:
+        for a, b in zip(run, outs[0]):
+            # FP32 sweeps: the same contributions summed in a different order
+            np.testing.assert_allclose(a, b, rtol=1e-5, atol=1e-6 * np.abs(b).max())
+
+
+def test_tally_modes_agree():
+    p, o, g = get("l17_small")
+    Q = np.random.default_rng(4).uniform(0.2, 1.0, size=(o.n_fsr, p.num_groups))
+    res = []
+    for mode in (MOC_TALLY_SHARED, MOC_TALLY_GLOBAL):
+        tr = Tracks(g, track_params(p, tally_mode=mode))
+        assert tr.info["tally_mode"] == mode
+        res.append(tr.sweep_from_source(Q)[0])
+        tr.close()
+    np.testing.assert_allclose(res[0], res[1], rtol=1e-5, atol=1e-6 * np.abs(res[0]).max())
+
+
+def test_graph_and_stream_agree():
+    p, o, g = get("lattice5")
+    a = Tracks(g, track_params(p))
+    b = Tracks(g, track_params(p))
+    ra = a.iterate(10, use_graph=True)
+    rb = b.iterate(10, use_graph=False)
+    assert abs(ra["k"] - rb["k"]) < 1e-6
+    np.testing.assert_allclose(a.flux()[0], b.flux()[0], rtol=1e-5)
+    a.close()
+    b.close()
