@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 3D MOC transport sweep.
+
+Metric: 3D MOC segment-group integrations per second (one integration = Eq. 3
+on one 3D segment, in one direction, for one energy group, plus its Eq. 4
+tally).  Workload: the 17x17 pin lattice (synthetic, seeded; 7 groups, 32
+azimuths x 4 polar angles, 0.05 cm radial and 0.5 cm axial spacing, 20 cm in
+10 layers, reflective radially, vacuum axially), FP32 sweep, all segment
+templates stored.  A step is one outer power iteration on the device-resident
+problem: source update, sweep, flux / k / residual update.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  With --impl reference the FP64 CPU oracle runs the
+same steps on the host cores (rank 0 only).
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "3D MOC segment-group integrations/s"
+UNIT = "integrations/s"
+WORKLOAD = "lattice17"
+WORKLOAD_DESC = ("17x17 pin lattice (264 fuel pins, 25 seeded guide tubes), 3 materials, 7 groups, "
+                 "20 cm in 10 layers, reflective radial / vacuum axial, 32 azimuthal x 4 polar, "
+                 "radial spacing 0.05 cm, axial spacing 0.5 cm; FP32 sweep, templates stored")
+# algorithmic work of one integration: 7 FP32 operations, one of them the exponential
+OPS_PER_INTEGRATION = 7
+# ALU roofline: the exponential runs on the MUFU pipe, 16 per SM per clock
+# (152 SMs at the 2070 MHz maximum clock): 5.03e12 integrations/s
+SMS, MUFU_PER_CLK, SM_MAX_MHZ = 152, 16, 2070.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def clock_sampler(device, path):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        f = open(path, "w")
+        return subprocess.Popen(["nvidia-smi", f"--id={device}", f"--query-gpu={q}",
+                                 "--format=csv,noheader,nounits", "-lms", "200"],
+                                stdout=f, stderr=subprocess.DEVNULL), f
+    except Exception:
+        return None, None
+
+
+def parse_clocks(path):
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+    except OSError:
+        pass
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def profile_traffic(src_hash):
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+    taken on the current sweep source; otherwise None."""
+    path = os.path.join(ROOT, "profiles", "k_sweep_lattice17.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9]+)", txt)
+    if not m or not t or m.group(1) != src_hash:
+        return None
+    return int(t.group(1))
+
+
+def sweep_source_hash():
+    h = hashlib.sha256()
+    for f in ("moc_sweep.cu", "moc_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2503_17743_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def cpu_baseline(prob, seconds_target=10.0):
+    """The oracle (as it stands) on the host cores: full FP64 sweeps of the
+    workload from a seeded source, as many as fit in about 10 s."""
+    import numpy as np
+
+    import oracle
+    cores = os.cpu_count() or 1
+    o = oracle.Oracle(prob, n_threads=cores)
+    Q = np.random.default_rng(7).uniform(0.2, 1.0, size=(o.n_fsr, prob.num_groups))
+    n_total, t_total, sweeps = 0, 0.0, 0
+    while t_total < seconds_target and sweeps < 20:
+        t0 = time.perf_counter()
+        n, _ = o.sweep_sample(Q, 0, o.n_tracks2d)
+        t_total += time.perf_counter() - t0
+        n_total += n
+        sweeps += 1
+    return {"value": n_total / t_total, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{sweeps} full FP64 sweep(s) of {WORKLOAD} from a seeded source "
+                      f"({n_total:.4g} integrations, {t_total:.1f} s)"}
+
+
+def run_reference(args):
+    import synth
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    prob = synth.workload(WORKLOAD)
+    cores = os.cpu_count() or 1
+    o = oracle.Oracle(prob, n_threads=cores)
+    o.reset()
+    integ_per_step = None
+    for _ in range(args.warmup):
+        o.iterate(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.iterate(1)
+    dt = time.perf_counter() - t0
+    # integrations of one sweep (the oracle counts them in a sample sweep)
+    import numpy as np
+    n, _ = o.sweep_sample(np.zeros((o.n_fsr, prob.num_groups)), 0, o.n_tracks2d)
+    integ_per_step = n
+    value = integ_per_step * args.steps / dt
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD_DESC, "step": "one outer power iteration (FP64 oracle)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} outer iterations of {WORKLOAD}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    import synth
+    from paper_2503_17743_gb300 import MOC_FP32, Geometry, Tracks, load, track_params
+    from paper_2503_17743_gb300 import build as libbuild
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    libbuild.build()
+    load()
+    prob = synth.workload(WORKLOAD)
+    geom = Geometry(prob)
+    tr = Tracks(geom, track_params(prob, precision=MOC_FP32, device=local))
+    info = tr.info
+    integ = info["integrations_per_sweep"]
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        tr.enqueue_source(sp)
+        ev_s0.record(stream)
+        tr.enqueue_sweep(sp)
+        ev_s1.record(stream)
+        tr.enqueue_update(sp)
+
+    # warm-up (also warms the kernels' first-launch costs)
+    tr.reset()
+    ev_s0, ev_s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 0)):
+            step()
+    torch.cuda.synchronize()
+
+    steps = []
+    for _ in range(args.steps):
+        steps.append([torch.cuda.Event(enable_timing=True) for _ in range(4)])
+    sampler, clk_file = (None, None)
+    clk_path = os.path.join(tempfile.gettempdir(), f"moc_bench_clocks_{os.getpid()}_{rank}.csv")
+    if rank == 0:
+        sampler, clk_file = clock_sampler(local, clk_path)
+        time.sleep(0.5)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for evs in steps:
+            flush.zero_()                 # L2 flushed between timed steps, outside the events
+            evs[0].record(stream)
+            tr.enqueue_source(sp)
+            evs[1].record(stream)
+            tr.enqueue_sweep(sp)
+            evs[2].record(stream)
+            tr.enqueue_update(sp)
+            evs[3].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    if sampler is not None:
+        sampler.terminate()
+        sampler.wait()
+        clk_file.close()
+    step_ms = [e[0].elapsed_time(e[3]) for e in steps]
+    sweep_ms = [e[1].elapsed_time(e[2]) for e in steps]
+    total_s = sum(step_ms) * 1e-3
+    res = tr.read_result(sp)
+    if world > 1:
+        t = torch.tensor([total_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * integ * args.steps / total_s
+
+    # end to end through the C ABI from host arrays: geometry, tracks, a
+    # converged eigenvalue solve, the flux read back
+    e2e = None
+    if rank == 0:
+        e2e_runs = []
+        for _ in range(max(1, min(args.steps, args.e2e_runs))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g2 = Geometry(prob)
+            t2 = Tracks(g2, track_params(prob, precision=MOC_FP32, device=local))
+            r2 = t2.solve_eigen(tol_k=1e-7, tol_src=1e-6, max_iter=5000, use_graph=True, check=False)
+            phi, k2 = t2.flux()
+            dt = time.perf_counter() - t0
+            h2d = t2.info.get("h2d_bytes", 0)
+            t2.close()
+            e2e_runs.append((r2["integrations"] / dt, dt, r2, h2d, phi.nbytes + 128 * r2["iterations"], k2))
+        best = max(e2e_runs, key=lambda x: x[0])
+        e2e = {"value": best[0], "unit": UNIT, "h2d_bytes_per_step": int(best[3]),
+               "d2h_bytes_per_step": int(best[4]), "seconds": best[1],
+               "iterations": best[2]["iterations"], "k": best[5],
+               "step": "moc_create_geometry + moc_generate_tracks + moc_solve_eigen "
+                       "(tol_k 1e-7, tol_src 1e-6, CUDA graphs) + moc_get_flux, from host arrays"}
+        gk = golden_k()
+        if gk is not None:
+            e2e["k_oracle"] = gk
+            e2e["k_err"] = abs(best[5] - gk)
+
+    if rank != 0:
+        return
+    sw = statistics.mean(sweep_ms) * 1e-3
+    ach = OPS_PER_INTEGRATION * integ / sw / 1e12
+    peak = OPS_PER_INTEGRATION * SMS * MUFU_PER_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": profile_traffic(sweep_source_hash()), "kernel": "k_sweep",
+            "sweep_ms": sw * 1e3,
+            "peak_basis": "derived: 7 FP32 ops per integration, exponential on MUFU at 16/SM/clk, "
+                          "152 SMs, 2070 MHz"}
+    clocks = parse_clocks(clk_path)
+    try:
+        os.remove(clk_path)
+    except OSError:
+        pass
+    cpu = cpu_baseline(prob) if (world == 1 and not args.no_cpu_baseline) else None
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_s / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "parallelism": f"replicas x{world}",
+                       "step": "one outer power iteration: source, sweep, flux/k/residual update",
+                       "integrations_per_step": integ, "segments3d": info["segments3d"],
+                       "l2": "flushed between timed steps (256 MiB write outside the events)",
+                       "k_after_steps": res["k"]},
+            "roofline": roof, "clocks": clocks, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 6 * args.steps}
+    print(json.dumps(line), flush=True)
+
+
+def run_profile_driver(args):
+    """Untimed driver for ncu captures: builds the workload's tracks, runs 3
+    outer iterations, then 2 more (the 4th and 5th sweeps are the ones a
+    capture with -s 3 selects)."""
+    import synth
+    from paper_2503_17743_gb300 import Geometry, Tracks, track_params
+    prob = synth.workload(args.workload)
+    tr = Tracks(Geometry(prob), track_params(prob, preload_budget_bytes=args.budget,
+                                             groups_per_lane=args.gpl))
+    tr.iterate(3, use_graph=False)
+    r = tr.iterate(2, use_graph=False)
+    print(json.dumps({"info": tr.info, "ms_per_iteration": r["seconds"] * 1e3 / 2}), flush=True)
+    tr.close()
+
+
+def golden_k():
+    path = os.path.join(ROOT, "tests", "golden", "oracle_k.json")
+    try:
+        return json.load(open(path))[WORKLOAD]["k"]
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-runs", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="untimed 3 + 2 iterations (driver of the ncu captures)")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--budget", type=int, default=-1, help="preload budget bytes (--profile)")
+    ap.add_argument("--gpl", type=int, default=0, help="groups per lane (--profile)")
+    args = ap.parse_args()
+    if args.profile:
+        run_profile_driver(args)
+        return
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -108,7 +108,9 @@ typedef struct {
  *   tally_mode         MOC_TALLY_*
  *   block_threads      threads per block of the sweep (0 = tuned default)
  *   blocks_per_sm      resident sweep blocks per SM (0 = occupancy maximum)
- *   device             CUDA device ordinal */
+ *   device             CUDA device ordinal
+ *   groups_per_lane    energy groups one thread carries along a track, 1 or
+ *                      2 (FP32 sweeps only; 0 = tuned default) */
 typedef struct {
     int32_t n_azim, n_polar;
     double radial_spacing, axial_spacing;
@@ -118,6 +120,7 @@ typedef struct {
     int32_t block_threads;
     int32_t blocks_per_sm;
     int32_t device;
+    int32_t groups_per_lane;
 } moc_track_params;
 
 /* Stopping rule of a solve: |k_n - k_(n-1)| < tol_k (eigenvalue problems
@@ -199,6 +202,19 @@ int moc_reset(moc_tracks *tracks);
  * the current state; eigenvalue or fixed-source by the geometry. */
 int moc_iterate(moc_tracks *tracks, int32_t n, int32_t use_graph, moc_result *res);
 
+/* Non-blocking pieces of one outer iteration, enqueued on `stream` (NULL: the
+ * handle's stream) in this order: the source update (moc_update_source with
+ * the device-resident k), one sweep (Eq. 3 / Eq. 4 tallies, boundary fluxes
+ * advance one Jacobi step), and the flux, k and residual update (FP64
+ * reductions; the scalars are copied to a pinned host mirror).  They return
+ * after enqueueing; moc_read_result synchronises `stream` and fills `res`
+ * (seconds = 0, iterations = outer iterations so far, integrations = those of
+ * that many sweeps).  Errors: MOC_ERR_INVALID_ARG for NULL, MOC_ERR_CUDA. */
+int moc_enqueue_source(moc_tracks *tracks, void *stream);
+int moc_enqueue_sweep(moc_tracks *tracks, void *stream);
+int moc_enqueue_update(moc_tracks *tracks, void *stream);
+int moc_read_result(moc_tracks *tracks, void *stream, moc_result *res);
+
 /* Copy the normalised scalar flux [n_fsr*G] (FP64, host) and k. */
 int moc_get_flux(moc_tracks *tracks, double *phi, double *k);
 
@@ -214,8 +230,9 @@ int moc_get_volumes(moc_tracks *tracks, double *volumes);
  *   8 preloaded stacks, 9 device bytes held, 10 axial lattice cells Nz,
  *   11 lattice cells per layer, 12 sweep blocks, 13 sweep threads per block,
  *   14 tally mode in use, 15 precision, 16 sweep shared memory bytes per block,
- *   17 shared tile entries, 18 lanes per track (groups, padded), 19 most
- *   segments on one track */
+ *   17 shared tile entries, 18 lanes per track, 19 most segments on one
+ *   track, 20 bytes copied host to device while generating, 21 energy
+ *   groups per lane */
 int moc_tracks_info(const moc_tracks *tracks, int64_t *out, int32_t n);
 
 /* 3D segments of z-stack (t, p) as the device generator produces them

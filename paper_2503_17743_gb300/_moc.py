@@ -50,7 +50,8 @@ class moc_track_params(C.Structure):
     _fields_ = [("n_azim", C.c_int32), ("n_polar", C.c_int32), ("radial_spacing", C.c_double),
                 ("axial_spacing", C.c_double), ("precision", C.c_int32),
                 ("preload_budget_bytes", C.c_int64), ("tally_mode", C.c_int32),
-                ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("device", C.c_int32)]
+                ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("device", C.c_int32),
+                ("groups_per_lane", C.c_int32)]
 
 
 class moc_solve_params(C.Structure):
@@ -94,6 +95,10 @@ SIGNATURES = {
     "moc_track_psi": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.c_int32, f64p,
                                 C.c_int32]),
     "moc_sweep_from_source": (C.c_int, [C.c_void_p, f64p, f64p, f64p]),
+    "moc_enqueue_source": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "moc_enqueue_sweep": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "moc_enqueue_update": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "moc_read_result": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(moc_result)]),
 }
 
 _lib = None
@@ -178,7 +183,7 @@ class Geometry:
 
 
 def track_params(prob, precision=MOC_FP32, preload_budget_bytes=-1, tally_mode=MOC_TALLY_AUTO,
-                 block_threads=0, blocks_per_sm=0, device=0):
+                 block_threads=0, blocks_per_sm=0, device=0, groups_per_lane=0):
     p = moc_track_params()
     p.n_azim, p.n_polar = prob.n_azim, prob.n_polar
     p.radial_spacing, p.axial_spacing = prob.radial_spacing, prob.axial_spacing
@@ -188,13 +193,15 @@ def track_params(prob, precision=MOC_FP32, preload_budget_bytes=-1, tally_mode=M
     p.block_threads = block_threads
     p.blocks_per_sm = blocks_per_sm
     p.device = device
+    p.groups_per_lane = groups_per_lane
     return p
 
 
 INFO_KEYS = ["n_fsr", "groups", "tracks2d", "stacks", "tracks3d", "segments3d",
              "integrations_per_sweep", "stored_segments", "preloaded_stacks", "device_bytes",
              "n_z", "cells_per_layer", "sweep_blocks", "sweep_threads", "tally_mode", "precision",
-             "sweep_smem_bytes", "tile_entries", "lanes_per_track", "max_segments_per_track"]
+             "sweep_smem_bytes", "tile_entries", "lanes_per_track", "max_segments_per_track",
+             "h2d_bytes", "groups_per_lane"]
 
 
 class Tracks:
@@ -234,6 +241,20 @@ class Tracks:
 
     def reset(self):
         _check(load().moc_reset(self._h))
+
+    def enqueue_source(self, stream=None):
+        _check(load().moc_enqueue_source(self._h, stream))
+
+    def enqueue_sweep(self, stream=None):
+        _check(load().moc_enqueue_sweep(self._h, stream))
+
+    def enqueue_update(self, stream=None):
+        _check(load().moc_enqueue_update(self._h, stream))
+
+    def read_result(self, stream=None):
+        r = moc_result()
+        _check(load().moc_read_result(self._h, stream, C.byref(r)))
+        return r.as_dict()
 
     def iterate(self, n, use_graph=True):
         r = moc_result()

@@ -50,8 +50,10 @@ struct moc_tracks {
     int nb_max = 0;
     double integrations = 0;    // per sweep
     size_t bytes = 0;
+    size_t h2d = 0;             // bytes copied from host arrays while generating
     // sweep launch
     int tally_smem = 0;
+    int gpl = 1;                // energy groups per lane
     int tile_cap = 0;
     int block = 256;
     int grid = 0;
@@ -96,6 +98,7 @@ template <typename T>
 cudaError_t upload(moc_tracks *h, DevBuf &b, const std::vector<T> &v) {
     cudaError_t e = dalloc(h, b, v.size() * sizeof(T));
     if (e != cudaSuccess || v.empty()) return e;
+    h->h2d += v.size() * sizeof(T);
     return cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream);
 }
 
@@ -157,7 +160,7 @@ cudaError_t enqueue_sweep(moc_tracks *h, cudaStream_t s, int cur) {
     if (e != cudaSuccess) return e;
     const void *pin = h->has_psi ? h->d_psi[cur].p : nullptr;
     void *pout = h->has_psi ? h->d_psi[1 - cur].p : nullptr;
-    return launch_sweep(h->precision, h->tally_smem, h->dl, h->ds, (const int32_t *)h->d_order.p,
+    return launch_sweep(h->precision, h->tally_smem, h->gpl, h->dl, h->ds, (const int32_t *)h->d_order.p,
                         (int32_t)h->order.size(), h->tile_cap, pin, pout, h->grid, h->block, h->smem, s);
 }
 
@@ -227,8 +230,12 @@ int run_iterations(moc_tracks *h, int n, bool stop_on_conv, bool graph, moc_resu
         else TRY(enqueue_iteration(h, h->stream, h->cur), "iteration");
         if (h->has_psi) h->cur = 1 - h->cur;
         ++it;
-        TRY(cudaStreamSynchronize(h->stream), "iteration");
-        if (stop_on_conv && h->h_scal[SC_CONV] != 0.0) break;
+        // the convergence test needs this iteration's scalars on the host;
+        // a fixed count only synchronises once at the end
+        if (stop_on_conv) {
+            TRY(cudaStreamSynchronize(h->stream), "iteration");
+            if (h->h_scal[SC_CONV] != 0.0) break;
+        }
     }
     TRY(cudaEventRecord(e1, h->stream), "event");
     TRY(cudaEventSynchronize(e1), "event");
@@ -333,9 +340,15 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     // tally mode: a shared tile of every (2D segment, layer) row of one unit
     // when it fits
     h->tile_cap = h->nb_max * geo.nl;
+    if (prm->groups_per_lane < 0 || prm->groups_per_lane > 2 ||
+        (prm->groups_per_lane == 2 && h->precision == MOC_FP64)) {
+        moc_set_error("groups_per_lane must be 0, 1 or 2 (2 for FP32 sweeps only)");
+        return MOC_ERR_INVALID_ARG;
+    }
+    h->gpl = prm->groups_per_lane > 0 ? prm->groups_per_lane : sweep_default_gpl(h->precision, G);
     {
         int mode = prm->tally_mode;
-        const size_t smem_tile = sweep_smem_bytes(h->precision, 1, geo.M, G, h->tile_cap);
+        const size_t smem_tile = sweep_smem_bytes(h->precision, 1, geo.M, G, h->gpl, h->tile_cap);
         const bool fits = smem_tile <= 200 * 1024;
         if (mode == MOC_TALLY_AUTO) mode = (fits && smem_tile <= 100 * 1024) ? MOC_TALLY_SHARED : MOC_TALLY_GLOBAL;
         if (mode == MOC_TALLY_SHARED && !fits) mode = MOC_TALLY_GLOBAL;
@@ -431,7 +444,9 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
             for (int r = 0; r < std::min(cpl, L.desc[s].n_trk); ++r) {
                 const int64_t q = tpl_first[s] + r;
                 need += tcnt[q] * rec_bytes + (int64_t)(tnlay[q] + 1) * 4 + 20;
-                ok = ok && tlmin[q] > -30000 && tlmin[q] + tnlay[q] < 30000;
+                // stored keys hold b * NL and the template layer in 16 bits each
+                ok = ok && tlmin[q] > -30000 && tlmin[q] + tnlay[q] < 30000 &&
+                     (int64_t)L.desc[s].nb * geo.nl < 65536;
             }
         }
         if (!ok || (budget >= 0 && used + need > budget)) {
@@ -538,10 +553,10 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     TRY(upload(h.get(), h->d_order, h->order), "upload");
     fill_views(h.get());
     // sweep launch shape (tally mode chosen above)
-    h->smem = sweep_smem_bytes(h->precision, h->tally_smem, geo.M, G, h->tile_cap);
+    h->smem = sweep_smem_bytes(h->precision, h->tally_smem, geo.M, G, h->gpl, h->tile_cap);
     h->block = prm->block_threads > 0 ? std::max(32, std::min(prm->block_threads, 256) / 32 * 32) : 256;
     int bps = 0;
-    TRY(sweep_occupancy(h->precision, h->tally_smem, G, h->block, h->smem, &bps), "occupancy");
+    TRY(sweep_occupancy(h->precision, h->tally_smem, G, h->gpl, h->block, h->smem, &bps), "occupancy");
     if (bps < 1) { moc_set_error("sweep kernel does not fit on an SM"); return MOC_ERR_UNSUPPORTED; }
     if (prm->blocks_per_sm > 0) bps = std::min(bps, prm->blocks_per_sm);
     h->grid = std::max(1, std::min<int>(h->sms * bps, (int)std::min<int64_t>(ns, 1 << 30)));
@@ -584,6 +599,41 @@ extern "C" int moc_sweep(moc_tracks *h, void *stream) {
     TRY(enqueue_finalize(h, s), "finalize");
     TRY(cudaMemcpyAsync(h->h_scal, h->d_scal.p, SC_COUNT * 8, cudaMemcpyDeviceToHost, s), "scalars");
     TRY(cudaStreamSynchronize(s), "sweep");
+    return MOC_OK;
+}
+
+extern "C" int moc_enqueue_source(moc_tracks *h, void *stream) {
+    if (!h) { moc_set_error("NULL handle"); return MOC_ERR_INVALID_ARG; }
+    TRY(cudaSetDevice(h->device), "cudaSetDevice");
+    cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+    TRY(launch_source(h->precision, h->dl, h->ds, h->geom.nfsr, h->red_grid, s), "source");
+    return MOC_OK;
+}
+
+extern "C" int moc_enqueue_sweep(moc_tracks *h, void *stream) {
+    if (!h) { moc_set_error("NULL handle"); return MOC_ERR_INVALID_ARG; }
+    TRY(cudaSetDevice(h->device), "cudaSetDevice");
+    cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+    TRY(enqueue_sweep(h, s, h->cur), "sweep");
+    if (h->has_psi) h->cur = 1 - h->cur;
+    return MOC_OK;
+}
+
+extern "C" int moc_enqueue_update(moc_tracks *h, void *stream) {
+    if (!h) { moc_set_error("NULL handle"); return MOC_ERR_INVALID_ARG; }
+    TRY(cudaSetDevice(h->device), "cudaSetDevice");
+    cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+    TRY(enqueue_finalize(h, s), "finalize");
+    TRY(cudaMemcpyAsync(h->h_scal, h->d_scal.p, SC_COUNT * 8, cudaMemcpyDeviceToHost, s), "scalars");
+    return MOC_OK;
+}
+
+extern "C" int moc_read_result(moc_tracks *h, void *stream, moc_result *res) {
+    if (!h || !res) { moc_set_error("NULL argument"); return MOC_ERR_INVALID_ARG; }
+    TRY(cudaSetDevice(h->device), "cudaSetDevice");
+    cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+    TRY(cudaStreamSynchronize(s), "synchronize");
+    fill_result(h, res, 0.0, (int)h->h_scal[SC_ITER]);
     return MOC_OK;
 }
 
@@ -665,13 +715,13 @@ extern "C" int moc_get_volumes(moc_tracks *h, double *v) {
 
 extern "C" int moc_tracks_info(const moc_tracks *h, int64_t *out, int32_t n) {
     if (!h || !out) { moc_set_error("NULL argument"); return MOC_ERR_INVALID_ARG; }
-    const int64_t v[20] = {h->geom.nfsr, h->geom.G, h->L.nt, 2 * h->L.n_stacks, 2 * h->L.n_gtrk,
+    const int64_t v[22] = {h->geom.nfsr, h->geom.G, h->L.nt, 2 * h->L.n_stacks, 2 * h->L.n_gtrk,
                            h->n_segments3d, (int64_t)h->integrations, h->n_stored, h->n_exp_stacks,
                            (int64_t)h->bytes, h->L.Nz, h->L.cpl, h->grid, h->block,
                            h->tally_smem ? MOC_TALLY_SHARED : MOC_TALLY_GLOBAL, h->precision,
-                           (int64_t)h->smem, h->tile_cap, sweep_lanes_per_track(h->geom.G),
-                           h->max_nseg};
-    for (int i = 0; i < n && i < 20; ++i) out[i] = v[i];
+                           (int64_t)h->smem, h->tile_cap, sweep_lanes_per_track(h->geom.G, h->gpl),
+                           h->max_nseg, (int64_t)h->h2d, h->gpl};
+    for (int i = 0; i < n && i < 22; ++i) out[i] = v[i];
     return MOC_OK;
 }
 

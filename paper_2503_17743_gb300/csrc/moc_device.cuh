@@ -285,4 +285,6 @@ __device__ __forceinline__ real tpl_len(const DevLayout &dl, const StackDesc &d,
     return (real)dl.cpl * lam;                                                              // Eq. 11
 }
 
-constexpr int kTplLayerBias = 32768;  // template layers are stored as L + bias in 16 bits
+// A stored template piece: key = (b * NL) << 16 | (L_t + bias), with b the 2D
+// segment and L_t the template layer (16 bits each).
+constexpr int kTplLayerBias = 32768;

@@ -17,7 +17,6 @@
 
 namespace {
 
-constexpr float kLog2e = 1.4426950408889634f;
 
 __device__ __forceinline__ double block_sum(double v, double *sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -100,7 +99,7 @@ __global__ void k_tpl_write(DevLayout dl, const int32_t *exp_stacks, int64_t n_e
                 for (int L = tr.La; L <= tr.Le; ++L) {
                     while (x <= L - Lmin && x <= nL) lidx[lb + x++] = pos;
                     SegRec<real> rec{};
-                    rec.key = ((uint32_t)b << 16) | (uint32_t)(L + kTplLayerBias);
+                    rec.key = ((uint32_t)(b * dl.NL) << 16) | (uint32_t)(L + kTplLayerBias);
                     rec.len = tpl_len(dl, d, b, tr, L);
                     out[pos++] = rec;
                 }

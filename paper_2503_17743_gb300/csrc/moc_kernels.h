@@ -19,13 +19,15 @@ cudaError_t launch_volumes(int precision, const DevLayout &dl, int64_t n_stacks,
                            int grid, cudaStream_t s);
 cudaError_t launch_stack_segments(int precision, const DevLayout &dl, int64_t stack,
                                   const int64_t *offs, int32_t *fsr, double *len, cudaStream_t s);
-// the sweep (moc_sweep.cu)
-int sweep_lanes_per_track(int G);
-size_t sweep_smem_bytes(int precision, int tally_smem, int M, int G, int cap);
-cudaError_t launch_sweep(int precision, int tally_smem, const DevLayout &dl, const DevState &st,
-                         const int32_t *order, int32_t n_work, int32_t cap, const void *psi_in,
-                         void *psi_out, int grid, int block, size_t smem, cudaStream_t s);
-cudaError_t sweep_occupancy(int precision, int tally_smem, int G, int block, size_t smem,
+// the sweep (moc_sweep.cu); gpl = energy groups per lane (1 or 2, FP32 only)
+int sweep_default_gpl(int precision, int G);
+int sweep_lanes_per_track(int G, int gpl);
+size_t sweep_smem_bytes(int precision, int tally_smem, int M, int G, int gpl, int cap);
+cudaError_t launch_sweep(int precision, int tally_smem, int gpl, const DevLayout &dl,
+                         const DevState &st, const int32_t *order, int32_t n_work, int32_t cap,
+                         const void *psi_in, void *psi_out, int grid, int block, size_t smem,
+                         cudaStream_t s);
+cudaError_t sweep_occupancy(int precision, int tally_smem, int G, int gpl, int block, size_t smem,
                             int *blocks_per_sm);
 cudaError_t launch_source(int precision, const DevLayout &dl, const DevState &st, int32_t nfsr,
                           int grid, cudaStream_t s);
