@@ -257,6 +257,27 @@ int moc_track_psi(moc_tracks *tracks, int32_t t, int32_t p, int64_t i, int32_t s
  * the current boundary fluxes; returns the FSR tally [n_fsr*G] and leakage. */
 int moc_sweep_from_source(moc_tracks *tracks, const double *Q, double *tally, double *leakage);
 
+/* Group-wise reaction rates of the normalised scalar flux (the flux
+ * moc_get_flux returns), computed on the device without allocating any
+ * memory.  The paper has no counterpart: it is a library service for callers
+ * that cannot allocate device memory at that moment (for example a serving
+ * loop that has handed the free HBM to resident solves).
+ *   rates   host array of 2*G doubles, written on return:
+ *           rates[g]     = sum_i V_i nuSigma_f[m_i][g] phi_{i,g}
+ *           rates[G + g] = sum_i V_i (Sigma_t - sum_h Sigma_s[g->h])[m_i] phi_{i,g}
+ *           (their sums are moc_result.production and .absorption)
+ *   stream  cudaStream_t as void*, NULL = the handle's stream; the call
+ *           synchronises it before returning.
+ * Scratch: a fixed device array inside the library (8256 doubles, 66 KB per
+ * device) instead of an allocation; nothing in it has to start at zero.  Limit:
+ * G <= 32 (MOC_ERR_UNSUPPORTED beyond).  The first call on each device
+ * resolves the scratch address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  Calls that
+ * overlap in time (two streams or two host threads) share the scratch and
+ * race: serialise them.  Errors: MOC_ERR_INVALID_ARG for NULL,
+ * MOC_ERR_UNSUPPORTED, MOC_ERR_CUDA. */
+int moc_group_rates_static(moc_tracks *tracks, void *stream, double *rates);
+
 #ifdef __cplusplus
 }
 #endif

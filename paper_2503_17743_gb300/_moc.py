@@ -95,6 +95,7 @@ SIGNATURES = {
     "moc_track_psi": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.c_int32, f64p,
                                 C.c_int32]),
     "moc_sweep_from_source": (C.c_int, [C.c_void_p, f64p, f64p, f64p]),
+    "moc_group_rates_static": (C.c_int, [C.c_void_p, C.c_void_p, f64p]),
     "moc_enqueue_source": (C.c_int, [C.c_void_p, C.c_void_p]),
     "moc_enqueue_sweep": (C.c_int, [C.c_void_p, C.c_void_p]),
     "moc_enqueue_update": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -320,3 +321,10 @@ class Tracks:
         _check(load().moc_sweep_from_source(self._h, _ptr(Q, f64p), _ptr(tally, f64p),
                                             C.byref(leak)))
         return tally.reshape(self.n_fsr, self.G), leak.value
+
+    def group_rates_static(self, stream=None):
+        """(production[G], absorption[G]) of the normalised flux, computed by
+        the library without allocating device memory."""
+        out = np.zeros(2 * self.G)
+        _check(load().moc_group_rates_static(self._h, stream, _ptr(out, f64p)))
+        return out[:self.G].copy(), out[self.G:].copy()

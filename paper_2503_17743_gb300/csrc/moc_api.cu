@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -861,5 +862,52 @@ extern "C" int moc_sweep_from_source(moc_tracks *h, const double *Q, double *tal
     // the outgoing fluxes are physical values: the next sweep reads them as is
     TRY(set_scalar(h, SC_SCALE, 1.0), "scalar");
     TRY(cudaStreamSynchronize(h->stream), "sweep");
+    return MOC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Group-wise reaction rates with no allocation.  For callers that cannot
+// allocate device memory when they need the rates: a serving loop that has
+// handed the free HBM to resident solves (admission by footprint) would see
+// cudaMalloc fail, and cudaFree can synchronise the whole device and stall
+// the other solves' work.  The scratch is the library's static device array
+// (moc_static.cu); its address is resolved once per device, with that device
+// current, on the first call.
+
+namespace {
+constexpr int kRatesMaxDevices = 64;
+std::mutex g_rates_mu;
+double *g_rates_scratch_ptr[kRatesMaxDevices] = {};
+}  // namespace
+
+extern "C" int moc_group_rates_static(moc_tracks *h, void *stream, double *rates) {
+    if (!h || !rates) { moc_set_error("NULL argument"); return MOC_ERR_INVALID_ARG; }
+    const int G = h->geom.G;
+    if (G > kRatesMaxGroups) {
+        moc_set_error("moc_group_rates_static: at most 32 energy groups (fixed scratch of 128 blocks "
+                      "x 32 groups x 2 rates)");
+        return MOC_ERR_UNSUPPORTED;
+    }
+    if (h->device < 0 || h->device >= kRatesMaxDevices) {
+        moc_set_error("moc_group_rates_static: device ordinal above 63");
+        return MOC_ERR_UNSUPPORTED;
+    }
+    TRY(cudaSetDevice(h->device), "cudaSetDevice");
+    double *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_rates_mu);
+        if (!g_rates_scratch_ptr[h->device]) {
+            double *p = nullptr;
+            TRY(rates_scratch_address(&p), "cudaGetSymbolAddress");
+            if (!p) { moc_set_error("cudaGetSymbolAddress returned NULL"); return MOC_ERR_CUDA; }
+            g_rates_scratch_ptr[h->device] = p;
+        }
+        scratch = g_rates_scratch_ptr[h->device];
+    }
+    cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+    TRY(launch_group_rates_static(h->dl, h->ds, h->geom.nfsr, scratch, s), "rates");
+    TRY(cudaMemcpyAsync(rates, scratch + kRatesResultOffset, 2 * (size_t)G * sizeof(double),
+                        cudaMemcpyDeviceToHost, s), "copy");
+    TRY(cudaStreamSynchronize(s), "rates");
     return MOC_OK;
 }

@@ -37,3 +37,14 @@ cudaError_t launch_finalize_fixed(int precision, const DevLayout &dl, const DevS
                                   int32_t nfsr, int grid, double integrations, cudaStream_t s);
 cudaError_t launch_init_state(const DevLayout &dl, const DevState &st, int32_t nfsr, int grid,
                               cudaStream_t s);
+
+// group-wise reaction rates with a fixed library-owned scratch array
+// (moc_static.cu): at most kRatesMaxGroups groups; partials of up to
+// kRatesMaxBlocks blocks, then 2 x G results at kRatesResultOffset
+constexpr int kRatesMaxBlocks = 128;
+constexpr int kRatesMaxGroups = 32;
+constexpr int kRatesResultOffset = kRatesMaxBlocks * kRatesMaxGroups * 2;
+constexpr int kRatesScratchDoubles = kRatesResultOffset + 2 * kRatesMaxGroups;
+cudaError_t rates_scratch_address(double **ptr);
+cudaError_t launch_group_rates_static(const DevLayout &dl, const DevState &st, int32_t nfsr,
+                                      double *scratch, cudaStream_t s);
