@@ -109,8 +109,8 @@ typedef struct {
  *   block_threads      threads per block of the sweep (0 = tuned default)
  *   blocks_per_sm      resident sweep blocks per SM (0 = occupancy maximum)
  *   device             CUDA device ordinal
- *   groups_per_lane    energy groups one thread carries along a track, 1 or
- *                      2 (FP32 sweeps only; 0 = tuned default) */
+ *   groups_per_lane    energy groups one thread carries along a track: 1, 2
+ *                      or 4 (2 and 4 for FP32 sweeps only; 0 = tuned default) */
 typedef struct {
     int32_t n_azim, n_polar;
     double radial_spacing, axial_spacing;

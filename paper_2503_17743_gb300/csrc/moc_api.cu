@@ -35,7 +35,7 @@ struct moc_tracks {
     // device buffers
     DevBuf d_desc, d_zn, d_zf, d_zf64, d_reg2d, d_len2d, d_len2d64, d_segs, d_fsr_mat, d_order;
     DevBuf d_tpl_off, d_tpl_loff, d_tpl_lmin, d_tpl_lidx;
-    DevBuf d_dst;
+    DevBuf d_dst, d_perm;
     DevBuf d_phi, d_qr, d_tally, d_vol, d_psi[2], d_fiss, d_fiss_old, d_partial, d_scal, d_counter;
     DevBuf d_sigt, d_sigt64, d_sigs64, d_nsf64, d_chi64, d_src64;
     double *h_scal = nullptr;  // pinned mirror of the device scalars
@@ -55,6 +55,7 @@ struct moc_tracks {
     // sweep launch
     int tally_smem = 0;
     int gpl = 1;                // energy groups per lane
+    int tally_bits = 0;         // fixed-point bits of the FP32 shared tally
     int tile_cap = 0;
     int block = 256;
     int grid = 0;
@@ -121,6 +122,7 @@ void fill_views(moc_tracks *h) {
     dl.segs = h->d_segs.p;
     dl.fsr_mat = (const int32_t *)h->d_fsr_mat.p;
     dl.dst = (const int64_t *)h->d_dst.p;
+    dl.perm = (const int32_t *)h->d_perm.p;
     dl.Ph = h->L.Ph;
     dl.Nz = h->L.Nz;
     dl.cpl = h->L.cpl;
@@ -130,6 +132,7 @@ void fill_views(moc_tracks *h) {
     dl.bc_zmin = h->geom.bc[FACE_ZMIN];
     dl.bc_zmax = h->geom.bc[FACE_ZMAX];
     dl.n_slots = h->L.n_gtrk * 4;
+    dl.tally_bits = h->tally_bits;
     DevState &s = h->ds;
     s.phi = (double *)h->d_phi.p;
     s.qr = h->d_qr.p;
@@ -217,6 +220,16 @@ void fill_result(moc_tracks *h, moc_result *r, double seconds, int iters) {
     r->converged = s[SC_CONV] != 0.0 ? 1 : 0;
 }
 
+// the sweep sets SC_ERR when a shared tally update gave up after its retry
+// limit (never expected: it needs that many consecutive lost races)
+int check_sweep_flag(moc_tracks *h) {
+    if (h->h_scal[SC_ERR] != 0.0) {
+        moc_set_error("sweep: a shared tally update exceeded its retry limit; results are invalid");
+        return MOC_ERR_CUDA;
+    }
+    return MOC_OK;
+}
+
 int run_iterations(moc_tracks *h, int n, bool stop_on_conv, bool graph, moc_result *res) {
     TRY(cudaSetDevice(h->device), "cudaSetDevice");
     if (graph) TRY(build_graphs(h), "graph capture");
@@ -246,7 +259,7 @@ int run_iterations(moc_tracks *h, int n, bool stop_on_conv, bool graph, moc_resu
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     fill_result(h, res, seconds_total, it);
-    return MOC_OK;
+    return check_sweep_flag(h);
 }
 
 int init_state(moc_tracks *h) {
@@ -341,9 +354,9 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     // tally mode: a shared tile of every (2D segment, layer) row of one unit
     // when it fits
     h->tile_cap = h->nb_max * geo.nl;
-    if (prm->groups_per_lane < 0 || prm->groups_per_lane > 2 ||
-        (prm->groups_per_lane == 2 && h->precision == MOC_FP64)) {
-        moc_set_error("groups_per_lane must be 0, 1 or 2 (2 for FP32 sweeps only)");
+    if (prm->groups_per_lane < 0 || prm->groups_per_lane > 4 || prm->groups_per_lane == 3 ||
+        (prm->groups_per_lane > 1 && h->precision == MOC_FP64)) {
+        moc_set_error("groups_per_lane must be 0, 1, 2 or 4 (2 and 4 for FP32 sweeps only)");
         return MOC_ERR_INVALID_ARG;
     }
     h->gpl = prm->groups_per_lane > 0 ? prm->groups_per_lane : sweep_default_gpl(h->precision, G);
@@ -354,6 +367,32 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
         if (mode == MOC_TALLY_AUTO) mode = (fits && smem_tile <= 100 * 1024) ? MOC_TALLY_SHARED : MOC_TALLY_GLOBAL;
         if (mode == MOC_TALLY_SHARED && !fits) mode = MOC_TALLY_GLOBAL;
         h->tally_smem = mode == MOC_TALLY_SHARED ? 1 : 0;
+    }
+    // FP32 shared tally in fixed point: each contribution becomes an integer
+    // multiple of 2^-bits of its unit's bound and is added with a native
+    // integer atomic, so one row of one unit must stay below 2^30.  Pieces
+    // that reach one row of one unit: per polar stack, 2 senses x 2 frames x
+    // the tracks crossing one layer inside one 2D segment (at most cpl plus
+    // the segment's lattice span plus 2).
+    if (h->tally_smem && h->precision == MOC_FP32) {
+        int64_t nmax = 1;
+        for (int t = 0; t < L.nt; ++t) {
+            const int nb = L.seg_off[t + 1] - L.seg_off[t];
+            int64_t n = 0;
+            for (int ph = 0; ph < L.Ph; ++ph) {
+                const int32_t z = L.zoff[(size_t)t * L.Ph + ph];
+                double span = 0.0;
+                for (int b = 0; b < nb; ++b)
+                    span = std::max(span, (L.zn[z + b + 1] + (double)L.zf[z + b + 1]) -
+                                              (L.zn[z + b] + (double)L.zf[z + b]));
+                n += 4 * (L.cpl + (int64_t)std::ceil(span) + 2);
+            }
+            nmax = std::max(nmax, n);
+        }
+        int bits = 21;
+        while (bits > 0 && (nmax << bits) >= ((int64_t)1 << 30)) --bits;
+        if (bits < 12) h->tally_smem = 0;  // too many pieces per row: FP64 global tally instead
+        else h->tally_bits = bits;
     }
     TRY(cudaSetDevice(h->device), "cudaSetDevice");
     TRY(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "stream");
@@ -375,17 +414,41 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     fill_views(h.get());
     // segment counts per stack
     const int64_t ns = L.n_stacks;
-    DevBuf d_nseg, d_max;
+    DevBuf d_nseg, d_max, d_tseg;
     TRY(dalloc(h.get(), d_nseg, ns * sizeof(int64_t)), "alloc");
     TRY(dalloc(h.get(), d_max, sizeof(int32_t)), "alloc");
+    TRY(dalloc(h.get(), d_tseg, std::max<int64_t>(1, L.n_gtrk) * sizeof(int32_t)), "alloc");
     TRY(cudaMemsetAsync(d_max.p, 0, sizeof(int32_t), h->stream), "memset");
     const int lgrid = (int)std::max<int64_t>(1, std::min<int64_t>(ns, (int64_t)h->sms * 16));
-    TRY(launch_count_stacks(h->dl, ns, (int64_t *)d_nseg.p, (int32_t *)d_max.p, lgrid, h->stream), "count");
+    TRY(launch_count_stacks(h->dl, ns, (int64_t *)d_nseg.p, (int32_t *)d_max.p, (int32_t *)d_tseg.p,
+                            lgrid, h->stream), "count");
     h->stack_nseg.resize(ns);
+    std::vector<int32_t> tseg(L.n_gtrk);
     TRY(cudaMemcpyAsync(h->stack_nseg.data(), d_nseg.p, ns * sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream), "copy");
     TRY(cudaMemcpyAsync(&h->max_nseg, d_max.p, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream), "copy");
+    if (L.n_gtrk > 0)
+        TRY(cudaMemcpyAsync(tseg.data(), d_tseg.p, L.n_gtrk * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream), "copy");
     TRY(cudaStreamSynchronize(h->stream), "count");
-    h->bytes -= d_nseg.n + d_max.n;
+    h->bytes -= d_nseg.n + d_max.n + d_tseg.n;
+    // sweep order inside each stack: by decreasing segment count, so that the
+    // tracks a warp sweeps side by side take the same number of steps; among
+    // equal counts class by class (tracks r, r + cpl, ... are whole-layer
+    // shifts of one another and rarely meet in the same FSR at the same step,
+    // so the shared tally updates of one warp seldom collide)
+    {
+        std::vector<int32_t> perm(L.n_gtrk);
+        for (int64_t s = 0; s < ns; ++s) {
+            const int64_t o = L.desc[s].trk_off;
+            const int n = L.desc[s].n_trk;
+            int32_t *q = perm.data() + o;
+            int32_t *p = q;
+            for (int r = 0; r < std::min(L.cpl, n); ++r)
+                for (int k = r; k < n; k += L.cpl) *p++ = k;
+            std::stable_sort(q, q + n, [&](int32_t a, int32_t b) { return tseg[o + a] > tseg[o + b]; });
+        }
+        TRY(upload(h.get(), h->d_perm, perm), "upload");
+        fill_views(h.get());
+    }
     int64_t segs_up = 0;
     for (auto v : h->stack_nseg) segs_up += v;
     h->n_segments3d = 2 * segs_up;
@@ -445,9 +508,10 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
             for (int r = 0; r < std::min(cpl, L.desc[s].n_trk); ++r) {
                 const int64_t q = tpl_first[s] + r;
                 need += tcnt[q] * rec_bytes + (int64_t)(tnlay[q] + 1) * 4 + 20;
-                // stored keys hold b * NL and the template layer in 16 bits each
-                ok = ok && tlmin[q] > -30000 && tlmin[q] + tnlay[q] < 30000 &&
-                     (int64_t)L.desc[s].nb * geo.nl < 65536;
+                // stored keys hold the two frames' tile rows b*NL + L_t and
+                // b*NL + NL-1-L_t as signed 16-bit numbers
+                ok = ok && tlmin[q] > -2000 && tlmin[q] + tnlay[q] < 2000 &&
+                     (int64_t)(L.desc[s].nb + 1) * geo.nl + 2000 < 32768;
             }
         }
         if (!ok || (budget >= 0 && used + need > budget)) {
@@ -635,7 +699,7 @@ extern "C" int moc_read_result(moc_tracks *h, void *stream, moc_result *res) {
     cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
     TRY(cudaStreamSynchronize(s), "synchronize");
     fill_result(h, res, 0.0, (int)h->h_scal[SC_ITER]);
-    return MOC_OK;
+    return check_sweep_flag(h);
 }
 
 extern "C" int moc_iterate(moc_tracks *h, int32_t n, int32_t use_graph, moc_result *res) {
@@ -857,6 +921,7 @@ extern "C" int moc_sweep_from_source(moc_tracks *h, const double *Q, double *tal
     TRY(cudaMemcpyAsync(h->h_scal, h->d_scal.p, SC_COUNT * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
     TRY(cudaStreamSynchronize(h->stream), "sweep");
     if (leakage) *leakage = h->h_scal[SC_LEAK];
+    if (check_sweep_flag(h)) return MOC_ERR_CUDA;
     TRY(cudaMemsetAsync(h->d_tally.p, 0, n * 8, h->stream), "memset");
     TRY(set_scalar(h, SC_LEAK, 0.0), "scalar");
     // the outgoing fluxes are physical values: the next sweep reads them as is

@@ -24,8 +24,11 @@ struct DevLayout {
     const void *segs;        // template records, SegRec<real>
     const int32_t *fsr_mat;  // material of each FSR
     const int64_t *dst;      // [n_gtrk*4] link destination of every track direction, or null (all vacuum)
+    const int32_t *perm;     // [n_gtrk] per stack, its track indices by decreasing segment
+                             // count (ties: class by class, then by index)
     int32_t Nz, cpl, NL, G, M, Ph;
     int32_t bc_zmin, bc_zmax;
+    int32_t tally_bits;      // FP32 shared tally: fixed-point bits per unit bound (0: not used)
     int64_t n_slots;         // geometric tracks * 4 variants (bound of every link)
 };
 
@@ -61,6 +64,7 @@ enum ScalarSlot {
     SC_EIGEN,      // 1 for an eigenvalue problem
     SC_INTEG,      // integrations performed
     SC_LEAK_PREV,  // leakage of the latest completed sweep, normalised
+    SC_ERR,        // nonzero: a sweep dropped a tally update (contention limit)
     SC_COUNT = 16
 };
 
@@ -76,7 +80,7 @@ enum ScalarSlot {
 // `visit(b, layer, len)` is called for every segment in traversal order:
 // along the 2D track for sense 0, against it for sense 1.
 
-// A stored segment: key = (2D segment b << 16) | layer, and its length.
+// A stored template piece: key (see tpl_key) and its length.
 template <typename real>
 struct SegRec;
 template <>
@@ -285,6 +289,13 @@ __device__ __forceinline__ real tpl_len(const DevLayout &dl, const StackDesc &d,
     return (real)dl.cpl * lam;                                                              // Eq. 11
 }
 
-// A stored template piece: key = (b * NL) << 16 | (L_t + bias), with b the 2D
-// segment and L_t the template layer (16 bits each).
-constexpr int kTplLayerBias = 32768;
+// A stored template piece: key = the tile rows of the piece in both frames,
+// A = b * NL + L_t (upward) and B = b * NL + NL - 1 - L_t (mirrored), as
+// signed 16-bit numbers (A low, B high), with b the 2D segment and L_t the
+// template layer.  Track r + m cpl of the class meets the piece in rows A + m
+// and B - m.
+__host__ __device__ __forceinline__ uint32_t tpl_key(int A, int B) {
+    return (uint32_t)(uint16_t)(int16_t)A | ((uint32_t)(uint16_t)(int16_t)B << 16);
+}
+__device__ __forceinline__ int tpl_row_up(uint32_t key) { return (int)(int16_t)(key & 0xffffu); }
+__device__ __forceinline__ int tpl_row_down(uint32_t key) { return (int)key >> 16; }

@@ -35,7 +35,7 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 // layout kernels
 
 __global__ void k_count_stacks(DevLayout dl, int64_t n_stacks, int64_t *stack_nseg,
-                               int32_t *max_nseg) {
+                               int32_t *max_nseg, int32_t *trk_nseg) {
     __shared__ double sh[32];
     for (int64_t s = blockIdx.x; s < n_stacks; s += gridDim.x) {
         const StackDesc d = dl.desc[s];
@@ -43,6 +43,7 @@ __global__ void k_count_stacks(DevLayout dl, int64_t n_stacks, int64_t *stack_ns
         int mx = 0;
         for (int k = threadIdx.x; k < d.n_trk; k += blockDim.x) {
             int n = count_otf(dl, d, d.i_lo + k);
+            trk_nseg[d.trk_off + k] = n;
             acc += n;
             mx = max(mx, n);
         }
@@ -99,7 +100,7 @@ __global__ void k_tpl_write(DevLayout dl, const int32_t *exp_stacks, int64_t n_e
                 for (int L = tr.La; L <= tr.Le; ++L) {
                     while (x <= L - Lmin && x <= nL) lidx[lb + x++] = pos;
                     SegRec<real> rec{};
-                    rec.key = ((uint32_t)(b * dl.NL) << 16) | (uint32_t)(L + kTplLayerBias);
+                    rec.key = tpl_key(b * dl.NL + L, b * dl.NL + dl.NL - 1 - L);
                     rec.len = tpl_len(dl, d, b, tr, L);
                     out[pos++] = rec;
                 }
@@ -340,6 +341,7 @@ __global__ void k_init_finish(DevState st, int nblocks, int32_t nfsr) {
         s[SC_RES] = 0.0;
         s[SC_ITER] = 0.0;
         s[SC_CONV] = 0.0;
+        s[SC_ERR] = 0.0;
         s_scale = s[SC_SCALE];
     }
     __syncthreads();
@@ -358,8 +360,8 @@ __global__ void k_init_finish(DevState st, int nblocks, int32_t nfsr) {
     } while (0)
 
 cudaError_t launch_count_stacks(const DevLayout &dl, int64_t n_stacks, int64_t *stack_nseg,
-                                int32_t *max_nseg, int grid, cudaStream_t s) {
-    k_count_stacks<<<grid, 128, 0, s>>>(dl, n_stacks, stack_nseg, max_nseg);
+                                int32_t *max_nseg, int32_t *trk_nseg, int grid, cudaStream_t s) {
+    k_count_stacks<<<grid, 128, 0, s>>>(dl, n_stacks, stack_nseg, max_nseg, trk_nseg);
     return cudaGetLastError();
 }
 

@@ -5,8 +5,9 @@
 
 #include "moc_device.cuh"
 
+// segments per stack (stack_nseg), their maximum, and per geometric track (trk_nseg)
 cudaError_t launch_count_stacks(const DevLayout &dl, int64_t n_stacks, int64_t *stack_nseg,
-                                int32_t *max_nseg, int grid, cudaStream_t s);
+                                int32_t *max_nseg, int32_t *trk_nseg, int grid, cudaStream_t s);
 cudaError_t launch_tpl_count(const DevLayout &dl, const int32_t *exp_stacks, int64_t n_exp,
                              int64_t *cnt, int32_t *lmin, int32_t *nlay, int grid, cudaStream_t s);
 cudaError_t launch_tpl_write(int precision, const DevLayout &dl, const int32_t *exp_stacks,

@@ -6,26 +6,29 @@
 // are one track shifted up by one layer each (Eq. 5 with the layer planes on
 // the axial lattice), so a single segment template serves all of them: track
 // r + m cpl crosses the template pieces whose layer L_t + m lies in [0, NL).
+// The layer never decreases along an upward line, so those pieces are one
+// contiguous range of the template's records.
 //
-// A warp task is (polar stack, class r, block of SLOTS = 32/GL consecutive
-// tracks of the class, sense).  Slot j (GL lanes) carries track m + j; each lane
-// carries GPL energy groups, kept in GPL group planes of the shared rows.  Every
-// lane sweeps both frames: the upward track and the mirrored downward track
-// that shares its segments (layer NL-1-L).  For one plane the 32 lanes of a
-// warp touch 32 consecutive words (SLOTS consecutive rows x GL groups), so
-// their shared-memory accesses never collide on a bank.
+// A warp task is (polar stack, class r, block of SLOTS = 32/GL tracks m of the
+// class, sense).  Slot j (GL lanes) walks its own track's record range; each
+// lane carries GPL energy groups, kept in GPL group planes of the shared rows.
+// Every lane sweeps both frames: the upward track and the mirrored downward
+// track that shares its segments (layer NL-1-L).  Slots of one warp run the
+// same number of steps except where a track is clipped by the top or bottom
+// face, so nearly every lane does useful work.
 //
 // Shared tally (SMEM = true): per unit the block stages one row per
 // (2D segment, layer) FSR the unit crosses, holding (Qr, Sigma_t) for every
 // group, plus a zeroed tally row; pieces touch only shared memory and the rows
-// are flushed into the FP64 global tally once per unit.  A slot outside the
-// layer range works on a zero row in the same bank group as the row it would
-// have touched (Qr = Sigma_t = 0 leaves psi exactly unchanged and adds 0), so
-// pieces run without branches or bank conflicts.  Templates come from
-// the stored set (EXP, Sec. 4.2; four pieces at a time with the next four
-// records in flight) or are generated on the fly (OTF).  Without the shared
+// are flushed into the FP64 global tally once per unit.  Templates come from
+// the stored set (EXP, Sec. 4.2; four records at a time with the next four in
+// flight) or each track is generated on the fly (OTF).  Without the shared
 // tally (SMEM = false) pieces read Qr from global memory and add straight into
 // the FP64 global tally.
+//
+// psi is carried multiplied by the track weight W: with d = W (psi - Qr) the
+// attenuated change W (psi_in - psi_out) = d (1 - e^{-Sigma_t l}) is both the
+// tally contribution and the psi update (Eq. 3, Eq. 4).
 #include <climits>
 
 #include "moc_device.cuh"
@@ -60,9 +63,12 @@ __device__ __forceinline__ double attenuation<double>(double x) {
 }
 
 // per polar stack of the work unit, cached in shared memory
+// (the track weight and its inverse in both precisions: the sweep's hot path
+// does no FP64 arithmetic in FP32 mode)
 struct UnitStack {
     int64_t trk_off, tpl_base;
-    double W;
+    double W, invW;
+    float Wf, invWf;
     int32_t n_trk, i_lo, task_pre, pad;
 };
 constexpr int kMaxPh = 16;
@@ -120,35 +126,137 @@ struct TplIter {
 };
 
 
+// The (Qr, Sigma_t) pairs of a lane's GPL groups in one shared row, read at a
+// 32-bit shared-memory address with one vector load
+template <typename real, int GPL>
+struct RowLoadS;
+template <>
+struct RowLoadS<float, 1> {
+    static __device__ __forceinline__ void get(unsigned a, float (&q)[1], float (&s)[1]) {
+        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(q[0]), "=f"(s[0]) : "r"(a));
+    }
+};
+template <>
+struct RowLoadS<float, 2> {
+    static __device__ __forceinline__ void get(unsigned a, float (&q)[2], float (&s)[2]) {
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(q[0]), "=f"(s[0]), "=f"(q[1]), "=f"(s[1])
+                     : "r"(a));
+    }
+};
+template <>
+struct RowLoadS<float, 4> {
+    static __device__ __forceinline__ void get(unsigned a, float (&q)[4], float (&s)[4]) {
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(q[0]), "=f"(s[0]), "=f"(q[1]), "=f"(s[1])
+                     : "r"(a));
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(q[2]), "=f"(s[2]), "=f"(q[3]), "=f"(s[3])
+                     : "r"(a + 16u));
+    }
+};
+template <>
+struct RowLoadS<double, 1> {
+    static __device__ __forceinline__ void get(unsigned a, double (&q)[1], double (&s)[1]) {
+        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(q[0]), "=d"(s[0]) : "r"(a));
+    }
+};
+
+// fixed-point tally += v at a 32-bit shared-memory address (native integer add)
+__device__ __forceinline__ void shared_red_add(unsigned a, int v) {
+    asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
+// tally[0..GPL) += t on shared memory with one compare-and-swap of the whole
+// 32- or 64-bit word per attempt (floating-point adds on shared memory have no
+// single-instruction form).  A word is retried only when another lane changed
+// it in between; after kCasLimit attempts the update is dropped and *err set,
+// which the host reports as an error.
+constexpr int kCasLimit = 1 << 16;
+
+template <typename real, int GPL>
+struct TallyAdd;
+template <>
+struct TallyAdd<float, 1> {
+    static __device__ __forceinline__ void add(float *p, const float (&t)[1], double *err) {
+        unsigned *w = reinterpret_cast<unsigned *>(p);
+        unsigned old = *w;
+        for (int it = 0; it < kCasLimit; ++it) {
+            const unsigned nw = __float_as_uint(__uint_as_float(old) + t[0]);
+            const unsigned prev = atomicCAS(w, old, nw);
+            if (prev == old) return;
+            old = prev;
+        }
+        *err = 1.0;
+    }
+};
+template <>
+struct TallyAdd<float, 2> {
+    static __device__ __forceinline__ void add(float *p, const float (&t)[2], double *err) {
+        unsigned long long *w = reinterpret_cast<unsigned long long *>(p);
+        unsigned long long old = *w;
+        for (int it = 0; it < kCasLimit; ++it) {
+            const float lo = __uint_as_float((unsigned)old) + t[0];
+            const float hi = __uint_as_float((unsigned)(old >> 32)) + t[1];
+            const unsigned long long nw =
+                ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+            const unsigned long long prev = atomicCAS(w, old, nw);
+            if (prev == old) return;
+            old = prev;
+        }
+        *err = 1.0;
+    }
+};
+template <>
+struct TallyAdd<double, 1> {
+    static __device__ __forceinline__ void add(double *p, const double (&t)[1], double *err) {
+        unsigned long long *w = reinterpret_cast<unsigned long long *>(p);
+        unsigned long long old = *w;
+        for (int it = 0; it < kCasLimit; ++it) {
+            const unsigned long long nw = __double_as_longlong(__longlong_as_double(old) + t[0]);
+            const unsigned long long prev = atomicCAS(w, old, nw);
+            if (prev == old) return;
+            old = prev;
+        }
+        *err = 1.0;
+    }
+};
+
 template <typename real, int GL, int GPL, bool SMEM>
 __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
     k_sweep(DevLayout dl, DevState st, const int32_t *order, int32_t n_work, int32_t cap,
             const real *psi_in, real *psi_out) {
-    using vec2 = typename Vec2<real>::type;
     constexpr int GP = GL * GPL;     // groups per chunk (padded)
     constexpr int SLOTS = 32 / GL;   // tracks per warp task
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_work, s_next, s_ntask;
     __shared__ UnitStack s_us[kMaxPh];
     __shared__ double s_leak[8];
+    __shared__ float s_scl[32];      // FP32 fixed-point tally: scale of each group of the chunk
+    __shared__ float s_inv[32];      // and its inverse
+    __shared__ unsigned s_bmax[32];  // bound of |W psi| and |W Qr| per group (float bits)
+    __shared__ float s_wmax;
+    constexpr bool kFixed = sizeof(real) == 4;  // FP32 sweeps tally in fixed point
     const int G = dl.G, NL = dl.NL, M = dl.M, Ph = dl.Ph, cpl = dl.cpl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-    const int j = lane / GL;         // slot: track of the block
-    const int ql = lane & (GL - 1);  // lane of the slot: groups ql, GL + ql, ...
-    // shared layout: sig [M*GP] | rows (Qr, Sigma_t) [GPL][ROWS][GL] | tally [GPL][ROWS][GL]
-    // with ROWS = cap + SLOTS: the last SLOTS rows are zero rows, one per bank group
-    const int ROWS = cap + SLOTS;
+    const int j = lane / GL;         // slot: track of the warp task
+    const int ql = lane & (GL - 1);  // lane of the slot: groups ql * GPL + c, c < GPL
+    // shared layout: sig [M][GP] | rows [cap][GP][2] (Qr, Sigma_t) | tally [cap][GP]
     real *sig = reinterpret_cast<real *>(smem);
     size_t off = ((size_t)M * GP * sizeof(real) + 15) & ~(size_t)15;
-    vec2 *rows = reinterpret_cast<vec2 *>(smem + off);
-    off += (size_t)ROWS * GP * sizeof(vec2);
+    real *rows = reinterpret_cast<real *>(smem + off);
+    off += (size_t)cap * GP * 2 * sizeof(real);
     real *tl_s = reinterpret_cast<real *>(smem + off);
+    int *tl_i = reinterpret_cast<int *>(smem + off);  // the same tally rows in fixed point
+    const unsigned rows_sa = (unsigned)__cvta_generic_to_shared(rows);
+    const unsigned tl_sa = (unsigned)__cvta_generic_to_shared(tl_s);
 
     const real scale = (real)st.scal[SC_SCALE];
     const real *qr_g = reinterpret_cast<const real *>(st.qr);
     const real *sig_g = reinterpret_cast<const real *>(st.sig_t);
     const SegRec<real> *recs = reinterpret_cast<const SegRec<real> *>(dl.segs);
-    double leak = 0.0;
+    double *err = st.scal + SC_ERR;
+    real leak = (real)0;  // this lane's W psi leaving through vacuum faces
 
     for (;;) {
         __syncthreads();
@@ -165,17 +273,21 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
                 u.trk_off = e.trk_off;
                 u.tpl_base = e.exp_base;
                 u.W = e.W;
+                u.invW = 1.0 / e.W;
+                u.Wf = (float)e.W;
+                u.invWf = (float)(1.0 / e.W);
                 u.n_trk = e.n_trk;
                 u.i_lo = e.i_lo;
                 u.task_pre = pre;
                 u.pad = 0;
                 s_us[ph] = u;
-                for (int r = 0; r < min(cpl, e.n_trk); ++r) {  // per class: blocks of SLOTS tracks, 2 senses
-                    const int cnt = (e.n_trk - r + cpl - 1) / cpl;
-                    pre += 2 * ((cnt + SLOTS - 1) / SLOTS);
-                }
+                pre += 2 * ((e.n_trk + SLOTS - 1) / SLOTS);  // blocks of SLOTS tracks, 2 senses
             }
             s_ntask = pre;
+            float wm = 0.0f;
+            for (int ph = 0; ph < Ph; ++ph) wm = fmaxf(wm, (float)s_us[ph].W);
+            s_wmax = wm;
+            for (int qq = 0; qq < 32; ++qq) s_bmax[qq] = 0u;
         }
         __syncthreads();
         const int ntask = s_ntask;
@@ -184,7 +296,9 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
         const int nb = d0.nb;
         const int32_t *reg2d = dl.reg2d + d0.seg2d_off;
         for (int g0 = 0; g0 < G; g0 += GP) {
+            __syncthreads();  // the previous chunk's flush is done with the tile
             const int gc = min(GP, G - g0);
+            float bmax = 0.0f;  // this thread's bound for group tid % GP of the chunk
             for (int e = tid; e < M * GP; e += blockDim.x) {
                 const int m = e / GP, qq = e - m * GP;
                 real v = qq < gc ? sig_g[m * G + g0 + qq] : (real)0;
@@ -197,33 +311,45 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
                     const int reg = __ldg(reg2d + b);
                     for (int x = lane; x < NL * GP; x += 32) {
                         const int L = x / GP, qq = x - L * GP;
-                        const int c = qq / GL, qx = qq - c * GL;
                         const int f = reg * NL + L;
-                        const int e = (c * ROWS + b * NL + L) * GL + qx;
-                        vec2 v;
-                        v.x = (real)0;
-                        v.y = (real)0;
+                        const int e = (b * NL + L) * GP + qq;
+                        real q = (real)0, sg = (real)0;
                         if (qq < gc) {
                             const int m = __ldg(dl.fsr_mat + f);
-                            real sg = sig_g[m * G + g0 + qq];
+                            sg = sig_g[m * G + g0 + qq];
                             if (sizeof(real) == 4) sg = (real)((float)sg * kLog2e);
-                            v.x = qr_g[(size_t)f * G + g0 + qq];
-                            v.y = sg;
+                            q = qr_g[(size_t)f * G + g0 + qq];
                         }
-                        rows[e] = v;
+                        rows[2 * e] = q;
+                        rows[2 * e + 1] = sg;
                         tl_s[e] = (real)0;
+                        if (kFixed) bmax = fmaxf(bmax, fabsf((float)q));
                     }
                 }
-                for (int e = tid; e < GPL * SLOTS * GL; e += blockDim.x) {
-                    const int c = e / (SLOTS * GL), x = e - c * SLOTS * GL;
-                    vec2 z;
-                    z.x = (real)0;
-                    z.y = (real)0;
-                    rows[(c * ROWS + cap) * GL + x] = z;
-                    tl_s[(c * ROWS + cap) * GL + x] = (real)0;
+                if (kFixed) {
+                    // incoming fluxes of the unit's tracks enter the bound too:
+                    // psi along a track stays between its incoming value and Qr
+                    const int qq = tid % GP;
+                    if (psi_in && qq < gc) {
+                        for (int ph = 0; ph < Ph; ++ph) {
+                            const int64_t base = s_us[ph].trk_off * 4;
+                            const int nrow = s_us[ph].n_trk * 4;
+                            for (int rr = tid / GP; rr < nrow; rr += blockDim.x / GP)
+                                bmax = fmaxf(bmax, fabsf((float)psi_in[(base + rr) * G + g0 + qq] * (float)scale));
+                        }
+                    }
+                    atomicMax(&s_bmax[qq], __float_as_uint(bmax));
                 }
             }
+            __syncthreads();
             if (tid == 0) s_next = 0;
+            if (kFixed && SMEM && tid < GP) {
+                // one unit of the fixed-point tally = 2^-bits of a bound of every
+                // contribution W |psi - Qr| <= W (|psi| + |Qr|)
+                const float B = 2.0f * s_wmax * __uint_as_float(s_bmax[tid]);
+                s_scl[tid] = B > 0.0f ? ldexpf(1.0f, dl.tally_bits) / B : 1.0f;
+                s_inv[tid] = B > 0.0f ? B * ldexpf(1.0f, -dl.tally_bits) : 1.0f;
+            }
             __syncthreads();
 
             for (;;) {
@@ -231,26 +357,26 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
                 if (lane == 0) t = atomicAdd(&s_next, 1);
                 t = __shfl_sync(0xffffffffu, t, 0);
                 if (t >= ntask) break;
-                // decode the warp task: polar stack, sense, class r, block mb
+                // warp task: polar stack ph, sense, block of SLOTS tracks taken in
+                // decreasing segment count
                 int ph = 0;
                 while (ph + 1 < Ph && t >= s_us[ph + 1].task_pre) ++ph;
                 const UnitStack u = s_us[ph];
-                int x = t - u.task_pre;
+                const int x = t - u.task_pre;
                 const int sense = x & 1;
-                x >>= 1;
-                int r = 0, cnt = 0;
-                for (;; ++r) {
-                    cnt = (u.n_trk - r + cpl - 1) / cpl;
-                    const int nmb = (cnt + SLOTS - 1) / SLOTS;
-                    if (x < nmb) break;
-                    x -= nmb;
-                }
-                const int mb = x;
-                const int J = min(SLOTS, cnt - mb * SLOTS);  // tracks in this block
-                const bool valid = j < J;
-                const int k = r + (mb * SLOTS + j) * cpl;    // track of this slot in the stack
+                const int q = (x >> 1) * SLOTS + j;
+                const bool valid = q < u.n_trk;
+                const int k = valid ? __ldg(dl.perm + u.trk_off + q) : 0;  // track in the stack
+                const int r = k % cpl, m = k / cpl;          // class and shift of the track
                 const int64_t gid = u.trk_off + k;
-                const real W = (real)u.W;
+                // psi is carried pre-multiplied by the track weight W, so that the
+                // tally contribution W (psi_in - psi_out) is the psi change itself
+                const real W = sizeof(real) == 4 ? (real)u.Wf : (real)u.W;
+                const real invW = sizeof(real) == 4 ? (real)u.invWf : (real)u.invW;
+                const int qlo = ql * GPL;                    // first group of this lane in the chunk
+                float scl[GPL];
+#pragma unroll
+                for (int c = 0; c < GPL; ++c) scl[c] = kFixed && SMEM ? s_scl[ql * GPL + c] : 1.0f;
                 real psiU[GPL], psiD[GPL];
 #pragma unroll
                 for (int c = 0; c < GPL; ++c) {
@@ -262,10 +388,10 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
                     if (psi_in) {
 #pragma unroll
                         for (int c = 0; c < GPL; ++c) {
-                            const int qq = c * GL + ql;
+                            const int qq = ql * GPL + c;
                             if (qq < gc) {
-                                psiU[c] = psi_in[(gid * 4 + 0 * 2 + sense) * G + g0 + qq] * scale;
-                                psiD[c] = psi_in[(gid * 4 + 1 * 2 + sense) * G + g0 + qq] * scale;
+                                psiU[c] = psi_in[(gid * 4 + 0 * 2 + sense) * G + g0 + qq] * (scale * W);
+                                psiD[c] = psi_in[(gid * 4 + 1 * 2 + sense) * G + g0 + qq] * (scale * W);
                             }
                         }
                     }
@@ -274,117 +400,200 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
                         dstD = dl.dst[gid * 4 + 1 * 2 + sense];
                     }
                 }
-                // one template piece for every slot: 2D segment b (bn = b * NL),
-                // slot j at layer Lt + lofs
-                auto visit = [&](int bn, int Lt, real len, int lofs) {
-                    const int L = Lt + lofs;
-                    const bool act = valid && (unsigned)L < (unsigned)NL;
+                // one segment of this slot's track, in tile rows rU (upward frame,
+                // row b * NL + L) and rD (mirrored frame, row b * NL + NL-1-L)
+                auto visit = [&](int rU, int rD, real len) {
+                    real tU[GPL], tD[GPL];
                     if (SMEM) {
-                        // rows of the upward and the mirrored downward frame, or
-                        // the zero row of the same bank group
-                        const int rU = bn + L, rD = bn + (NL - 1 - L);
-                        const int zU = act ? rU : cap + (rU & (SLOTS - 1));
-                        const int zD = act ? rD : cap + (rD & (SLOTS - 1));
+                        const int eU = rU * GP + qlo, eD = rD * GP + qlo;
+                        real qU[GPL], sU[GPL], qD[GPL], sD[GPL];
+                        RowLoadS<real, GPL>::get(rows_sa + eU * (unsigned)(2 * sizeof(real)), qU, sU);
+                        RowLoadS<real, GPL>::get(rows_sa + eD * (unsigned)(2 * sizeof(real)), qD, sD);
 #pragma unroll
                         for (int c = 0; c < GPL; ++c) {
-                            const int eU = (c * ROWS + zU) * GL + ql, eD = (c * ROWS + zD) * GL + ql;
-                            const vec2 aU = rows[eU], aD = rows[eD];
-                            // Eq. 3: psi_out = Qr + (psi_in - Qr) e^{-Sigma_t l}
-                            const real xU = attenuation<real>(aU.y * len);
-                            const real xD = attenuation<real>(aD.y * len);
-                            const real nU = aU.x + (psiU[c] - aU.x) * xU;
-                            const real nD = aD.x + (psiD[c] - aD.x) * xD;
-                            atomicAdd(tl_s + eU, (psiU[c] - nU) * W);
-                            atomicAdd(tl_s + eD, (psiD[c] - nD) * W);
-                            psiU[c] = nU;
-                            psiD[c] = nD;
+                            // Eq. 3 on W psi: d = W (psi_in - Qr),
+                            // W (psi_in - psi_out) = d (1 - e^{-Sigma_t l})
+                            const real xU = attenuation<real>(sU[c] * len);
+                            const real xD = attenuation<real>(sD[c] * len);
+                            const real dU = fma(-W, qU[c], psiU[c]), dD = fma(-W, qD[c], psiD[c]);
+                            tU[c] = fma(-dU, xU, dU);
+                            tD[c] = fma(-dD, xD, dD);
+                            psiU[c] -= tU[c];
+                            psiD[c] -= tD[c];
+                        }
+                        if constexpr (kFixed) {
+                            // round to the fixed-point grid: adding 1.5 * 2^23 leaves the
+                            // integer in the low mantissa bits (|t scl| < 2^22)
+#pragma unroll
+                            for (int c = 0; c < GPL; ++c) {
+                                shared_red_add(tl_sa + (eU + c) * 4u,
+                                               __float_as_int(fmaf((float)tU[c], scl[c], 12582912.0f)) - 0x4B400000);
+                                shared_red_add(tl_sa + (eD + c) * 4u,
+                                               __float_as_int(fmaf((float)tD[c], scl[c], 12582912.0f)) - 0x4B400000);
+                            }
+                        } else {
+                            TallyAdd<real, GPL>::add(tl_s + eU, tU, err);
+                            TallyAdd<real, GPL>::add(tl_s + eD, tD, err);
                         }
                     } else {
-                        if (!act) return;
-                        const int LD = NL - 1 - L;
-                        const int reg = __ldg(reg2d + bn / NL);
+                        const int b = rU / NL, L = rU - b * NL, LD = NL - 1 - L;
+                        const int reg = __ldg(reg2d + b);
                         const size_t fU = (size_t)reg * NL + L, fD = (size_t)reg * NL + LD;
                         const int mU = __ldg(dl.fsr_mat + fU), mD = __ldg(dl.fsr_mat + fD);
 #pragma unroll
                         for (int c = 0; c < GPL; ++c) {
-                            const int qq = c * GL + ql;
+                            const int qq = qlo + c;
                             const real qU = qq < gc ? qr_g[fU * G + g0 + qq] : (real)0;
                             const real qD = qq < gc ? qr_g[fD * G + g0 + qq] : (real)0;
                             const real xU = attenuation<real>(sig[mU * GP + qq] * len);
                             const real xD = attenuation<real>(sig[mD * GP + qq] * len);
-                            const real nU = qU + (psiU[c] - qU) * xU;
-                            const real nD = qD + (psiD[c] - qD) * xD;
+                            const real dU = fma(-W, qU, psiU[c]), dD = fma(-W, qD, psiD[c]);
+                            tU[c] = fma(-dU, xU, dU);
+                            tD[c] = fma(-dD, xD, dD);
                             if (qq < gc) {
-                                atomicAdd(st.tally + fU * G + g0 + qq, (double)(psiU[c] - nU) * (double)W);
-                                atomicAdd(st.tally + fD * G + g0 + qq, (double)(psiD[c] - nD) * (double)W);
+                                atomicAdd(st.tally + fU * G + g0 + qq, (double)tU[c]);
+                                atomicAdd(st.tally + fD * G + g0 + qq, (double)tD[c]);
                             }
-                            psiU[c] = nU;
-                            psiD[c] = nD;
+                            psiU[c] -= tU[c];
+                            psiD[c] -= tD[c];
+                        }
+                    }
+                };
+                // four consecutive segments of the track at once (shared tally):
+                // all row loads and exponentials first, then the psi recurrence,
+                // then the tally updates, so that the loads overlap each other
+                auto visit4 = [&](const int (&rU)[4], const int (&rD)[4], const real (&len)[4]) {
+                    if constexpr (!SMEM) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) visit(rU[i], rD[i], len[i]);
+                    } else {
+                        int eU[4], eD[4];
+                        real qU[4][GPL], sU[4][GPL], qD[4][GPL], sD[4][GPL];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            eU[i] = rU[i] * GP + qlo;
+                            eD[i] = rD[i] * GP + qlo;
+                            RowLoadS<real, GPL>::get(rows_sa + eU[i] * (unsigned)(2 * sizeof(real)), qU[i], sU[i]);
+                            RowLoadS<real, GPL>::get(rows_sa + eD[i] * (unsigned)(2 * sizeof(real)), qD[i], sD[i]);
+                        }
+                        real tU[4][GPL], tD[4][GPL];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int c = 0; c < GPL; ++c) {
+                                sU[i][c] = attenuation<real>(sU[i][c] * len[i]);  // now e^{-Sigma_t l}
+                                sD[i][c] = attenuation<real>(sD[i][c] * len[i]);
+                            }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int c = 0; c < GPL; ++c) {
+                                const real dU = fma(-W, qU[i][c], psiU[c]), dD = fma(-W, qD[i][c], psiD[c]);
+                                tU[i][c] = fma(-dU, sU[i][c], dU);
+                                tD[i][c] = fma(-dD, sD[i][c], dD);
+                                psiU[c] -= tU[i][c];
+                                psiD[c] -= tD[i][c];
+                            }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            if constexpr (kFixed) {
+#pragma unroll
+                                for (int c = 0; c < GPL; ++c) {
+                                    shared_red_add(tl_sa + (eU[i] + c) * 4u,
+                                                   __float_as_int(fmaf((float)tU[i][c], scl[c], 12582912.0f)) - 0x4B400000);
+                                    shared_red_add(tl_sa + (eD[i] + c) * 4u,
+                                                   __float_as_int(fmaf((float)tD[i][c], scl[c], 12582912.0f)) - 0x4B400000);
+                                }
+                            } else {
+                                TallyAdd<real, GPL>::add(tl_s + eU[i], tU[i], err);
+                                TallyAdd<real, GPL>::add(tl_s + eD[i], tD[i], err);
+                            }
                         }
                     }
                 };
                 if (u.tpl_base >= 0) {
-                    // stored template of class r: line i_lo + r, slot layer offset mb*SLOTS + j
-                    const int64_t tpl = u.tpl_base + r;
-                    const int lofs = mb * SLOTS + j;
-                    const int lo = -(mb * SLOTS + J - 1), hi = NL - mb * SLOTS;
-                    const int Lmin = dl.tpl_lmin[tpl];
-                    const int64_t lb = dl.tpl_loff[tpl];
-                    const int nL = (int)(dl.tpl_loff[tpl + 1] - lb) - 1;
-                    const int64_t tb = dl.tpl_off[tpl];
-                    const int64_t p0 = tb + dl.tpl_lidx[lb + min(max(lo - Lmin, 0), nL)];
-                    const int64_t p1 = tb + dl.tpl_lidx[lb + min(max(hi - Lmin, 0), nL)];
+                    // stored template of class r (line i_lo + r): this track is its
+                    // pieces with template layer in [-m, NL - m), a contiguous record
+                    // range because the layer never decreases along an upward line
+                    int64_t p0 = 0, p1 = 0;
+                    if (valid) {
+                        const int64_t tpl = u.tpl_base + r;
+                        const int Lmin = dl.tpl_lmin[tpl];
+                        const int64_t lb = dl.tpl_loff[tpl];
+                        const int nL = (int)(dl.tpl_loff[tpl + 1] - lb) - 1;
+                        const int64_t tb = dl.tpl_off[tpl];
+                        p0 = tb + dl.tpl_lidx[lb + min(max(-m - Lmin, 0), nL)];
+                        p1 = tb + dl.tpl_lidx[lb + min(max(NL - m - Lmin, 0), nL)];
+                    }
                     const int n = (int)(p1 - p0);
                     const int dir = sense == 0 ? 1 : -1;
-                    int64_t p = sense == 0 ? p0 : p1 - 1;
-                    int s = 0;
-                    SegRec<real> c0, c1, c2, c3;
-                    if (n >= 4) {
-                        c0 = recs[p]; c1 = recs[p + dir]; c2 = recs[p + 2 * dir]; c3 = recs[p + 3 * dir];
-                    }
-                    for (; s + 4 <= n; s += 4) {
-                        // the next four records in flight while these four are swept
-                        SegRec<real> n0, n1, n2, n3;
-                        const bool more = s + 8 <= n;
-                        if (more) {
-                            n0 = recs[p + 4 * dir]; n1 = recs[p + 5 * dir];
-                            n2 = recs[p + 6 * dir]; n3 = recs[p + 7 * dir];
+                    const SegRec<real> *pr = recs + (sense == 0 ? p0 : p1 - 1);
+                    // all slots step together to the longest track of the warp; a
+                    // slot past its own end repeats its last record with length 0,
+                    // which leaves psi unchanged and adds exactly 0 to the tally
+                    const int nmax = __reduce_max_sync(0xffffffffu, n);
+                    auto fetch4 = [&](SegRec<real> (&c)[4], int s0) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            if (n > 0) {
+                                c[i] = pr[min(s0 + i, n - 1) * dir];
+                                if (s0 + i >= n) c[i].len = (real)0;
+                            } else {
+                                c[i].key = tpl_key(-m, m);  // rows 0 and 0 after the shift
+                                c[i].len = (real)0;
+                            }
                         }
-                        visit((int)(c0.key >> 16), (int)(c0.key & 0xffffu) - kTplLayerBias, c0.len, lofs);
-                        visit((int)(c1.key >> 16), (int)(c1.key & 0xffffu) - kTplLayerBias, c1.len, lofs);
-                        visit((int)(c2.key >> 16), (int)(c2.key & 0xffffu) - kTplLayerBias, c2.len, lofs);
-                        visit((int)(c3.key >> 16), (int)(c3.key & 0xffffu) - kTplLayerBias, c3.len, lofs);
-                        p += 4 * dir;
-                        if (more) { c0 = n0; c1 = n1; c2 = n2; c3 = n3; }
+                    };
+                    auto sweep4 = [&](const SegRec<real> (&c)[4]) {
+                        int ru[4], rd[4];
+                        real ln[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            ru[i] = tpl_row_up(c[i].key) + m;
+                            rd[i] = tpl_row_down(c[i].key) - m;
+                            ln[i] = c[i].len;
+                        }
+                        if constexpr (GPL >= 4) {
+                            // eight recurrences per segment already: no batching
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) visit(ru[i], rd[i], ln[i]);
+                        } else {
+                            visit4(ru, rd, ln);
+                        }
+                    };
+                    // two sets of four records: one set in flight while the other
+                    // is swept
+                    SegRec<real> ra[4], rb[4];
+                    fetch4(ra, 0);
+                    for (int s = 0; s < nmax; s += 8) {
+                        fetch4(rb, s + 4);
+                        sweep4(ra);
+                        if (s + 4 >= nmax) break;
+                        fetch4(ra, s + 8);
+                        sweep4(rb);
                     }
-                    for (; s < n; ++s) {
-                        const SegRec<real> c = recs[p];
-                        p += dir;
-                        visit((int)(c.key >> 16), (int)(c.key & 0xffffu) - kTplLayerBias, c.len, lofs);
-                    }
-                } else {
-                    // template generated on the fly: line of the block's lowest track
+                } else if (valid) {
+                    // generated on the fly: this track's own line, layers [0, NL)
                     const StackDesc &d = dl.desc[(int64_t)T * Ph + ph];
-                    const int ibase = u.i_lo + r + mb * SLOTS * cpl;
+                    const int i = u.i_lo + k;
                     TplIter<real> it;
-                    it.init(dl, d, ibase, first_seg(dl, d, ibase + (J - 1) * cpl), last_seg(dl, d, ibase),
-                            -(J - 1), NL, sense == 0 ? 1 : -1);
+                    it.init(dl, d, i, first_seg(dl, d, i), last_seg(dl, d, i), 0, NL, sense == 0 ? 1 : -1);
                     while (!it.done) {
                         int b, L;
                         real len;
                         it.next(dl, d, b, L, len);
-                        visit(b * NL, L, len, j);
+                        visit(b * NL + L, b * NL + NL - 1 - L, len);
                     }
                 }
                 if (valid) {
 #pragma unroll
                     for (int c = 0; c < GPL; ++c) {
-                        const int qq = c * GL + ql;
+                        const int qq = ql * GPL + c;
                         if (qq >= gc) continue;
-                        if (dstU >= 0 && dstU < dl.n_slots) psi_out[dstU * G + g0 + qq] = psiU[c];
-                        else leak += (double)W * (double)psiU[c];
-                        if (dstD >= 0 && dstD < dl.n_slots) psi_out[dstD * G + g0 + qq] = psiD[c];
-                        else leak += (double)W * (double)psiD[c];
+                        if (dstU >= 0 && dstU < dl.n_slots) psi_out[dstU * G + g0 + qq] = psiU[c] * invW;
+                        else leak += psiU[c];
+                        if (dstD >= 0 && dstD < dl.n_slots) psi_out[dstD * G + g0 + qq] = psiD[c] * invW;
+                        else leak += psiD[c];
                     }
                 }
             }
@@ -395,16 +604,18 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
                     for (int x = lane; x < NL * GP; x += 32) {
                         const int L = x / GP, qq = x - L * GP;
                         if (qq >= gc) continue;
-                        const int c = qq / GL, qx = qq - c * GL;
-                        const double v = (double)tl_s[(c * ROWS + b * NL + L) * GL + qx];
+                        const int e = (b * NL + L) * GP + qq;
+                        const double v = kFixed ? (double)((float)tl_i[e] * s_inv[qq]) : (double)tl_s[e];
                         if (v != 0.0) atomicAdd(st.tally + ((size_t)reg * NL + L) * G + g0 + qq, v);
                     }
                 }
+                if (tid < 32) s_bmax[tid] = 0u;  // next chunk's bound (read only before its tasks)
             }
         }
     }
-    for (int o = 16; o > 0; o >>= 1) leak += __shfl_down_sync(0xffffffffu, leak, o);
-    if (lane == 0) s_leak[warp] = leak;
+    double leak64 = (double)leak;
+    for (int o = 16; o > 0; o >>= 1) leak64 += __shfl_down_sync(0xffffffffu, leak64, o);
+    if (lane == 0) s_leak[warp] = leak64;
     __syncthreads();
     if (tid == 0) {
         double v = 0.0;
@@ -415,35 +626,30 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
 
 // lanes per track: the smallest power of two that holds ceil(G / gpl) groups
 int lanes_for_groups(int G, int gpl) {
-    const int cap = gpl == 2 ? 16 : 32;
+    const int cap = 32 / gpl;
     const int need = (G + gpl - 1) / gpl;
     int gl = 1;
     while (gl < need && gl < cap) gl <<= 1;
     return gl;
 }
 
-template <typename real, int GPL, bool SMEM>
+// the kernel for gl lanes per track; only shapes with gl * GPL <= 32 exist
+template <typename real, int GPL, bool SMEM, int GL = 32 / GPL>
 const void *pick(int gl) {
-    switch (gl) {
-        case 1: return (const void *)k_sweep<real, 1, GPL, SMEM>;
-        case 2: return (const void *)k_sweep<real, 2, GPL, SMEM>;
-        case 4: return (const void *)k_sweep<real, 4, GPL, SMEM>;
-        case 8: return (const void *)k_sweep<real, 8, GPL, SMEM>;
-        case 16: return (const void *)k_sweep<real, 16, GPL, SMEM>;
-        default: return (const void *)k_sweep<real, (GPL == 1 ? 32 : 16), GPL, SMEM>;
+    if constexpr (GL > 1) {
+        if (gl < GL) return pick<real, GPL, SMEM, GL / 2>(gl);
     }
+    return (const void *)k_sweep<real, GL, GPL, SMEM>;
 }
 
 const void *sweep_fn(int precision, int tally_smem, int G, int gpl) {
     const int gl = lanes_for_groups(G, gpl);
     if (precision == MOC_FP64) return tally_smem ? pick<double, 1, true>(gl) : pick<double, 1, false>(gl);
+    if (gpl == 4) return tally_smem ? pick<float, 4, true>(gl) : pick<float, 4, false>(gl);
     if (gpl == 2) return tally_smem ? pick<float, 2, true>(gl) : pick<float, 2, false>(gl);
     return tally_smem ? pick<float, 1, true>(gl) : pick<float, 1, false>(gl);
 }
 
-// rows of the tile rounded to whole bank groups, so that a zero row shares
-// the banks of the row it stands in for
-int round_cap(int cap) { return (cap + 31) & ~31; }
 
 }  // namespace
 
@@ -459,8 +665,7 @@ size_t sweep_smem_bytes(int precision, int tally_smem, int M, int G, int gpl, in
     const size_t rs = precision == MOC_FP64 ? 8 : 4;
     const size_t gp = (size_t)lanes_for_groups(G, gpl) * gpl;
     size_t b = ((size_t)M * gp * rs + 15) & ~(size_t)15;
-    // (Qr, Sigma_t) rows + tally rows, including one zero row per slot
-    if (tally_smem) b += (size_t)(round_cap(cap) + 32) * gp * rs * 3;
+    if (tally_smem) b += (size_t)cap * gp * rs * 3;  // (Qr, Sigma_t) rows + tally rows
     return b;
 }
 
@@ -482,7 +687,7 @@ cudaError_t launch_sweep(int precision, int tally_smem, int gpl, const DevLayout
     DevLayout a0 = dl;
     DevState a1 = st;
     const int32_t *a2 = order;
-    int32_t a3 = n_work, a4 = tally_smem ? round_cap(cap) : 0;
+    int32_t a3 = n_work, a4 = tally_smem ? cap : 0;
     const void *a5 = psi_in;
     void *a6 = psi_out;
     void *args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6};

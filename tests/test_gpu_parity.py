@@ -235,3 +235,22 @@ def test_graph_and_stream_agree():
     np.testing.assert_allclose(a.flux()[0], b.flux()[0], rtol=1e-5)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("gpl", [1, 2, 4])
+@pytest.mark.parametrize("name", ["lat3_mixed", "l17_small"])
+def test_groups_per_lane_against_oracle(name, gpl):
+    """Every lane shape (1, 2 or 4 groups per lane) sweeps like the oracle."""
+    p, o, g = get(name)
+    tr = Tracks(g, track_params(p, groups_per_lane=gpl))
+    assert tr.info["groups_per_lane"] == gpl
+    Q = np.random.default_rng(6).uniform(0.2, 1.0, size=(o.n_fsr, p.num_groups))
+    o.reset()
+    for sweep in range(2):
+        ot, ol = o.sweep_once(Q)
+        gt, gl = tr.sweep_from_source(Q)
+        scale = np.abs(ot).max()
+        assert np.abs(gt - ot).max() <= 2e-5 * scale, (sweep, np.abs(gt - ot).max() / scale)
+        assert abs(gl - ol) <= 2e-5 * max(abs(ol), 1e-300) + 1e-300
+    o.reset()
+    tr.close()
