@@ -1,0 +1,82 @@
+"""Parity at the benchmark's full size (17x17 lattice, 7 groups, 32 azimuths x
+4 polar angles, 0.05 cm / 0.5 cm spacing) in the launch configuration the
+benchmark times (FP32 sweep, every template stored, default lane shape).
+
+* FSR-id sequences and segment counts of sampled z-stacks: bit-exact.
+* One sweep from a seeded source (both hemispheres, every track): tallies
+  within 2e-5 of the largest, element by element, against the FP64 oracle.
+* Converged k-eff within 1e-5 of the oracle's converged value (stored in
+  tests/golden/oracle_k.json by tests/golden/make_golden.py, which runs the
+  oracle only), with neutron balance P / k = absorption + leakage.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_2503_17743_gb300 import MOC_FP32, Geometry, Tracks, track_params
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+NTH = os.cpu_count() or 4
+
+
+def golden(name):
+    return json.load(open(os.path.join(HERE, "golden", "oracle_k.json")))[name]
+
+
+@pytest.fixture(scope="module")
+def l17():
+    p = synth.workload("lattice17")
+    o = oracle.Oracle(p, n_threads=NTH)
+    tr = Tracks(Geometry(p), track_params(p, precision=MOC_FP32))
+    yield p, o, tr
+    tr.close()
+
+
+def test_sampled_stacks_bit_exact(l17):
+    p, o, tr = l17
+    rng = np.random.default_rng(17)
+    for _ in range(120):
+        t = int(rng.integers(o.n_tracks2d))
+        pp = int(rng.integers(p.n_polar))
+        oi, on, of, ol = o.stack(t, pp)
+        gi, gn, gf, gl = tr.stack_segments(t, pp)
+        np.testing.assert_array_equal(gi, oi)
+        np.testing.assert_array_equal(gn, on)
+        np.testing.assert_array_equal(gf, of)
+        assert np.all(np.abs(gl - ol) <= 1e-6 * ol + 1e-6)
+
+
+def test_one_sweep_against_oracle(l17):
+    p, o, tr = l17
+    Q = np.random.default_rng(23).uniform(0.2, 1.0, size=(o.n_fsr, p.num_groups))
+    o.reset()
+    tr.reset()
+    ot, ol = o.sweep_once(Q)
+    gt, gl = tr.sweep_from_source(Q)
+    scale = np.abs(ot).max()
+    assert np.abs(gt - ot).max() <= 2e-5 * scale, np.abs(gt - ot).max() / scale
+    assert abs(gl - ol) <= 2e-5 * abs(ol)
+    o.reset()
+    tr.reset()
+
+
+@pytest.mark.parametrize("name", ["lattice17", "lattice17_small"])
+def test_converged_k_within_1e5_of_oracle(name, l17):
+    if name == "lattice17":
+        p, _, tr = l17
+    else:
+        p = synth.workload(name)
+        tr = Tracks(Geometry(p), track_params(p, precision=MOC_FP32))
+    res = tr.solve_eigen(tol_k=1e-8, tol_src=1e-6, max_iter=8000)
+    assert res["converged"]
+    assert abs(res["k"] - golden(name)["k"]) < 1e-5, (res["k"], golden(name)["k"])
+    # balance of the normalised flux: 1 / k = absorption + leakage
+    assert abs(1.0 / res["k"] - (res["absorption"] + res["leakage"])) < 1e-4
+    if name != "lattice17":
+        tr.close()
