@@ -37,9 +37,12 @@ WORKLOAD_DESC = ("17x17 pin lattice (264 fuel pins, 25 seeded guide tubes), 3 ma
                  "radial spacing 0.05 cm, axial spacing 0.5 cm; FP32 sweep, templates stored")
 # algorithmic work of one integration: 7 FP32 operations, one of them the exponential
 OPS_PER_INTEGRATION = 7
-# ALU roofline: the exponential runs on the MUFU pipe, 16 per SM per clock
-# (152 SMs at the 2070 MHz maximum clock): 5.03e12 integrations/s
-SMS, MUFU_PER_CLK, SM_MAX_MHZ = 152, 16, 2070.0
+# ALU roofline: FP32 instruction issue, 4 schedulers x 32 lanes = 128 lane
+# operations per SM per clock (152 SMs at the 2070 MHz maximum clock):
+# 40.3e12 operations/s = 5.75e12 integrations/s.  The exponential unit
+# (31.4 ex2 per SM per clock, measured by moc_measure_ex2_rate) would allow
+# 9.9e12 integrations/s, so it is not the binding unit.
+SMS, LANES_PER_CLK, SM_MAX_MHZ = 152, 128, 2070.0
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -270,12 +273,12 @@ def run_ours(args):
         return
     sw = statistics.mean(sweep_ms) * 1e-3
     ach = OPS_PER_INTEGRATION * integ / sw / 1e12
-    peak = OPS_PER_INTEGRATION * SMS * MUFU_PER_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    peak = SMS * LANES_PER_CLK * SM_MAX_MHZ * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
             "traffic": profile_traffic(sweep_source_hash()), "kernel": "k_sweep",
             "sweep_ms": sw * 1e3,
-            "peak_basis": "derived: 7 FP32 ops per integration, exponential on MUFU at 16/SM/clk, "
-                          "152 SMs, 2070 MHz"}
+            "peak_basis": "derived: FP32 issue 128 lane-ops per SM per clock x 152 SMs x 2070 MHz; "
+                          "7 FP32 ops per integration (ex2 unit measured 31.4/SM/clk, not binding)"}
     clocks = parse_clocks(clk_path)
     try:
         os.remove(clk_path)

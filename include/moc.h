@@ -278,6 +278,16 @@ int moc_sweep_from_source(moc_tracks *tracks, const double *Q, double *tally, do
  * MOC_ERR_UNSUPPORTED, MOC_ERR_CUDA. */
 int moc_group_rates_static(moc_tracks *tracks, void *stream, double *rates);
 
+/* Sustained rate of the device's exponential unit (ex2.approx.ftz.f32, one
+ * per integration of Eq. 3): 8 independent chains per thread on every SM,
+ * the last of three runs timed with CUDA events.  Measurement support for
+ * the sweep's ALU roofline; the paper has no counterpart.  Allocates and
+ * frees a small device buffer.
+ *   ex2_per_second  out: exponentials per second over the whole device
+ *   sm_count        out (may be NULL): multiprocessors of the device
+ * Errors: MOC_ERR_INVALID_ARG for NULL, MOC_ERR_CUDA. */
+int moc_measure_ex2_rate(int32_t device, double *ex2_per_second, double *sm_count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -96,6 +96,7 @@ SIGNATURES = {
                                 C.c_int32]),
     "moc_sweep_from_source": (C.c_int, [C.c_void_p, f64p, f64p, f64p]),
     "moc_group_rates_static": (C.c_int, [C.c_void_p, C.c_void_p, f64p]),
+    "moc_measure_ex2_rate": (C.c_int, [C.c_int32, f64p, f64p]),
     "moc_enqueue_source": (C.c_int, [C.c_void_p, C.c_void_p]),
     "moc_enqueue_sweep": (C.c_int, [C.c_void_p, C.c_void_p]),
     "moc_enqueue_update": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -328,3 +329,11 @@ class Tracks:
         out = np.zeros(2 * self.G)
         _check(load().moc_group_rates_static(self._h, stream, _ptr(out, f64p)))
         return out[:self.G].copy(), out[self.G:].copy()
+
+
+def measure_ex2_rate(device=0):
+    """(exponentials per second of the whole device, SM count): throughput of
+    the ex2 unit that bounds the sweep (one exponential per integration)."""
+    rate, sms = C.c_double(), C.c_double()
+    _check(load().moc_measure_ex2_rate(device, C.byref(rate), C.byref(sms)))
+    return rate.value, int(sms.value)

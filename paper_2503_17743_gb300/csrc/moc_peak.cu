@@ -1,0 +1,67 @@
+// Throughput probe of the exponential unit, used to state the ALU roofline of
+// the sweep: every integration (Eq. 3) costs one ex2.approx.ftz.f32.
+//
+// Each thread runs 8 independent chains x <- 2^(x * c) for `iters` steps
+// (c < 0 keeps x in (0, 1]); the grid is sized to fill every SM.  Returns the
+// sustained ex2 rate of the whole device.
+#include <cuda_runtime.h>
+
+#include "moc_internal.h"
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_ex2_rate(int iters, float c, float *sink) {
+    float x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = 0.25f + 0.01f * (float)((threadIdx.x + j) & 31);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float y;
+            asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x[j] * c));
+            x[j] = y;
+        }
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += x[j];
+    if (s == -1.0f) sink[blockIdx.x] = s;  // never true; keeps the chains alive
+}
+
+}  // namespace
+
+extern "C" int moc_measure_ex2_rate(int32_t device, double *ex2_per_second, double *sm_count) {
+    if (!ex2_per_second) { moc_set_error("NULL argument"); return MOC_ERR_INVALID_ARG; }
+    if (cudaSetDevice(device) != cudaSuccess) { moc_set_error("cudaSetDevice failed"); return MOC_ERR_CUDA; }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        moc_set_error("cudaDeviceGetAttribute failed");
+        return MOC_ERR_CUDA;
+    }
+    const int blocks = sms * 8, threads = 256, iters = 4096;
+    float *sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float ms = 0.0f;
+    cudaError_t e = cudaMalloc(&sink, blocks * sizeof(float));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {  // the last of 3 runs is timed
+        k_ex2_rate<<<blocks, threads>>>(iters, -0.5f, sink);
+        e = cudaEventRecord(e0);
+        if (e == cudaSuccess) k_ex2_rate<<<blocks, threads>>>(iters, -0.5f, sink);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(e1);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (sink) cudaFree(sink);
+    if (e != cudaSuccess || ms <= 0.0f) {
+        moc_set_error(std::string("ex2 probe: ") + cudaGetErrorString(e));
+        return MOC_ERR_CUDA;
+    }
+    *ex2_per_second = (double)blocks * threads * iters * 8.0 / (ms * 1e-3);
+    if (sm_count) *sm_count = sms;
+    return MOC_OK;
+}
