@@ -288,6 +288,65 @@ int moc_group_rates_static(moc_tracks *tracks, void *stream, double *rates);
  * Errors: MOC_ERR_INVALID_ARG for NULL, MOC_ERR_CUDA. */
 int moc_measure_ex2_rate(int32_t device, double *ex2_per_second, double *sm_count);
 
+/* ---------------------------------------------------------------------------
+ * Serving engine: independent eigenvalue and fixed-source solves of different
+ * geometries, group counts and track layouts, kept resident on one device and
+ * advanced together as they arrive (continuous batching).  The paper solves
+ * one problem at a time; this is a library service around that solver.
+ *
+ * Requests queue in arrival order and are admitted while a slot is free and
+ * their device footprint (moc_query_footprint: resident state plus stored
+ * templates) fits next to the resident solves in the memory budget; the
+ * oldest request is always admitted into an empty engine.  Each resident solve
+ * owns a stream and captured iteration graphs; a step enqueues a quantum of
+ * outer iterations on every idle solve (their kernels overlap on the device),
+ * waits for the oldest quantum in flight and retires every solve whose
+ * stopping rule held or that reached max_iter.  Iterations after convergence
+ * are no-ops on the device, so a solve's result does not depend on the mix it
+ * ran in.  One host thread drives an engine; calls on one engine must not
+ * overlap. */
+typedef struct {
+    int32_t device;
+    int32_t max_active;           /* resident solves at most (0 = 16) */
+    int64_t memory_budget_bytes;  /* device bytes for resident solves (0 = 80% of free memory) */
+    int32_t iterations_per_poll;  /* outer iterations per solve between host checks (0 = 8) */
+} moc_server_params;
+
+typedef struct moc_server moc_server;
+
+int moc_server_create(const moc_server_params *params, moc_server **out);
+void moc_server_destroy(moc_server *server);
+
+/* Queue one solve.  The geometry and both parameter sets are copied, so the
+ * caller may destroy them after the call; eigenvalue or fixed source follows
+ * the geometry (external source present or not); solve->use_graph is ignored
+ * (graphs are always used).  *ticket identifies the request.  Errors:
+ * MOC_ERR_INVALID_ARG (NULL, max_iter < 1, track parameters naming another
+ * device), errors of moc_query_footprint. */
+int moc_server_submit(moc_server *server, const moc_geometry *geom, const moc_track_params *tracks,
+                      const moc_solve_params *solve, int64_t *ticket);
+
+/* One engine step: admit, enqueue, wait for the oldest quantum in flight,
+ * retire finished solves, admit and enqueue again.  *finished = solves
+ * retired by this call, *pending = queued + resident requests left (either may
+ * be NULL).  Blocks at most until one quantum completes. */
+int moc_server_step(moc_server *server, int32_t *finished, int32_t *pending);
+
+/* Result of a ticket: *ready = 0 while it is queued or resident.  Once ready,
+ * fills res (may be NULL), phi (n_fsr*G normalised flux, may be NULL; phi_len
+ * its capacity) and times[2] (may be NULL: seconds queued before admission and
+ * seconds from submission to retirement), then forgets the ticket.  Returns
+ * the solve's own status (MOC_ERR_NOT_CONVERGED when the stopping rule never
+ * held).  MOC_ERR_INVALID_ARG for an unknown or already fetched ticket. */
+int moc_server_result(moc_server *server, int64_t ticket, moc_result *res, double *phi,
+                      int64_t phi_len, double *times, int32_t *ready);
+
+/* Counters, int64 values written to out[0..n-1]: 0 queued, 1 resident,
+ * 2 admitted so far, 3 retired so far, 4 device bytes held by resident
+ * solves (footprint estimates), 5 memory budget, 6 most solves resident at
+ * once. */
+int moc_server_stats(const moc_server *server, int64_t *out, int32_t n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -54,6 +54,11 @@ class moc_track_params(C.Structure):
                 ("groups_per_lane", C.c_int32)]
 
 
+class moc_server_params(C.Structure):
+    _fields_ = [("device", C.c_int32), ("max_active", C.c_int32),
+                ("memory_budget_bytes", C.c_int64), ("iterations_per_poll", C.c_int32)]
+
+
 class moc_solve_params(C.Structure):
     _fields_ = [("tol_k", C.c_double), ("tol_src", C.c_double), ("max_iter", C.c_int32),
                 ("use_graph", C.c_int32)]
@@ -97,6 +102,12 @@ SIGNATURES = {
     "moc_sweep_from_source": (C.c_int, [C.c_void_p, f64p, f64p, f64p]),
     "moc_group_rates_static": (C.c_int, [C.c_void_p, C.c_void_p, f64p]),
     "moc_measure_ex2_rate": (C.c_int, [C.c_int32, f64p, f64p]),
+    "moc_server_create": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "moc_server_destroy": (None, [C.c_void_p]),
+    "moc_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, i64p]),
+    "moc_server_step": (C.c_int, [C.c_void_p, i32p, i32p]),
+    "moc_server_result": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, f64p, C.c_int64, f64p, i32p]),
+    "moc_server_stats": (C.c_int, [C.c_void_p, i64p, C.c_int32]),
     "moc_enqueue_source": (C.c_int, [C.c_void_p, C.c_void_p]),
     "moc_enqueue_sweep": (C.c_int, [C.c_void_p, C.c_void_p]),
     "moc_enqueue_update": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -337,3 +348,73 @@ def measure_ex2_rate(device=0):
     rate, sms = C.c_double(), C.c_double()
     _check(load().moc_measure_ex2_rate(device, C.byref(rate), C.byref(sms)))
     return rate.value, int(sms.value)
+
+
+SERVER_STATS = ["queued", "resident", "admitted", "retired", "bytes_resident", "budget",
+                "max_resident"]
+
+
+class Server:
+    """moc_server_*: solves of different problems resident on one device and
+    advanced together as they arrive (continuous batching)."""
+
+    def __init__(self, device=0, max_active=0, memory_budget_bytes=0, iterations_per_poll=0):
+        p = moc_server_params()
+        p.device, p.max_active = device, max_active
+        p.memory_budget_bytes, p.iterations_per_poll = memory_budget_bytes, iterations_per_poll
+        h = C.c_void_p()
+        _check(load().moc_server_create(C.byref(p), C.byref(h)))
+        self._h = h
+        self._shape = {}
+
+    def submit(self, geom, params, tol_k=1e-6, tol_src=1e-5, max_iter=5000):
+        """Queue a solve of `geom` (a Geometry) with track parameters `params`;
+        returns the ticket."""
+        sp = moc_solve_params()
+        sp.tol_k, sp.tol_src, sp.max_iter, sp.use_graph = tol_k, tol_src, max_iter, 1
+        t = C.c_int64()
+        _check(load().moc_server_submit(self._h, geom._h, C.byref(params), C.byref(sp), C.byref(t)))
+        prob = geom.prob
+        n_fsr = int(np.sum(np.where(np.asarray(prob.has_pin) != 0, 2, 1))) * prob.n_layers
+        self._shape[t.value] = (n_fsr, prob.num_groups)
+        return t.value
+
+    def step(self):
+        """One engine step; returns (solves retired by it, requests left)."""
+        f, p = C.c_int32(), C.c_int32()
+        _check(load().moc_server_step(self._h, C.byref(f), C.byref(p)))
+        return f.value, p.value
+
+    def result(self, ticket, check=True):
+        """None while pending, else (result dict, phi [n_fsr, G], seconds
+        queued, seconds from submission to retirement, status)."""
+        n_fsr, G = self._shape[ticket]
+        r = moc_result()
+        phi = np.zeros(n_fsr * G)
+        times = np.zeros(2)
+        ready = C.c_int32()
+        rc = load().moc_server_result(self._h, C.c_int64(ticket), C.byref(r), _ptr(phi, f64p),
+                                      phi.size, _ptr(times, f64p), C.byref(ready))
+        if not ready.value:
+            _check(rc)
+            return None
+        del self._shape[ticket]
+        if check:
+            _check(rc)
+        return r.as_dict(), phi.reshape(n_fsr, G), float(times[0]), float(times[1]), rc
+
+    def stats(self):
+        out = np.zeros(len(SERVER_STATS), dtype=np.int64)
+        _check(load().moc_server_stats(self._h, _ptr(out, i64p), len(SERVER_STATS)))
+        return dict(zip(SERVER_STATS, (int(v) for v in out)))
+
+    def close(self):
+        if self._h:
+            load().moc_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "moc_kernels.h"
+#include "moc_serve.h"
 
 namespace {
 
@@ -153,6 +154,12 @@ void fill_views(moc_tracks *h) {
     s.src64 = (const double *)h->d_src64.p;
 }
 
+// The per-iteration kernels are no-ops once SC_CONV is set (a converged
+// solve); the single-step entry points below clear it first on their stream.
+cudaError_t clear_conv(moc_tracks *h, cudaStream_t s) {
+    return cudaMemsetAsync((double *)h->d_scal.p + SC_CONV, 0, sizeof(double), s);
+}
+
 cudaError_t set_scalar(moc_tracks *h, int slot, double v) {
     return cudaMemcpyAsync((double *)h->d_scal.p + slot, &v, sizeof(double), cudaMemcpyHostToDevice,
                            h->stream);
@@ -230,23 +237,31 @@ int check_sweep_flag(moc_tracks *h) {
     return MOC_OK;
 }
 
+// Runs up to n outer iterations.  With stop_on_conv the scalars are checked
+// every kSyncEvery iterations: the iteration that converges sets SC_CONV on the
+// device and every later one is a no-op there, so the result does not depend
+// on how often the host looks.
+constexpr int kSyncEvery = 16;
+
 int run_iterations(moc_tracks *h, int n, bool stop_on_conv, bool graph, moc_result *res) {
     TRY(cudaSetDevice(h->device), "cudaSetDevice");
     if (graph) TRY(build_graphs(h), "graph capture");
+    TRY(cudaMemcpyAsync(h->h_scal, h->d_scal.p, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
+                        h->stream), "scalars");
+    TRY(cudaStreamSynchronize(h->stream), "scalars");
+    const int iter0 = (int)h->h_scal[SC_ITER];
+    const int cur0 = h->cur;
     cudaEvent_t e0, e1;
     TRY(cudaEventCreate(&e0), "event");
     TRY(cudaEventCreate(&e1), "event");
     TRY(cudaEventRecord(e0, h->stream), "event");
     int it = 0;
-    double seconds_total = 0.0;
     for (; it < n;) {
         if (graph) TRY(cudaGraphLaunch(h->graph[h->cur], h->stream), "graph launch");
         else TRY(enqueue_iteration(h, h->stream, h->cur), "iteration");
         if (h->has_psi) h->cur = 1 - h->cur;
         ++it;
-        // the convergence test needs this iteration's scalars on the host;
-        // a fixed count only synchronises once at the end
-        if (stop_on_conv) {
+        if (stop_on_conv && (it % kSyncEvery == 0 || it == n)) {
             TRY(cudaStreamSynchronize(h->stream), "iteration");
             if (h->h_scal[SC_CONV] != 0.0) break;
         }
@@ -255,10 +270,12 @@ int run_iterations(moc_tracks *h, int n, bool stop_on_conv, bool graph, moc_resu
     TRY(cudaEventSynchronize(e1), "event");
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
-    seconds_total = ms * 1e-3;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    fill_result(h, res, seconds_total, it);
+    // iterations that did work; the no-ops after convergence left psi in place
+    const int done = (int)h->h_scal[SC_ITER] - iter0;
+    if (h->has_psi) h->cur = (cur0 + done) & 1;
+    fill_result(h, res, ms * 1e-3, done);
     return check_sweep_flag(h);
 }
 
@@ -269,6 +286,8 @@ int init_state(moc_tracks *h) {
     h->cur = 0;
     TRY(set_scalar(h, SC_INTEG, 0.0), "scalar");
     TRY(set_scalar(h, SC_LEAK_PREV, 0.0), "scalar");
+    TRY(set_scalar(h, SC_TOLS, 0.0), "scalar");  // no convergence test unless a solve sets one
+    TRY(set_scalar(h, SC_TOLK, 0.0), "scalar");
     TRY(launch_init_state(h->dl, h->ds, h->geom.nfsr, h->red_grid, h->stream), "init state");
     TRY(cudaMemcpyAsync(h->h_scal, h->d_scal.p, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
                         h->stream), "scalars");
@@ -650,6 +669,7 @@ extern "C" int moc_update_source(moc_tracks *h, double k, void *stream) {
     cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
     double kk = k;
     TRY(cudaMemcpyAsync((double *)h->d_scal.p + SC_K, &kk, 8, cudaMemcpyHostToDevice, s), "scalar");
+    TRY(clear_conv(h, s), "scalar");
     TRY(launch_source(h->precision, h->dl, h->ds, h->geom.nfsr, h->red_grid, s), "source");
     TRY(cudaStreamSynchronize(s), "source");
     return MOC_OK;
@@ -659,6 +679,7 @@ extern "C" int moc_sweep(moc_tracks *h, void *stream) {
     if (!h) { moc_set_error("NULL handle"); return MOC_ERR_INVALID_ARG; }
     TRY(cudaSetDevice(h->device), "cudaSetDevice");
     cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+    TRY(clear_conv(h, s), "scalar");
     TRY(enqueue_sweep(h, s, h->cur), "sweep");
     if (h->has_psi) h->cur = 1 - h->cur;
     TRY(enqueue_finalize(h, s), "finalize");
@@ -671,6 +692,7 @@ extern "C" int moc_enqueue_source(moc_tracks *h, void *stream) {
     if (!h) { moc_set_error("NULL handle"); return MOC_ERR_INVALID_ARG; }
     TRY(cudaSetDevice(h->device), "cudaSetDevice");
     cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+    TRY(clear_conv(h, s), "scalar");
     TRY(launch_source(h->precision, h->dl, h->ds, h->geom.nfsr, h->red_grid, s), "source");
     return MOC_OK;
 }
@@ -679,6 +701,7 @@ extern "C" int moc_enqueue_sweep(moc_tracks *h, void *stream) {
     if (!h) { moc_set_error("NULL handle"); return MOC_ERR_INVALID_ARG; }
     TRY(cudaSetDevice(h->device), "cudaSetDevice");
     cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+    TRY(clear_conv(h, s), "scalar");
     TRY(enqueue_sweep(h, s, h->cur), "sweep");
     if (h->has_psi) h->cur = 1 - h->cur;
     return MOC_OK;
@@ -688,6 +711,7 @@ extern "C" int moc_enqueue_update(moc_tracks *h, void *stream) {
     if (!h) { moc_set_error("NULL handle"); return MOC_ERR_INVALID_ARG; }
     TRY(cudaSetDevice(h->device), "cudaSetDevice");
     cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+    TRY(clear_conv(h, s), "scalar");
     TRY(enqueue_finalize(h, s), "finalize");
     TRY(cudaMemcpyAsync(h->h_scal, h->d_scal.p, SC_COUNT * 8, cudaMemcpyDeviceToHost, s), "scalars");
     return MOC_OK;
@@ -704,6 +728,10 @@ extern "C" int moc_read_result(moc_tracks *h, void *stream, moc_result *res) {
 
 extern "C" int moc_iterate(moc_tracks *h, int32_t n, int32_t use_graph, moc_result *res) {
     if (!h || n < 0) { moc_set_error("bad arguments"); return MOC_ERR_INVALID_ARG; }
+    TRY(cudaSetDevice(h->device), "cudaSetDevice");
+    // exactly n iterations: no convergence test, and a converged state resumes
+    TRY(set_scalar(h, SC_TOLS, 0.0), "scalar");
+    TRY(set_scalar(h, SC_CONV, 0.0), "scalar");
     return run_iterations(h, n, false, use_graph != 0, res);
 }
 
@@ -915,6 +943,7 @@ extern "C" int moc_sweep_from_source(moc_tracks *h, const double *Q, double *tal
     }
     TRY(cudaMemsetAsync(h->d_tally.p, 0, n * 8, h->stream), "memset");
     TRY(set_scalar(h, SC_LEAK, 0.0), "scalar");
+    TRY(clear_conv(h, h->stream), "scalar");
     TRY(enqueue_sweep(h, h->stream, h->cur), "sweep");
     if (h->has_psi) h->cur = 1 - h->cur;
     if (tally) TRY(cudaMemcpyAsync(tally, h->d_tally.p, n * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
@@ -975,4 +1004,40 @@ extern "C" int moc_group_rates_static(moc_tracks *h, void *stream, double *rates
                         cudaMemcpyDeviceToHost, s), "copy");
     TRY(cudaStreamSynchronize(s), "rates");
     return MOC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Pieces of a solve for the serving engine (moc_server.cu): start a solve,
+// enqueue iterations without waiting, read the state once the stream is idle.
+// A converged solve's later iterations are no-ops on the device, so how many
+// iterations the engine enqueues between looks does not change the result.
+
+int tracks_start_solve(moc_tracks *h, const moc_solve_params *p) {
+    if (!h || !p || p->max_iter < 1) { moc_set_error("bad arguments"); return MOC_ERR_INVALID_ARG; }
+    TRY(cudaSetDevice(h->device), "cudaSetDevice");
+    int rc = init_state(h);
+    if (rc) return rc;
+    TRY(set_scalar(h, SC_TOLK, p->tol_k), "scalar");
+    TRY(set_scalar(h, SC_TOLS, p->tol_src), "scalar");
+    TRY(build_graphs(h), "graph capture");
+    return MOC_OK;
+}
+
+int tracks_enqueue_iterations(moc_tracks *h, int n, cudaEvent_t done) {
+    TRY(cudaSetDevice(h->device), "cudaSetDevice");
+    for (int i = 0; i < n; ++i) {
+        TRY(cudaGraphLaunch(h->graph[h->cur], h->stream), "graph launch");
+        if (h->has_psi) h->cur = 1 - h->cur;
+    }
+    TRY(cudaEventRecord(done, h->stream), "event");
+    return MOC_OK;
+}
+
+int tracks_read_state(moc_tracks *h, moc_result *res, int *converged) {
+    // the scalars were copied to the pinned mirror by the last iteration
+    const int done = (int)h->h_scal[SC_ITER];
+    *converged = h->h_scal[SC_CONV] != 0.0 ? 1 : 0;
+    if (*converged && h->has_psi) h->cur = done & 1;
+    fill_result(h, res, 0.0, done);
+    return check_sweep_flag(h);
 }

@@ -180,6 +180,7 @@ __global__ void k_stack_segments(DevLayout dl, int64_t s, const int64_t *offs, i
 // phi normalised on the fly by the latest scale; qr = Q / Sigma_t.
 template <typename real>
 __global__ void k_source(DevLayout dl, DevState st, int32_t nfsr) {
+    if (st.scal[SC_CONV] != 0.0) return;  // converged: later iterations are no-ops
     const int G = dl.G;
     const double scale = st.scal[SC_SCALE];
     const double k = st.scal[SC_K];
@@ -207,6 +208,7 @@ __global__ void k_source(DevLayout dl, DevState st, int32_t nfsr) {
 // production, absorption and (fixed source) the flux residual.
 template <typename real>
 __global__ void k_finalize(DevLayout dl, DevState st, int32_t nfsr) {
+    if (st.scal[SC_CONV] != 0.0) return;
     __shared__ double sh[32];
     const int G = dl.G;
     const bool eig = st.scal[SC_EIGEN] != 0.0;
@@ -245,7 +247,7 @@ __global__ void k_finalize(DevLayout dl, DevState st, int32_t nfsr) {
 
 // single block: production, absorption, k update and normalisation scale
 __global__ void k_reduce_k(DevState st, int nblocks, double integrations) {
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x != 0 || st.scal[SC_CONV] != 0.0) return;
     double P = 0, Ab = 0, r2 = 0, cnt = 0;
     for (int b = 0; b < nblocks; ++b) {
         P += st.partial[b * 4 + 0];
@@ -277,6 +279,7 @@ __global__ void k_reduce_k(DevState st, int nblocks, double integrations) {
 
 // eigenvalue residual: RMS relative change of the normalised fission rate
 __global__ void k_residual(DevState st, int32_t nfsr) {
+    if (st.scal[SC_CONV] != 0.0) return;
     __shared__ double sh[32];
     const double scale = st.scal[SC_SCALE];
     double r2 = 0, cnt = 0;
@@ -295,7 +298,7 @@ __global__ void k_residual(DevState st, int32_t nfsr) {
 }
 
 __global__ void k_reduce_res(DevState st, int nblocks) {
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x != 0 || st.scal[SC_CONV] != 0.0) return;
     double r2 = 0, cnt = 0;
     for (int b = 0; b < nblocks; ++b) {
         r2 += st.partial[b * 4 + 2];

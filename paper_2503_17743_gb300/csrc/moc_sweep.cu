@@ -242,6 +242,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
     const int j = lane / GL;         // slot: track of the warp task
     const int ql = lane & (GL - 1);  // lane of the slot: groups ql * GPL + c, c < GPL
     // shared layout: sig [M][GP] | rows [cap][GP][2] (Qr, Sigma_t) | tally [cap][GP]
+    if (st.scal[SC_CONV] != 0.0) return;  // converged: later iterations are no-ops
     real *sig = reinterpret_cast<real *>(smem);
     size_t off = ((size_t)M * GP * sizeof(real) + 15) & ~(size_t)15;
     real *rows = reinterpret_cast<real *>(smem + off);

@@ -1,0 +1,126 @@
+"""The serving engine (moc_server_*): every solve gives the same answer alone
+and in a mix of resident solves, admission respects the memory budget, and
+requests submitted while others run are served (continuous batching)."""
+import numpy as np
+import pytest
+
+import synth
+from paper_2503_17743_gb300 import Geometry, Server, Tracks, track_params
+
+pytestmark = pytest.mark.gpu
+
+TOL = dict(tol_k=1e-7, tol_src=1e-6, max_iter=4000)
+
+
+def requests(n, seed=5):
+    return [synth.serving_request(seed, i) for i in range(n)]
+
+
+def alone(p):
+    tr = Tracks(Geometry(p), track_params(p))
+    if p.ext_source is None:
+        r = tr.solve_eigen(**TOL)
+    else:
+        r = tr.solve_fixed_source(tol_src=TOL["tol_src"], max_iter=TOL["max_iter"])
+    phi, _ = tr.flux()
+    tr.close()
+    return r, phi
+
+
+def check_same(r_mix, phi_mix, r_alone, phi_alone):
+    # the same iterations on the same data: only the order of FP64 atomic
+    # adds into the global tally may differ
+    assert abs(r_mix["iterations"] - r_alone["iterations"]) <= 1
+    assert abs(r_mix["k"] - r_alone["k"]) < 1e-8
+    np.testing.assert_allclose(phi_mix, phi_alone, rtol=1e-6, atol=1e-12 * np.abs(phi_alone).max())
+
+
+def drain(srv, tickets, limit=100000):
+    out = {}
+    for _ in range(limit):
+        srv.step()
+        for t in tickets:
+            if t not in out:
+                r = srv.result(t)
+                if r is not None:
+                    out[t] = r
+        if len(out) == len(tickets):
+            return out
+    raise AssertionError("server did not finish")
+
+
+def test_mix_matches_alone():
+    probs = requests(8)
+    ref = [alone(p) for p in probs]
+    srv = Server(max_active=4, iterations_per_poll=8)
+    geoms = [Geometry(p) for p in probs]
+    tickets = [srv.submit(g, track_params(p), **TOL) for g, p in zip(geoms, probs)]
+    out = drain(srv, tickets)
+    for t, (r0, phi0) in zip(tickets, ref):
+        r, phi, queued, latency, rc = out[t]
+        assert rc == 0 and latency >= queued >= 0.0
+        check_same(r, phi, r0, phi0)
+    st = srv.stats()
+    assert st["retired"] == len(probs) and st["resident"] == 0 and st["queued"] == 0
+    assert 1 < st["max_resident"] <= 4
+    srv.close()
+
+
+def test_quantum_does_not_change_results():
+    probs = requests(3, seed=9)
+    res = []
+    for q in (1, 13):
+        srv = Server(max_active=3, iterations_per_poll=q)
+        geoms = [Geometry(p) for p in probs]
+        tickets = [srv.submit(g, track_params(p), **TOL) for g, p in zip(geoms, probs)]
+        out = drain(srv, tickets)
+        res.append([out[t] for t in tickets])
+        srv.close()
+    for a, b in zip(*res):
+        check_same(a[0], a[1], b[0], b[1])
+
+
+def test_memory_budget_limits_residency():
+    probs = requests(6, seed=11)
+    geoms = [Geometry(p) for p in probs]
+    params = [track_params(p) for p in probs]
+    foot = [sum(g.footprint(tp)) for g, tp in zip(geoms, params)]
+    budget = max(foot) + min(foot) // 2  # never room for the two largest together
+    srv = Server(max_active=6, memory_budget_bytes=budget)
+    tickets = [srv.submit(g, tp, **TOL) for g, tp in zip(geoms, params)]
+    peak = 0
+    out = {}
+    while len(out) < len(tickets):
+        srv.step()
+        st = srv.stats()
+        assert st["bytes_resident"] <= budget or st["resident"] == 1
+        peak = max(peak, st["resident"])
+        for t in tickets:
+            if t not in out:
+                r = srv.result(t)
+                if r is not None:
+                    out[t] = r
+    assert all(out[t][4] == 0 for t in tickets)
+    srv.close()
+
+
+def test_requests_arriving_while_others_run():
+    probs = requests(6, seed=13)
+    ref = [alone(p) for p in probs]
+    srv = Server(max_active=4)
+    geoms = [Geometry(p) for p in probs]
+    tickets = []
+    out = {}
+    for i, (g, p) in enumerate(zip(geoms, probs)):
+        tickets.append(srv.submit(g, track_params(p), **TOL))
+        for _ in range(2):  # a couple of steps before the next arrival
+            srv.step()
+            for t in tickets:
+                if t not in out:
+                    r = srv.result(t)
+                    if r is not None:
+                        out[t] = r
+    out.update({t: r for t, r in drain(srv, [t for t in tickets if t not in out]).items()})
+    for t, (r0, phi0) in zip(tickets, ref):
+        check_same(out[t][0], out[t][1], r0, phi0)
+    srv.close()
