@@ -285,6 +285,21 @@ def run_ours(args):
     except OSError:
         pass
     cpu = cpu_baseline(prob) if (world == 1 and not args.no_cpu_baseline) else None
+    # the same workload with FP64 sweeps (parity precision), device-resident
+    fp64 = None
+    if rank == 0 and args.fp64_steps > 0:
+        from paper_2503_17743_gb300 import MOC_FP64
+        t64 = Tracks(geom, track_params(prob, precision=MOC_FP64, device=local))
+        t64.iterate(3, use_graph=True)
+        r64 = t64.iterate(args.fp64_steps, use_graph=True)
+        fp64 = {"value": r64["integrations"] / r64["seconds"], "unit": UNIT,
+                "ms_per_step": r64["seconds"] / args.fp64_steps * 1e3, "steps": args.fp64_steps,
+                "dtype": "f64", "timing": "CUDA events around the graph launches of the steps"}
+        t64.close()
+    serving = None
+    if args.serving_requests > 0:
+        tr.close()
+        serving = run_serving(args.serving_requests, device=local)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_s / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -294,7 +309,8 @@ def run_ours(args):
                        "integrations_per_step": integ, "segments3d": info["segments3d"],
                        "l2": "flushed between timed steps (256 MiB write outside the events)",
                        "k_after_steps": res["k"]},
-            "roofline": roof, "clocks": clocks, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "clocks": clocks, "cpu_baseline": cpu, "e2e": e2e, "fp64": fp64,
+            "serving": serving,
             "gpu_launches": 6 * args.steps}
     print(json.dumps(line), flush=True)
 
@@ -314,6 +330,74 @@ def run_profile_driver(args):
     tr.close()
 
 
+SERVE_TOL = dict(tol_k=1e-7, tol_src=1e-6, max_iter=4000)
+
+
+def run_serving(n_requests, seed=1, load_factor=2.0, device=0):
+    """Serving stream (seeded serving_request mix: n x n lattices, 2-7 groups,
+    2-20 cm, 16-64 azimuths x 2-4 polar, half eigenvalue, half fixed source).
+    First every request is solved one at a time in arrival order (sequential
+    rate R); then the same requests arrive as a Poisson process at
+    load_factor x R into the serving engine.  Latency = completion time minus
+    scheduled arrival time."""
+    import numpy as np
+
+    import synth
+    from paper_2503_17743_gb300 import Geometry, Server, Tracks, track_params
+    probs = [synth.serving_request(seed, i) for i in range(n_requests)]
+    # sequential: one solve at a time, end to end through the C ABI
+    t0 = time.perf_counter()
+    ks = []
+    for p in probs:
+        tr = Tracks(Geometry(p), track_params(p, device=device))
+        if p.ext_source is None:
+            r = tr.solve_eigen(**SERVE_TOL)
+        else:
+            r = tr.solve_fixed_source(tol_src=SERVE_TOL["tol_src"], max_iter=SERVE_TOL["max_iter"])
+        tr.flux()
+        ks.append(r["k"])
+        tr.close()
+    t_seq = time.perf_counter() - t0
+    rate_seq = n_requests / t_seq
+    # batched: Poisson arrivals into the engine
+    rng = np.random.default_rng(seed + 1000)
+    arrivals = np.cumsum(rng.exponential(1.0 / (load_factor * rate_seq), size=n_requests))
+    srv = Server(device=device)
+    geoms, tickets, done = {}, {}, {}
+    t0 = time.perf_counter()
+    nxt = 0
+    while len(done) < n_requests:
+        now = time.perf_counter() - t0
+        while nxt < n_requests and arrivals[nxt] <= now:
+            p = probs[nxt]
+            geoms[nxt] = Geometry(p)
+            tickets[nxt] = srv.submit(geoms[nxt], track_params(p, device=device), **SERVE_TOL)
+            nxt += 1
+        if len(tickets) > len(done):
+            srv.step()
+            for i, t in tickets.items():
+                if i not in done:
+                    r = srv.result(t)
+                    if r is not None:
+                        done[i] = (time.perf_counter() - t0, r)
+                        del geoms[i]
+        elif nxt < n_requests:
+            time.sleep(max(0.0, min(0.002, arrivals[nxt] - (time.perf_counter() - t0))))
+    t_end = max(v[0] for v in done.values())
+    lat = np.array([done[i][0] - arrivals[i] for i in range(n_requests)])
+    kerr = max(abs(done[i][1][0]["k"] - ks[i]) for i in range(n_requests))
+    st = srv.stats()
+    srv.close()
+    return {"requests": n_requests, "load_factor": load_factor,
+            "sequential_solves_per_s": rate_seq, "solves_per_s": n_requests / (t_end - arrivals[0]),
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "max_resident": st["max_resident"], "max_k_diff_vs_sequential": kerr,
+            "tolerance": "tol_k 1e-7, tol_src 1e-6, FP32 sweeps",
+            "workload": f"seeded serving_request mix, seed {seed}: n x n pin lattices (n 1-17), 2-7 groups, "
+                        "2-20 cm, 16-64 azimuths x 2-4 polar, half eigenvalue / half fixed source, "
+                        "Poisson arrivals at load_factor x the sequential rate"}
+
+
 def golden_k():
     path = os.path.join(ROOT, "tests", "golden", "oracle_k.json")
     try:
@@ -330,6 +414,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-runs", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=5, help="timed FP64 steps (0 = skip)")
+    ap.add_argument("--serving-requests", type=int, default=48,
+                    help="requests of the serving leg (0 = skip)")
     ap.add_argument("--profile", action="store_true",
                     help="untimed 3 + 2 iterations (driver of the ncu captures)")
     ap.add_argument("--workload", default=WORKLOAD)
