@@ -257,6 +257,18 @@ int moc_track_psi(moc_tracks *tracks, int32_t t, int32_t p, int64_t i, int32_t s
  * the current boundary fluxes; returns the FSR tally [n_fsr*G] and leakage. */
 int moc_sweep_from_source(moc_tracks *tracks, const double *Q, double *tally, double *leakage);
 
+/* One sweep of only the 2D tracks t in [t0, t1) (every polar angle, both
+ * senses) from the isotropic source Q [n_fsr*G] (per steradian, FP64, host)
+ * with zero incoming boundary fluxes: a bounded sample of a sweep that an
+ * oracle can reproduce on large problems.  tally [n_fsr*G] (host, FP64) gets
+ * sum over those tracks' segments of W (psi_in - psi_out) (Eq. 4 before the
+ * division by volume); *leakage (may be NULL) their W psi leaving through
+ * vacuum faces.  Afterwards the stored boundary fluxes are undefined: call
+ * moc_reset before iterating.  Errors: MOC_ERR_INVALID_ARG (NULL, range
+ * outside [0, 2D tracks]), MOC_ERR_CUDA. */
+int moc_sweep_units_from_source(moc_tracks *tracks, const double *Q, int32_t t0, int32_t t1,
+                                double *tally, double *leakage);
+
 /* Group-wise reaction rates of the normalised scalar flux (the flux
  * moc_get_flux returns), computed on the device without allocating any
  * memory.  The paper has no counterpart: it is a library service for callers

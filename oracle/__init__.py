@@ -45,6 +45,7 @@ class _Input(C.Structure):
         ("n_azim", C.c_int), ("n_polar", C.c_int),
         ("radial_spacing", C.c_double), ("axial_spacing", C.c_double),
         ("n_threads", C.c_int),
+        ("light", C.c_int),
     ]
 
 
@@ -104,7 +105,9 @@ def _p(a, t):
 class Oracle:
     """FP64 CPU oracle for one synthetic problem (see ``synth.Problem``)."""
 
-    def __init__(self, prob, n_threads: int | None = None):
+    def __init__(self, prob, n_threads: int | None = None, light: bool = False):
+        """light: tracks and segments only (stack, sweep_sample): no links,
+        boundary fluxes or volumes, for sampled checks of large problems."""
         lib = _load()
         self.prob = prob
         self._keep = []
@@ -132,6 +135,7 @@ class Oracle:
         inp.n_azim, inp.n_polar = prob.n_azim, prob.n_polar
         inp.radial_spacing, inp.axial_spacing = prob.radial_spacing, prob.axial_spacing
         inp.n_threads = int(n_threads or os.cpu_count() or 1)
+        inp.light = 1 if light else 0
         self.n_threads = inp.n_threads
         err = C.create_string_buffer(256)
         h = lib.orc_create(C.byref(inp), err, 256)

@@ -57,6 +57,8 @@ typedef struct {
     int n_azim, n_polar;
     double radial_spacing, axial_spacing;
     int n_threads;
+    int light;  /* 1: tracks and segments only (no links, boundary fluxes or
+                   volumes): for sampled checks of problems too large to solve */
 } orc_input;
 
 /* faces */
@@ -772,6 +774,10 @@ void *orc_create(const orc_input *in, char *err, int errlen) {
     }
     o->stk_slot[nstk] = slot;
     o->n3d = slot;
+    if (in->light) {
+        o->phi = calloc((size_t)o->nfsr * G, sizeof(double));
+        return o;  /* stacks and segments only: orc_stack, orc_sweep_sample */
+    }
     o->dest = malloc(sizeof(long) * (size_t)(2 * o->n3d));
     int ok = 1;
     for (int t = 0; t < o->nt; t++)
@@ -925,6 +931,7 @@ int orc_stack_range(void *h, int t, int p, int64_t *out) {
 /* destination of (t, p, i, sense): out = t2, p2, i2, sense2 (all -1 if it leaks) */
 int orc_link(void *h, int t, int p, int64_t i, int sense, int64_t *out) {
     orc_t *o = (orc_t *)h;
+    if (!o->dest) return -1;
     long sl = slot_of(o, t, p, i);
     if (sl < 0) return -1;
     long d = o->dest[sl * 2 + sense];
@@ -945,6 +952,7 @@ int orc_link(void *h, int t, int p, int64_t i, int sense, int64_t *out) {
 
 int orc_volumes(void *h, double *V) {
     orc_t *o = (orc_t *)h;
+    if (!o->V) return -1;
     memcpy(V, o->V, sizeof(double) * (size_t)o->nfsr);
     return 0;
 }
@@ -1079,6 +1087,7 @@ int orc_set_threads(void *h, int n) { ((orc_t *)h)->nthreads = n > 0 ? n : 1; re
  * to one for eigenvalue problems) */
 int orc_reset(void *h) {
     orc_t *o = (orc_t *)h;
+    if (!o->psi0) return -1;
     size_t n = (size_t)o->nfsr * o->G;
     for (size_t q = 0; q < n; q++) o->phi[q] = 1.0;
     memset(o->psi0, 0, sizeof(double) * (size_t)o->n3d * 2 * o->G);
@@ -1104,6 +1113,7 @@ int orc_reset(void *h) {
  * fixed-source problems).  tol_src <= 0 runs exactly max_iter iterations. */
 int orc_iterate(void *h, int max_iter, double tol_k, double tol_src, double *out) {
     orc_t *o = (orc_t *)h;
+    if (!o->psi0) return -1;
     int G = o->G;
     size_t n = (size_t)o->nfsr * G;
     double *Q = malloc(sizeof(double) * n), *tally = malloc(sizeof(double) * n);
@@ -1178,6 +1188,7 @@ int orc_set_flux(void *h, const double *phi, double k) {
  * fluxes.  Used for sampled single-sweep parity and CPU timing. */
 int orc_sweep_once(void *h, const double *Q, double *tally, double *leak) {
     orc_t *o = (orc_t *)h;
+    if (!o->psi0) return -1;
     sweep(o, Q, tally, leak);
     return 0;
 }
@@ -1243,6 +1254,7 @@ int64_t orc_sweep_sample(void *h, const double *Q, int t0, int t1, double *tally
  * sweep for that track and direction */
 int orc_psi(void *h, int t, int p, int64_t i, int sense, double *val, int set) {
     orc_t *o = (orc_t *)h;
+    if (!o->psi0) return -1;
     long sl = slot_of(o, t, p, i);
     if (sl < 0) return -1;
     double *ps = o->psi0 + (sl * 2 + sense) * o->G;
@@ -1254,6 +1266,7 @@ int orc_psi(void *h, int t, int p, int64_t i, int sense, double *val, int set) {
 
 int orc_clear_psi(void *h) {
     orc_t *o = (orc_t *)h;
+    if (!o->psi0) return -1;
     memset(o->psi0, 0, sizeof(double) * (size_t)o->n3d * 2 * o->G);
     return 0;
 }

@@ -100,6 +100,7 @@ SIGNATURES = {
     "moc_track_psi": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.c_int32, f64p,
                                 C.c_int32]),
     "moc_sweep_from_source": (C.c_int, [C.c_void_p, f64p, f64p, f64p]),
+    "moc_sweep_units_from_source": (C.c_int, [C.c_void_p, f64p, C.c_int32, C.c_int32, f64p, f64p]),
     "moc_group_rates_static": (C.c_int, [C.c_void_p, C.c_void_p, f64p]),
     "moc_measure_ex2_rate": (C.c_int, [C.c_int32, f64p, f64p]),
     "moc_server_create": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -332,6 +333,16 @@ class Tracks:
         leak = C.c_double()
         _check(load().moc_sweep_from_source(self._h, _ptr(Q, f64p), _ptr(tally, f64p),
                                             C.byref(leak)))
+        return tally.reshape(self.n_fsr, self.G), leak.value
+
+    def sweep_units_from_source(self, Q, t0, t1):
+        """Tally and leakage of one sweep of the 2D tracks [t0, t1) from source
+        Q with zero incoming fluxes (the boundary fluxes are undefined after)."""
+        Q = np.ascontiguousarray(Q, dtype=np.float64).ravel()
+        tally = np.zeros(self.n_fsr * self.G)
+        leak = C.c_double()
+        _check(load().moc_sweep_units_from_source(self._h, _ptr(Q, f64p), int(t0), int(t1),
+                                                  _ptr(tally, f64p), C.byref(leak)))
         return tally.reshape(self.n_fsr, self.G), leak.value
 
     def group_rates_static(self, stream=None):

@@ -1006,6 +1006,51 @@ extern "C" int moc_group_rates_static(moc_tracks *h, void *stream, double *rates
     return MOC_OK;
 }
 
+extern "C" int moc_sweep_units_from_source(moc_tracks *h, const double *Q, int32_t t0, int32_t t1,
+                                           double *tally, double *leakage) {
+    if (!h || !Q || !tally) { moc_set_error("NULL argument"); return MOC_ERR_INVALID_ARG; }
+    if (t0 < 0 || t1 > h->L.nt || t0 > t1) { moc_set_error("2D track range out of bounds"); return MOC_ERR_INVALID_ARG; }
+    TRY(cudaSetDevice(h->device), "cudaSetDevice");
+    const moc_geometry &g = h->geom;
+    const size_t n = (size_t)g.nfsr * g.G;
+    std::vector<double> qr(n);
+    for (int i = 0; i < g.nfsr; ++i)
+        for (int gr = 0; gr < g.G; ++gr)
+            qr[(size_t)i * g.G + gr] = Q[(size_t)i * g.G + gr] / g.sigt[(size_t)g.fsr_mat[i] * g.G + gr];
+    if (real_size(h->precision) == 8) {
+        TRY(cudaMemcpyAsync(h->d_qr.p, qr.data(), n * 8, cudaMemcpyHostToDevice, h->stream), "upload");
+        TRY(cudaStreamSynchronize(h->stream), "upload");
+    } else {
+        std::vector<float> q32(qr.begin(), qr.end());
+        TRY(cudaMemcpyAsync(h->d_qr.p, q32.data(), n * 4, cudaMemcpyHostToDevice, h->stream), "upload");
+        TRY(cudaStreamSynchronize(h->stream), "upload");
+    }
+    std::vector<int32_t> units;
+    for (int32_t t : h->order)
+        if (t >= t0 && t < t1) units.push_back(t);
+    DevBuf d_units;
+    TRY(upload(h, d_units, units.empty() ? std::vector<int32_t>(1, 0) : units), "upload");
+    TRY(cudaMemsetAsync(h->d_tally.p, 0, n * 8, h->stream), "memset");
+    TRY(set_scalar(h, SC_LEAK, 0.0), "scalar");
+    TRY(set_scalar(h, SC_SCALE, 1.0), "scalar");
+    TRY(clear_conv(h, h->stream), "scalar");
+    TRY(cudaMemsetAsync(h->d_counter.p, 0, sizeof(int32_t), h->stream), "memset");
+    void *pout = h->has_psi ? h->d_psi[1 - h->cur].p : nullptr;
+    TRY(launch_sweep(h->precision, h->tally_smem, h->gpl, h->dl, h->ds, (const int32_t *)d_units.p,
+                     (int32_t)units.size(), h->tile_cap, nullptr, pout, h->grid, h->block, h->smem,
+                     h->stream), "sweep");
+    TRY(cudaMemcpyAsync(tally, h->d_tally.p, n * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
+    TRY(cudaMemcpyAsync(h->h_scal, h->d_scal.p, SC_COUNT * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
+    TRY(cudaStreamSynchronize(h->stream), "sweep");
+    h->bytes -= d_units.n;
+    if (leakage) *leakage = h->h_scal[SC_LEAK];
+    if (check_sweep_flag(h)) return MOC_ERR_CUDA;
+    TRY(cudaMemsetAsync(h->d_tally.p, 0, n * 8, h->stream), "memset");
+    TRY(set_scalar(h, SC_LEAK, 0.0), "scalar");
+    TRY(cudaStreamSynchronize(h->stream), "sweep");
+    return MOC_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Pieces of a solve for the serving engine (moc_server.cu): start a solve,
 // enqueue iterations without waiting, read the state once the stream is idle.
