@@ -182,7 +182,20 @@ def run_ours(args):
     load()
     prob = synth.workload(WORKLOAD)
     geom = Geometry(prob)
-    tr = Tracks(geom, track_params(prob, precision=MOC_FP32, device=local))
+    params = track_params(prob, precision=MOC_FP32, device=local)
+    schedule = None
+    if args.tune:
+        # the launch schedule (groups per lane, tally mode, preload split) from
+        # the project's autotuner; every candidate is timed outside the
+        # measured region
+        from paper_2503_17743_gb300 import autotune
+        params, t_best, table = autotune(geom, params, iterations=5)
+        schedule = {"groups_per_lane": params.groups_per_lane, "tally_mode": params.tally_mode,
+                    "preload_budget_bytes": params.preload_budget_bytes,
+                    "tuned_ms_per_iteration": t_best * 1e3,
+                    "candidates": [[int(r[0]), int(r[1]), int(r[2]), round(r[4] * 1e3, 4)] for r in table],
+                    "candidate_columns": ["groups_per_lane", "tally_mode", "preload_budget", "ms_per_iteration"]}
+    tr = Tracks(geom, params)
     info = tr.info
     integ = info["integrations_per_sweep"]
     stream = torch.cuda.Stream()
@@ -251,7 +264,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             g2 = Geometry(prob)
-            t2 = Tracks(g2, track_params(prob, precision=MOC_FP32, device=local))
+            t2 = Tracks(g2, params)
             r2 = t2.solve_eigen(tol_k=1e-7, tol_src=1e-6, max_iter=5000, use_graph=True, check=False)
             phi, k2 = t2.flux()
             dt = time.perf_counter() - t0
@@ -308,7 +321,7 @@ def run_ours(args):
                        "step": "one outer power iteration: source, sweep, flux/k/residual update",
                        "integrations_per_step": integ, "segments3d": info["segments3d"],
                        "l2": "flushed between timed steps (256 MiB write outside the events)",
-                       "k_after_steps": res["k"]},
+                       "k_after_steps": res["k"], "schedule": schedule},
             "roofline": roof, "clocks": clocks, "cpu_baseline": cpu, "e2e": e2e, "fp64": fp64,
             "serving": serving,
             "gpu_launches": 6 * args.steps}
@@ -415,6 +428,8 @@ def main():
     ap.add_argument("--e2e-runs", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=5, help="timed FP64 steps (0 = skip)")
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="skip the schedule autotuner (default parameters)")
     ap.add_argument("--serving-requests", type=int, default=48,
                     help="requests of the serving leg (0 = skip)")
     ap.add_argument("--profile", action="store_true",

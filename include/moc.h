@@ -300,6 +300,24 @@ int moc_group_rates_static(moc_tracks *tracks, void *stream, double *rates);
  * Errors: MOC_ERR_INVALID_ARG for NULL, MOC_ERR_CUDA. */
 int moc_measure_ex2_rate(int32_t device, double *ex2_per_second, double *sm_count);
 
+/* Autotuner of the sweep's launch schedule: generates the tracks of `geom`
+ * under every candidate schedule (energy groups per lane 1, 2, 4 for FP32
+ * sweeps; shared-memory or global tally; preload budget: everything stored,
+ * base->preload_budget_bytes when >= 0, nothing stored), times `iterations`
+ * outer iterations of each after 2 warm-up iterations (CUDA events), and
+ * writes the fastest schedule to *best (base's other fields unchanged, the
+ * tally mode resolved).  *seconds_per_iteration (may be NULL) is its time;
+ * report (may be NULL) gets up to max_report rows of 5 doubles: groups per
+ * lane, tally mode in use, preload budget, stored template pieces, seconds per
+ * iteration; *n_report the rows written.  The paper fixes its launch shape by
+ * hand; this tunes it per problem.  Runs on base->device and frees
+ * everything it generated.  Errors: MOC_ERR_INVALID_ARG (NULL, iterations <
+ * 1), MOC_ERR_UNSUPPORTED (no candidate could be generated), errors of
+ * moc_generate_tracks and moc_iterate. */
+int moc_autotune(const moc_geometry *geom, const moc_track_params *base, int32_t iterations,
+                 moc_track_params *best, double *seconds_per_iteration, int32_t max_report,
+                 double *report, int32_t *n_report);
+
 /* ---------------------------------------------------------------------------
  * Serving engine: independent eigenvalue and fixed-source solves of different
  * geometries, group counts and track layouts, kept resident on one device and

@@ -103,6 +103,8 @@ SIGNATURES = {
     "moc_sweep_units_from_source": (C.c_int, [C.c_void_p, f64p, C.c_int32, C.c_int32, f64p, f64p]),
     "moc_group_rates_static": (C.c_int, [C.c_void_p, C.c_void_p, f64p]),
     "moc_measure_ex2_rate": (C.c_int, [C.c_int32, f64p, f64p]),
+    "moc_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, f64p, C.c_int32,
+                               f64p, i32p]),
     "moc_server_create": (C.c_int, [C.c_void_p, C.c_void_p]),
     "moc_server_destroy": (None, [C.c_void_p]),
     "moc_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, i64p]),
@@ -429,3 +431,16 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def autotune(geom, params, iterations=5):
+    """moc_autotune: (best track parameters, seconds per iteration, table of
+    the candidates [groups per lane, tally mode, preload budget, stored
+    pieces, seconds per iteration])."""
+    best = moc_track_params()
+    sec = C.c_double()
+    rep = np.zeros((64, 5))
+    n = C.c_int32()
+    _check(load().moc_autotune(geom._h, C.byref(params), int(iterations), C.byref(best),
+                               C.byref(sec), 64, _ptr(rep, f64p), C.byref(n)))
+    return best, sec.value, rep[:n.value].copy()

@@ -21,7 +21,7 @@ INCLUDE = os.path.join(ROOT, "include")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["moc_kernels.cu", "moc_sweep.cu", "moc_api.cu", "moc_static.cu", "moc_peak.cu",
-              "moc_server.cu"]
+              "moc_server.cu", "moc_tune.cu"]
 CPP_SOURCES = ["moc_host.cpp"]
 
 
