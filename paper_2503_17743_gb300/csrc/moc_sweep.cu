@@ -222,6 +222,9 @@ struct TallyAdd<double, 1> {
     }
 };
 
+// words per shared tally row
+__host__ __device__ constexpr int tally_stride(int GL, int GPL) { return GL * GPL + (GPL > 1 ? 1 : 0); }
+
 template <typename real, int GL, int GPL, bool SMEM>
 __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
     k_sweep(DevLayout dl, DevState st, const int32_t *order, int32_t n_work, int32_t cap,
@@ -241,7 +244,10 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int j = lane / GL;         // slot: track of the warp task
     const int ql = lane & (GL - 1);  // lane of the slot: groups ql * GPL + c, c < GPL
-    // shared layout: sig [M][GP] | rows [cap][GP][2] (Qr, Sigma_t) | tally [cap][GP]
+    // shared layout: sig [M][GP] | rows [cap][GP][2] (Qr, Sigma_t) | tally [cap][TS]; with
+    // several groups per lane the tally rows are padded by one word so that
+    // the rows of the warp's eight or more slots spread over the banks
+    constexpr int TS = tally_stride(GL, GPL);
     if (st.scal[SC_CONV] != 0.0) return;  // converged: later iterations are no-ops
     real *sig = reinterpret_cast<real *>(smem);
     size_t off = ((size_t)M * GP * sizeof(real) + 15) & ~(size_t)15;
@@ -314,6 +320,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
                         const int L = x / GP, qq = x - L * GP;
                         const int f = reg * NL + L;
                         const int e = (b * NL + L) * GP + qq;
+                        const int et = (b * NL + L) * TS + qq;
                         real q = (real)0, sg = (real)0;
                         if (qq < gc) {
                             const int m = __ldg(dl.fsr_mat + f);
@@ -323,7 +330,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
                         }
                         rows[2 * e] = q;
                         rows[2 * e + 1] = sg;
-                        tl_s[e] = (real)0;
+                        tl_s[et] = (real)0;
                         if (kFixed) bmax = fmaxf(bmax, fabsf((float)q));
                     }
                 }
@@ -407,6 +414,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
                     real tU[GPL], tD[GPL];
                     if (SMEM) {
                         const int eU = rU * GP + qlo, eD = rD * GP + qlo;
+                        const int tU_ = rU * TS + qlo, tD_ = rD * TS + qlo;
                         real qU[GPL], sU[GPL], qD[GPL], sD[GPL];
                         RowLoadS<real, GPL>::get(rows_sa + eU * (unsigned)(2 * sizeof(real)), qU, sU);
                         RowLoadS<real, GPL>::get(rows_sa + eD * (unsigned)(2 * sizeof(real)), qD, sD);
@@ -427,14 +435,14 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
                             // integer in the low mantissa bits (|t scl| < 2^22)
 #pragma unroll
                             for (int c = 0; c < GPL; ++c) {
-                                shared_red_add(tl_sa + (eU + c) * 4u,
+                                shared_red_add(tl_sa + (tU_ + c) * 4u,
                                                __float_as_int(fmaf((float)tU[c], scl[c], 12582912.0f)) - 0x4B400000);
-                                shared_red_add(tl_sa + (eD + c) * 4u,
+                                shared_red_add(tl_sa + (tD_ + c) * 4u,
                                                __float_as_int(fmaf((float)tD[c], scl[c], 12582912.0f)) - 0x4B400000);
                             }
                         } else {
-                            TallyAdd<real, GPL>::add(tl_s + eU, tU, err);
-                            TallyAdd<real, GPL>::add(tl_s + eD, tD, err);
+                            TallyAdd<real, GPL>::add(tl_s + tU_, tU, err);
+                            TallyAdd<real, GPL>::add(tl_s + tD_, tD, err);
                         }
                     } else {
                         const int b = rU / NL, L = rU - b * NL, LD = NL - 1 - L;
@@ -468,12 +476,14 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
 #pragma unroll
                         for (int i = 0; i < 4; ++i) visit(rU[i], rD[i], len[i]);
                     } else {
-                        int eU[4], eD[4];
+                        int eU[4], eD[4], fU[4], fD[4];
                         real qU[4][GPL], sU[4][GPL], qD[4][GPL], sD[4][GPL];
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             eU[i] = rU[i] * GP + qlo;
                             eD[i] = rD[i] * GP + qlo;
+                            fU[i] = rU[i] * TS + qlo;
+                            fD[i] = rD[i] * TS + qlo;
                             RowLoadS<real, GPL>::get(rows_sa + eU[i] * (unsigned)(2 * sizeof(real)), qU[i], sU[i]);
                             RowLoadS<real, GPL>::get(rows_sa + eD[i] * (unsigned)(2 * sizeof(real)), qD[i], sD[i]);
                         }
@@ -500,14 +510,14 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
                             if constexpr (kFixed) {
 #pragma unroll
                                 for (int c = 0; c < GPL; ++c) {
-                                    shared_red_add(tl_sa + (eU[i] + c) * 4u,
+                                    shared_red_add(tl_sa + (fU[i] + c) * 4u,
                                                    __float_as_int(fmaf((float)tU[i][c], scl[c], 12582912.0f)) - 0x4B400000);
-                                    shared_red_add(tl_sa + (eD[i] + c) * 4u,
+                                    shared_red_add(tl_sa + (fD[i] + c) * 4u,
                                                    __float_as_int(fmaf((float)tD[i][c], scl[c], 12582912.0f)) - 0x4B400000);
                                 }
                             } else {
-                                TallyAdd<real, GPL>::add(tl_s + eU[i], tU[i], err);
-                                TallyAdd<real, GPL>::add(tl_s + eD[i], tD[i], err);
+                                TallyAdd<real, GPL>::add(tl_s + fU[i], tU[i], err);
+                                TallyAdd<real, GPL>::add(tl_s + fD[i], tD[i], err);
                             }
                         }
                     }
@@ -605,7 +615,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
                     for (int x = lane; x < NL * GP; x += 32) {
                         const int L = x / GP, qq = x - L * GP;
                         if (qq >= gc) continue;
-                        const int e = (b * NL + L) * GP + qq;
+                        const int e = (b * NL + L) * TS + qq;
                         const double v = kFixed ? (double)((float)tl_i[e] * s_inv[qq]) : (double)tl_s[e];
                         if (v != 0.0) atomicAdd(st.tally + ((size_t)reg * NL + L) * G + g0 + qq, v);
                     }
@@ -654,10 +664,10 @@ const void *sweep_fn(int precision, int tally_smem, int G, int gpl) {
 
 }  // namespace
 
+// two groups per lane in FP32 (half the per-segment bookkeeping per
+// integration; the autotuner's usual pick), one in FP64
 int sweep_default_gpl(int precision, int G) {
-    (void)precision;
-    (void)G;
-    return 1;
+    return (precision == MOC_FP32 && G > 1) ? 2 : 1;
 }
 
 int sweep_lanes_per_track(int G, int gpl) { return lanes_for_groups(G, gpl); }
@@ -666,7 +676,8 @@ size_t sweep_smem_bytes(int precision, int tally_smem, int M, int G, int gpl, in
     const size_t rs = precision == MOC_FP64 ? 8 : 4;
     const size_t gp = (size_t)lanes_for_groups(G, gpl) * gpl;
     size_t b = ((size_t)M * gp * rs + 15) & ~(size_t)15;
-    if (tally_smem) b += (size_t)cap * gp * rs * 3;  // (Qr, Sigma_t) rows + tally rows
+    if (tally_smem)  // (Qr, Sigma_t) rows + tally rows
+        b += (size_t)cap * gp * rs * 2 + (size_t)cap * tally_stride((int)(gp / gpl), gpl) * rs;
     return b;
 }
 
