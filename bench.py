@@ -53,6 +53,21 @@ def dist_env():
     return rank, world, local
 
 
+def whole_job_rate(local_seconds, units_per_rank, world, device=None):
+    """Whole-job rate of weakly scaled replicas: every rank processed
+    units_per_rank units in local_seconds; the job's time is the slowest
+    rank's (an all-reduce MAX over the default process group when world > 1).
+    Returns (units per second over all ranks, job seconds)."""
+    total_s = float(local_seconds)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_s], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    return world * units_per_rank / total_s, total_s
+
+
 def clock_sampler(device, path):
     q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -247,13 +262,8 @@ def run_ours(args):
         clk_file.close()
     step_ms = [e[0].elapsed_time(e[3]) for e in steps]
     sweep_ms = [e[1].elapsed_time(e[2]) for e in steps]
-    total_s = sum(step_ms) * 1e-3
     res = tr.read_result(sp)
-    if world > 1:
-        t = torch.tensor([total_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * integ * args.steps / total_s
+    value, total_s = whole_job_rate(sum(step_ms) * 1e-3, integ * args.steps, world, device="cuda")
 
     # end to end through the C ABI from host arrays: geometry, tracks, a
     # converged eigenvalue solve, the flux read back
