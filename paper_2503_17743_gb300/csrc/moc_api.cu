@@ -36,7 +36,7 @@ struct moc_tracks {
     // device buffers
     DevBuf d_desc, d_zn, d_zf, d_zf64, d_reg2d, d_len2d, d_len2d64, d_segs, d_fsr_mat, d_order;
     DevBuf d_tpl_off, d_tpl_loff, d_tpl_lmin, d_tpl_lidx;
-    DevBuf d_dst, d_perm;
+    DevBuf d_dst, d_perm, d_win;
     DevBuf d_phi, d_qr, d_tally, d_vol, d_psi[2], d_fiss, d_fiss_old, d_partial, d_scal, d_counter;
     DevBuf d_sigt, d_sigt64, d_sigs64, d_nsf64, d_chi64, d_src64;
     double *h_scal = nullptr;  // pinned mirror of the device scalars
@@ -124,6 +124,7 @@ void fill_views(moc_tracks *h) {
     dl.fsr_mat = (const int32_t *)h->d_fsr_mat.p;
     dl.dst = (const int64_t *)h->d_dst.p;
     dl.perm = (const int32_t *)h->d_perm.p;
+    dl.win = (const uint64_t *)h->d_win.p;
     dl.Ph = h->L.Ph;
     dl.Nz = h->L.Nz;
     dl.cpl = h->L.cpl;
@@ -331,7 +332,8 @@ extern "C" int moc_query_footprint(const moc_geometry *g, const moc_track_params
     b += (int64_t)g->nfsr * G * (8 + rs + 8) + (int64_t)g->nfsr * 8 * 3;
     bool refl = false;
     for (int f = 0; f < 6; ++f) refl |= g->bc[f] != 0;
-    if (refl) b += 2 * L.n_gtrk * 4 * G * (int64_t)rs;
+    if (refl) b += 2 * L.n_gtrk * 4 * G * (int64_t)rs + L.n_gtrk * 4 * 8;  // boundary fluxes, links
+    b += L.n_gtrk * (4 + 8);  // sweep order and record windows
     if (resident) *resident = b;
     if (preload_all) {
         // an upper estimate from the 2D segments: each 3D track crosses its 2D
@@ -533,6 +535,7 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
                      (int64_t)(L.desc[s].nb + 1) * geo.nl + 2000 < 32768;
             }
         }
+        ok = ok && h->max_nseg < 65536;  // record windows hold the count in 16 bits
         if (!ok || (budget >= 0 && used + need > budget)) {
             for (int ph = 0; ph < Ph; ++ph) L.desc[(int64_t)t * Ph + ph].exp_base = -1;
             continue;
@@ -565,6 +568,9 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
         const int egrid = (int)std::max<int64_t>(1, std::min<int64_t>(h->n_exp_stacks, (int64_t)h->sms * 16));
         TRY(launch_tpl_write(h->precision, h->dl, (const int32_t *)d_exp_stacks.p, h->n_exp_stacks,
                              h->d_segs.p, (int32_t *)h->d_tpl_lidx.p, egrid, h->stream), "templates");
+        TRY(dalloc(h.get(), h->d_win, (size_t)L.n_gtrk * 8), "alloc record windows");
+        fill_views(h.get());
+        TRY(launch_windows(h->dl, ns, (uint64_t *)h->d_win.p, lgrid, h->stream), "record windows");
         TRY(cudaStreamSynchronize(h->stream), "templates");
         h->bytes -= d_exp_stacks.n;
     }

@@ -112,6 +112,29 @@ __global__ void k_tpl_write(DevLayout dl, const int32_t *exp_stacks, int64_t n_e
 
 // destination of the outgoing flux of every stored track direction (slot
 // gid*4+v of the next sweep's incoming flux, -1 at a vacuum face)
+// Record window of every track of a stored stack, in the stack's sweep order
+// (perm): track r + m cpl of class r is the pieces of template r whose layer
+// lies in [-m, NL - m), a contiguous record range; stored as (count << 48) |
+// first record.
+__global__ void k_windows(DevLayout dl, int64_t n_stacks, uint64_t *win) {
+    for (int64_t s = blockIdx.x; s < n_stacks; s += gridDim.x) {
+        const StackDesc &d = dl.desc[s];
+        if (d.exp_base < 0) continue;
+        for (int q = threadIdx.x; q < d.n_trk; q += blockDim.x) {
+            const int k = dl.perm[d.trk_off + q];
+            const int r = k % dl.cpl, m = k / dl.cpl;
+            const int64_t tpl = d.exp_base + r;
+            const int Lmin = dl.tpl_lmin[tpl];
+            const int64_t lb = dl.tpl_loff[tpl];
+            const int nL = (int)(dl.tpl_loff[tpl + 1] - lb) - 1;
+            const int64_t tb = dl.tpl_off[tpl];
+            const int64_t p0 = tb + dl.tpl_lidx[lb + min(max(-m - Lmin, 0), nL)];
+            const int64_t p1 = tb + dl.tpl_lidx[lb + min(max(dl.NL - m - Lmin, 0), nL)];
+            win[d.trk_off + q] = ((uint64_t)(p1 - p0) << 48) | (uint64_t)p0;
+        }
+    }
+}
+
 __global__ void k_links(DevLayout dl, int64_t n_stacks, int64_t *dst) {
     for (int64_t s = blockIdx.x; s < n_stacks; s += gridDim.x) {
         const StackDesc d = dl.desc[s];
@@ -397,6 +420,12 @@ __global__ void k_track_counts(DevLayout dl, int64_t s, int64_t *cnt) {
 
 cudaError_t launch_track_counts(const DevLayout &dl, int64_t stack, int64_t *cnt, cudaStream_t s) {
     k_track_counts<<<1, 128, 0, s>>>(dl, stack, cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_windows(const DevLayout &dl, int64_t n_stacks, uint64_t *win, int grid,
+                           cudaStream_t s) {
+    k_windows<<<grid, 128, 0, s>>>(dl, n_stacks, win);
     return cudaGetLastError();
 }
 

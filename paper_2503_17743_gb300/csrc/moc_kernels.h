@@ -14,6 +14,9 @@ cudaError_t launch_tpl_write(int precision, const DevLayout &dl, const int32_t *
                              int64_t n_exp, void *recs, int32_t *lidx, int grid, cudaStream_t s);
 size_t segrec_size(int precision);
 cudaError_t launch_track_counts(const DevLayout &dl, int64_t stack, int64_t *cnt, cudaStream_t s);
+// per track of the stored stacks, in sweep order: (record count << 48) | first record
+cudaError_t launch_windows(const DevLayout &dl, int64_t n_stacks, uint64_t *win, int grid,
+                           cudaStream_t s);
 cudaError_t launch_links(const DevLayout &dl, int64_t n_stacks, int64_t *dst, int grid,
                          cudaStream_t s);
 cudaError_t launch_volumes(int precision, const DevLayout &dl, int64_t n_stacks, double *vol,

@@ -526,17 +526,11 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
                     // stored template of class r (line i_lo + r): this track is its
                     // pieces with template layer in [-m, NL - m), a contiguous record
                     // range because the layer never decreases along an upward line
-                    int64_t p0 = 0, p1 = 0;
-                    if (valid) {
-                        const int64_t tpl = u.tpl_base + r;
-                        const int Lmin = dl.tpl_lmin[tpl];
-                        const int64_t lb = dl.tpl_loff[tpl];
-                        const int nL = (int)(dl.tpl_loff[tpl + 1] - lb) - 1;
-                        const int64_t tb = dl.tpl_off[tpl];
-                        p0 = tb + dl.tpl_lidx[lb + min(max(-m - Lmin, 0), nL)];
-                        p1 = tb + dl.tpl_lidx[lb + min(max(NL - m - Lmin, 0), nL)];
-                    }
-                    const int n = (int)(p1 - p0);
+                    // (precomputed per track in sweep order: count << 48 | first record)
+                    const uint64_t wn = valid ? __ldg(dl.win + u.trk_off + q) : 0ull;
+                    const int64_t p0 = (int64_t)(wn & 0xffffffffffffull);
+                    const int n = (int)(wn >> 48);
+                    const int64_t p1 = p0 + n;
                     const int dir = sense == 0 ? 1 : -1;
                     const SegRec<real> *pr = recs + (sense == 0 ? p0 : p1 - 1);
                     // all slots step together to the longest track of the warp; a
