@@ -333,8 +333,9 @@ int moc_autotune(const moc_geometry *geom, const moc_track_params *base, int32_t
  * waits for the oldest quantum in flight and retires every solve whose
  * stopping rule held or that reached max_iter.  Iterations after convergence
  * are no-ops on the device, so a solve's result does not depend on the mix it
- * ran in.  One host thread drives an engine; calls on one engine must not
- * overlap. */
+ * ran in.  Track generation of admitted requests runs on 4 host worker
+ * threads inside the engine, so it overlaps the resident solves' work.  One
+ * host thread drives an engine; calls on one engine must not overlap. */
 typedef struct {
     int32_t device;
     int32_t max_active;           /* resident solves at most (0 = 16) */

@@ -67,7 +67,7 @@ def build(force: bool = False, verbose: bool = False, extra_nvcc=()) -> str:
         for o in outs:
             sys.stdout.write(o)
     tmp = LIB + ".tmp"
-    _run([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+    _run([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"])
     os.replace(tmp, LIB)
     return LIB
 

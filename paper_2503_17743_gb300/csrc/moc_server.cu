@@ -13,14 +13,21 @@
 //   device, then waits for the oldest quantum in flight and retires every
 //   solve whose stopping rule held (or that reached max_iter), freeing its
 //   slot and memory for the queue.
+// * Track generation (host laydown and tracing, device tables, graph capture)
+//   runs on a pool of host worker threads, so admitting a request does not
+//   stall the quanta of the resident solves.
 // * A converged solve's later iterations are no-ops on the device, so the
 //   quantum does not change any result: a solve gives the same answer alone
 //   and in any mix (up to the order of floating-point atomic adds).
 #include <chrono>
+#include <condition_variable>
 #include <deque>
 #include <map>
 #include <memory>
+#include <mutex>
+#include <set>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "moc_serve.h"
@@ -48,6 +55,8 @@ struct Slot {
     int enqueued = 0;
     bool in_flight = false;
     double t_start = 0;
+    int gen_status = MOC_OK;  // outcome of the generation on a worker thread
+    std::string gen_error;
 };
 
 struct Finished {
@@ -71,12 +80,61 @@ struct moc_server {
     std::deque<Request> queue;
     std::vector<std::unique_ptr<Slot>> active;
     std::map<int64_t, Finished> done;
+    // generation on worker threads: `generating` counts admitted requests not
+    // yet resident; `to_gen` / `gen_done` are guarded by `mu`
+    int generating = 0;
+    std::set<int64_t> gen_tickets;  // main thread only
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::unique_ptr<Slot>> to_gen, gen_done;
+    bool stop = false;
+    std::vector<std::thread> workers;
+
+    void worker() {
+        cudaSetDevice(device);
+        for (;;) {
+            std::unique_ptr<Slot> s;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv_work.wait(lk, [&] { return stop || !to_gen.empty(); });
+                if (stop && to_gen.empty()) return;
+                s = std::move(to_gen.front());
+                to_gen.pop_front();
+            }
+            int rc = moc_generate_tracks(s->req.geom.get(), &s->req.tp, &s->tr);
+            if (rc == MOC_OK) rc = tracks_start_solve(s->tr, &s->req.sp);
+            if (rc == MOC_OK && cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess) {
+                moc_set_error("cudaEventCreate failed");
+                rc = MOC_ERR_CUDA;
+            }
+            s->gen_status = rc;
+            if (rc != MOC_OK) s->gen_error = moc_last_error();
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                gen_done.push_back(std::move(s));
+            }
+            cv_done.notify_all();
+        }
+    }
+
+    void start_workers(int n) {
+        for (int i = 0; i < n; ++i) workers.emplace_back([this] { worker(); });
+    }
 
     ~moc_server() {
-        for (auto &s : active) {
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            stop = true;
+        }
+        cv_work.notify_all();
+        for (auto &t : workers) t.join();
+        auto drop = [](std::unique_ptr<Slot> &s) {
             if (s->tr) moc_destroy_tracks(s->tr);
             if (s->ev) cudaEventDestroy(s->ev);
-        }
+        };
+        for (auto &s : active) drop(s);
+        for (auto &s : to_gen) drop(s);
+        for (auto &s : gen_done) drop(s);
     }
 
     void finish(std::unique_ptr<Slot> &s, int status, const std::string &err) {
@@ -110,22 +168,42 @@ struct moc_server {
         ++n_finished;
     }
 
-    // admit queued requests while a slot and the memory allow
+    // admit queued requests while a slot and the memory allow; their tracks
+    // are generated on the worker threads
     void admit() {
-        while (!queue.empty() && (int)active.size() < max_active &&
-               (active.empty() || bytes_resident + queue.front().bytes <= budget)) {
+        int added = 0;
+        while (!queue.empty() && (int)active.size() + generating < max_active &&
+               ((active.empty() && generating == 0) || bytes_resident + queue.front().bytes <= budget)) {
             auto s = std::make_unique<Slot>();
             s->req = std::move(queue.front());
             queue.pop_front();
             s->t_start = now_seconds();
             bytes_resident += s->req.bytes;
             ++n_admitted;
-            int rc = moc_generate_tracks(s->req.geom.get(), &s->req.tp, &s->tr);
-            if (rc == MOC_OK) rc = tracks_start_solve(s->tr, &s->req.sp);
-            if (rc == MOC_OK && cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess)
-                rc = MOC_ERR_CUDA;
-            if (rc != MOC_OK) {
-                finish(s, rc, moc_last_error());
+            ++generating;
+            ++added;
+            gen_tickets.insert(s->req.ticket);
+            std::lock_guard<std::mutex> lk(mu);
+            to_gen.push_back(std::move(s));
+        }
+        if (added) cv_work.notify_all();
+    }
+
+    // generated requests become resident (or finish with their error); with
+    // `wait` and nothing resident, block until one generation completes
+    void take_generated(bool wait) {
+        std::deque<std::unique_ptr<Slot>> got;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            if (wait && gen_done.empty() && generating > 0)
+                cv_done.wait_for(lk, std::chrono::milliseconds(200), [&] { return !gen_done.empty(); });
+            got.swap(gen_done);
+        }
+        for (auto &s : got) {
+            --generating;
+            gen_tickets.erase(s->req.ticket);
+            if (s->gen_status != MOC_OK) {
+                finish(s, s->gen_status, s->gen_error);
                 continue;
             }
             active.push_back(std::move(s));
@@ -194,6 +272,7 @@ extern "C" int moc_server_create(const moc_server_params *p, moc_server **out) {
         }
         s->budget = (int64_t)(0.8 * (double)free_b);
     }
+    s->start_workers(4);
     *out = s.release();
     return MOC_OK;
 }
@@ -230,6 +309,7 @@ extern "C" int moc_server_step(moc_server *s, int32_t *finished, int32_t *pendin
     if (cudaSetDevice(s->device) != cudaSuccess) { moc_set_error("cudaSetDevice failed"); return MOC_ERR_CUDA; }
     int nf = 0;
     s->admit();
+    s->take_generated(s->active.empty());
     int rc = s->launch();
     if (rc) return rc;
     // wait for the oldest quantum in flight, then retire what is done and
@@ -242,10 +322,11 @@ extern "C" int moc_server_step(moc_server *s, int32_t *finished, int32_t *pendin
     }
     s->collect(&nf);
     s->admit();
+    s->take_generated(false);
     rc = s->launch();
     if (rc) return rc;
     if (finished) *finished = nf;
-    if (pending) *pending = (int32_t)(s->queue.size() + s->active.size());
+    if (pending) *pending = (int32_t)(s->queue.size() + s->active.size() + s->generating);
     return MOC_OK;
 }
 
@@ -257,6 +338,7 @@ extern "C" int moc_server_result(moc_server *s, int64_t ticket, moc_result *res,
         bool known = false;
         for (auto &r : s->queue) known |= r.ticket == ticket;
         for (auto &a : s->active) known |= a->req.ticket == ticket;
+        known |= s->gen_tickets.count(ticket) > 0;
         if (!known) { moc_set_error("moc_server_result: unknown or already fetched ticket"); return MOC_ERR_INVALID_ARG; }
         *ready = 0;
         return MOC_OK;
@@ -280,7 +362,7 @@ extern "C" int moc_server_result(moc_server *s, int64_t ticket, moc_result *res,
 
 extern "C" int moc_server_stats(const moc_server *s, int64_t *out, int32_t n) {
     if (!s || !out) { moc_set_error("NULL argument"); return MOC_ERR_INVALID_ARG; }
-    const int64_t v[7] = {(int64_t)s->queue.size(), (int64_t)s->active.size(), s->n_admitted,
+    const int64_t v[7] = {(int64_t)s->queue.size() + s->generating, (int64_t)s->active.size(), s->n_admitted,
                           s->n_finished, s->bytes_resident, s->budget, s->max_resident};
     for (int i = 0; i < n && i < 7; ++i) out[i] = v[i];
     return MOC_OK;
