@@ -26,9 +26,11 @@
 // tally (SMEM = false) pieces read Qr from global memory and add straight into
 // the FP64 global tally.
 //
-// psi is carried multiplied by the track weight W: with d = W (psi - Qr) the
-// attenuated change W (psi_in - psi_out) = d (1 - e^{-Sigma_t l}) is both the
-// tally contribution and the psi update (Eq. 3, Eq. 4).
+// psi is carried multiplied by the track weight W and by the group's
+// fixed-point tally scale S (1 without a fixed-point tile): with
+// d = W S (psi - Qr) the attenuated change W S (psi_in - psi_out) =
+// d (1 - e^{-Sigma_t l}) is both the psi update and the tally contribution in
+// tally units (Eq. 3, Eq. 4), rounded to an integer by one conversion.
 #include <climits>
 
 #include "moc_device.cuh"
@@ -385,6 +387,17 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
                 float scl[GPL];
 #pragma unroll
                 for (int c = 0; c < GPL; ++c) scl[c] = kFixed && SMEM ? s_scl[ql * GPL + c] : 1.0f;
+                // psi is carried as W S psi, S the group's fixed-point scale (1 when
+                // the tally is not in fixed point), so that the change of the
+                // carried value is the tally contribution in tally units
+                real WS[GPL], iWS[GPL], iS[GPL];
+#pragma unroll
+                for (int c = 0; c < GPL; ++c) {
+                    const real is = kFixed && SMEM ? (real)s_inv[ql * GPL + c] : (real)1;
+                    WS[c] = W * (real)scl[c];
+                    iWS[c] = invW * is;
+                    iS[c] = is;
+                }
                 real psiU[GPL], psiD[GPL];
 #pragma unroll
                 for (int c = 0; c < GPL; ++c) {
@@ -398,8 +411,8 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
                         for (int c = 0; c < GPL; ++c) {
                             const int qq = ql * GPL + c;
                             if (qq < gc) {
-                                psiU[c] = psi_in[(gid * 4 + 0 * 2 + sense) * G + g0 + qq] * (scale * W);
-                                psiD[c] = psi_in[(gid * 4 + 1 * 2 + sense) * G + g0 + qq] * (scale * W);
+                                psiU[c] = psi_in[(gid * 4 + 0 * 2 + sense) * G + g0 + qq] * (scale * WS[c]);
+                                psiD[c] = psi_in[(gid * 4 + 1 * 2 + sense) * G + g0 + qq] * (scale * WS[c]);
                             }
                         }
                     }
@@ -420,11 +433,11 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
                         RowLoadS<real, GPL>::get(rows_sa + eD * (unsigned)(2 * sizeof(real)), qD, sD);
 #pragma unroll
                         for (int c = 0; c < GPL; ++c) {
-                            // Eq. 3 on W psi: d = W (psi_in - Qr),
-                            // W (psi_in - psi_out) = d (1 - e^{-Sigma_t l})
+                            // Eq. 3 on W S psi: d = W S (psi_in - Qr),
+                            // W S (psi_in - psi_out) = d (1 - e^{-Sigma_t l})
                             const real xU = attenuation<real>(sU[c] * len);
                             const real xD = attenuation<real>(sD[c] * len);
-                            const real dU = fma(-W, qU[c], psiU[c]), dD = fma(-W, qD[c], psiD[c]);
+                            const real dU = fma(-WS[c], qU[c], psiU[c]), dD = fma(-WS[c], qD[c], psiD[c]);
                             tU[c] = fma(-dU, xU, dU);
                             tD[c] = fma(-dD, xD, dD);
                             psiU[c] -= tU[c];
@@ -436,9 +449,9 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
 #pragma unroll
                             for (int c = 0; c < GPL; ++c) {
                                 shared_red_add(tl_sa + (tU_ + c) * 4u,
-                                               __float_as_int(fmaf((float)tU[c], scl[c], 12582912.0f)) - 0x4B400000);
+                                               __float2int_rn((float)tU[c]));
                                 shared_red_add(tl_sa + (tD_ + c) * 4u,
-                                               __float_as_int(fmaf((float)tD[c], scl[c], 12582912.0f)) - 0x4B400000);
+                                               __float2int_rn((float)tD[c]));
                             }
                         } else {
                             TallyAdd<real, GPL>::add(tl_s + tU_, tU, err);
@@ -456,7 +469,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
                             const real qD = qq < gc ? qr_g[fD * G + g0 + qq] : (real)0;
                             const real xU = attenuation<real>(sig[mU * GP + qq] * len);
                             const real xD = attenuation<real>(sig[mD * GP + qq] * len);
-                            const real dU = fma(-W, qU, psiU[c]), dD = fma(-W, qD, psiD[c]);
+                            const real dU = fma(-WS[c], qU, psiU[c]), dD = fma(-WS[c], qD, psiD[c]);
                             tU[c] = fma(-dU, xU, dU);
                             tD[c] = fma(-dD, xD, dD);
                             if (qq < gc) {
@@ -499,7 +512,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
                         for (int i = 0; i < 4; ++i)
 #pragma unroll
                             for (int c = 0; c < GPL; ++c) {
-                                const real dU = fma(-W, qU[i][c], psiU[c]), dD = fma(-W, qD[i][c], psiD[c]);
+                                const real dU = fma(-WS[c], qU[i][c], psiU[c]), dD = fma(-WS[c], qD[i][c], psiD[c]);
                                 tU[i][c] = fma(-dU, sU[i][c], dU);
                                 tD[i][c] = fma(-dD, sD[i][c], dD);
                                 psiU[c] -= tU[i][c];
@@ -511,9 +524,9 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
 #pragma unroll
                                 for (int c = 0; c < GPL; ++c) {
                                     shared_red_add(tl_sa + (fU[i] + c) * 4u,
-                                                   __float_as_int(fmaf((float)tU[i][c], scl[c], 12582912.0f)) - 0x4B400000);
+                                                   __float2int_rn((float)tU[i][c]));
                                     shared_red_add(tl_sa + (fD[i] + c) * 4u,
-                                                   __float_as_int(fmaf((float)tD[i][c], scl[c], 12582912.0f)) - 0x4B400000);
+                                                   __float2int_rn((float)tD[i][c]));
                                 }
                             } else {
                                 TallyAdd<real, GPL>::add(tl_s + fU[i], tU[i], err);
@@ -595,10 +608,10 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
                     for (int c = 0; c < GPL; ++c) {
                         const int qq = ql * GPL + c;
                         if (qq >= gc) continue;
-                        if (dstU >= 0 && dstU < dl.n_slots) psi_out[dstU * G + g0 + qq] = psiU[c] * invW;
-                        else leak += psiU[c];
-                        if (dstD >= 0 && dstD < dl.n_slots) psi_out[dstD * G + g0 + qq] = psiD[c] * invW;
-                        else leak += psiD[c];
+                        if (dstU >= 0 && dstU < dl.n_slots) psi_out[dstU * G + g0 + qq] = psiU[c] * iWS[c];
+                        else leak += psiU[c] * iS[c];
+                        if (dstD >= 0 && dstD < dl.n_slots) psi_out[dstD * G + g0 + qq] = psiD[c] * iWS[c];
+                        else leak += psiD[c] * iS[c];
                     }
                 }
             }
