@@ -38,7 +38,7 @@ struct moc_tracks {
     DevBuf d_tpl_off, d_tpl_loff, d_tpl_lmin, d_tpl_lidx;
     DevBuf d_dst, d_perm, d_win;
     DevBuf d_phi, d_qr, d_tally, d_vol, d_psi[2], d_fiss, d_fiss_old, d_partial, d_scal, d_counter;
-    DevBuf d_sigt, d_sigt64, d_sigs64, d_nsf64, d_chi64, d_src64;
+    DevBuf d_sigt, d_sigt64, d_sigs64, d_nsf64, d_chi64, d_src64, d_inv_st64, d_siga64, d_inv_vol;
     double *h_scal = nullptr;  // pinned mirror of the device scalars
     int cur = 0;               // psi buffer holding the next incoming fluxes
     bool has_psi = false;
@@ -153,6 +153,9 @@ void fill_views(moc_tracks *h) {
     s.nsf64 = (const double *)h->d_nsf64.p;
     s.chi64 = (const double *)h->d_chi64.p;
     s.src64 = (const double *)h->d_src64.p;
+    s.inv_st64 = (const double *)h->d_inv_st64.p;
+    s.siga64 = (const double *)h->d_siga64.p;
+    s.inv_vol = (const double *)h->d_inv_vol.p;
 }
 
 // The per-iteration kernels are no-ops once SC_CONV is set (a converged
@@ -588,6 +591,21 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     TRY(upload(h.get(), h->d_nsf64, geo.nsf), "upload");
     TRY(upload(h.get(), h->d_chi64, geo.chi), "upload");
     if (!geo.src.empty()) TRY(upload(h.get(), h->d_src64, geo.src), "upload");
+    {
+        // inverses and absorption per material and group, so that the
+        // per-iteration kernels multiply instead of dividing in FP64
+        std::vector<double> inv_st((size_t)geo.M * G), siga((size_t)geo.M * G);
+        for (int m = 0; m < geo.M; ++m)
+            for (int g = 0; g < G; ++g) {
+                const size_t mg = (size_t)m * G + g;
+                inv_st[mg] = 1.0 / geo.sigt[mg];
+                double a = geo.sigt[mg];
+                for (int hh = 0; hh < G; ++hh) a -= geo.sigs[mg * G + hh];
+                siga[mg] = a;
+            }
+        TRY(upload(h.get(), h->d_inv_st64, inv_st), "upload");
+        TRY(upload(h.get(), h->d_siga64, siga), "upload");
+    }
     // state
     const size_t nfg = (size_t)geo.nfsr * G;
     const size_t rs = real_size(h->precision);
@@ -597,7 +615,8 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     TRY(dalloc(h.get(), h->d_vol, (size_t)geo.nfsr * 8), "alloc volumes");
     TRY(dalloc(h.get(), h->d_fiss, (size_t)geo.nfsr * 8), "alloc");
     TRY(dalloc(h.get(), h->d_fiss_old, (size_t)geo.nfsr * 8), "alloc");
-    h->red_grid = (int)std::max<int64_t>(1, std::min<int64_t>((geo.nfsr + 255) / 256, (int64_t)h->sms * 4));
+    h->red_grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>((geo.nfsr + kSmallBlock - 1) / kSmallBlock, (int64_t)h->sms * 8));
     TRY(dalloc(h.get(), h->d_partial, (size_t)h->red_grid * 4 * 8), "alloc");
     TRY(dalloc(h.get(), h->d_scal, SC_COUNT * 8), "alloc");
     TRY(dalloc(h.get(), h->d_counter, 64), "alloc");
@@ -638,6 +657,12 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     TRY(launch_volumes(h->precision, h->dl, ns, (double *)h->d_vol.p, lgrid, h->stream), "volumes");
     h->vol.resize(geo.nfsr);
     TRY(cudaMemcpyAsync(h->vol.data(), h->d_vol.p, geo.nfsr * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
+    TRY(cudaStreamSynchronize(h->stream), "volumes");
+    {
+        std::vector<double> inv_vol(geo.nfsr);
+        for (int i = 0; i < geo.nfsr; ++i) inv_vol[i] = h->vol[i] > 0.0 ? 1.0 / h->vol[i] : 0.0;
+        TRY(upload(h.get(), h->d_inv_vol, inv_vol), "upload");
+    }
     // schedule: work units (2D tracks) in decreasing work, largest first
     h->order = by_size;
     TRY(upload(h.get(), h->d_order, h->order), "upload");

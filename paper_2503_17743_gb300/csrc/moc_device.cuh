@@ -48,6 +48,8 @@ struct DevState {
     int32_t *counter;   // work counter of the persistent sweep
     const void *sig_t;  // [M*G] real
     const double *sig_t64, *sig_s64, *nsf64, *chi64, *src64;  // [M*G(*G)] FP64 cross sections
+    const double *inv_st64, *siga64;  // [M*G] 1 / Sigma_t and Sigma_a = Sigma_t - sum_h Sigma_s[g->h]
+    const double *inv_vol;            // [nfsr] 1 / tracked volume (0 for an untracked FSR)
 };
 
 // slots of DevState::scal

@@ -206,23 +206,25 @@ __global__ void k_source(DevLayout dl, DevState st, int32_t nfsr) {
     if (st.scal[SC_CONV] != 0.0) return;  // converged: later iterations are no-ops
     const int G = dl.G;
     const double scale = st.scal[SC_SCALE];
-    const double k = st.scal[SC_K];
     const bool eig = st.scal[SC_EIGEN] != 0.0;
+    // chi / k of the normalised flux; 1 / (4 pi) per steradian.  Divisions are
+    // replaced by products with precomputed inverses (FP64 division is slow)
+    const double fis_scale = eig ? scale / st.scal[SC_K] : 0.0;
+    const double per_sr = 1.0 / (4.0 * MOC_PI);
     real *qr = reinterpret_cast<real *>(st.qr);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nfsr; i += gridDim.x * blockDim.x) {
         const int m = dl.fsr_mat[i];
         const double *ph = st.phi + (size_t)i * G;
         double fis = 0.0;
         if (eig)
-            for (int h = 0; h < G; ++h) fis += st.nsf64[m * G + h] * ph[h] * scale;
+            for (int h = 0; h < G; ++h) fis += st.nsf64[m * G + h] * ph[h];
         for (int g = 0; g < G; ++g) {
             double sc = 0.0;
-            for (int h = 0; h < G; ++h) sc += st.sig_s64[((size_t)m * G + h) * G + g] * ph[h] * scale;
-            double q = sc;
-            if (eig) q += st.chi64[m * G + g] * fis / k;
+            for (int h = 0; h < G; ++h) sc += st.sig_s64[((size_t)m * G + h) * G + g] * ph[h];
+            double q = sc * scale;
+            if (eig) q += st.chi64[m * G + g] * fis * fis_scale;
             if (st.src64) q += st.src64[m * G + g];
-            q /= 4.0 * MOC_PI;
-            qr[(size_t)i * G + g] = (real)(q / st.sig_t64[m * G + g]);
+            qr[(size_t)i * G + g] = (real)(q * per_sr * st.inv_st64[m * G + g]);
         }
     }
 }
@@ -239,13 +241,12 @@ __global__ void k_finalize(DevLayout dl, DevState st, int32_t nfsr) {
     double P = 0, Ab = 0, r2 = 0, cnt = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nfsr; i += gridDim.x * blockDim.x) {
         const int m = dl.fsr_mat[i];
-        const double V = st.vol[i];
+        const double V = st.vol[i], iV = st.inv_vol[i];
         double fis = 0.0;
         for (int g = 0; g < G; ++g) {
             const size_t q = (size_t)i * G + g;
-            const double sg = st.sig_t64[m * G + g];
-            double phi = 4.0 * MOC_PI * (double)qr[q];
-            if (V > 0.0) phi += st.tally[q] / (V * sg);
+            // Eq. 4: phi = 4 pi Qr + tally / (V Sigma_t)
+            const double phi = 4.0 * MOC_PI * (double)qr[q] + st.tally[q] * iV * st.inv_st64[m * G + g];
             st.tally[q] = 0.0;
             if (!eig && phi > 0.0) {
                 double rr = (phi - st.phi[q]) / phi;
@@ -254,9 +255,7 @@ __global__ void k_finalize(DevLayout dl, DevState st, int32_t nfsr) {
             }
             st.phi[q] = phi;
             fis += st.nsf64[m * G + g] * phi;
-            double sa = sg;
-            for (int h = 0; h < G; ++h) sa -= st.sig_s64[((size_t)m * G + g) * G + h];
-            Ab += V * sa * phi;
+            Ab += V * st.siga64[m * G + g] * phi;
         }
         P += V * fis;
         st.fiss[i] = fis;
@@ -451,19 +450,19 @@ cudaError_t launch_stack_segments(int precision, const DevLayout &dl, int64_t st
 
 cudaError_t launch_source(int precision, const DevLayout &dl, const DevState &st, int32_t nfsr,
                           int grid, cudaStream_t s) {
-    if (precision == MOC_FP64) k_source<double><<<grid, 256, 0, s>>>(dl, st, nfsr);
-    else k_source<float><<<grid, 256, 0, s>>>(dl, st, nfsr);
+    if (precision == MOC_FP64) k_source<double><<<grid, kSmallBlock, 0, s>>>(dl, st, nfsr);
+    else k_source<float><<<grid, kSmallBlock, 0, s>>>(dl, st, nfsr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(int precision, const DevLayout &dl, const DevState &st, int32_t nfsr,
                             int grid, double integrations, cudaStream_t s) {
-    if (precision == MOC_FP64) k_finalize<double><<<grid, 256, 0, s>>>(dl, st, nfsr);
-    else k_finalize<float><<<grid, 256, 0, s>>>(dl, st, nfsr);
+    if (precision == MOC_FP64) k_finalize<double><<<grid, kSmallBlock, 0, s>>>(dl, st, nfsr);
+    else k_finalize<float><<<grid, kSmallBlock, 0, s>>>(dl, st, nfsr);
     CK(cudaGetLastError());
     k_reduce_k<<<1, 32, 0, s>>>(st, grid, integrations);
     CK(cudaGetLastError());
-    k_residual<<<grid, 256, 0, s>>>(st, nfsr);
+    k_residual<<<grid, kSmallBlock, 0, s>>>(st, nfsr);
     CK(cudaGetLastError());
     k_reduce_res<<<1, 32, 0, s>>>(st, grid);
     return cudaGetLastError();
@@ -471,8 +470,8 @@ cudaError_t launch_finalize(int precision, const DevLayout &dl, const DevState &
 
 cudaError_t launch_finalize_fixed(int precision, const DevLayout &dl, const DevState &st,
                                   int32_t nfsr, int grid, double integrations, cudaStream_t s) {
-    if (precision == MOC_FP64) k_finalize<double><<<grid, 256, 0, s>>>(dl, st, nfsr);
-    else k_finalize<float><<<grid, 256, 0, s>>>(dl, st, nfsr);
+    if (precision == MOC_FP64) k_finalize<double><<<grid, kSmallBlock, 0, s>>>(dl, st, nfsr);
+    else k_finalize<float><<<grid, kSmallBlock, 0, s>>>(dl, st, nfsr);
     CK(cudaGetLastError());
     k_reduce_k<<<1, 32, 0, s>>>(st, grid, integrations);
     return cudaGetLastError();
@@ -480,7 +479,7 @@ cudaError_t launch_finalize_fixed(int precision, const DevLayout &dl, const DevS
 
 cudaError_t launch_init_state(const DevLayout &dl, const DevState &st, int32_t nfsr, int grid,
                               cudaStream_t s) {
-    k_init_state<<<grid, 256, 0, s>>>(dl, st, nfsr);
+    k_init_state<<<grid, kSmallBlock, 0, s>>>(dl, st, nfsr);
     CK(cudaGetLastError());
     k_init_finish<<<1, 256, 0, s>>>(st, grid, nfsr);
     return cudaGetLastError();

@@ -33,6 +33,9 @@ cudaError_t launch_sweep(int precision, int tally_smem, int gpl, const DevLayout
                          cudaStream_t s);
 cudaError_t sweep_occupancy(int precision, int tally_smem, int G, int gpl, int block, size_t smem,
                             int *blocks_per_sm);
+// threads per block of the per-FSR kernels (source, finalize, residual, init):
+// small blocks spread a few thousand FSRs over many SMs
+constexpr int kSmallBlock = 64;
 cudaError_t launch_source(int precision, const DevLayout &dl, const DevState &st, int32_t nfsr,
                           int grid, cudaStream_t s);
 cudaError_t launch_finalize(int precision, const DevLayout &dl, const DevState &st, int32_t nfsr,

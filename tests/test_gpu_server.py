@@ -29,10 +29,14 @@ def alone(p):
 
 def check_same(r_mix, phi_mix, r_alone, phi_alone):
     # the same iterations on the same data: only the order of FP64 atomic
-    # adds into the global tally may differ
+    # adds into the global tally may differ, which can move the stopping test
+    # by one iteration at the tolerance boundary (one iteration changes k by
+    # less than tol_k and the flux by about tol_src)
+    same = r_mix["iterations"] == r_alone["iterations"]
     assert abs(r_mix["iterations"] - r_alone["iterations"]) <= 1
-    assert abs(r_mix["k"] - r_alone["k"]) < 1e-8
-    np.testing.assert_allclose(phi_mix, phi_alone, rtol=1e-6, atol=1e-12 * np.abs(phi_alone).max())
+    assert abs(r_mix["k"] - r_alone["k"]) < (1e-8 if same else TOL["tol_k"])
+    np.testing.assert_allclose(phi_mix, phi_alone, rtol=1e-6 if same else 20 * TOL["tol_src"],
+                               atol=1e-12 * np.abs(phi_alone).max())
 
 
 def drain(srv, tickets, limit=100000):
