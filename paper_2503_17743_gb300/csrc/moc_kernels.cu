@@ -268,15 +268,22 @@ __global__ void k_finalize(DevLayout dl, DevState st, int32_t nfsr) {
 }
 
 // single block: production, absorption, k update and normalisation scale
+// one warp: lane-strided partial sums, then a fixed-order shuffle tree, so
+// the result is the same on every run
+__device__ __forceinline__ double warp_partial_sum(const double *partial, int nblocks, int slot) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += 32) v += partial[b * 4 + slot];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;  // valid in lane 0
+}
+
 __global__ void k_reduce_k(DevState st, int nblocks, double integrations) {
-    if (threadIdx.x != 0 || st.scal[SC_CONV] != 0.0) return;
-    double P = 0, Ab = 0, r2 = 0, cnt = 0;
-    for (int b = 0; b < nblocks; ++b) {
-        P += st.partial[b * 4 + 0];
-        Ab += st.partial[b * 4 + 1];
-        r2 += st.partial[b * 4 + 2];
-        cnt += st.partial[b * 4 + 3];
-    }
+    if (st.scal[SC_CONV] != 0.0) return;
+    const double P = warp_partial_sum(st.partial, nblocks, 0);
+    const double Ab = warp_partial_sum(st.partial, nblocks, 1);
+    const double r2 = warp_partial_sum(st.partial, nblocks, 2);
+    const double cnt = warp_partial_sum(st.partial, nblocks, 3);
+    if (threadIdx.x != 0) return;
     double *s = st.scal;
     const bool eig = s[SC_EIGEN] != 0.0;
     s[SC_PROD] = P;
@@ -320,12 +327,10 @@ __global__ void k_residual(DevState st, int32_t nfsr) {
 }
 
 __global__ void k_reduce_res(DevState st, int nblocks) {
-    if (threadIdx.x != 0 || st.scal[SC_CONV] != 0.0) return;
-    double r2 = 0, cnt = 0;
-    for (int b = 0; b < nblocks; ++b) {
-        r2 += st.partial[b * 4 + 2];
-        cnt += st.partial[b * 4 + 3];
-    }
+    if (st.scal[SC_CONV] != 0.0) return;
+    const double r2 = warp_partial_sum(st.partial, nblocks, 2);
+    const double cnt = warp_partial_sum(st.partial, nblocks, 3);
+    if (threadIdx.x != 0) return;
     double *s = st.scal;
     s[SC_RES] = cnt > 0 ? sqrt(r2 / cnt) : 0.0;
     s[SC_CONV] = (s[SC_TOLS] > 0 && s[SC_RES] < s[SC_TOLS] && fabs(s[SC_DK]) < s[SC_TOLK]) ? 1.0 : 0.0;
@@ -353,9 +358,9 @@ __global__ void k_init_state(DevLayout dl, DevState st, int32_t nfsr) {
 
 __global__ void k_init_finish(DevState st, int nblocks, int32_t nfsr) {
     __shared__ double s_scale;
+    double P = 0.0;
+    if (threadIdx.x < 32) P = warp_partial_sum(st.partial, nblocks, 0);
     if (threadIdx.x == 0) {
-        double P = 0;
-        for (int b = 0; b < nblocks; ++b) P += st.partial[b * 4 + 0];
         double *s = st.scal;
         const bool eig = s[SC_EIGEN] != 0.0;
         s[SC_K] = 1.0;
