@@ -669,7 +669,10 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     fill_views(h.get());
     // sweep launch shape (tally mode chosen above)
     h->smem = sweep_smem_bytes(h->precision, h->tally_smem, geo.M, G, h->gpl, h->tile_cap);
-    h->block = prm->block_threads > 0 ? std::max(32, std::min(prm->block_threads, 256) / 32 * 32) : 256;
+    {
+        const int bmax = sweep_block_threads(h->precision, h->gpl);
+        h->block = prm->block_threads > 0 ? std::max(32, std::min(prm->block_threads, bmax) / 32 * 32) : bmax;
+    }
     int bps = 0;
     TRY(sweep_occupancy(h->precision, h->tally_smem, G, h->gpl, h->block, h->smem, &bps), "occupancy");
     if (bps < 1) { moc_set_error("sweep kernel does not fit on an SM"); return MOC_ERR_UNSUPPORTED; }

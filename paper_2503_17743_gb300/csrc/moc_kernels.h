@@ -26,6 +26,8 @@ cudaError_t launch_stack_segments(int precision, const DevLayout &dl, int64_t st
 // the sweep (moc_sweep.cu); gpl = energy groups per lane (1 or 2, FP32 only)
 int sweep_default_gpl(int precision, int G);
 int sweep_lanes_per_track(int G, int gpl);
+// threads per sweep block the kernel is compiled for (its launch bound)
+int sweep_block_threads(int precision, int gpl);
 size_t sweep_smem_bytes(int precision, int tally_smem, int M, int G, int gpl, int cap);
 cudaError_t launch_sweep(int precision, int tally_smem, int gpl, const DevLayout &dl,
                          const DevState &st, const int32_t *order, int32_t n_work, int32_t cap,

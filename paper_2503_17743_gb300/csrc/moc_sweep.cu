@@ -224,11 +224,18 @@ struct TallyAdd<double, 1> {
     }
 };
 
+// threads per sweep block, three blocks per SM in FP32: ten warps with one
+// group per lane, nine with more (their extra registers), eight in FP64
+__host__ __device__ constexpr int sweep_block(bool fp32, int GPL) {
+    return fp32 ? (GPL == 1 ? 320 : 288) : 256;
+}
+constexpr int kMaxSweepBlock = 320;
+
 // words per shared tally row
 __host__ __device__ constexpr int tally_stride(int GL, int GPL) { return GL * GPL + (GPL > 1 ? 1 : 0); }
 
 template <typename real, int GL, int GPL, bool SMEM>
-__global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(real) == 4 ? 3 : 2)
     k_sweep(DevLayout dl, DevState st, const int32_t *order, int32_t n_work, int32_t cap,
             const real *psi_in, real *psi_out) {
     constexpr int GP = GL * GPL;     // groups per chunk (padded)
@@ -236,7 +243,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2)
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_work, s_next, s_ntask;
     __shared__ UnitStack s_us[kMaxPh];
-    __shared__ double s_leak[8];
+    __shared__ double s_leak[kMaxSweepBlock / 32];
     __shared__ float s_scl[32];      // FP32 fixed-point tally: scale of each group of the chunk
     __shared__ float s_inv[32];      // and its inverse
     __shared__ unsigned s_bmax[32];  // bound of |W psi| and |W Qr| per group (float bits)
@@ -678,6 +685,8 @@ int sweep_default_gpl(int precision, int G) {
 }
 
 int sweep_lanes_per_track(int G, int gpl) { return lanes_for_groups(G, gpl); }
+
+int sweep_block_threads(int precision, int gpl) { return sweep_block(precision != MOC_FP64, gpl); }
 
 size_t sweep_smem_bytes(int precision, int tally_smem, int M, int G, int gpl, int cap) {
     const size_t rs = precision == MOC_FP64 ? 8 : 4;
