@@ -31,25 +31,12 @@
 // d = W S (psi - Qr) the attenuated change W S (psi_in - psi_out) =
 // d (1 - e^{-Sigma_t l}) is both the psi update and the tally contribution in
 // tally units (Eq. 3, Eq. 4), rounded to an integer by one conversion.
-#include <climits>
-
 #include "moc_device.cuh"
 #include "moc_kernels.h"
 
 namespace {
 
 constexpr float kLog2e = 1.4426950408889634f;
-
-template <typename real>
-struct Vec2;
-template <>
-struct Vec2<float> {
-    using type = float2;
-};
-template <>
-struct Vec2<double> {
-    using type = double2;
-};
 
 // e^{-Sigma_t l} from x = Sigma_t l: FP32 on the MUFU pipe (Sigma_t pre-scaled
 // by log2 e, the negation folds into the multiply), FP64 exp
@@ -169,46 +156,16 @@ __device__ __forceinline__ void shared_red_add(unsigned a, int v) {
     asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
 
-// tally[0..GPL) += t on shared memory with one compare-and-swap of the whole
-// 32- or 64-bit word per attempt (floating-point adds on shared memory have no
-// single-instruction form).  A word is retried only when another lane changed
-// it in between; after kCasLimit attempts the update is dropped and *err set,
-// which the host reports as an error.
+// FP64 sweeps: tally += t on shared memory with one compare-and-swap of the
+// 64-bit word per attempt (floating-point adds on shared memory have no
+// single-instruction form; FP32 sweeps use the fixed-point tally instead).  A
+// word is retried only when another lane changed it in between; after
+// kCasLimit attempts the update is dropped and *err set, which the host
+// reports as an error.
 constexpr int kCasLimit = 1 << 16;
 
 template <typename real, int GPL>
 struct TallyAdd;
-template <>
-struct TallyAdd<float, 1> {
-    static __device__ __forceinline__ void add(float *p, const float (&t)[1], double *err) {
-        unsigned *w = reinterpret_cast<unsigned *>(p);
-        unsigned old = *w;
-        for (int it = 0; it < kCasLimit; ++it) {
-            const unsigned nw = __float_as_uint(__uint_as_float(old) + t[0]);
-            const unsigned prev = atomicCAS(w, old, nw);
-            if (prev == old) return;
-            old = prev;
-        }
-        *err = 1.0;
-    }
-};
-template <>
-struct TallyAdd<float, 2> {
-    static __device__ __forceinline__ void add(float *p, const float (&t)[2], double *err) {
-        unsigned long long *w = reinterpret_cast<unsigned long long *>(p);
-        unsigned long long old = *w;
-        for (int it = 0; it < kCasLimit; ++it) {
-            const float lo = __uint_as_float((unsigned)old) + t[0];
-            const float hi = __uint_as_float((unsigned)(old >> 32)) + t[1];
-            const unsigned long long nw =
-                ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
-            const unsigned long long prev = atomicCAS(w, old, nw);
-            if (prev == old) return;
-            old = prev;
-        }
-        *err = 1.0;
-    }
-};
 template <>
 struct TallyAdd<double, 1> {
     static __device__ __forceinline__ void add(double *p, const double (&t)[1], double *err) {
