@@ -421,6 +421,43 @@ def run_serving(n_requests, seed=1, load_factor=2.0, device=0):
                         "Poisson arrivals at load_factor x the sequential rate"}
 
 
+def run_ablation(args):
+    """The paper's two optimisations measured on this sweep (Sec. 4.2, 4.3;
+    Figs. 6 and 7): the stored (EXP) share of the segment templates from 0 to
+    100%, and load balancing off (work units and tracks in index order) or on.
+    Each line: mean outer-iteration time of 10 graph-launched iterations after
+    3 warm-up ones; one JSON line with the table."""
+    import synth
+    from paper_2503_17743_gb300 import (MOC_SCHED_TRACKS_NATURAL, MOC_SCHED_UNITS_NATURAL, Geometry,
+                                        Tracks, track_params)
+    prob = synth.workload(args.workload)
+    geom = Geometry(prob)
+    full = Tracks(geom, track_params(prob, preload_budget_bytes=-1))
+    tpl_bytes = full.info["stored_segments"] * 8
+    full.close()
+    rows = []
+
+    def measure(label, **kw):
+        tr = Tracks(geom, track_params(prob, **kw))
+        tr.iterate(3, use_graph=True)
+        r = tr.iterate(10, use_graph=True)
+        info = tr.info
+        rows.append({"case": label, "ms_per_iteration": r["seconds"] * 100.0,
+                     "integrations_per_s": r["integrations"] / r["seconds"],
+                     "stored_segments": info["stored_segments"],
+                     "preloaded_stacks": info["preloaded_stacks"], "stacks": info["stacks"]})
+        tr.close()
+
+    for frac in (0.0, 0.25, 0.5, 0.75, 1.0):
+        measure(f"EXP share {frac:.2f}", preload_budget_bytes=int(frac * tpl_bytes) if frac < 1 else -1)
+    measure("load balancing off (units and tracks in index order)",
+            schedule=MOC_SCHED_UNITS_NATURAL | MOC_SCHED_TRACKS_NATURAL)
+    measure("units largest first, tracks in index order", schedule=MOC_SCHED_TRACKS_NATURAL)
+    measure("units in index order, tracks by segment count", schedule=MOC_SCHED_UNITS_NATURAL)
+    measure("load balancing on (default)")
+    print(json.dumps({"ablation": args.workload, "rows": rows}), flush=True)
+
+
 def golden_k():
     path = os.path.join(ROOT, "tests", "golden", "oracle_k.json")
     try:
@@ -442,6 +479,8 @@ def main():
                     help="skip the schedule autotuner (default parameters)")
     ap.add_argument("--serving-requests", type=int, default=48,
                     help="requests of the serving leg (0 = skip)")
+    ap.add_argument("--ablation", action="store_true",
+                    help="EXP share and load-balancing ablation table (JSON)")
     ap.add_argument("--profile", action="store_true",
                     help="untimed 3 + 2 iterations (driver of the ncu captures)")
     ap.add_argument("--workload", default=WORKLOAD)
@@ -450,6 +489,9 @@ def main():
     args = ap.parse_args()
     if args.profile:
         run_profile_driver(args)
+        return
+    if args.ablation:
+        run_ablation(args)
         return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

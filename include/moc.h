@@ -46,6 +46,10 @@ extern "C" {
 #define MOC_ERR_TIMEOUT 5
 #define MOC_ERR_UNSUPPORTED 6
 
+/* moc_track_params.schedule flags (load balancing, Sec. 4.3; default 0 uses both) */
+#define MOC_SCHED_UNITS_NATURAL 1   /* work units (2D tracks) in index order, not largest first */
+#define MOC_SCHED_TRACKS_NATURAL 2  /* a stack's tracks in index order, not by segment count */
+
 /* arithmetic of the sweep */
 #define MOC_FP32 0
 #define MOC_FP64 1
@@ -110,7 +114,9 @@ typedef struct {
  *   blocks_per_sm      resident sweep blocks per SM (0 = occupancy maximum)
  *   device             CUDA device ordinal
  *   groups_per_lane    energy groups one thread carries along a track: 1, 2
- *                      or 4 (2 and 4 for FP32 sweeps only; 0 = tuned default) */
+ *                      or 4 (2 and 4 for FP32 sweeps only; 0 = tuned default)
+ *   schedule           0, or MOC_SCHED_* flags that switch off a load-balancing
+ *                      step (Sec. 4.3), for ablations */
 typedef struct {
     int32_t n_azim, n_polar;
     double radial_spacing, axial_spacing;
@@ -121,6 +127,7 @@ typedef struct {
     int32_t blocks_per_sm;
     int32_t device;
     int32_t groups_per_lane;
+    int32_t schedule;
 } moc_track_params;
 
 /* Stopping rule of a solve: |k_n - k_(n-1)| < tol_k (eigenvalue problems

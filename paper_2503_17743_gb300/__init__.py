@@ -6,10 +6,12 @@ the on-the-fly 3D segment generation, the preloaded/on-the-fly transport
 sweep, the source update and the FP64 reductions.  This package is the
 ctypes binding (argument marshalling only) plus the build script.
 """
-from ._moc import (MOC_FP32, MOC_FP64, MOC_TALLY_AUTO, MOC_TALLY_GLOBAL, MOC_TALLY_SHARED,
+from ._moc import (MOC_FP32, MOC_FP64, MOC_SCHED_TRACKS_NATURAL, MOC_SCHED_UNITS_NATURAL,
+                   MOC_TALLY_AUTO, MOC_TALLY_GLOBAL, MOC_TALLY_SHARED,
                    Geometry, MocError, Server, Tracks, autotune, load, measure_ex2_rate,
                    track_params)
 
 __all__ = ["Geometry", "Tracks", "Server", "MocError", "autotune", "load", "track_params",
            "measure_ex2_rate",
-           "MOC_FP32", "MOC_FP64", "MOC_TALLY_AUTO", "MOC_TALLY_SHARED", "MOC_TALLY_GLOBAL"]
+           "MOC_FP32", "MOC_FP64", "MOC_TALLY_AUTO", "MOC_TALLY_SHARED", "MOC_TALLY_GLOBAL",
+           "MOC_SCHED_UNITS_NATURAL", "MOC_SCHED_TRACKS_NATURAL"]

@@ -24,6 +24,8 @@ MOC_ERR_TIMEOUT = 5
 MOC_ERR_UNSUPPORTED = 6
 MOC_FP32 = 0
 MOC_FP64 = 1
+MOC_SCHED_UNITS_NATURAL = 1
+MOC_SCHED_TRACKS_NATURAL = 2
 MOC_TALLY_AUTO = 0
 MOC_TALLY_SHARED = 1
 MOC_TALLY_GLOBAL = 2
@@ -51,7 +53,7 @@ class moc_track_params(C.Structure):
                 ("axial_spacing", C.c_double), ("precision", C.c_int32),
                 ("preload_budget_bytes", C.c_int64), ("tally_mode", C.c_int32),
                 ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("device", C.c_int32),
-                ("groups_per_lane", C.c_int32)]
+                ("groups_per_lane", C.c_int32), ("schedule", C.c_int32)]
 
 
 class moc_server_params(C.Structure):
@@ -199,7 +201,7 @@ class Geometry:
 
 
 def track_params(prob, precision=MOC_FP32, preload_budget_bytes=-1, tally_mode=MOC_TALLY_AUTO,
-                 block_threads=0, blocks_per_sm=0, device=0, groups_per_lane=0):
+                 block_threads=0, blocks_per_sm=0, device=0, groups_per_lane=0, schedule=0):
     p = moc_track_params()
     p.n_azim, p.n_polar = prob.n_azim, prob.n_polar
     p.radial_spacing, p.axial_spacing = prob.radial_spacing, prob.axial_spacing
@@ -210,6 +212,7 @@ def track_params(prob, precision=MOC_FP32, preload_budget_bytes=-1, tally_mode=M
     p.blocks_per_sm = blocks_per_sm
     p.device = device
     p.groups_per_lane = groups_per_lane
+    p.schedule = schedule
     return p
 
 

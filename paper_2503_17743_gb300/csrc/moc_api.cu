@@ -468,7 +468,8 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
             int32_t *p = q;
             for (int r = 0; r < std::min(L.cpl, n); ++r)
                 for (int k = r; k < n; k += L.cpl) *p++ = k;
-            std::stable_sort(q, q + n, [&](int32_t a, int32_t b) { return tseg[o + a] > tseg[o + b]; });
+            if (!(prm->schedule & MOC_SCHED_TRACKS_NATURAL))
+                std::stable_sort(q, q + n, [&](int32_t a, int32_t b) { return tseg[o + a] > tseg[o + b]; });
         }
         TRY(upload(h.get(), h->d_perm, perm), "upload");
         fill_views(h.get());
@@ -665,6 +666,7 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     }
     // schedule: work units (2D tracks) in decreasing work, largest first
     h->order = by_size;
+    if (prm->schedule & MOC_SCHED_UNITS_NATURAL) std::sort(h->order.begin(), h->order.end());
     TRY(upload(h.get(), h->d_order, h->order), "upload");
     fill_views(h.get());
     // sweep launch shape (tally mode chosen above)
