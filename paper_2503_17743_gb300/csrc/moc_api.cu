@@ -169,14 +169,30 @@ cudaError_t set_scalar(moc_tracks *h, int slot, double v) {
                            h->stream);
 }
 
-// one sweep into the other psi buffer (no source update, no finalize)
-cudaError_t enqueue_sweep(moc_tracks *h, cudaStream_t s, int cur) {
-    cudaError_t e = cudaMemsetAsync(h->d_counter.p, 0, sizeof(int32_t), s);
+// Per psi buffer p, one small block of d_counter: the work counter of the
+// sweep that writes buffer p, then the bound of |psi| over buffer p per group
+// (float bits; written by that sweep, read by the next one to size its
+// fixed-point tally)
+size_t sweep_block_bytes(const moc_tracks *h) { return 16 + (((size_t)h->geom.G * 4 + 15) & ~(size_t)15); }
+int32_t *sweep_counter(moc_tracks *h, int p) {
+    return (int32_t *)((char *)h->d_counter.p + (size_t)p * sweep_block_bytes(h));
+}
+unsigned *psi_bound(moc_tracks *h, int p) { return (unsigned *)((char *)sweep_counter(h, p) + 16); }
+
+// one sweep into the other psi buffer (no source update, no finalize).
+// zero_bound = false: the output bound was zeroed by the source kernel just
+// before (outer iterations, where a converged solve's iterations are no-ops
+// and the bound of a psi buffer that is not rewritten must survive)
+cudaError_t enqueue_sweep(moc_tracks *h, cudaStream_t s, int cur, bool zero_bound = true) {
+    const int out = h->has_psi ? 1 - cur : 0;
+    cudaError_t e = cudaMemsetAsync(sweep_counter(h, out), 0, zero_bound ? sweep_block_bytes(h) : 4, s);
     if (e != cudaSuccess) return e;
     const void *pin = h->has_psi ? h->d_psi[cur].p : nullptr;
     void *pout = h->has_psi ? h->d_psi[1 - cur].p : nullptr;
     return launch_sweep(h->precision, h->tally_smem, h->gpl, h->dl, h->ds, (const int32_t *)h->d_order.p,
-                        (int32_t)h->order.size(), h->tile_cap, pin, pout, h->grid, h->block, h->smem, s);
+                        (int32_t)h->order.size(), h->tile_cap, pin, pout, sweep_counter(h, out),
+                        h->has_psi ? psi_bound(h, cur) : nullptr, h->has_psi ? psi_bound(h, out) : nullptr,
+                        h->grid, h->block, h->smem, s);
 }
 
 cudaError_t enqueue_finalize(moc_tracks *h, cudaStream_t s) {
@@ -189,9 +205,10 @@ cudaError_t enqueue_finalize(moc_tracks *h, cudaStream_t s) {
 // one outer iteration: source, sweep, flux update, k / residual; the scalars
 // are copied to the pinned host mirror at the end
 cudaError_t enqueue_iteration(moc_tracks *h, cudaStream_t s, int cur) {
-    cudaError_t e = launch_source(h->precision, h->dl, h->ds, h->geom.nfsr, h->red_grid, s);
+    cudaError_t e = launch_source(h->precision, h->dl, h->ds, h->geom.nfsr, h->red_grid, s,
+                                  h->has_psi ? psi_bound(h, 1 - cur) : nullptr);
     if (e != cudaSuccess) return e;
-    e = enqueue_sweep(h, s, cur);
+    e = enqueue_sweep(h, s, cur, false);
     if (e != cudaSuccess) return e;
     e = enqueue_finalize(h, s);
     if (e != cudaSuccess) return e;
@@ -285,6 +302,7 @@ int run_iterations(moc_tracks *h, int n, bool stop_on_conv, bool graph, moc_resu
 
 int init_state(moc_tracks *h) {
     TRY(cudaMemsetAsync(h->d_tally.p, 0, h->d_tally.n, h->stream), "memset");
+    TRY(cudaMemsetAsync(h->d_counter.p, 0, h->d_counter.n, h->stream), "memset");  // psi = 0: bounds 0
     for (int c = 0; c < 2; ++c)
         if (h->d_psi[c].p) TRY(cudaMemsetAsync(h->d_psi[c].p, 0, h->d_psi[c].n, h->stream), "memset");
     h->cur = 0;
@@ -620,7 +638,7 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
         1, std::min<int64_t>((geo.nfsr + kSmallBlock - 1) / kSmallBlock, (int64_t)h->sms * 8));
     TRY(dalloc(h.get(), h->d_partial, (size_t)h->red_grid * 4 * 8), "alloc");
     TRY(dalloc(h.get(), h->d_scal, SC_COUNT * 8), "alloc");
-    TRY(dalloc(h.get(), h->d_counter, 64), "alloc");
+    TRY(dalloc(h.get(), h->d_counter, 2 * sweep_block_bytes(h.get())), "alloc");
     bool refl = false;
     for (int f = 0; f < 6; ++f) refl |= geo.bc[f] != 0;
     h->has_psi = refl;
@@ -945,6 +963,11 @@ extern "C" int moc_track_psi(moc_tracks *h, int32_t t, int32_t p, int64_t i, int
             std::vector<float> tmp(G);
             for (int g = 0; g < G; ++g) tmp[g] = (float)(values[g] / sc);
             TRY(cudaMemcpy(base, tmp.data(), G * 4, cudaMemcpyHostToDevice), "copy");
+            // keep the bound of |psi| over this buffer a bound
+            std::vector<float> bnd(G);
+            TRY(cudaMemcpy(bnd.data(), psi_bound(h, h->cur), G * 4, cudaMemcpyDeviceToHost), "copy");
+            for (int g = 0; g < G; ++g) bnd[g] = std::max(bnd[g], std::fabs(tmp[g]));
+            TRY(cudaMemcpy(psi_bound(h, h->cur), bnd.data(), G * 4, cudaMemcpyHostToDevice), "copy");
         }
     } else {
         if (rs == 8) {
@@ -1070,11 +1093,13 @@ extern "C" int moc_sweep_units_from_source(moc_tracks *h, const double *Q, int32
     TRY(set_scalar(h, SC_LEAK, 0.0), "scalar");
     TRY(set_scalar(h, SC_SCALE, 1.0), "scalar");
     TRY(clear_conv(h, h->stream), "scalar");
-    TRY(cudaMemsetAsync(h->d_counter.p, 0, sizeof(int32_t), h->stream), "memset");
+    const int out = h->has_psi ? 1 - h->cur : 0;
+    TRY(cudaMemsetAsync(sweep_counter(h, out), 0, sweep_block_bytes(h), h->stream), "memset");
     void *pout = h->has_psi ? h->d_psi[1 - h->cur].p : nullptr;
     TRY(launch_sweep(h->precision, h->tally_smem, h->gpl, h->dl, h->ds, (const int32_t *)d_units.p,
-                     (int32_t)units.size(), h->tile_cap, nullptr, pout, h->grid, h->block, h->smem,
-                     h->stream), "sweep");
+                     (int32_t)units.size(), h->tile_cap, nullptr, pout, sweep_counter(h, out), nullptr,
+                     h->has_psi ? psi_bound(h, out) : nullptr, h->grid, h->block, h->smem, h->stream),
+        "sweep");
     TRY(cudaMemcpyAsync(tally, h->d_tally.p, n * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
     TRY(cudaMemcpyAsync(h->h_scal, h->d_scal.p, SC_COUNT * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
     TRY(cudaStreamSynchronize(h->stream), "sweep");

@@ -202,9 +202,11 @@ __global__ void k_stack_segments(DevLayout dl, int64_t s, const int64_t *offs, i
 // Q = (sum_h Sigma_s[h->g] phi_h + chi_g / k sum_h nuSigma_f,h phi_h + S_g) / 4pi, with
 // phi normalised on the fly by the latest scale; qr = Q / Sigma_t.
 template <typename real>
-__global__ void k_source(DevLayout dl, DevState st, int32_t nfsr) {
+__global__ void k_source(DevLayout dl, DevState st, int32_t nfsr, unsigned *zero_bound) {
     if (st.scal[SC_CONV] != 0.0) return;  // converged: later iterations are no-ops
     const int G = dl.G;
+    if (zero_bound && blockIdx.x == 0)
+        for (int g = threadIdx.x; g < G; g += blockDim.x) zero_bound[g] = 0u;
     const double scale = st.scal[SC_SCALE];
     const bool eig = st.scal[SC_EIGEN] != 0.0;
     // chi / k of the normalised flux; 1 / (4 pi) per steradian.  Divisions are
@@ -454,9 +456,9 @@ cudaError_t launch_stack_segments(int precision, const DevLayout &dl, int64_t st
 }
 
 cudaError_t launch_source(int precision, const DevLayout &dl, const DevState &st, int32_t nfsr,
-                          int grid, cudaStream_t s) {
-    if (precision == MOC_FP64) k_source<double><<<grid, kSmallBlock, 0, s>>>(dl, st, nfsr);
-    else k_source<float><<<grid, kSmallBlock, 0, s>>>(dl, st, nfsr);
+                          int grid, cudaStream_t s, unsigned *zero_bound) {
+    if (precision == MOC_FP64) k_source<double><<<grid, kSmallBlock, 0, s>>>(dl, st, nfsr, zero_bound);
+    else k_source<float><<<grid, kSmallBlock, 0, s>>>(dl, st, nfsr, zero_bound);
     return cudaGetLastError();
 }
 

@@ -29,17 +29,23 @@ int sweep_lanes_per_track(int G, int gpl);
 // threads per sweep block the kernel is compiled for (its launch bound)
 int sweep_block_threads(int precision, int gpl);
 size_t sweep_smem_bytes(int precision, int tally_smem, int M, int G, int gpl, int cap);
+// counter: the work counter (zero at launch); bound_in: per group, a bound of
+// |psi_in| (float bits, may be null when psi_in is); bound_out: zeroed,
+// receives the bound of |psi_out| (FP32 fixed-point tally only; may be null)
 cudaError_t launch_sweep(int precision, int tally_smem, int gpl, const DevLayout &dl,
                          const DevState &st, const int32_t *order, int32_t n_work, int32_t cap,
-                         const void *psi_in, void *psi_out, int grid, int block, size_t smem,
-                         cudaStream_t s);
+                         const void *psi_in, void *psi_out, int32_t *counter,
+                         const unsigned *bound_in, unsigned *bound_out, int grid, int block,
+                         size_t smem, cudaStream_t s);
 cudaError_t sweep_occupancy(int precision, int tally_smem, int G, int gpl, int block, size_t smem,
                             int *blocks_per_sm);
 // threads per block of the per-FSR kernels (source, finalize, residual, init):
 // small blocks spread a few thousand FSRs over many SMs
 constexpr int kSmallBlock = 64;
+// zero_bound (may be null): G words set to 0 unless the solve has converged
+// (the bound of the psi buffer the following sweep writes)
 cudaError_t launch_source(int precision, const DevLayout &dl, const DevState &st, int32_t nfsr,
-                          int grid, cudaStream_t s);
+                          int grid, cudaStream_t s, unsigned *zero_bound = nullptr);
 cudaError_t launch_finalize(int precision, const DevLayout &dl, const DevState &st, int32_t nfsr,
                             int grid, double integrations, cudaStream_t s);
 cudaError_t launch_finalize_fixed(int precision, const DevLayout &dl, const DevState &st,

@@ -194,7 +194,7 @@ __host__ __device__ constexpr int tally_stride(int GL, int GPL) { return GL * GP
 template <typename real, int GL, int GPL, bool SMEM>
 __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(real) == 4 ? 3 : 2)
     k_sweep(DevLayout dl, DevState st, const int32_t *order, int32_t n_work, int32_t cap,
-            const real *psi_in, real *psi_out) {
+            const real *psi_in, real *psi_out, const unsigned *bound_in, unsigned *bound_out) {
     constexpr int GP = GL * GPL;     // groups per chunk (padded)
     constexpr int SLOTS = 32 / GL;   // tracks per warp task
     extern __shared__ __align__(16) unsigned char smem[];
@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
     __shared__ float s_scl[32];      // FP32 fixed-point tally: scale of each group of the chunk
     __shared__ float s_inv[32];      // and its inverse
     __shared__ unsigned s_bmax[32];  // bound of |W psi| and |W Qr| per group (float bits)
+    __shared__ unsigned s_pmax[32];  // max |psi_out| the block stored per group (float bits)
     __shared__ float s_wmax;
     constexpr bool kFixed = sizeof(real) == 4;  // FP32 sweeps tally in fixed point
     const int G = dl.G, NL = dl.NL, M = dl.M, Ph = dl.Ph, cpl = dl.cpl;
@@ -230,6 +231,24 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
     const SegRec<real> *recs = reinterpret_cast<const SegRec<real> *>(dl.segs);
     double *err = st.scal + SC_ERR;
     real leak = (real)0;  // this lane's W psi leaving through vacuum faces
+    // the fixed-point tally needs a bound of |psi_in| per group: the previous
+    // sweep left one, and this sweep leaves one for the next (every psi_in is
+    // a psi_out of the previous sweep)
+    const bool track_bound = kFixed && SMEM && bound_out != nullptr;
+    float pmax[GPL];  // this lane's max |psi_out| for its groups of the current chunk
+#pragma unroll
+    for (int c = 0; c < GPL; ++c) pmax[c] = 0.0f;
+    if (tid < 32) s_pmax[tid] = 0u;
+    // lanes with the same groups (one per slot) fold their maxima into s_pmax
+    auto fold_pmax = [&](int gc_) {
+#pragma unroll
+        for (int c = 0; c < GPL; ++c) {
+            float v = pmax[c];
+            for (int o = GL; o < 32; o <<= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+            if (j == 0 && ql * GPL + c < gc_ && v > 0.0f) atomicMax(&s_pmax[ql * GPL + c], __float_as_uint(v));
+            pmax[c] = 0.0f;
+        }
+    };
 
     for (;;) {
         __syncthreads();
@@ -301,17 +320,12 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                     }
                 }
                 if (kFixed) {
-                    // incoming fluxes of the unit's tracks enter the bound too:
-                    // psi along a track stays between its incoming value and Qr
+                    // incoming fluxes enter the bound too (psi along a track stays
+                    // between its incoming value and Qr): the previous sweep's
+                    // bound of every psi it stored
                     const int qq = tid % GP;
-                    if (psi_in && qq < gc) {
-                        for (int ph = 0; ph < Ph; ++ph) {
-                            const int64_t base = s_us[ph].trk_off * 4;
-                            const int nrow = s_us[ph].n_trk * 4;
-                            for (int rr = tid / GP; rr < nrow; rr += blockDim.x / GP)
-                                bmax = fmaxf(bmax, fabsf((float)psi_in[(base + rr) * G + g0 + qq] * (float)scale));
-                        }
-                    }
+                    if (bound_in && psi_in && qq < gc)
+                        bmax = fmaxf(bmax, __uint_as_float(__ldg(bound_in + g0 + qq)) * fabsf((float)scale));
                     atomicMax(&s_bmax[qq], __float_as_uint(bmax));
                 }
             }
@@ -341,7 +355,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                 const int q = (x >> 1) * SLOTS + j;
                 const bool valid = q < u.n_trk;
                 const int k = valid ? __ldg(dl.perm + u.trk_off + q) : 0;  // track in the stack
-                const int r = k % cpl, m = k / cpl;          // class and shift of the track
+                const int m = k / cpl;                       // shift of the track within its class
                 const int64_t gid = u.trk_off + k;
                 // psi is carried pre-multiplied by the track weight W, so that the
                 // tally contribution W (psi_in - psi_out) is the psi change itself
@@ -572,14 +586,29 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                     for (int c = 0; c < GPL; ++c) {
                         const int qq = ql * GPL + c;
                         if (qq >= gc) continue;
-                        if (dstU >= 0 && dstU < dl.n_slots) psi_out[dstU * G + g0 + qq] = psiU[c] * iWS[c];
-                        else leak += psiU[c] * iS[c];
-                        if (dstD >= 0 && dstD < dl.n_slots) psi_out[dstD * G + g0 + qq] = psiD[c] * iWS[c];
-                        else leak += psiD[c] * iS[c];
+                        if (dstU >= 0 && dstU < dl.n_slots) {
+                            const real v = psiU[c] * iWS[c];
+                            psi_out[dstU * G + g0 + qq] = v;
+                            pmax[c] = fmaxf(pmax[c], fabsf((float)v));
+                        } else {
+                            leak += psiU[c] * iS[c];
+                        }
+                        if (dstD >= 0 && dstD < dl.n_slots) {
+                            const real v = psiD[c] * iWS[c];
+                            psi_out[dstD * G + g0 + qq] = v;
+                            pmax[c] = fmaxf(pmax[c], fabsf((float)v));
+                        } else {
+                            leak += psiD[c] * iS[c];
+                        }
                     }
                 }
             }
+            if (track_bound && G > GP) fold_pmax(gc);  // several chunks: publish per chunk
             __syncthreads();
+            if (track_bound && G > GP && tid < gc) {
+                if (s_pmax[tid]) atomicMax(bound_out + g0 + tid, s_pmax[tid]);
+                s_pmax[tid] = 0u;  // read again only after the next chunk's barriers
+            }
             if (SMEM) {
                 for (int b = warp; b < nb; b += nwarps) {
                     const int reg = __ldg(reg2d + b);
@@ -594,6 +623,12 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                 if (tid < 32) s_bmax[tid] = 0u;  // next chunk's bound (read only before its tasks)
             }
         }
+    }
+    if (track_bound && G <= GP) {
+        // one chunk: the maxima span every unit of the block, published once
+        fold_pmax(G);
+        __syncthreads();
+        if (tid < G && s_pmax[tid]) atomicMax(bound_out + tid, s_pmax[tid]);
     }
     double leak64 = (double)leak;
     for (int o = 16; o > 0; o >>= 1) leak64 += __shfl_down_sync(0xffffffffu, leak64, o);
@@ -664,17 +699,21 @@ cudaError_t sweep_occupancy(int precision, int tally_smem, int G, int gpl, int b
 
 cudaError_t launch_sweep(int precision, int tally_smem, int gpl, const DevLayout &dl,
                          const DevState &st, const int32_t *order, int32_t n_work, int32_t cap,
-                         const void *psi_in, void *psi_out, int grid, int block, size_t smem,
-                         cudaStream_t s) {
+                         const void *psi_in, void *psi_out, int32_t *counter,
+                         const unsigned *bound_in, unsigned *bound_out, int grid, int block,
+                         size_t smem, cudaStream_t s) {
     const void *f = sweep_fn(precision, tally_smem, dl.G, gpl);
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     DevLayout a0 = dl;
     DevState a1 = st;
+    a1.counter = counter;
     const int32_t *a2 = order;
     int32_t a3 = n_work, a4 = tally_smem ? cap : 0;
     const void *a5 = psi_in;
     void *a6 = psi_out;
-    void *args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6};
+    const unsigned *a7 = bound_in;
+    unsigned *a8 = bound_out;
+    void *args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8};
     return cudaLaunchKernel(f, dim3(grid), dim3(block), args, smem, s);
 }
