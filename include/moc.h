@@ -176,8 +176,10 @@ int moc_query_footprint(const moc_geometry *geom, const moc_track_params *params
  * the preload plan (Sec. 4.2) and the stored segments, tracked FSR volumes,
  * and the initial state (phi = 1, boundary fluxes 0, k = 1).  Errors:
  * MOC_ERR_UNSUPPORTED when the layer height is not a whole number of axial
- * spacings, MOC_ERR_OUT_OF_MEMORY when the device cannot hold the state,
- * MOC_ERR_CUDA on a CUDA failure. */
+ * spacings or a problem with reflective faces has more than 2^29 3D tracks
+ * (link destinations are 32-bit track-direction indices),
+ * MOC_ERR_OUT_OF_MEMORY when the device cannot hold the state, MOC_ERR_CUDA on
+ * a CUDA failure. */
 int moc_generate_tracks(const moc_geometry *geom, const moc_track_params *params,
                         moc_tracks **out);
 void moc_destroy_tracks(moc_tracks *tracks);

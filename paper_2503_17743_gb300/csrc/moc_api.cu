@@ -122,7 +122,7 @@ void fill_views(moc_tracks *h) {
     dl.tpl_lidx = (const int32_t *)h->d_tpl_lidx.p;
     dl.segs = h->d_segs.p;
     dl.fsr_mat = (const int32_t *)h->d_fsr_mat.p;
-    dl.dst = (const int64_t *)h->d_dst.p;
+    dl.dst = (const int32_t *)h->d_dst.p;
     dl.perm = (const int32_t *)h->d_perm.p;
     dl.win = (const uint64_t *)h->d_win.p;
     dl.Ph = h->L.Ph;
@@ -353,7 +353,7 @@ extern "C" int moc_query_footprint(const moc_geometry *g, const moc_track_params
     b += (int64_t)g->nfsr * G * (8 + rs + 8) + (int64_t)g->nfsr * 8 * 3;
     bool refl = false;
     for (int f = 0; f < 6; ++f) refl |= g->bc[f] != 0;
-    if (refl) b += 2 * L.n_gtrk * 4 * G * (int64_t)rs + L.n_gtrk * 4 * 8;  // boundary fluxes, links
+    if (refl) b += 2 * L.n_gtrk * 4 * G * (int64_t)rs + L.n_gtrk * 4 * 4;  // boundary fluxes, links
     b += L.n_gtrk * (4 + 8);  // sweep order and record windows
     if (resident) *resident = b;
     if (preload_all) {
@@ -391,7 +391,16 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     if ((int64_t)geo.nfsr * G > 0x7fffffffLL) { moc_set_error("too many FSR-groups"); return MOC_ERR_UNSUPPORTED; }
     for (int t = 0; t < L.nt; ++t) h->nb_max = std::max(h->nb_max, L.seg_off[t + 1] - L.seg_off[t]);
     if (h->nb_max >= 65536) { moc_set_error("a 2D track has too many segments"); return MOC_ERR_UNSUPPORTED; }
-    if (L.n_gtrk * 4 >= (int64_t)1 << 40) { moc_set_error("too many 3D tracks"); return MOC_ERR_UNSUPPORTED; }
+    {
+        // link destinations are 32-bit track-direction indices (reflective faces only)
+        bool has_links = false;
+        for (int f = 0; f < 6; ++f) has_links |= geo.bc[f] != 0;
+        if (has_links && L.n_gtrk * 4 >= (int64_t)1 << 31) {
+            moc_set_error("too many 3D tracks with reflective faces (at most 2^29)");
+            return MOC_ERR_UNSUPPORTED;
+        }
+        if (L.n_gtrk * 4 >= (int64_t)1 << 40) { moc_set_error("too many 3D tracks"); return MOC_ERR_UNSUPPORTED; }
+    }
     if (L.Ph > 16) { moc_set_error("at most 32 polar angles"); return MOC_ERR_UNSUPPORTED; }
     // tally mode: a shared tile of every (2D segment, layer) row of one unit
     // when it fits
@@ -659,9 +668,9 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
                     hit[dst] = 1;
                 }
         }
-        TRY(dalloc(h.get(), h->d_dst, (size_t)L.n_gtrk * 4 * sizeof(int64_t)), "alloc links");
+        TRY(dalloc(h.get(), h->d_dst, (size_t)L.n_gtrk * 4 * sizeof(int32_t)), "alloc links");
         fill_views(h.get());
-        TRY(launch_links(h->dl, ns, (int64_t *)h->d_dst.p, lgrid, h->stream), "links");
+        TRY(launch_links(h->dl, ns, (int32_t *)h->d_dst.p, lgrid, h->stream), "links");
         const size_t pb = (size_t)L.n_gtrk * 4 * G * rs;
         TRY(dalloc(h.get(), h->d_psi[0], pb), "alloc boundary fluxes");
         TRY(dalloc(h.get(), h->d_psi[1], pb), "alloc boundary fluxes");

@@ -23,7 +23,7 @@ struct DevLayout {
     const int32_t *tpl_lidx; // first record of each template layer (relative), + count
     const void *segs;        // template records, SegRec<real>
     const int32_t *fsr_mat;  // material of each FSR
-    const int64_t *dst;      // [n_gtrk*4] link destination of every track direction, or null (all vacuum)
+    const int32_t *dst;      // [n_gtrk*4] link destination of every track direction, or null (all vacuum)
     const uint64_t *win;     // [n_gtrk] stored stacks: each track's record window, in perm order
     const int32_t *perm;     // [n_gtrk] per stack, its track indices by decreasing segment
                              // count (ties: class by class, then by index)

@@ -135,7 +135,7 @@ __global__ void k_windows(DevLayout dl, int64_t n_stacks, uint64_t *win) {
     }
 }
 
-__global__ void k_links(DevLayout dl, int64_t n_stacks, int64_t *dst) {
+__global__ void k_links(DevLayout dl, int64_t n_stacks, int32_t *dst) {
     for (int64_t s = blockIdx.x; s < n_stacks; s += gridDim.x) {
         const StackDesc d = dl.desc[s];
         for (int k = threadIdx.x; k < d.n_trk; k += blockDim.x) {
@@ -144,7 +144,7 @@ __global__ void k_links(DevLayout dl, int64_t n_stacks, int64_t *dst) {
             for (int v = 0; v < 4; ++v) {
                 int64_t t = exit_dest(dl, dl.desc, d, dl.desc + s, i, v);
                 if (t >= dl.n_slots) t = -1;
-                dst[gid * 4 + v] = t;
+                dst[gid * 4 + v] = (int32_t)t;
             }
         }
     }
@@ -435,7 +435,7 @@ cudaError_t launch_windows(const DevLayout &dl, int64_t n_stacks, uint64_t *win,
     return cudaGetLastError();
 }
 
-cudaError_t launch_links(const DevLayout &dl, int64_t n_stacks, int64_t *dst, int grid,
+cudaError_t launch_links(const DevLayout &dl, int64_t n_stacks, int32_t *dst, int grid,
                          cudaStream_t s) {
     k_links<<<grid, 128, 0, s>>>(dl, n_stacks, dst);
     return cudaGetLastError();

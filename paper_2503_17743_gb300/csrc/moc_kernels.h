@@ -17,7 +17,7 @@ cudaError_t launch_track_counts(const DevLayout &dl, int64_t stack, int64_t *cnt
 // per track of the stored stacks, in sweep order: (record count << 48) | first record
 cudaError_t launch_windows(const DevLayout &dl, int64_t n_stacks, uint64_t *win, int grid,
                            cudaStream_t s);
-cudaError_t launch_links(const DevLayout &dl, int64_t n_stacks, int64_t *dst, int grid,
+cudaError_t launch_links(const DevLayout &dl, int64_t n_stacks, int32_t *dst, int grid,
                          cudaStream_t s);
 cudaError_t launch_volumes(int precision, const DevLayout &dl, int64_t n_stacks, double *vol,
                            int grid, cudaStream_t s);
