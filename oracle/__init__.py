@@ -46,6 +46,7 @@ class _Input(C.Structure):
         ("radial_spacing", C.c_double), ("axial_spacing", C.c_double),
         ("n_threads", C.c_int),
         ("light", C.c_int),
+        ("fuel_rings", C.c_int), ("mod_rings", C.c_int), ("sectors", C.c_int),
     ]
 
 
@@ -136,6 +137,9 @@ class Oracle:
         inp.radial_spacing, inp.axial_spacing = prob.radial_spacing, prob.axial_spacing
         inp.n_threads = int(n_threads or os.cpu_count() or 1)
         inp.light = 1 if light else 0
+        inp.fuel_rings = int(getattr(prob, "fuel_rings", 1))
+        inp.mod_rings = int(getattr(prob, "moderator_rings", 0))
+        inp.sectors = int(getattr(prob, "sectors", 1))
         self.n_threads = inp.n_threads
         err = C.create_string_buffer(256)
         h = lib.orc_create(C.byref(inp), err, 256)

@@ -10,7 +10,9 @@
  *
  * What it computes, step by step, in the order the paper gives them:
  *   1. Flat source regions: radial regions of an axially extruded pin lattice
- *      (Sec. 2.2, extruded geometry) times uniform axial layers.
+ *      (Sec. 2.2, extruded geometry) times uniform axial layers.  A pin cell
+ *      may be refined into rings (equal areas inside the fuel circle, equal
+ *      area steps out to the inscribed circle) and equal angular sectors.
  *   2. 2D cyclic tracks and their 2D segments (kept on the CPU, Sec. 3.1).
  *   3. z-stacks of 3D tracks z_i(s) = z_0 + i dz + s cot(theta) (Eq. 5); the
  *      tracks crossing each (2D segment, layer) FSR from Eqs. 6-7, the full
@@ -59,6 +61,7 @@ typedef struct {
     int n_threads;
     int light;  /* 1: tracks and segments only (no links, boundary fluxes or
                    volumes): for sampled checks of problems too large to solve */
+    int fuel_rings, mod_rings, sectors;  /* pin-cell refinement (0 read as 1, 0, 1) */
 } orc_input;
 
 /* faces */
@@ -74,6 +77,8 @@ typedef struct {
     /* FSRs */
     double Wx, Wy;
     int nreg, nfsr;
+    int nfuel_rings, ncirc, nsec;  /* pin cells: circles (fuel ones first), sectors */
+    double circ_r2[130];           /* squared radii of the circles, increasing */
     int *reg_base;      /* per cell */
     int *fsr_mat;       /* per FSR */
     int Nz, cpl;
@@ -306,7 +311,17 @@ static int region_at(orc_t *o, double x, double y) {
     if (!o->has_pin[c]) return o->reg_base[c];
     double ccx = (cx + 0.5) * o->pitch, ccy = (cy + 0.5) * o->pitch;
     double d2 = (x - ccx) * (x - ccx) + (y - ccy) * (y - ccy);
-    return d2 < o->radius * o->radius ? o->reg_base[c] : o->reg_base[c] + 1;
+    int ring = o->ncirc;
+    for (int k = o->ncirc - 1; k >= 0; k--)
+        if (d2 < o->circ_r2[k]) ring = k;
+    int sec = 0;
+    if (o->nsec > 1) {
+        double ang = atan2(y - ccy, x - ccx);
+        if (ang < 0.0) ang += 2.0 * ORC_PI;
+        sec = (int)floor(ang / (2.0 * ORC_PI / o->nsec));
+        if (sec >= o->nsec) sec = o->nsec - 1;
+    }
+    return o->reg_base[c] + ring * o->nsec + sec;
 }
 
 static int cmp_dbl(const void *a, const void *b) {
@@ -321,7 +336,7 @@ static int trace_track(orc_t *o, int t, double **bp_out, int *nbp_out) {
     double dx = (a < o->nq ? ux : -ux) / o->lu[m], dy = uy / o->lu[m];
     double x0 = o->t_x0[t], y0 = o->t_y0[t], L = o->t_len[t];
     int cap = 2 * (o->ncx + o->ncy) + 8;
-    double *bp = malloc(sizeof(double) * (size_t)(cap * 3));
+    double *bp = malloc(sizeof(double) * (size_t)(cap * (2 * o->ncirc + o->nsec + 2)));
     int n = 0;
     bp[n++] = 0.0;
     bp[n++] = L;
@@ -345,13 +360,28 @@ static int trace_track(orc_t *o, int t, double **bp_out, int *nbp_out) {
         double ccx = (cx + 0.5) * o->pitch, ccy = (cy + 0.5) * o->pitch;
         double fx = x0 - ccx, fy = y0 - ccy;
         double b = fx * dx + fy * dy;
-        double cc = fx * fx + fy * fy - o->radius * o->radius;
-        double disc = b * b - cc;
-        if (disc <= 0.0) continue;
-        double sq = sqrt(disc);
-        double t1 = -b - sq, t2 = -b + sq;
-        if (t1 > bp[i] && t1 < bp[i + 1]) bp[n++] = t1;
-        if (t2 > bp[i] && t2 < bp[i + 1]) bp[n++] = t2;
+        for (int k = 0; k < o->ncirc; k++) {
+            double cc = fx * fx + fy * fy - o->circ_r2[k];
+            double disc = b * b - cc;
+            if (disc <= 0.0) continue;
+            double sq = sqrt(disc);
+            double t1 = -b - sq, t2 = -b + sq;
+            if (t1 > bp[i] && t1 < bp[i + 1]) bp[n++] = t1;
+            if (t2 > bp[i] && t2 < bp[i + 1]) bp[n++] = t2;
+        }
+        /* sector boundaries: the half-lines from the centre at the angles
+           2 pi s / S; the chord meets the full line of angle th where the
+           cross product with (cos th, sin th) vanishes, and that point is on
+           the half-line when its projection on it is not negative */
+        for (int s = 0; o->nsec > 1 && s < o->nsec; s++) {
+            double th = 2.0 * ORC_PI * s / o->nsec;
+            double ux = cos(th), uy = sin(th);
+            double cr = dx * uy - dy * ux;
+            if (cr == 0.0) continue;
+            double tt = (fy * ux - fx * uy) / cr;
+            if (!(tt > bp[i] && tt < bp[i + 1])) continue;
+            if ((fx + tt * dx) * ux + (fy + tt * dy) * uy >= 0.0) bp[n++] = tt;
+        }
     }
     qsort(bp, (size_t)n, sizeof(double), cmp_dbl);
     /* merge tiny intervals */
@@ -668,18 +698,42 @@ void *orc_create(const orc_input *in, char *err, int errlen) {
     }
     o->Wx = o->ncx * o->pitch;
     o->Wy = o->ncy * o->pitch;
-    /* FSRs: radial regions cell by cell (inner, outer), times layers */
+    /* pin-cell circles: the fuel circle split into rings of equal area
+       (r_k^2 = r_f^2 k / F), then mod_rings circles whose squared radii step
+       evenly from r_f^2 towards (pitch/2)^2 (that last circle excluded);
+       sector s of S covers the angles [2 pi s / S, 2 pi (s + 1) / S) */
+    if (in->fuel_rings < 0 || in->fuel_rings > 64 || in->mod_rings < 0 || in->mod_rings > 64 ||
+        in->sectors < 0 || in->sectors > 64) {
+        set_err(err, errlen, "rings and sectors must lie in [0, 64]");
+        orc_destroy(o);
+        return NULL;
+    }
+    o->nfuel_rings = in->fuel_rings > 0 ? in->fuel_rings : 1;
+    o->nsec = in->sectors > 0 ? in->sectors : 1;
+    o->ncirc = 0;
+    for (int k = 1; k <= o->nfuel_rings; k++)
+        o->circ_r2[o->ncirc++] = o->radius * o->radius * k / o->nfuel_rings;
+    {
+        double rf2 = o->radius * o->radius, rc2 = 0.25 * o->pitch * o->pitch;
+        for (int k = 1; k <= in->mod_rings; k++)
+            o->circ_r2[o->ncirc++] = rf2 + (rc2 - rf2) * k / (in->mod_rings + 1);
+    }
+    int per_pin = (o->ncirc + 1) * o->nsec;
+    /* FSRs: radial regions cell by cell (pin cells: ring * sectors + sector,
+       innermost ring first; other cells: one region), times layers */
     o->reg_base = malloc(sizeof(int) * (size_t)nc);
     int nr = 0;
-    for (int c = 0; c < nc; c++) { o->reg_base[c] = nr; nr += o->has_pin[c] ? 2 : 1; }
+    for (int c = 0; c < nc; c++) { o->reg_base[c] = nr; nr += o->has_pin[c] ? per_pin : 1; }
     o->nreg = nr;
     o->nfsr = nr * o->nl;
     o->fsr_mat = malloc(sizeof(int) * (size_t)o->nfsr);
     for (int c = 0; c < nc; c++) {
         for (int L = 0; L < o->nl; L++) {
             if (o->has_pin[c]) {
-                o->fsr_mat[(o->reg_base[c]) * o->nl + L] = o->mat_in[c * o->nl + L];
-                o->fsr_mat[(o->reg_base[c] + 1) * o->nl + L] = o->mat_out[c * o->nl + L];
+                for (int ring = 0; ring <= o->ncirc; ring++)
+                    for (int s = 0; s < o->nsec; s++)
+                        o->fsr_mat[(o->reg_base[c] + ring * o->nsec + s) * o->nl + L] =
+                            ring < o->nfuel_rings ? o->mat_in[c * o->nl + L] : o->mat_out[c * o->nl + L];
             } else {
                 o->fsr_mat[o->reg_base[c] * o->nl + L] = o->mat_out[c * o->nl + L];
             }

@@ -12,9 +12,16 @@ assemblies, an axially inserted absorber) and use none of its numbers.
 Conventions shared by both consumers (they are inputs, not arithmetic):
 
 * cells are indexed ``c = cy * ncx + cx`` with ``cx`` along x;
-* a pin cell has two radial regions (inside the circle, then the moderator
-  around it), every other cell one region; radial regions are numbered cell
-  by cell in that order;
+* a pin cell has (circles + 1) x sectors radial regions, numbered
+  ``ring * sectors + sector`` from the centre outwards: ``fuel_rings`` rings
+  of equal area inside the fuel circle, ``moderator_rings`` circles whose
+  squared radii step evenly from the fuel radius towards half the pitch,
+  then the rest of the cell; sector s covers the angles
+  [2 pi s / S, 2 pi (s+1) / S) counterclockwise from +x about the cell
+  centre.  Rings inside the fuel circle hold ``mat_in``, the others
+  ``mat_out``.  With the defaults (1, 0, 1) a pin cell has two regions
+  (circle, then moderator).  Every other cell is one region; radial regions
+  are numbered cell by cell;
 * a flat source region (FSR) is ``region * n_layers + layer`` (axially
   uniform layers, layer 0 at z = 0);
 * ``bc`` lists the faces xmin, xmax, ymin, ymax, zmin, zmax with 1 =
@@ -62,6 +69,9 @@ class Problem:
     radial_spacing: float
     axial_spacing: float
     seed: int = 0
+    fuel_rings: int = 1
+    moderator_rings: int = 0
+    sectors: int = 1
     meta: dict = field(default_factory=dict)
 
     @property
@@ -73,8 +83,12 @@ class Problem:
         return int(self.sigma_t.shape[0])
 
     @property
+    def pin_regions(self) -> int:
+        return (self.fuel_rings + self.moderator_rings + 1) * self.sectors
+
+    @property
     def n_regions(self) -> int:
-        return int(np.sum(np.where(self.has_pin != 0, 2, 1)))
+        return int(np.sum(np.where(self.has_pin != 0, self.pin_regions, 1)))
 
     @property
     def n_fsr(self) -> int:
@@ -303,6 +317,10 @@ def workload(name: str, seed: int = 1) -> Problem:
                        throughput workload
     * ``lattice17_small`` - the same lattice with a coarse track layout for
                        fast parity runs
+    * ``lattice5_rings`` - 5x5 lattice with 3 fuel rings, 1 moderator ring
+                       and 8 sectors per pin cell
+    * ``pin_cell_rings`` - the pin cell with 3 fuel rings, 2 moderator rings
+                       and 4 sectors
     * ``asm3x3``     - 3x3 assemblies + reflector on two sides, 64 cm
     * ``core7x7``    - 7x7 assemblies + reflector ring, 200 cm
     """
@@ -318,6 +336,14 @@ def workload(name: str, seed: int = 1) -> Problem:
     if name == "lattice5":
         return lattice(seed, n=5, n_azim=16, n_polar=4, radial_spacing=0.1,
                        axial_spacing=0.5, height=4.0, n_layers=4, name="lattice5")
+    if name == "lattice5_rings":
+        # finer FSRs: 3 fuel rings, 1 moderator ring, 8 sectors (40 regions a pin)
+        return replace(lattice(seed, n=5, n_azim=16, n_polar=4, radial_spacing=0.1,
+                               axial_spacing=0.5, height=4.0, n_layers=4, name="lattice5_rings"),
+                       fuel_rings=3, moderator_rings=1, sectors=8)
+    if name == "pin_cell_rings":
+        return replace(pin_cell(seed), name="pin_cell_rings", fuel_rings=3, moderator_rings=2,
+                       sectors=4)
     if name == "asm3x3":
         return assemblies(seed)
     if name == "core7x7":

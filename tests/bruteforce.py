@@ -11,18 +11,36 @@ import math
 import numpy as np
 
 
+def circle_radii2(prob):
+    """Squared radii of a pin cell's circles, from the problem's conventions:
+    equal-area rings of the fuel circle, then equal steps of r^2 from the fuel
+    radius towards half the pitch (half the pitch itself excluded)."""
+    F = max(1, getattr(prob, "fuel_rings", 1))
+    Mr = getattr(prob, "moderator_rings", 0)
+    rf2, rh2 = prob.fuel_radius ** 2, (0.5 * prob.pitch) ** 2
+    return np.array([rf2 * k / F for k in range(1, F + 1)] +
+                    [rf2 + (rh2 - rf2) * k / (Mr + 1) for k in range(1, Mr + 1)])
+
+
 def region_ids(prob, x, y):
-    """Radial region of points (x, y): cell by cell, inner circle then moderator."""
+    """Radial region of points (x, y) by direct point location: cell by cell;
+    in a pin cell, ring (number of circles the point lies outside) times the
+    sector count plus the sector (angle about the centre from +x)."""
+    r2 = circle_radii2(prob)
+    S = max(1, getattr(prob, "sectors", 1))
     cx = np.clip(np.floor(x / prob.pitch).astype(np.int64), 0, prob.ncx - 1)
     cy = np.clip(np.floor(y / prob.pitch).astype(np.int64), 0, prob.ncy - 1)
     c = cy * prob.ncx + cx
-    nreg = np.where(prob.has_pin != 0, 2, 1)
+    nreg = np.where(prob.has_pin != 0, (len(r2) + 1) * S, 1)
     base = np.concatenate([[0], np.cumsum(nreg)[:-1]])
-    px = (cx + 0.5) * prob.pitch
-    py = (cy + 0.5) * prob.pitch
-    inside = (x - px) ** 2 + (y - py) ** 2 < prob.fuel_radius ** 2
+    ux = x - (cx + 0.5) * prob.pitch
+    uy = y - (cy + 0.5) * prob.pitch
+    d2 = ux ** 2 + uy ** 2
+    ring = np.sum(d2[..., None] >= r2, axis=-1)
+    ang = np.mod(np.arctan2(uy, ux), 2 * math.pi)
+    sec = np.minimum(S - 1, np.floor(ang * S / (2 * math.pi)).astype(np.int64))
     pin = prob.has_pin[c] != 0
-    return np.where(pin & ~inside, base[c] + 1, base[c])
+    return np.where(pin, base[c] + ring * S + sec, base[c])
 
 
 def laydown(prob, m):

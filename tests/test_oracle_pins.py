@@ -30,6 +30,16 @@ def pin(oracle_mod):
 
 
 @pytest.fixture(scope="module")
+def lat3r(oracle_mod):
+    """lat3 with finer pin-cell regions: 2 fuel rings, 1 moderator ring, 8 sectors."""
+    p = synth.lattice(3, n=3, G=3, height=4.0, n_layers=4, n_azim=8, n_polar=4,
+                      radial_spacing=0.15, axial_spacing=0.5, bc=(1, 1, 1, 1, 1, 1),
+                      n_gt=2, name="lat3r")
+    p = p.with_tracks(fuel_rings=2, moderator_rings=1, sectors=8)
+    return p, oracle_mod.Oracle(p, n_threads=2)
+
+
+@pytest.fixture(scope="module")
 def lat3(oracle_mod):
     p = synth.lattice(3, n=3, G=3, height=4.0, n_layers=4, n_azim=8, n_polar=4,
                       radial_spacing=0.15, axial_spacing=0.5, bc=(1, 1, 1, 1, 1, 1),
@@ -157,8 +167,8 @@ def test_cycle_positions_chain(pin, lat3):
                 assert tr2["M"] == (Mc - (tr["M"] + tr["steps"]) - tr2["steps"]) % Mc
 
 
-def test_2d_segments_bruteforce(pin, lat3):
-    for p, o in (pin, lat3):
+def test_2d_segments_bruteforce(pin, lat3, lat3r):
+    for p, o in (pin, lat3, lat3r):
         for t in range(0, o.n_tracks2d, max(1, o.n_tracks2d // 25)):
             tr = o.track2d(t)
             reg, ln, pos = o.segments2d(t)
@@ -209,8 +219,8 @@ def _stack_checks(p, o, t, p_idx):
         assert abs(l.sum() - (s_hi - s_lo) / sin) < 1e-9
 
 
-def test_3d_segments_bruteforce(pin, lat3):
-    for p, o in (pin, lat3):
+def test_3d_segments_bruteforce(pin, lat3, lat3r):
+    for p, o in (pin, lat3, lat3r):
         for t in range(0, o.n_tracks2d, max(1, o.n_tracks2d // 8)):
             for p_idx in range(p.n_polar):
                 _stack_checks(p, o, t, p_idx)
@@ -293,6 +303,33 @@ def test_tracked_volumes_match_analytic(oracle_mod):
         errs.append(max(abs(V[0] / fuel - 1).max(), abs(V[1] / mod - 1).max()))
     # midpoint-rule chord sums: well inside 1 % at these spacings
     assert max(errs) < 0.005, errs
+
+
+def _ring_sector_volumes(p):
+    """Analytic volume of every radial region of a one-pin cell with rings and
+    sectors (2, 4 or 8 sectors: the square's corner region splits evenly)."""
+    from tests.bruteforce import circle_radii2
+    r2 = circle_radii2(p)
+    S = p.sectors
+    areas = [math.pi * (r2[0])] + [math.pi * (r2[k] - r2[k - 1]) for k in range(1, len(r2))]
+    areas.append(p.pitch ** 2 - math.pi * r2[-1])
+    return np.repeat(np.array(areas) / S, S) * (p.height / p.n_layers)
+
+
+@pytest.mark.parametrize("sectors", [1, 4, 8])
+def test_ring_sector_volumes_match_analytic(oracle_mod, sectors):
+    """Tracked volumes of rings and sectors converge to the analytic areas
+    under track refinement; the cell total stays exact."""
+    errs = []
+    for spacing in (0.04, 0.02, 0.01):
+        p = synth.pin_cell(1, radial_spacing=spacing, n_azim=32).with_tracks(
+            fuel_rings=3, moderator_rings=2, sectors=sectors)
+        o = oracle_mod.Oracle(p, n_threads=4)
+        V = o.volumes().reshape(p.pin_regions, p.n_layers)
+        ref = _ring_sector_volumes(p)
+        assert abs(V.sum() - p.pitch ** 2 * p.height) < 1e-9 * p.pitch ** 2 * p.height
+        errs.append(np.abs(V / ref[:, None] - 1).max())
+    assert errs[-1] < 0.01 and errs[-1] < errs[0], errs
 
 
 # --------------------------------------------------------------- Eq. 3
