@@ -67,11 +67,25 @@ typedef struct moc_tracks moc_tracks;
  *   ncx, ncy      cells along x and y, square cells of side `pitch` (cm)
  *   fuel_radius   radius (cm) of the circle of a pin cell, < pitch/2
  *   height        axial extent (cm), split into n_layers equal layers
- *   has_pin       [ncy*ncx] 1 = cell holds a circle (two regions), 0 = one region
+ *   has_pin       [ncy*ncx] 1 = cell holds a pin (circle), 0 = one region
  *   mat_in        [ncy*ncx*n_layers] material inside the circle, per layer
  *   mat_out       [ncy*ncx*n_layers] material outside the circle (whole cell
  *                 for has_pin = 0), per layer
- *   bc            faces xmin, xmax, ymin, ymax, zmin, zmax: 1 reflective, 0 vacuum */
+ *   bc            faces xmin, xmax, ymin, ymax, zmin, zmax: 1 reflective, 0 vacuum
+ *   fuel_rings    finer flat source regions of a pin cell (0 is read as 1):
+ *                 rings of equal area inside the fuel circle,
+ *   moderator_rings  (0 or more) circles of equal area steps between the
+ *                 fuel circle and the cell's inscribed circle (radius pitch/2,
+ *                 itself not a boundary),
+ *   sectors       (0 is read as 1) equal angular sectors about the cell
+ *                 centre, sector s covering [2 pi s / S, 2 pi (s+1) / S)
+ *                 counterclockwise from +x, applied to every ring and to the
+ *                 region outside the last circle.
+ * Radial regions are numbered cell by cell; within a pin cell region
+ * ring * sectors + sector, rings from the centre outwards and the region
+ * outside every circle last.  Rings inside the fuel circle take mat_in, the
+ * others mat_out.  With 1, 0, 1 a pin cell has two regions (circle, then
+ * moderator).  Cells without a pin stay one region. */
 typedef struct {
     int32_t ncx, ncy;
     double pitch, fuel_radius, height;
@@ -80,6 +94,7 @@ typedef struct {
     const int32_t *mat_in;
     const int32_t *mat_out;
     int32_t bc[6];
+    int32_t fuel_rings, moderator_rings, sectors;
 } moc_geometry_desc;
 
 /* Multigroup macroscopic cross sections (1/cm), host arrays:

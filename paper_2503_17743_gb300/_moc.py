@@ -39,7 +39,8 @@ f64p = C.POINTER(C.c_double)
 class moc_geometry_desc(C.Structure):
     _fields_ = [("ncx", C.c_int32), ("ncy", C.c_int32), ("pitch", C.c_double),
                 ("fuel_radius", C.c_double), ("height", C.c_double), ("n_layers", C.c_int32),
-                ("has_pin", i32p), ("mat_in", i32p), ("mat_out", i32p), ("bc", C.c_int32 * 6)]
+                ("has_pin", i32p), ("mat_in", i32p), ("mat_out", i32p), ("bc", C.c_int32 * 6),
+                ("fuel_rings", C.c_int32), ("moderator_rings", C.c_int32), ("sectors", C.c_int32)]
 
 
 class moc_materials(C.Structure):
@@ -173,6 +174,9 @@ class Geometry:
         d.mat_out = _ptr(arr(prob.mat_out, np.int32), i32p)
         for i in range(6):
             d.bc[i] = int(prob.bc[i])
+        d.fuel_rings = int(getattr(prob, "fuel_rings", 1))
+        d.moderator_rings = int(getattr(prob, "moderator_rings", 0))
+        d.sectors = int(getattr(prob, "sectors", 1))
         m = moc_materials()
         m.num_materials, m.num_groups = prob.num_materials, prob.num_groups
         m.sigma_t = _ptr(arr(prob.sigma_t, np.float64), f64p)

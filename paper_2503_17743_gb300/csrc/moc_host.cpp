@@ -97,6 +97,7 @@ void trace_2d(const moc_geometry &g, double x0, double y0, double dx, double dy,
     cy = std::min(std::max(cy, 0), g.ncy - 1);
     double t = 0.0;
     const int stepx = dx > 0 ? 1 : -1;
+    std::vector<double> cuts;
     while (t < L) {
         double tx = ((cx + (dx > 0 ? 1 : 0)) * p - x0) / dx;
         double ty = ((cy + 1) * p - y0) / dy;
@@ -104,26 +105,46 @@ void trace_2d(const moc_geometry &g, double x0, double y0, double dx, double dy,
         int c = cy * g.ncx + cx;
         int base = g.reg_base[c];
         if (g.has_pin[c]) {
-            double ccx = (cx + 0.5) * p, ccy = (cy + 0.5) * p;
-            double fx = x0 - ccx, fy = y0 - ccy;
-            double b = fx * dx + fy * dy;
-            double cc = fx * fx + fy * fy - g.radius * g.radius;
-            double disc = b * b - cc;
-            double t1 = 0, t2 = 0;
-            bool hit = false;
-            if (disc > 0.0) {
-                double sq = std::sqrt(disc);
-                t1 = -b - sq;
-                t2 = -b + sq;
-                hit = t2 > t && t1 < te;
+            // cut the chord at every circle and every sector ray of the cell,
+            // then name each piece by its midpoint
+            const double ccx = (cx + 0.5) * p, ccy = (cy + 0.5) * p;
+            const double fx = x0 - ccx, fy = y0 - ccy;
+            const double b = fx * dx + fy * dy, f2 = fx * fx + fy * fy;
+            cuts.clear();
+            for (double r2 : g.ring_r2) {
+                const double disc = b * b - (f2 - r2);
+                if (!(disc > 0.0)) continue;
+                const double sq = std::sqrt(disc);
+                if (-b - sq > t && -b - sq < te) cuts.push_back(-b - sq);
+                if (-b + sq > t && -b + sq < te) cuts.push_back(-b + sq);
             }
-            if (hit) {
-                double a0 = std::max(t1, t), a1 = std::min(t2, te);
-                if (a0 > t) out.push_back({base + 1, t, a0});
-                out.push_back({base, a0, a1});
-                if (a1 < te) out.push_back({base + 1, a1, te});
-            } else {
-                out.push_back({base + 1, t, te});
+            for (int s = 0; g.sectors > 1 && s < g.sectors; ++s) {
+                const double th = 2.0 * kPi * s / g.sectors, cs = std::cos(th), sn = std::sin(th);
+                const double den = dx * sn - dy * cs;  // crossing of the line through the centre
+                if (den == 0.0) continue;
+                const double ts = (fy * cs - fx * sn) / den;
+                if (!(ts > t && ts < te)) continue;
+                // on the ray (the centre itself counts: a chord through it
+                // changes sector there)
+                if ((fx + ts * dx) * cs + (fy + ts * dy) * sn >= 0.0) cuts.push_back(ts);
+            }
+            std::sort(cuts.begin(), cuts.end());
+            double a = t;
+            for (size_t k = 0; k <= cuts.size(); ++k) {
+                const double e = k < cuts.size() ? cuts[k] : te;
+                if (!(e > a)) continue;
+                const double tm = 0.5 * (a + e);
+                const double mx = fx + tm * dx, my = fy + tm * dy, d2 = mx * mx + my * my;
+                int ring = 0;
+                while (ring < (int)g.ring_r2.size() && !(d2 < g.ring_r2[ring])) ++ring;
+                int sec = 0;
+                if (g.sectors > 1) {
+                    double ang = std::atan2(my, mx);
+                    if (ang < 0.0) ang += 2.0 * kPi;
+                    sec = std::min(g.sectors - 1, (int)(ang * g.sectors / (2.0 * kPi)));
+                }
+                out.push_back({base + ring * g.sectors + sec, a, e});
+                a = e;
             }
         } else {
             out.push_back({base, t, te});
@@ -561,6 +582,11 @@ extern "C" int moc_create_geometry(const moc_geometry_desc *d, const moc_materia
         moc_set_error("geometry: lattice too large");
         return MOC_ERR_UNSUPPORTED;
     }
+    if (d->fuel_rings < 0 || d->fuel_rings > 64 || d->moderator_rings < 0 || d->moderator_rings > 64 ||
+        d->sectors < 0 || d->sectors > 64) {
+        moc_set_error("geometry: fuel_rings, moderator_rings and sectors must lie in [0, 64]");
+        return MOC_ERR_INVALID_ARG;
+    }
     if (mt->num_materials < 1 || mt->num_groups < 1 || mt->num_groups > 1024 || !mt->sigma_t ||
         !mt->sigma_s || !mt->nu_sigma_f || !mt->chi) {
         moc_set_error("materials: bad sizes or NULL arrays");
@@ -609,13 +635,24 @@ extern "C" int moc_create_geometry(const moc_geometry_desc *d, const moc_materia
             return fail("geometry: material index out of range");
     g->Wx = g->ncx * g->pitch;
     g->Wy = g->ncy * g->pitch;
+    // pin-cell circles: equal-area rings of the fuel circle, then equal-area
+    // steps between the fuel circle and the inscribed circle of the cell
+    g->fuel_rings = std::max(1, (int)d->fuel_rings);
+    g->sectors = std::max(1, (int)d->sectors);
+    const int mrings = std::max(0, (int)d->moderator_rings);
+    const double rf2 = g->radius * g->radius, ri2 = 0.25 * g->pitch * g->pitch;
+    g->ring_r2.clear();
+    for (int k = 1; k <= g->fuel_rings; ++k) g->ring_r2.push_back(rf2 * k / g->fuel_rings);
+    for (int k = 1; k <= mrings; ++k) g->ring_r2.push_back(rf2 + (ri2 - rf2) * k / (mrings + 1));
+    const int pin_regions = ((int)g->ring_r2.size() + 1) * g->sectors;
     g->reg_base.resize(nc);
-    int nr = 0;
+    int64_t nr = 0;
     for (size_t c = 0; c < nc; ++c) {
-        g->reg_base[c] = nr;
-        nr += g->has_pin[c] ? 2 : 1;
+        g->reg_base[c] = (int32_t)std::min<int64_t>(nr, 0x7fffffff);
+        nr += g->has_pin[c] ? pin_regions : 1;
     }
-    g->nreg = nr;
+    if (nr > 0x7fffffffLL) nr = 0x7fffffffLL;
+    g->nreg = (int)nr;
     if ((int64_t)nr * g->nl > 0x7fffffffLL / std::max(1, g->G)) {
         moc_set_error("geometry: too many FSRs");
         delete g;
@@ -626,8 +663,12 @@ extern "C" int moc_create_geometry(const moc_geometry_desc *d, const moc_materia
     for (size_t c = 0; c < nc; ++c) {
         for (int l = 0; l < g->nl; ++l) {
             if (g->has_pin[c]) {
-                g->fsr_mat[(size_t)g->reg_base[c] * g->nl + l] = g->mat_in[c * g->nl + l];
-                g->fsr_mat[(size_t)(g->reg_base[c] + 1) * g->nl + l] = g->mat_out[c * g->nl + l];
+                // rings inside the fuel circle: the pin's material; the rest: moderator
+                for (int r = 0; r < pin_regions; ++r) {
+                    const bool fuel = r / g->sectors < g->fuel_rings;
+                    g->fsr_mat[(size_t)(g->reg_base[c] + r) * g->nl + l] =
+                        fuel ? g->mat_in[c * g->nl + l] : g->mat_out[c * g->nl + l];
+                }
             } else {
                 g->fsr_mat[(size_t)g->reg_base[c] * g->nl + l] = g->mat_out[c * g->nl + l];
             }

@@ -21,6 +21,10 @@ struct moc_geometry {
     double Wx = 0, Wy = 0;
     int nreg = 0, nfsr = 0;
     std::vector<int32_t> reg_base;  // first radial region of each cell
+    // pin cells: circles (squared radii, increasing), fuel rings among them,
+    // angular sectors; a pin cell has (circles + 1) * sectors regions
+    std::vector<double> ring_r2;
+    int fuel_rings = 1, sectors = 1;
     std::vector<int32_t> fsr_mat;   // material of each FSR
 };
 

@@ -31,6 +31,10 @@ PROBLEMS = {
     "lat3_mixed": lambda: _lat3(bc=(1, 0, 1, 1, 0, 1), seed=4),
     "lattice5": lambda: synth.workload("lattice5"),
     "l17_small": lambda: synth.workload("lattice17_small"),
+    # finer pin-cell regions: rings and angular sectors
+    "lat3_rings": lambda: _lat3(bc=(1, 0, 1, 1, 0, 1), seed=5).with_tracks(
+        fuel_rings=2, moderator_rings=1, sectors=8, name="lat3_rings"),
+    "lattice5_rings": lambda: synth.workload("lattice5_rings"),
 }
 
 _cache = {}
@@ -73,7 +77,7 @@ def test_volumes(name):
 
 
 @pytest.mark.parametrize("prec,rtol", [(MOC_FP64, 1e-11), (MOC_FP32, 2e-5)])
-@pytest.mark.parametrize("name", ["pin", "lat3", "lat3_mixed", "l17_small"])
+@pytest.mark.parametrize("name", ["pin", "lat3", "lat3_mixed", "l17_small", "lat3_rings"])
 def test_two_sweeps_from_source(name, prec, rtol):
     """Seeded source, zero incoming fluxes, two sweeps: the second one runs on
     the boundary fluxes the first one passed through the links."""
@@ -122,7 +126,7 @@ def test_single_track_links(name):
 
 
 @pytest.mark.parametrize("prec,ktol,ftol", [(MOC_FP64, 1e-11, 1e-10), (MOC_FP32, 1e-5, 1e-4)])
-@pytest.mark.parametrize("name", ["pin", "lat3_mixed", "lattice5", "l17_small"])
+@pytest.mark.parametrize("name", ["pin", "lat3_mixed", "lattice5", "l17_small", "lattice5_rings"])
 def test_power_iterations(name, prec, ktol, ftol):
     p, o, tr = make(name, precision=prec)
     n = 15
