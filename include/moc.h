@@ -131,7 +131,13 @@ typedef struct {
  *   groups_per_lane    energy groups one thread carries along a track: 1, 2
  *                      or 4 (2 and 4 for FP32 sweeps only; 0 = tuned default)
  *   schedule           0, or MOC_SCHED_* flags that switch off a load-balancing
- *                      step (Sec. 4.3), for ablations */
+ *                      step (Sec. 4.3), for ablations
+ *   chunk_segments     shared tally only: sweep a unit (2D track) in radial
+ *                      chunks of at most this many 2D segments; 0 = only the
+ *                      units whose tile does not fit in shared memory, in the
+ *                      largest chunks that keep three blocks per SM.  A
+ *                      track's psi passes from chunk to chunk; results equal
+ *                      the whole-unit sweep up to FP rounding. */
 typedef struct {
     int32_t n_azim, n_polar;
     double radial_spacing, axial_spacing;
@@ -143,6 +149,7 @@ typedef struct {
     int32_t device;
     int32_t groups_per_lane;
     int32_t schedule;
+    int32_t chunk_segments;
 } moc_track_params;
 
 /* Stopping rule of a solve: |k_n - k_(n-1)| < tol_k (eigenvalue problems
@@ -256,7 +263,8 @@ int moc_get_volumes(moc_tracks *tracks, double *volumes);
  *   14 tally mode in use, 15 precision, 16 sweep shared memory bytes per block,
  *   17 shared tile entries, 18 lanes per track, 19 most segments on one
  *   track, 20 bytes copied host to device while generating, 21 energy
- *   groups per lane */
+ *   groups per lane, 22 2D segments per radial chunk (0: no unit is
+ *   chunked) */
 int moc_tracks_info(const moc_tracks *tracks, int64_t *out, int32_t n);
 
 /* 3D segments of z-stack (t, p) as the device generator produces them

@@ -54,7 +54,8 @@ class moc_track_params(C.Structure):
                 ("axial_spacing", C.c_double), ("precision", C.c_int32),
                 ("preload_budget_bytes", C.c_int64), ("tally_mode", C.c_int32),
                 ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("device", C.c_int32),
-                ("groups_per_lane", C.c_int32), ("schedule", C.c_int32)]
+                ("groups_per_lane", C.c_int32), ("schedule", C.c_int32),
+                ("chunk_segments", C.c_int32)]
 
 
 class moc_server_params(C.Structure):
@@ -205,7 +206,8 @@ class Geometry:
 
 
 def track_params(prob, precision=MOC_FP32, preload_budget_bytes=-1, tally_mode=MOC_TALLY_AUTO,
-                 block_threads=0, blocks_per_sm=0, device=0, groups_per_lane=0, schedule=0):
+                 block_threads=0, blocks_per_sm=0, device=0, groups_per_lane=0, schedule=0,
+                 chunk_segments=0):
     p = moc_track_params()
     p.n_azim, p.n_polar = prob.n_azim, prob.n_polar
     p.radial_spacing, p.axial_spacing = prob.radial_spacing, prob.axial_spacing
@@ -217,6 +219,7 @@ def track_params(prob, precision=MOC_FP32, preload_budget_bytes=-1, tally_mode=M
     p.device = device
     p.groups_per_lane = groups_per_lane
     p.schedule = schedule
+    p.chunk_segments = chunk_segments
     return p
 
 
@@ -224,7 +227,7 @@ INFO_KEYS = ["n_fsr", "groups", "tracks2d", "stacks", "tracks3d", "segments3d",
              "integrations_per_sweep", "stored_segments", "preloaded_stacks", "device_bytes",
              "n_z", "cells_per_layer", "sweep_blocks", "sweep_threads", "tally_mode", "precision",
              "sweep_smem_bytes", "tile_entries", "lanes_per_track", "max_segments_per_track",
-             "h2d_bytes", "groups_per_lane"]
+             "h2d_bytes", "groups_per_lane", "chunk_segments"]
 
 
 class Tracks:

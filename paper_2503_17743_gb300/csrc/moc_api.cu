@@ -36,7 +36,7 @@ struct moc_tracks {
     // device buffers
     DevBuf d_desc, d_zn, d_zf, d_zf64, d_reg2d, d_len2d, d_len2d64, d_segs, d_fsr_mat, d_order;
     DevBuf d_tpl_off, d_tpl_loff, d_tpl_lmin, d_tpl_lidx;
-    DevBuf d_dst, d_perm, d_win;
+    DevBuf d_dst, d_perm, d_win, d_chunk, d_hand;
     DevBuf d_phi, d_qr, d_tally, d_vol, d_psi[2], d_fiss, d_fiss_old, d_partial, d_scal, d_counter;
     DevBuf d_sigt, d_sigt64, d_sigs64, d_nsf64, d_chi64, d_src64, d_inv_st64, d_siga64, d_inv_vol;
     double *h_scal = nullptr;  // pinned mirror of the device scalars
@@ -58,6 +58,8 @@ struct moc_tracks {
     int gpl = 1;                // energy groups per lane
     int tally_bits = 0;         // fixed-point bits of the FP32 shared tally
     int tile_cap = 0;
+    int chunk_b = 0;            // 2D segments per radial chunk (0: units swept whole)
+    int64_t hand_trk = 0;       // tracks of the largest chunked unit
     int block = 256;
     int grid = 0;
     size_t smem = 0;
@@ -135,6 +137,10 @@ void fill_views(moc_tracks *h) {
     dl.bc_zmax = h->geom.bc[FACE_ZMAX];
     dl.n_slots = h->L.n_gtrk * 4;
     dl.tally_bits = h->tally_bits;
+    dl.chunk_tab = (const int64_t *)h->d_chunk.p;
+    dl.chunk_b = h->chunk_b;
+    dl.hand_trk = (int32_t)h->hand_trk;
+    dl.hand = h->d_hand.p;
     DevState &s = h->ds;
     s.phi = (double *)h->d_phi.p;
     s.qr = h->d_qr.p;
@@ -412,12 +418,33 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     }
     h->gpl = prm->groups_per_lane > 0 ? prm->groups_per_lane : sweep_default_gpl(h->precision, G);
     {
+        // a unit whose tile exceeds kWholeTile is swept in radial chunks of
+        // chunk_b 2D segments, sized for three blocks per SM; GLOBAL when not
+        // even one 2D segment's layers fit
+        constexpr size_t kWholeTile = 100 * 1024, kChunkTile = 72 * 1024;
         int mode = prm->tally_mode;
-        const size_t smem_tile = sweep_smem_bytes(h->precision, 1, geo.M, G, h->gpl, h->tile_cap);
-        const bool fits = smem_tile <= 200 * 1024;
-        if (mode == MOC_TALLY_AUTO) mode = (fits && smem_tile <= 100 * 1024) ? MOC_TALLY_SHARED : MOC_TALLY_GLOBAL;
-        if (mode == MOC_TALLY_SHARED && !fits) mode = MOC_TALLY_GLOBAL;
+        if (prm->chunk_segments < 0) {
+            moc_set_error("chunk_segments must be >= 0");
+            return MOC_ERR_INVALID_ARG;
+        }
+        if (mode == MOC_TALLY_AUTO) mode = MOC_TALLY_SHARED;
+        if (mode == MOC_TALLY_SHARED &&
+            (prm->chunk_segments > 0 ||
+             sweep_smem_bytes(h->precision, 1, geo.M, G, h->gpl, h->tile_cap) > kWholeTile)) {
+            int cb = 0;
+            while (cb < h->nb_max &&
+                   sweep_smem_bytes(h->precision, 1, geo.M, G, h->gpl, (cb + 1) * geo.nl) <= kChunkTile)
+                ++cb;
+            if (prm->chunk_segments > 0) cb = std::min(cb, (int)prm->chunk_segments);
+            if (cb >= 1) {
+                h->chunk_b = cb;
+                h->tile_cap = cb * geo.nl;
+            } else {
+                mode = MOC_TALLY_GLOBAL;
+            }
+        }
         h->tally_smem = mode == MOC_TALLY_SHARED ? 1 : 0;
+        if (!h->tally_smem) h->chunk_b = 0;
     }
     // FP32 shared tally in fixed point: each contribution becomes an integer
     // multiple of 2^-bits of its unit's bound and is added with a native
@@ -442,7 +469,10 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
         }
         int bits = 21;
         while (bits > 0 && (nmax << bits) >= ((int64_t)1 << 30)) --bits;
-        if (bits < 12) h->tally_smem = 0;  // too many pieces per row: FP64 global tally instead
+        if (bits < 12) {  // too many pieces per row: FP64 global tally instead
+            h->tally_smem = 0;
+            h->chunk_b = 0;
+        }
         else h->tally_bits = bits;
     }
     TRY(cudaSetDevice(h->device), "cudaSetDevice");
@@ -493,6 +523,12 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
             const int n = L.desc[s].n_trk;
             int32_t *q = perm.data() + o;
             int32_t *p = q;
+            if (h->chunk_b > 0 && L.desc[s].nb > h->chunk_b) {
+                // radially chunked unit: tracks in index order, so that the
+                // tracks crossing one chunk are one contiguous range
+                for (int k = 0; k < n; ++k) q[k] = k;
+                continue;
+            }
             for (int r = 0; r < std::min(L.cpl, n); ++r)
                 for (int k = r; k < n; k += L.cpl) *p++ = k;
             if (!(prm->schedule & MOC_SCHED_TRACKS_NATURAL))
@@ -560,10 +596,8 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
             for (int r = 0; r < std::min(cpl, L.desc[s].n_trk); ++r) {
                 const int64_t q = tpl_first[s] + r;
                 need += tcnt[q] * rec_bytes + (int64_t)(tnlay[q] + 1) * 4 + 20;
-                // stored keys hold the two frames' tile rows b*NL + L_t and
-                // b*NL + NL-1-L_t as signed 16-bit numbers
-                ok = ok && tlmin[q] > -2000 && tlmin[q] + tnlay[q] < 2000 &&
-                     (int64_t)(L.desc[s].nb + 1) * geo.nl + 2000 < 32768;
+                // stored keys hold the template layer as a signed 16-bit number
+                ok = ok && tlmin[q] > -32768 && tlmin[q] + tnlay[q] < 32767;
             }
         }
         ok = ok && h->max_nseg < 65536;  // record windows hold the count in 16 bits
@@ -604,6 +638,43 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
         TRY(launch_windows(h->dl, ns, (uint64_t *)h->d_win.p, lgrid, h->stream), "record windows");
         TRY(cudaStreamSynchronize(h->stream), "templates");
         h->bytes -= d_exp_stacks.n;
+    }
+    fill_views(h.get());
+    if (h->chunk_b > 0) {
+        // chunk tables of the radially chunked units (see StackDesc::chunk_base)
+        const int cb = h->chunk_b;
+        std::vector<int32_t> cst;
+        int64_t n_ent = 0;
+        for (int t = 0; t < L.nt; ++t) {
+            const int64_t s0 = (int64_t)t * Ph;
+            if (L.desc[s0].nb <= cb) continue;
+            const int64_t C = (L.desc[s0].nb + cb - 1) / cb;
+            int64_t trk = 0;
+            for (int ph = 0; ph < Ph; ++ph) {
+                StackDesc &d = L.desc[s0 + ph];
+                const int64_t ntpl = d.exp_base >= 0 ? std::min(cpl, d.n_trk) : 0;
+                d.chunk_base = n_ent;
+                n_ent += C + ntpl * (C + 1);
+                trk += d.n_trk;
+                cst.push_back((int32_t)(s0 + ph));
+            }
+            h->hand_trk = std::max(h->hand_trk, trk);
+        }
+        if (!cst.empty()) {
+            DevBuf d_cst;
+            TRY(cudaMemcpyAsync(h->d_desc.p, L.desc.data(), ns * sizeof(StackDesc), cudaMemcpyHostToDevice,
+                                h->stream), "upload");
+            TRY(upload(h.get(), d_cst, cst), "upload");
+            TRY(dalloc(h.get(), h->d_chunk, (size_t)n_ent * 8), "alloc chunk tables");
+            fill_views(h.get());
+            const int cgrid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)cst.size(), (int64_t)h->sms * 16));
+            TRY(launch_chunk_tables(h->precision, h->dl, (const int32_t *)d_cst.p, (int64_t)cst.size(),
+                                    (int64_t *)h->d_chunk.p, cgrid, h->stream), "chunk tables");
+            TRY(cudaStreamSynchronize(h->stream), "chunk tables");
+            h->bytes -= d_cst.n;
+        } else {
+            h->chunk_b = 0;  // no unit needs chunks after all
+        }
     }
     fill_views(h.get());
     // cross sections
@@ -703,10 +774,17 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
         h->block = prm->block_threads > 0 ? std::max(32, std::min(prm->block_threads, bmax) / 32 * 32) : bmax;
     }
     int bps = 0;
-    TRY(sweep_occupancy(h->precision, h->tally_smem, G, h->gpl, h->block, h->smem, &bps), "occupancy");
+    TRY(sweep_occupancy(h->precision, h->tally_smem, h->chunk_b > 0, G, h->gpl, h->block, h->smem, &bps),
+        "occupancy");
     if (bps < 1) { moc_set_error("sweep kernel does not fit on an SM"); return MOC_ERR_UNSUPPORTED; }
     if (prm->blocks_per_sm > 0) bps = std::min(bps, prm->blocks_per_sm);
     h->grid = std::max(1, std::min<int>(h->sms * bps, (int)std::min<int64_t>(ns, 1 << 30)));
+    if (h->chunk_b > 0) {
+        // psi of the tracks between radial chunks: one region per block
+        TRY(dalloc(h.get(), h->d_hand, (size_t)h->grid * h->hand_trk * 2 * G * real_size(h->precision)),
+            "alloc chunk hand-off");
+        fill_views(h.get());
+    }
     rc = init_state(h.get());
     if (rc) return rc;
     *out = h.release();
@@ -871,13 +949,13 @@ extern "C" int moc_get_volumes(moc_tracks *h, double *v) {
 
 extern "C" int moc_tracks_info(const moc_tracks *h, int64_t *out, int32_t n) {
     if (!h || !out) { moc_set_error("NULL argument"); return MOC_ERR_INVALID_ARG; }
-    const int64_t v[22] = {h->geom.nfsr, h->geom.G, h->L.nt, 2 * h->L.n_stacks, 2 * h->L.n_gtrk,
+    const int64_t v[23] = {h->geom.nfsr, h->geom.G, h->L.nt, 2 * h->L.n_stacks, 2 * h->L.n_gtrk,
                            h->n_segments3d, (int64_t)h->integrations, h->n_stored, h->n_exp_stacks,
                            (int64_t)h->bytes, h->L.Nz, h->L.cpl, h->grid, h->block,
                            h->tally_smem ? MOC_TALLY_SHARED : MOC_TALLY_GLOBAL, h->precision,
                            (int64_t)h->smem, h->tile_cap, sweep_lanes_per_track(h->geom.G, h->gpl),
-                           h->max_nseg, (int64_t)h->h2d, h->gpl};
-    for (int i = 0; i < n && i < 22; ++i) out[i] = v[i];
+                           h->max_nseg, (int64_t)h->h2d, h->gpl, h->chunk_b};
+    for (int i = 0; i < n && i < 23; ++i) out[i] = v[i];
     return MOC_OK;
 }
 

@@ -31,6 +31,11 @@ struct DevLayout {
     int32_t bc_zmin, bc_zmax;
     int32_t tally_bits;      // FP32 shared tally: fixed-point bits per unit bound (0: not used)
     int64_t n_slots;         // geometric tracks * 4 variants (bound of every link)
+    // radial chunks of units whose tile does not fit in shared memory
+    const int64_t *chunk_tab; // see StackDesc::chunk_base
+    int32_t chunk_b;         // 2D segments per chunk (0: every unit is swept whole)
+    int32_t hand_trk;        // tracks per block in the chunk hand-off buffer
+    void *hand;              // [grid][hand_trk][2 frames][G] real: psi between chunks
 };
 
 // State buffers of one solve.
@@ -292,13 +297,12 @@ __device__ __forceinline__ real tpl_len(const DevLayout &dl, const StackDesc &d,
     return (real)dl.cpl * lam;                                                              // Eq. 11
 }
 
-// A stored template piece: key = the tile rows of the piece in both frames,
-// A = b * NL + L_t (upward) and B = b * NL + NL - 1 - L_t (mirrored), as
-// signed 16-bit numbers (A low, B high), with b the 2D segment and L_t the
-// template layer.  Track r + m cpl of the class meets the piece in rows A + m
-// and B - m.
-__host__ __device__ __forceinline__ uint32_t tpl_key(int A, int B) {
-    return (uint32_t)(uint16_t)(int16_t)A | ((uint32_t)(uint16_t)(int16_t)B << 16);
+// A stored template piece: key = b << 16 | L_t, the 2D segment b (0..65535)
+// and the template layer L_t (signed 16 bits).  Track r + m cpl of the class
+// meets the piece in tile rows b NL + L_t + m (upward frame) and
+// b NL + NL - 1 - L_t - m (mirrored frame).
+__host__ __device__ __forceinline__ uint32_t tpl_key(int b, int L) {
+    return ((uint32_t)b << 16) | (uint32_t)(uint16_t)(int16_t)L;
 }
-__device__ __forceinline__ int tpl_row_up(uint32_t key) { return (int)(int16_t)(key & 0xffffu); }
-__device__ __forceinline__ int tpl_row_down(uint32_t key) { return (int)key >> 16; }
+__device__ __forceinline__ int tpl_seg(uint32_t key) { return (int)(key >> 16); }
+__device__ __forceinline__ int tpl_layer(uint32_t key) { return (int)(int16_t)(key & 0xffffu); }

@@ -483,12 +483,7 @@ int moc_build_layout(const moc_geometry &g, const moc_track_params &prm, Layout 
             d.lam64 = L.dz / L.cosp[k];
             d.inv_sin64 = 1.0 / L.sinp[k];
             d.W = L.W[k];
-            // golden-ratio stride through the stack, coprime with its size
-            {
-                int64_t n = d.n_trk, st = std::max<int64_t>(1, (int64_t)std::llround(0.381966 * (double)n));
-                while (n > 1 && gcd64(st, n) != 1) ++st;
-                d.task_stride = (int32_t)(n > 1 ? st : 1);
-            }
+            d.chunk_base = -1;
             for (int v = 0; v < 4; ++v) {
                 const int frame = v >> 1, sense = v & 1;
                 const bool up = (frame == 0) == (sense == 0);

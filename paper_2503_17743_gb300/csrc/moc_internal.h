@@ -57,8 +57,12 @@ struct StackDesc {
     int8_t rad_sign[4];
     int8_t rad_bc[4];       // 1 if the radial face of that exit is reflective
     int8_t pad[4];
-    int32_t task_stride;    // coprime with n_trk: order in which the sweep takes the tracks
-    int32_t pad2;
+    // units swept in radial chunks (their tile does not fit in shared
+    // memory): first entry of the stack in the chunk table, -1 otherwise.
+    // Entries: per chunk c < C the stack's tracks that cross it (first track
+    // | count << 32), then per stored template r < min(cpl, n_trk) and
+    // c <= C the first record at or beyond 2D segment c * chunk_b
+    int64_t chunk_base;
 };
 
 // ---------------------------------------------------------------------------

@@ -100,7 +100,7 @@ __global__ void k_tpl_write(DevLayout dl, const int32_t *exp_stacks, int64_t n_e
                 for (int L = tr.La; L <= tr.Le; ++L) {
                     while (x <= L - Lmin && x <= nL) lidx[lb + x++] = pos;
                     SegRec<real> rec{};
-                    rec.key = tpl_key(b * dl.NL + L, b * dl.NL + dl.NL - 1 - L);
+                    rec.key = tpl_key(b, L);
                     rec.len = tpl_len(dl, d, b, tr, L);
                     out[pos++] = rec;
                 }
@@ -131,6 +131,56 @@ __global__ void k_windows(DevLayout dl, int64_t n_stacks, uint64_t *win) {
             const int64_t p0 = tb + dl.tpl_lidx[lb + min(max(-m - Lmin, 0), nL)];
             const int64_t p1 = tb + dl.tpl_lidx[lb + min(max(dl.NL - m - Lmin, 0), nL)];
             win[d.trk_off + q] = ((uint64_t)(p1 - p0) << 48) | (uint64_t)p0;
+        }
+    }
+}
+
+// Chunk tables of radially chunked units.  Tracks crossing chunk c: the
+// 2D segment range [first_seg, last_seg] of track i shrinks towards lower b
+// as i grows (both ends are monotone in i), so they are one index range,
+// found by two bisections.  Template records are in order of the 2D segment
+// of their keys.
+template <typename real>
+__global__ void k_chunk_tables(DevLayout dl, const int32_t *stacks, int64_t n, int64_t *tab) {
+    const SegRec<real> *recs = reinterpret_cast<const SegRec<real> *>(dl.segs);
+    const int cb = dl.chunk_b, NL = dl.NL;
+    for (int64_t x = blockIdx.x; x < n; x += gridDim.x) {
+        const StackDesc &d = dl.desc[stacks[x]];
+        const int C = (d.nb + cb - 1) / cb;
+        const int ntpl = d.exp_base >= 0 ? min(dl.cpl, d.n_trk) : 0;
+        int64_t *t = tab + d.chunk_base;
+        for (int e = threadIdx.x; e < C + ntpl * (C + 1); e += blockDim.x) {
+            if (e < C) {
+                // first track whose last segment reaches chunk e, first whose
+                // first segment does not lie beyond it
+                int lo = 0, hi = d.n_trk;  // first k with last_seg < e * cb
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (last_seg(dl, d, d.i_lo + mid) < e * cb) hi = mid; else lo = mid + 1;
+                }
+                const int k1 = lo;
+                lo = 0;
+                hi = d.n_trk;  // first k with first_seg < (e + 1) * cb
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (first_seg(dl, d, d.i_lo + mid) < (e + 1) * cb) hi = mid; else lo = mid + 1;
+                }
+                const int k0 = lo;
+                const int cnt = max(0, k1 - k0);
+                t[e] = (int64_t)k0 | ((int64_t)cnt << 32);
+            } else {
+                const int r = (e - C) / (C + 1), c = (e - C) - r * (C + 1);
+                const int64_t q = d.exp_base + r;
+                int64_t lo = dl.tpl_off[q], hi = dl.tpl_off[q + 1];
+                const int bb = c * cb;
+                while (lo < hi) {  // first record with b >= c * cb
+                    const int64_t mid = (lo + hi) >> 1;
+                    const uint32_t key = recs[mid].key;
+                    const int b = tpl_seg(key);
+                    if (b >= bb) hi = mid; else lo = mid + 1;
+                }
+                t[e] = lo;
+            }
         }
     }
 }
@@ -432,6 +482,13 @@ cudaError_t launch_track_counts(const DevLayout &dl, int64_t stack, int64_t *cnt
 cudaError_t launch_windows(const DevLayout &dl, int64_t n_stacks, uint64_t *win, int grid,
                            cudaStream_t s) {
     k_windows<<<grid, 128, 0, s>>>(dl, n_stacks, win);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chunk_tables(int precision, const DevLayout &dl, const int32_t *stacks, int64_t n,
+                                int64_t *tab, int grid, cudaStream_t s) {
+    if (precision == MOC_FP64) k_chunk_tables<double><<<grid, 128, 0, s>>>(dl, stacks, n, tab);
+    else k_chunk_tables<float><<<grid, 128, 0, s>>>(dl, stacks, n, tab);
     return cudaGetLastError();
 }
 

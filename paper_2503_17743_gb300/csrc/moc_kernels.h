@@ -17,6 +17,9 @@ cudaError_t launch_track_counts(const DevLayout &dl, int64_t stack, int64_t *cnt
 // per track of the stored stacks, in sweep order: (record count << 48) | first record
 cudaError_t launch_windows(const DevLayout &dl, int64_t n_stacks, uint64_t *win, int grid,
                            cudaStream_t s);
+// chunk tables of the stacks of radially chunked units (StackDesc::chunk_base)
+cudaError_t launch_chunk_tables(int precision, const DevLayout &dl, const int32_t *stacks, int64_t n,
+                                int64_t *tab, int grid, cudaStream_t s);
 cudaError_t launch_links(const DevLayout &dl, int64_t n_stacks, int32_t *dst, int grid,
                          cudaStream_t s);
 cudaError_t launch_volumes(int precision, const DevLayout &dl, int64_t n_stacks, double *vol,
@@ -37,8 +40,8 @@ cudaError_t launch_sweep(int precision, int tally_smem, int gpl, const DevLayout
                          const void *psi_in, void *psi_out, int32_t *counter,
                          const unsigned *bound_in, unsigned *bound_out, int grid, int block,
                          size_t smem, cudaStream_t s);
-cudaError_t sweep_occupancy(int precision, int tally_smem, int G, int gpl, int block, size_t smem,
-                            int *blocks_per_sm);
+cudaError_t sweep_occupancy(int precision, int tally_smem, int chunk, int G, int gpl, int block,
+                            size_t smem, int *blocks_per_sm);
 // threads per block of the per-FSR kernels (source, finalize, residual, init):
 // small blocks spread a few thousand FSRs over many SMs
 constexpr int kSmallBlock = 64;

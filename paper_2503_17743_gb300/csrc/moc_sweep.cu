@@ -55,7 +55,7 @@ __device__ __forceinline__ double attenuation<double>(double x) {
 // (the track weight and its inverse in both precisions: the sweep's hot path
 // does no FP64 arithmetic in FP32 mode)
 struct UnitStack {
-    int64_t trk_off, tpl_base;
+    int64_t trk_off, tpl_base, cbase;
     double W, invW;
     float Wf, invWf;
     int32_t n_trk, i_lo, task_pre, pad;
@@ -191,7 +191,7 @@ constexpr int kMaxSweepBlock = 320;
 // words per shared tally row
 __host__ __device__ constexpr int tally_stride(int GL, int GPL) { return GL * GPL + (GPL > 1 ? 1 : 0); }
 
-template <typename real, int GL, int GPL, bool SMEM>
+template <typename real, int GL, int GPL, bool SMEM, bool CHUNK>
 __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(real) == 4 ? 3 : 2)
     k_sweep(DevLayout dl, DevState st, const int32_t *order, int32_t n_work, int32_t cap,
             const real *psi_in, real *psi_out, const unsigned *bound_in, unsigned *bound_out) {
@@ -205,6 +205,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
     __shared__ float s_inv[32];      // and its inverse
     __shared__ unsigned s_bmax[32];  // bound of |W psi| and |W Qr| per group (float bits)
     __shared__ unsigned s_pmax[32];  // max |psi_out| the block stored per group (float bits)
+    __shared__ unsigned s_hmax[32];  // max |psi| handed to the next radial chunk (float bits)
     __shared__ float s_wmax;
     constexpr bool kFixed = sizeof(real) == 4;  // FP32 sweeps tally in fixed point
     const int G = dl.G, NL = dl.NL, M = dl.M, Ph = dl.Ph, cpl = dl.cpl;
@@ -239,6 +240,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
 #pragma unroll
     for (int c = 0; c < GPL; ++c) pmax[c] = 0.0f;
     if (tid < 32) s_pmax[tid] = 0u;
+    if (tid < 32) s_hmax[tid] = 0u;
     // lanes with the same groups (one per slot) fold their maxima into s_pmax
     auto fold_pmax = [&](int gc_) {
 #pragma unroll
@@ -264,6 +266,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                 UnitStack u;
                 u.trk_off = e.trk_off;
                 u.tpl_base = e.exp_base;
+                u.cbase = e.chunk_base;
                 u.W = e.W;
                 u.invW = 1.0 / e.W;
                 u.Wf = (float)e.W;
@@ -287,7 +290,21 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
         const StackDesc &d0 = dl.desc[(int64_t)T * Ph];
         const int nb = d0.nb;
         const int32_t *reg2d = dl.reg2d + d0.seg2d_off;
-        for (int g0 = 0; g0 < G; g0 += GP) {
+        // A unit whose tile does not fit is swept in C radial chunks of
+        // chunk_b 2D segments: first every track in sense 0, chunk by chunk
+        // along the 2D track, then in sense 1 back again; a track's psi passes
+        // from chunk to chunk through this block's hand-off buffer.
+        const int C = (CHUNK && nb > dl.chunk_b) ? (nb + dl.chunk_b - 1) / dl.chunk_b : 1;
+        real *hand = CHUNK ? reinterpret_cast<real *>(dl.hand) + (size_t)blockIdx.x * dl.hand_trk * 2 * G
+                           : nullptr;
+        const int64_t unit_trk0 = s_us[0].trk_off;
+        for (int g0 = 0; g0 < G; g0 += GP)
+        for (int pass = 0; pass < (C > 1 ? 2 : 1); ++pass)
+        for (int ci = 0; ci < C; ++ci) {
+            const int c_ch = pass ? C - 1 - ci : ci;             // radial chunk
+            const int b0 = C > 1 ? c_ch * dl.chunk_b : 0;       // its 2D segments [b0, b1)
+            const int b1 = C > 1 ? min(nb, b0 + dl.chunk_b) : nb;
+            const int rowoff = b0 * NL;                          // tile row of (b0, layer 0)
             __syncthreads();  // the previous chunk's flush is done with the tile
             const int gc = min(GP, G - g0);
             float bmax = 0.0f;  // this thread's bound for group tid % GP of the chunk
@@ -297,15 +314,30 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                 if (sizeof(real) == 4) v = (real)((float)v * kLog2e);
                 sig[e] = v;
             }
+            if (C > 1 && warp == 0) {
+                // this chunk's warp tasks: per polar stack, blocks of SLOTS of the
+                // tracks that cross the chunk (one sense per pass)
+                int cnt = 0;
+                if (lane < Ph) cnt = (int)(__ldg(dl.chunk_tab + s_us[lane].cbase + c_ch) >> 32);
+                cnt = (cnt + SLOTS - 1) / SLOTS;
+                int incl = cnt;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                if (lane < Ph) s_us[lane].task_pre = incl - cnt;
+                if (lane == 31) s_ntask = incl;
+            }
             if (SMEM) {
-                // rows of the (2D segment, layer) FSRs the unit crosses
-                for (int b = warp; b < nb; b += nwarps) {
+                // rows of the (2D segment, layer) FSRs the unit (chunk) crosses
+                for (int bb = warp; bb < b1 - b0; bb += nwarps) {
+                    const int b = b0 + bb;
                     const int reg = __ldg(reg2d + b);
                     for (int x = lane; x < NL * GP; x += 32) {
                         const int L = x / GP, qq = x - L * GP;
                         const int f = reg * NL + L;
-                        const int e = (b * NL + L) * GP + qq;
-                        const int et = (b * NL + L) * TS + qq;
+                        const int e = (bb * NL + L) * GP + qq;
+                        const int et = (bb * NL + L) * TS + qq;
                         real q = (real)0, sg = (real)0;
                         if (qq < gc) {
                             const int m = __ldg(dl.fsr_mat + f);
@@ -326,11 +358,15 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                     const int qq = tid % GP;
                     if (bound_in && psi_in && qq < gc)
                         bmax = fmaxf(bmax, __uint_as_float(__ldg(bound_in + g0 + qq)) * fabsf((float)scale));
+                    // and psi handed over from the previous chunk of this pass
+                    if (C > 1 && ci > 0) bmax = fmaxf(bmax, __uint_as_float(s_hmax[qq]));
                     atomicMax(&s_bmax[qq], __float_as_uint(bmax));
                 }
             }
             __syncthreads();
             if (tid == 0) s_next = 0;
+            if (C > 1 && tid < 32) s_hmax[tid] = 0u;  // read above; refilled by this chunk's tasks
+            const int ntask_c = C > 1 ? s_ntask : ntask;
             if (kFixed && SMEM && tid < GP) {
                 // one unit of the fixed-point tally = 2^-bits of a bound of every
                 // contribution W |psi - Qr| <= W (|psi| + |Qr|)
@@ -340,23 +376,70 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
             }
             __syncthreads();
 
+            float hmx[GPL];  // this lane's max |psi| handed to the next chunk
+#pragma unroll
+            for (int c = 0; c < GPL; ++c) hmx[c] = 0.0f;
             for (;;) {
                 int t = 0;
                 if (lane == 0) t = atomicAdd(&s_next, 1);
                 t = __shfl_sync(0xffffffffu, t, 0);
-                if (t >= ntask) break;
+                if (t >= ntask_c) break;
                 // warp task: polar stack ph, sense, block of SLOTS tracks taken in
                 // decreasing segment count
                 int ph = 0;
                 while (ph + 1 < Ph && t >= s_us[ph + 1].task_pre) ++ph;
                 const UnitStack u = s_us[ph];
                 const int x = t - u.task_pre;
-                const int sense = x & 1;
-                const int q = (x >> 1) * SLOTS + j;
-                const bool valid = q < u.n_trk;
-                const int k = valid ? __ldg(dl.perm + u.trk_off + q) : 0;  // track in the stack
+                int sense, q, k, widx;
+                bool valid;
+                if (C > 1) {
+                    // tracks k0 .. k0 + count - 1 of the stack cross this chunk
+                    // (index order), one sense per pass
+                    const int64_t rng = __ldg(dl.chunk_tab + u.cbase + c_ch);
+                    sense = pass;
+                    q = x * SLOTS + j;
+                    valid = q < (int)(rng >> 32);
+                    k = valid ? (int)(rng & 0xffffffff) + q : 0;
+                    widx = k;
+                } else {
+                    sense = x & 1;
+                    q = (x >> 1) * SLOTS + j;
+                    valid = q < u.n_trk;
+                    k = valid ? __ldg(dl.perm + u.trk_off + q) : 0;  // track in the stack
+                    widx = q;
+                }
                 const int m = k / cpl;                       // shift of the track within its class
                 const int64_t gid = u.trk_off + k;
+                // the track's part in this chunk: records [p0, p0 + n) of its
+                // window (stored) or 2D segments [sb0, sb1] (on the fly), and
+                // whether its first / last piece lies here (psi from psi_in /
+                // to its successor) or it continues across a chunk boundary
+                bool first_in = true, last_out = true;
+                int64_t p0 = 0;
+                int n = 0, sb0 = 0, sb1 = -1;
+                if (CHUNK && C > 1 && u.tpl_base >= 0) {
+                    const uint64_t wn = valid ? __ldg(dl.win + u.trk_off + widx) : 0ull;
+                    p0 = (int64_t)(wn & 0xffffffffffffull);
+                    n = (int)(wn >> 48);
+                    if (valid) {
+                        const int64_t *cb = dl.chunk_tab + u.cbase + C + (int64_t)(k - m * cpl) * (C + 1) + c_ch;
+                        const int64_t lo = max(p0, __ldg(cb)), hi = min(p0 + n, __ldg(cb + 1));
+                        first_in = sense == 0 ? lo == p0 : hi == p0 + n;
+                        last_out = sense == 0 ? hi == p0 + n : lo == p0;
+                        p0 = lo;
+                        n = hi > lo ? (int)(hi - lo) : 0;
+                    }
+                } else if (CHUNK && C > 1 && valid) {
+                    const StackDesc &dsk = dl.desc[(int64_t)T * Ph + ph];
+                    const int i_trk = u.i_lo + k;
+                    const int fb = first_seg(dl, dsk, i_trk), lb = last_seg(dl, dsk, i_trk);
+                    sb0 = max(fb, b0);
+                    sb1 = min(lb, b1 - 1);
+                    first_in = sense == 0 ? fb >= b0 : lb < b1;
+                    last_out = sense == 0 ? lb < b1 : fb >= b0;
+                }
+                const bool active = valid && (C == 1 || (u.tpl_base >= 0 ? n > 0 : sb0 <= sb1));
+                const int64_t lt = gid - unit_trk0;  // hand-off slot of the track
                 // psi is carried pre-multiplied by the track weight W, so that the
                 // tally contribution W (psi_in - psi_out) is the psi change itself
                 const real W = sizeof(real) == 4 ? (real)u.Wf : (real)u.W;
@@ -383,8 +466,18 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                     psiD[c] = (real)0;
                 }
                 int64_t dstU = -1, dstD = -1;
-                if (valid) {
-                    if (psi_in) {
+                if (active) {
+                    if (!first_in) {
+                        // psi left by the previous chunk of this pass
+#pragma unroll
+                        for (int c = 0; c < GPL; ++c) {
+                            const int qq = ql * GPL + c;
+                            if (qq < gc) {
+                                psiU[c] = hand[(lt * 2 + 0) * G + g0 + qq] * WS[c];
+                                psiD[c] = hand[(lt * 2 + 1) * G + g0 + qq] * WS[c];
+                            }
+                        }
+                    } else if (psi_in) {
 #pragma unroll
                         for (int c = 0; c < GPL; ++c) {
                             const int qq = ql * GPL + c;
@@ -394,7 +487,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                             }
                         }
                     }
-                    if (dl.dst) {
+                    if (last_out && dl.dst) {
                         dstU = dl.dst[gid * 4 + 0 * 2 + sense];
                         dstD = dl.dst[gid * 4 + 1 * 2 + sense];
                     }
@@ -514,13 +607,15 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                     }
                 };
                 if (u.tpl_base >= 0) {
-                    // stored template of class r (line i_lo + r): this track is its
-                    // pieces with template layer in [-m, NL - m), a contiguous record
-                    // range because the layer never decreases along an upward line
-                    // (precomputed per track in sweep order: count << 48 | first record)
-                    const uint64_t wn = valid ? __ldg(dl.win + u.trk_off + q) : 0ull;
-                    const int64_t p0 = (int64_t)(wn & 0xffffffffffffull);
-                    const int n = (int)(wn >> 48);
+                    if (!(CHUNK && C > 1)) {
+                        // stored template of class r (line i_lo + r): this track is
+                        // its pieces with template layer in [-m, NL - m), a contiguous
+                        // record range because the layer never decreases along an
+                        // upward line (per track in sweep order: count << 48 | first)
+                        const uint64_t wn = valid ? __ldg(dl.win + u.trk_off + widx) : 0ull;
+                        p0 = (int64_t)(wn & 0xffffffffffffull);
+                        n = (int)(wn >> 48);
+                    }
                     const int64_t p1 = p0 + n;
                     const int dir = sense == 0 ? 1 : -1;
                     const SegRec<real> *pr = recs + (sense == 0 ? p0 : p1 - 1);
@@ -535,7 +630,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                                 c[i] = pr[min(s0 + i, n - 1) * dir];
                                 if (s0 + i >= n) c[i].len = (real)0;
                             } else {
-                                c[i].key = tpl_key(-m, m);  // rows 0 and 0 after the shift
+                                c[i].key = tpl_key(b0, -m);  // tile rows 0 and NL - 1
                                 c[i].len = (real)0;
                             }
                         }
@@ -545,8 +640,9 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                         real ln[4];
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
-                            ru[i] = tpl_row_up(c[i].key) + m;
-                            rd[i] = tpl_row_down(c[i].key) - m;
+                            const int bN = tpl_seg(c[i].key) * NL, Lt = tpl_layer(c[i].key);
+                            ru[i] = bN + Lt + (m - rowoff);
+                            rd[i] = bN - Lt + (NL - 1 - m - rowoff);
                             ln[i] = c[i].len;
                         }
                         if constexpr (GPL >= 4) {
@@ -568,20 +664,34 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                         fetch4(ra, s + 8);
                         sweep4(rb);
                     }
-                } else if (valid) {
-                    // generated on the fly: this track's own line, layers [0, NL)
-                    const StackDesc &d = dl.desc[(int64_t)T * Ph + ph];
-                    const int i = u.i_lo + k;
+                } else if (active) {
+                    // generated on the fly: this track's own line, layers [0, NL),
+                    // 2D segments [sb0, sb1]
+                    const StackDesc &dsk = dl.desc[(int64_t)T * Ph + ph];
+                    const int i_trk = u.i_lo + k;
                     TplIter<real> it;
-                    it.init(dl, d, i, first_seg(dl, d, i), last_seg(dl, d, i), 0, NL, sense == 0 ? 1 : -1);
+                    if (CHUNK && C > 1) it.init(dl, dsk, i_trk, sb0, sb1, 0, NL, sense == 0 ? 1 : -1);
+                    else it.init(dl, dsk, i_trk, first_seg(dl, dsk, i_trk), last_seg(dl, dsk, i_trk), 0, NL,
+                                 sense == 0 ? 1 : -1);
                     while (!it.done) {
                         int b, L;
                         real len;
-                        it.next(dl, d, b, L, len);
-                        visit(b * NL + L, b * NL + NL - 1 - L, len);
+                        it.next(dl, dsk, b, L, len);
+                        visit((b - b0) * NL + L, (b - b0) * NL + NL - 1 - L, len);
                     }
                 }
-                if (valid) {
+                if (active && !last_out) {
+                    // the track goes on in the next chunk of this pass
+#pragma unroll
+                    for (int c = 0; c < GPL; ++c) {
+                        const int qq = ql * GPL + c;
+                        if (qq >= gc) continue;
+                        const real vU = psiU[c] * iWS[c], vD = psiD[c] * iWS[c];
+                        hand[(lt * 2 + 0) * G + g0 + qq] = vU;
+                        hand[(lt * 2 + 1) * G + g0 + qq] = vD;
+                        hmx[c] = fmaxf(hmx[c], fmaxf(fabsf((float)vU), fabsf((float)vD)));
+                    }
+                } else if (active) {
 #pragma unroll
                     for (int c = 0; c < GPL; ++c) {
                         const int qq = ql * GPL + c;
@@ -604,18 +714,27 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                 }
             }
             if (track_bound && G > GP) fold_pmax(gc);  // several chunks: publish per chunk
+            if (kFixed && C > 1) {
+                // the next chunk's bound covers the psi handed over to it
+#pragma unroll
+                for (int c = 0; c < GPL; ++c) {
+                    float v = hmx[c];
+                    for (int o = GL; o < 32; o <<= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+                    if (j == 0 && ql * GPL + c < gc && v > 0.0f) atomicMax(&s_hmax[ql * GPL + c], __float_as_uint(v));
+                }
+            }
             __syncthreads();
             if (track_bound && G > GP && tid < gc) {
                 if (s_pmax[tid]) atomicMax(bound_out + g0 + tid, s_pmax[tid]);
                 s_pmax[tid] = 0u;  // read again only after the next chunk's barriers
             }
             if (SMEM) {
-                for (int b = warp; b < nb; b += nwarps) {
-                    const int reg = __ldg(reg2d + b);
+                for (int bb = warp; bb < b1 - b0; bb += nwarps) {
+                    const int reg = __ldg(reg2d + b0 + bb);
                     for (int x = lane; x < NL * GP; x += 32) {
                         const int L = x / GP, qq = x - L * GP;
                         if (qq >= gc) continue;
-                        const int e = (b * NL + L) * TS + qq;
+                        const int e = (bb * NL + L) * TS + qq;
                         const double v = kFixed ? (double)((float)tl_i[e] * s_inv[qq]) : (double)tl_s[e];
                         if (v != 0.0) atomicAdd(st.tally + ((size_t)reg * NL + L) * G + g0 + qq, v);
                     }
@@ -651,20 +770,27 @@ int lanes_for_groups(int G, int gpl) {
 }
 
 // the kernel for gl lanes per track; only shapes with gl * GPL <= 32 exist
-template <typename real, int GPL, bool SMEM, int GL = 32 / GPL>
+template <typename real, int GPL, bool SMEM, bool CHUNK, int GL = 32 / GPL>
 const void *pick(int gl) {
     if constexpr (GL > 1) {
-        if (gl < GL) return pick<real, GPL, SMEM, GL / 2>(gl);
+        if (gl < GL) return pick<real, GPL, SMEM, CHUNK, GL / 2>(gl);
     }
-    return (const void *)k_sweep<real, GL, GPL, SMEM>;
+    return (const void *)k_sweep<real, GL, GPL, SMEM, CHUNK>;
 }
 
-const void *sweep_fn(int precision, int tally_smem, int G, int gpl) {
+template <typename real, int GPL>
+const void *pick_tally(int tally_smem, int chunk, int gl) {
+    if (!tally_smem) return pick<real, GPL, false, false>(gl);
+    return chunk ? pick<real, GPL, true, true>(gl) : pick<real, GPL, true, false>(gl);
+}
+
+// chunk: some units are swept in radial chunks (shared tally only)
+const void *sweep_fn(int precision, int tally_smem, int chunk, int G, int gpl) {
     const int gl = lanes_for_groups(G, gpl);
-    if (precision == MOC_FP64) return tally_smem ? pick<double, 1, true>(gl) : pick<double, 1, false>(gl);
-    if (gpl == 4) return tally_smem ? pick<float, 4, true>(gl) : pick<float, 4, false>(gl);
-    if (gpl == 2) return tally_smem ? pick<float, 2, true>(gl) : pick<float, 2, false>(gl);
-    return tally_smem ? pick<float, 1, true>(gl) : pick<float, 1, false>(gl);
+    if (precision == MOC_FP64) return pick_tally<double, 1>(tally_smem, chunk, gl);
+    if (gpl == 4) return pick_tally<float, 4>(tally_smem, chunk, gl);
+    if (gpl == 2) return pick_tally<float, 2>(tally_smem, chunk, gl);
+    return pick_tally<float, 1>(tally_smem, chunk, gl);
 }
 
 
@@ -689,9 +815,9 @@ size_t sweep_smem_bytes(int precision, int tally_smem, int M, int G, int gpl, in
     return b;
 }
 
-cudaError_t sweep_occupancy(int precision, int tally_smem, int G, int gpl, int block, size_t smem,
-                            int *blocks_per_sm) {
-    const void *f = sweep_fn(precision, tally_smem, G, gpl);
+cudaError_t sweep_occupancy(int precision, int tally_smem, int chunk, int G, int gpl, int block,
+                            size_t smem, int *blocks_per_sm) {
+    const void *f = sweep_fn(precision, tally_smem, chunk, G, gpl);
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, block, smem);
@@ -702,7 +828,7 @@ cudaError_t launch_sweep(int precision, int tally_smem, int gpl, const DevLayout
                          const void *psi_in, void *psi_out, int32_t *counter,
                          const unsigned *bound_in, unsigned *bound_out, int grid, int block,
                          size_t smem, cudaStream_t s) {
-    const void *f = sweep_fn(precision, tally_smem, dl.G, gpl);
+    const void *f = sweep_fn(precision, tally_smem, tally_smem && dl.chunk_b > 0, dl.G, gpl);
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     DevLayout a0 = dl;
