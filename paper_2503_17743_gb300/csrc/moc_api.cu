@@ -436,7 +436,9 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
                    sweep_smem_bytes(h->precision, 1, geo.M, G, h->gpl, (cb + 1) * geo.nl) <= kChunkTile)
                 ++cb;
             if (prm->chunk_segments > 0) cb = std::min(cb, (int)prm->chunk_segments);
-            if (cb >= 1) {
+            if (cb >= h->nb_max) {
+                cb = 0;  // every unit fits whole
+            } else if (cb >= 1) {
                 h->chunk_b = cb;
                 h->tile_cap = cb * geo.nl;
             } else {
@@ -596,8 +598,12 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
             for (int r = 0; r < std::min(cpl, L.desc[s].n_trk); ++r) {
                 const int64_t q = tpl_first[s] + r;
                 need += tcnt[q] * rec_bytes + (int64_t)(tnlay[q] + 1) * 4 + 20;
-                // stored keys hold the template layer as a signed 16-bit number
+                // stored keys: the template layer as a signed 16-bit number
+                // (chunked layouts), else both tile rows as 16-bit numbers
                 ok = ok && tlmin[q] > -32768 && tlmin[q] + tnlay[q] < 32767;
+                if (h->chunk_b == 0)
+                    ok = ok && tlmin[q] > -2000 && tlmin[q] + tnlay[q] < 2000 &&
+                         (int64_t)(L.desc[s].nb + 1) * geo.nl + 2000 < 32768;
             }
         }
         ok = ok && h->max_nseg < 65536;  // record windows hold the count in 16 bits
@@ -672,8 +678,6 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
                                     (int64_t *)h->d_chunk.p, cgrid, h->stream), "chunk tables");
             TRY(cudaStreamSynchronize(h->stream), "chunk tables");
             h->bytes -= d_cst.n;
-        } else {
-            h->chunk_b = 0;  // no unit needs chunks after all
         }
     }
     fill_views(h.get());

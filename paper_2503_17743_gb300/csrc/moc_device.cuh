@@ -297,11 +297,21 @@ __device__ __forceinline__ real tpl_len(const DevLayout &dl, const StackDesc &d,
     return (real)dl.cpl * lam;                                                              // Eq. 11
 }
 
-// A stored template piece: key = b << 16 | L_t, the 2D segment b (0..65535)
-// and the template layer L_t (signed 16 bits).  Track r + m cpl of the class
-// meets the piece in tile rows b NL + L_t + m (upward frame) and
-// b NL + NL - 1 - L_t - m (mirrored frame).
-__host__ __device__ __forceinline__ uint32_t tpl_key(int b, int L) {
+// A stored template piece (b the 2D segment, L_t the template layer; track
+// r + m cpl of the class meets the piece in tile rows b NL + L_t + m in the
+// upward frame and b NL + NL - 1 - L_t - m in the mirrored one).  Two key
+// formats:
+// * units swept whole (every tile row < 2^15): the two rows of the class's
+//   own line, A = b NL + L_t and B = b NL + NL - 1 - L_t, as signed 16-bit
+//   numbers (A low, B high): the sweep adds m and subtracts m;
+// * layouts with radial chunks (large units): b << 16 | L_t (b < 2^16, L_t
+//   signed 16 bits).
+__host__ __device__ __forceinline__ uint32_t tpl_key(int A, int B) {
+    return (uint32_t)(uint16_t)(int16_t)A | ((uint32_t)(uint16_t)(int16_t)B << 16);
+}
+__device__ __forceinline__ int tpl_row_up(uint32_t key) { return (int)(int16_t)(key & 0xffffu); }
+__device__ __forceinline__ int tpl_row_down(uint32_t key) { return (int)key >> 16; }
+__host__ __device__ __forceinline__ uint32_t tpl_key_seg(int b, int L) {
     return ((uint32_t)b << 16) | (uint32_t)(uint16_t)(int16_t)L;
 }
 __device__ __forceinline__ int tpl_seg(uint32_t key) { return (int)(key >> 16); }

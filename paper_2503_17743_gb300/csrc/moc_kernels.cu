@@ -100,7 +100,8 @@ __global__ void k_tpl_write(DevLayout dl, const int32_t *exp_stacks, int64_t n_e
                 for (int L = tr.La; L <= tr.Le; ++L) {
                     while (x <= L - Lmin && x <= nL) lidx[lb + x++] = pos;
                     SegRec<real> rec{};
-                    rec.key = tpl_key(b, L);
+                    rec.key = dl.chunk_b > 0 ? tpl_key_seg(b, L)
+                                             : tpl_key(b * dl.NL + L, b * dl.NL + dl.NL - 1 - L);
                     rec.len = tpl_len(dl, d, b, tr, L);
                     out[pos++] = rec;
                 }

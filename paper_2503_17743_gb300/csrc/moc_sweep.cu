@@ -630,7 +630,8 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                                 c[i] = pr[min(s0 + i, n - 1) * dir];
                                 if (s0 + i >= n) c[i].len = (real)0;
                             } else {
-                                c[i].key = tpl_key(b0, -m);  // tile rows 0 and NL - 1
+                                // tile rows 0 and NL - 1 (0 and 0 for whole units)
+                                c[i].key = CHUNK ? tpl_key_seg(b0, -m) : tpl_key(-m, m);
                                 c[i].len = (real)0;
                             }
                         }
@@ -640,9 +641,14 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                         real ln[4];
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
-                            const int bN = tpl_seg(c[i].key) * NL, Lt = tpl_layer(c[i].key);
-                            ru[i] = bN + Lt + (m - rowoff);
-                            rd[i] = bN - Lt + (NL - 1 - m - rowoff);
+                            if constexpr (CHUNK) {
+                                const int bN = tpl_seg(c[i].key) * NL, Lt = tpl_layer(c[i].key);
+                                ru[i] = bN + Lt + (m - rowoff);
+                                rd[i] = bN - Lt + (NL - 1 - m - rowoff);
+                            } else {
+                                ru[i] = tpl_row_up(c[i].key) + m;
+                                rd[i] = tpl_row_down(c[i].key) - m;
+                            }
                             ln[i] = c[i].len;
                         }
                         if constexpr (GPL >= 4) {
