@@ -346,7 +346,8 @@ def run_profile_driver(args):
     from paper_2503_17743_gb300 import Geometry, Tracks, track_params
     prob = synth.workload(args.workload)
     tr = Tracks(Geometry(prob), track_params(prob, preload_budget_bytes=args.budget,
-                                             groups_per_lane=args.gpl))
+                                             groups_per_lane=args.gpl,
+                                             chunk_segments=args.chunk))
     tr.iterate(3, use_graph=False)
     r = tr.iterate(2, use_graph=False)
     print(json.dumps({"info": tr.info, "ms_per_iteration": r["seconds"] * 1e3 / 2}), flush=True)
@@ -486,6 +487,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--budget", type=int, default=-1, help="preload budget bytes (--profile)")
     ap.add_argument("--gpl", type=int, default=0, help="groups per lane (--profile)")
+    ap.add_argument("--chunk", type=int, default=0,
+                    help="2D segments per radial chunk, 0 = automatic (--profile)")
     args = ap.parse_args()
     if args.profile:
         run_profile_driver(args)
