@@ -122,7 +122,7 @@ def profile_traffic(src_hash):
 
 def sweep_source_hash():
     h = hashlib.sha256()
-    for f in ("moc_sweep.cu", "moc_device.cuh"):
+    for f in ("moc_sweep_kernel.cuh", "moc_device.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2503_17743_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 

@@ -144,7 +144,7 @@ __global__ void k_windows(DevLayout dl, int64_t n_stacks, uint64_t *win) {
 template <typename real>
 __global__ void k_chunk_tables(DevLayout dl, const int32_t *stacks, int64_t n, int64_t *tab) {
     const SegRec<real> *recs = reinterpret_cast<const SegRec<real> *>(dl.segs);
-    const int cb = dl.chunk_b, NL = dl.NL;
+    const int cb = dl.chunk_b;
     for (int64_t x = blockIdx.x; x < n; x += gridDim.x) {
         const StackDesc &d = dl.desc[stacks[x]];
         const int C = (d.nb + cb - 1) / cb;

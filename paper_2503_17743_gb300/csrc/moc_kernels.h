@@ -40,6 +40,11 @@ cudaError_t launch_sweep(int precision, int tally_smem, int gpl, const DevLayout
                          const void *psi_in, void *psi_out, int32_t *counter,
                          const unsigned *bound_in, unsigned *bound_out, int grid, int block,
                          size_t smem, cudaStream_t s);
+// the sweep kernel for one lane shape (moc_sweep_f32g1/g2/g4.cu, moc_sweep_f64.cu)
+const void *sweep_kernel_f32_gpl1(int tally_smem, int chunk, int gl);
+const void *sweep_kernel_f32_gpl2(int tally_smem, int chunk, int gl);
+const void *sweep_kernel_f32_gpl4(int tally_smem, int chunk, int gl);
+const void *sweep_kernel_f64(int tally_smem, int chunk, int gl);
 cudaError_t sweep_occupancy(int precision, int tally_smem, int chunk, int G, int gpl, int block,
                             size_t smem, int *blocks_per_sm);
 // threads per block of the per-FSR kernels (source, finalize, residual, init):

@@ -1,0 +1,791 @@
+// The transport sweep kernel (Eq. 3 on every segment, Eq. 4 tallies).
+//
+// Work decomposition.  A persistent grid; each block takes one work unit at a
+// time from a global counter: a 2D track with all its polar z-stacks (units in
+// decreasing work order).  The tracks r, r + cpl, r + 2 cpl, ... of a z-stack
+// are one track shifted up by one layer each (Eq. 5 with the layer planes on
+// the axial lattice), so a single segment template serves all of them: track
+// r + m cpl crosses the template pieces whose layer L_t + m lies in [0, NL).
+// The layer never decreases along an upward line, so those pieces are one
+// contiguous range of the template's records.
+//
+// A warp task is (polar stack, class r, block of SLOTS = 32/GL tracks m of the
+// class, sense).  Slot j (GL lanes) walks its own track's record range; each
+// lane carries GPL energy groups, kept in GPL group planes of the shared rows.
+// Every lane sweeps both frames: the upward track and the mirrored downward
+// track that shares its segments (layer NL-1-L).  Slots of one warp run the
+// same number of steps except where a track is clipped by the top or bottom
+// face, so nearly every lane does useful work.
+//
+// Shared tally (SMEM = true): per unit the block stages one row per
+// (2D segment, layer) FSR the unit crosses, holding (Qr, Sigma_t) for every
+// group, plus a zeroed tally row; pieces touch only shared memory and the rows
+// are flushed into the FP64 global tally once per unit.  Templates come from
+// the stored set (EXP, Sec. 4.2; four records at a time with the next four in
+// flight) or each track is generated on the fly (OTF).  Without the shared
+// tally (SMEM = false) pieces read Qr from global memory and add straight into
+// the FP64 global tally.
+//
+// psi is carried multiplied by the track weight W and by the group's
+// fixed-point tally scale S (1 without a fixed-point tile): with
+// d = W S (psi - Qr) the attenuated change W S (psi_in - psi_out) =
+// d (1 - e^{-Sigma_t l}) is both the psi update and the tally contribution in
+// tally units (Eq. 3, Eq. 4), rounded to an integer by one conversion.
+#pragma once
+
+#include <type_traits>
+
+#include "moc_device.cuh"
+#include "moc_kernels.h"
+
+namespace {
+
+constexpr float kLog2e = 1.4426950408889634f;
+
+// e^{-Sigma_t l} from x = Sigma_t l: FP32 on the MUFU pipe (Sigma_t pre-scaled
+// by log2 e, the negation folds into the multiply), FP64 exp
+template <typename real>
+__device__ __forceinline__ real attenuation(real x);
+template <>
+__device__ __forceinline__ float attenuation<float>(float x) {
+    return fast_exp2(-x);
+}
+template <>
+__device__ __forceinline__ double attenuation<double>(double x) {
+    return exp(-x);
+}
+
+// per polar stack of the work unit, cached in shared memory
+// (the track weight and its inverse in both precisions: the sweep's hot path
+// does no FP64 arithmetic in FP32 mode)
+struct UnitStack {
+    int64_t trk_off, tpl_base, cbase;
+    double W, invW;
+    float Wf, invWf;
+    int32_t n_trk, i_lo, task_pre, pad;
+};
+constexpr int kMaxPh = 16;
+
+// Template pieces generated on the fly, in the order of one sense, limited to
+// the layers [lo, hi) of the unclipped line i0.
+template <typename real>
+struct TplIter {
+    int i0, b, bend, L, Lend, lo, hi, dir;
+    TplRange<real> r;
+    bool done;
+
+    __device__ __forceinline__ void init(const DevLayout &dl, const StackDesc &d, int i0_, int b0,
+                                         int b1, int lo_, int hi_, int dir_) {
+        i0 = i0_;
+        lo = lo_;
+        hi = hi_;
+        dir = dir_;
+        b = dir > 0 ? b0 : b1;
+        bend = dir > 0 ? b1 : b0;
+        done = b0 > b1;
+        if (!done) load_b(dl, d);
+    }
+    // load 2D segment b, moving on while its layer range is empty
+    __device__ __forceinline__ void load_b(const DevLayout &dl, const StackDesc &d) {
+        for (;;) {
+            tpl_range(dl, d, i0, b, r);
+            const int a = max(r.La, lo), e = min(r.Le, hi - 1);
+            if (a <= e) {
+                L = dir > 0 ? a : e;
+                Lend = dir > 0 ? e : a;
+                return;
+            }
+            if (b == bend) {
+                done = true;
+                return;
+            }
+            b += dir;
+        }
+    }
+    __device__ __forceinline__ void next(const DevLayout &dl, const StackDesc &d, int &ob, int &oL,
+                                         real &len) {
+        ob = b;
+        oL = L;
+        len = tpl_len(dl, d, b, r, L);
+        if (L != Lend) {
+            L += dir;
+        } else if (b != bend) {
+            b += dir;
+            load_b(dl, d);
+        } else {
+            done = true;
+        }
+    }
+};
+
+
+// The (Qr, Sigma_t) pairs of a lane's GPL groups in one shared row, read at a
+// 32-bit shared-memory address with one vector load
+template <typename real, int GPL>
+struct RowLoadS;
+template <>
+struct RowLoadS<float, 1> {
+    static __device__ __forceinline__ void get(unsigned a, float (&q)[1], float (&s)[1]) {
+        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(q[0]), "=f"(s[0]) : "r"(a));
+    }
+};
+template <>
+struct RowLoadS<float, 2> {
+    static __device__ __forceinline__ void get(unsigned a, float (&q)[2], float (&s)[2]) {
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(q[0]), "=f"(s[0]), "=f"(q[1]), "=f"(s[1])
+                     : "r"(a));
+    }
+};
+template <>
+struct RowLoadS<float, 4> {
+    static __device__ __forceinline__ void get(unsigned a, float (&q)[4], float (&s)[4]) {
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(q[0]), "=f"(s[0]), "=f"(q[1]), "=f"(s[1])
+                     : "r"(a));
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(q[2]), "=f"(s[2]), "=f"(q[3]), "=f"(s[3])
+                     : "r"(a + 16u));
+    }
+};
+template <>
+struct RowLoadS<double, 1> {
+    static __device__ __forceinline__ void get(unsigned a, double (&q)[1], double (&s)[1]) {
+        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(q[0]), "=d"(s[0]) : "r"(a));
+    }
+};
+
+// fixed-point tally += v at a 32-bit shared-memory address (native integer add)
+__device__ __forceinline__ void shared_red_add(unsigned a, int v) {
+    asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
+// FP64 sweeps: tally += t on shared memory with one compare-and-swap of the
+// 64-bit word per attempt (floating-point adds on shared memory have no
+// single-instruction form; FP32 sweeps use the fixed-point tally instead).  A
+// word is retried only when another lane changed it in between; after
+// kCasLimit attempts the update is dropped and *err set, which the host
+// reports as an error.
+constexpr int kCasLimit = 1 << 16;
+
+template <typename real, int GPL>
+struct TallyAdd;
+template <>
+struct TallyAdd<double, 1> {
+    static __device__ __forceinline__ void add(double *p, const double (&t)[1], double *err) {
+        unsigned long long *w = reinterpret_cast<unsigned long long *>(p);
+        unsigned long long old = *w;
+        for (int it = 0; it < kCasLimit; ++it) {
+            const unsigned long long nw = __double_as_longlong(__longlong_as_double(old) + t[0]);
+            const unsigned long long prev = atomicCAS(w, old, nw);
+            if (prev == old) return;
+            old = prev;
+        }
+        *err = 1.0;
+    }
+};
+
+// threads per sweep block, three blocks per SM in FP32: ten warps with one
+// group per lane, nine with more (their extra registers), eight in FP64
+__host__ __device__ constexpr int sweep_block(bool fp32, int GPL) {
+    return fp32 ? (GPL == 1 ? 320 : 288) : 256;
+}
+constexpr int kMaxSweepBlock = 320;
+
+// words per shared tally row
+__host__ __device__ constexpr int tally_stride(int GL, int GPL) { return GL * GPL + (GPL > 1 ? 1 : 0); }
+
+template <typename real, int GL, int GPL, bool SMEM, bool CHUNK>
+__global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(real) == 4 ? 3 : 2)
+    k_sweep(DevLayout dl, DevState st, const int32_t *order, int32_t n_work, int32_t cap,
+            const real *psi_in, real *psi_out, const unsigned *bound_in, unsigned *bound_out) {
+    constexpr int GP = GL * GPL;     // groups per chunk (padded)
+    constexpr int SLOTS = 32 / GL;   // tracks per warp task
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_work, s_next, s_ntask;
+    __shared__ UnitStack s_us[kMaxPh];
+    __shared__ double s_leak[kMaxSweepBlock / 32];
+    __shared__ float s_scl[32];      // FP32 fixed-point tally: scale of each group of the chunk
+    __shared__ float s_inv[32];      // and its inverse
+    __shared__ unsigned s_bmax[32];  // bound of |W psi| and |W Qr| per group (float bits)
+    __shared__ unsigned s_pmax[32];  // max |psi_out| the block stored per group (float bits)
+    __shared__ unsigned s_hmax[32];  // max |psi| handed to the next radial chunk (float bits)
+    __shared__ float s_wmax;
+    constexpr bool kFixed = sizeof(real) == 4;  // FP32 sweeps tally in fixed point
+    const int G = dl.G, NL = dl.NL, M = dl.M, Ph = dl.Ph, cpl = dl.cpl;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int j = lane / GL;         // slot: track of the warp task
+    const int ql = lane & (GL - 1);  // lane of the slot: groups ql * GPL + c, c < GPL
+    // shared layout: sig [M][GP] | rows [cap][GP][2] (Qr, Sigma_t) | tally [cap][TS]; with
+    // several groups per lane the tally rows are padded by one word so that
+    // the rows of the warp's eight or more slots spread over the banks
+    constexpr int TS = tally_stride(GL, GPL);
+    if (st.scal[SC_CONV] != 0.0) return;  // converged: later iterations are no-ops
+    real *sig = reinterpret_cast<real *>(smem);
+    size_t off = ((size_t)M * GP * sizeof(real) + 15) & ~(size_t)15;
+    real *rows = reinterpret_cast<real *>(smem + off);
+    off += (size_t)cap * GP * 2 * sizeof(real);
+    real *tl_s = reinterpret_cast<real *>(smem + off);
+    int *tl_i = reinterpret_cast<int *>(smem + off);  // the same tally rows in fixed point
+    const unsigned rows_sa = (unsigned)__cvta_generic_to_shared(rows);
+    const unsigned tl_sa = (unsigned)__cvta_generic_to_shared(tl_s);
+
+    const real scale = (real)st.scal[SC_SCALE];
+    const real *qr_g = reinterpret_cast<const real *>(st.qr);
+    const real *sig_g = reinterpret_cast<const real *>(st.sig_t);
+    const SegRec<real> *recs = reinterpret_cast<const SegRec<real> *>(dl.segs);
+    double *err = st.scal + SC_ERR;
+    real leak = (real)0;  // this lane's W psi leaving through vacuum faces
+    // the fixed-point tally needs a bound of |psi_in| per group: the previous
+    // sweep left one, and this sweep leaves one for the next (every psi_in is
+    // a psi_out of the previous sweep)
+    const bool track_bound = kFixed && SMEM && bound_out != nullptr;
+    float pmax[GPL];  // this lane's max |psi_out| for its groups of the current chunk
+#pragma unroll
+    for (int c = 0; c < GPL; ++c) pmax[c] = 0.0f;
+    if (tid < 32) s_pmax[tid] = 0u;
+    if (tid < 32) s_hmax[tid] = 0u;
+    // lanes with the same groups (one per slot) fold their maxima into s_pmax
+    auto fold_pmax = [&](int gc_) {
+#pragma unroll
+        for (int c = 0; c < GPL; ++c) {
+            float v = pmax[c];
+            for (int o = GL; o < 32; o <<= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+            if (j == 0 && ql * GPL + c < gc_ && v > 0.0f) atomicMax(&s_pmax[ql * GPL + c], __float_as_uint(v));
+            pmax[c] = 0.0f;
+        }
+    };
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_work = atomicAdd(st.counter, 1);
+        __syncthreads();
+        const int w = s_work;
+        if (w >= n_work) break;
+        const int T = order[w];
+        if (tid == 0) {
+            int pre = 0;
+            for (int ph = 0; ph < Ph; ++ph) {
+                const StackDesc &e = dl.desc[(int64_t)T * Ph + ph];
+                UnitStack u;
+                u.trk_off = e.trk_off;
+                u.tpl_base = e.exp_base;
+                u.cbase = e.chunk_base;
+                u.W = e.W;
+                u.invW = 1.0 / e.W;
+                u.Wf = (float)e.W;
+                u.invWf = (float)(1.0 / e.W);
+                u.n_trk = e.n_trk;
+                u.i_lo = e.i_lo;
+                u.task_pre = pre;
+                u.pad = 0;
+                s_us[ph] = u;
+                pre += 2 * ((e.n_trk + SLOTS - 1) / SLOTS);  // blocks of SLOTS tracks, 2 senses
+            }
+            s_ntask = pre;
+            float wm = 0.0f;
+            for (int ph = 0; ph < Ph; ++ph) wm = fmaxf(wm, (float)s_us[ph].W);
+            s_wmax = wm;
+            for (int qq = 0; qq < 32; ++qq) s_bmax[qq] = 0u;
+        }
+        __syncthreads();
+        const int ntask = s_ntask;
+        if (ntask == 0) continue;
+        const StackDesc &d0 = dl.desc[(int64_t)T * Ph];
+        const int nb = d0.nb;
+        const int32_t *reg2d = dl.reg2d + d0.seg2d_off;
+        // A unit whose tile does not fit is swept in C radial chunks of
+        // chunk_b 2D segments: first every track in sense 0, chunk by chunk
+        // along the 2D track, then in sense 1 back again; a track's psi passes
+        // from chunk to chunk through this block's hand-off buffer.
+        const int C = (CHUNK && nb > dl.chunk_b) ? (nb + dl.chunk_b - 1) / dl.chunk_b : 1;
+        real *hand = CHUNK ? reinterpret_cast<real *>(dl.hand) + (size_t)blockIdx.x * dl.hand_trk * 2 * G
+                           : nullptr;
+        const int64_t unit_trk0 = s_us[0].trk_off;
+        for (int g0 = 0; g0 < G; g0 += GP)
+        for (int pass = 0; pass < (C > 1 ? 2 : 1); ++pass)
+        for (int ci = 0; ci < C; ++ci) {
+            const int c_ch = pass ? C - 1 - ci : ci;             // radial chunk
+            const int b0 = C > 1 ? c_ch * dl.chunk_b : 0;       // its 2D segments [b0, b1)
+            const int b1 = C > 1 ? min(nb, b0 + dl.chunk_b) : nb;
+            const int rowoff = b0 * NL;                          // tile row of (b0, layer 0)
+            __syncthreads();  // the previous chunk's flush is done with the tile
+            const int gc = min(GP, G - g0);
+            float bmax = 0.0f;  // this thread's bound for group tid % GP of the chunk
+            for (int e = tid; e < M * GP; e += blockDim.x) {
+                const int m = e / GP, qq = e - m * GP;
+                real v = qq < gc ? sig_g[m * G + g0 + qq] : (real)0;
+                if (sizeof(real) == 4) v = (real)((float)v * kLog2e);
+                sig[e] = v;
+            }
+            if (C > 1 && warp == 0) {
+                // this chunk's warp tasks: per polar stack, blocks of SLOTS of the
+                // tracks that cross the chunk (one sense per pass)
+                int cnt = 0;
+                if (lane < Ph) cnt = (int)(__ldg(dl.chunk_tab + s_us[lane].cbase + c_ch) >> 32);
+                cnt = (cnt + SLOTS - 1) / SLOTS;
+                int incl = cnt;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                if (lane < Ph) s_us[lane].task_pre = incl - cnt;
+                if (lane == 31) s_ntask = incl;
+            }
+            if (SMEM) {
+                // rows of the (2D segment, layer) FSRs the unit (chunk) crosses
+                for (int bb = warp; bb < b1 - b0; bb += nwarps) {
+                    const int b = b0 + bb;
+                    const int reg = __ldg(reg2d + b);
+                    for (int x = lane; x < NL * GP; x += 32) {
+                        const int L = x / GP, qq = x - L * GP;
+                        const int f = reg * NL + L;
+                        const int e = (bb * NL + L) * GP + qq;
+                        const int et = (bb * NL + L) * TS + qq;
+                        real q = (real)0, sg = (real)0;
+                        if (qq < gc) {
+                            const int m = __ldg(dl.fsr_mat + f);
+                            sg = sig_g[m * G + g0 + qq];
+                            if (sizeof(real) == 4) sg = (real)((float)sg * kLog2e);
+                            q = qr_g[(size_t)f * G + g0 + qq];
+                        }
+                        rows[2 * e] = q;
+                        rows[2 * e + 1] = sg;
+                        tl_s[et] = (real)0;
+                        if (kFixed) bmax = fmaxf(bmax, fabsf((float)q));
+                    }
+                }
+                if (kFixed) {
+                    // incoming fluxes enter the bound too (psi along a track stays
+                    // between its incoming value and Qr): the previous sweep's
+                    // bound of every psi it stored
+                    const int qq = tid % GP;
+                    if (bound_in && psi_in && qq < gc)
+                        bmax = fmaxf(bmax, __uint_as_float(__ldg(bound_in + g0 + qq)) * fabsf((float)scale));
+                    // and psi handed over from the previous chunk of this pass
+                    if (C > 1 && ci > 0) bmax = fmaxf(bmax, __uint_as_float(s_hmax[qq]));
+                    atomicMax(&s_bmax[qq], __float_as_uint(bmax));
+                }
+            }
+            __syncthreads();
+            if (tid == 0) s_next = 0;
+            if (C > 1 && tid < 32) s_hmax[tid] = 0u;  // read above; refilled by this chunk's tasks
+            const int ntask_c = C > 1 ? s_ntask : ntask;
+            if (kFixed && SMEM && tid < GP) {
+                // one unit of the fixed-point tally = 2^-bits of a bound of every
+                // contribution W |psi - Qr| <= W (|psi| + |Qr|)
+                const float B = 2.0f * s_wmax * __uint_as_float(s_bmax[tid]);
+                s_scl[tid] = B > 0.0f ? ldexpf(1.0f, dl.tally_bits) / B : 1.0f;
+                s_inv[tid] = B > 0.0f ? B * ldexpf(1.0f, -dl.tally_bits) : 1.0f;
+            }
+            __syncthreads();
+
+            float hmx[GPL];  // this lane's max |psi| handed to the next chunk
+#pragma unroll
+            for (int c = 0; c < GPL; ++c) hmx[c] = 0.0f;
+            for (;;) {
+                int t = 0;
+                if (lane == 0) t = atomicAdd(&s_next, 1);
+                t = __shfl_sync(0xffffffffu, t, 0);
+                if (t >= ntask_c) break;
+                // warp task: polar stack ph, sense, block of SLOTS tracks taken in
+                // decreasing segment count
+                int ph = 0;
+                while (ph + 1 < Ph && t >= s_us[ph + 1].task_pre) ++ph;
+                const UnitStack u = s_us[ph];
+                const int x = t - u.task_pre;
+                int sense, q, k, widx;
+                bool valid;
+                if (C > 1) {
+                    // tracks k0 .. k0 + count - 1 of the stack cross this chunk
+                    // (index order), one sense per pass
+                    const int64_t rng = __ldg(dl.chunk_tab + u.cbase + c_ch);
+                    sense = pass;
+                    q = x * SLOTS + j;
+                    valid = q < (int)(rng >> 32);
+                    k = valid ? (int)(rng & 0xffffffff) + q : 0;
+                    widx = k;
+                } else {
+                    sense = x & 1;
+                    q = (x >> 1) * SLOTS + j;
+                    valid = q < u.n_trk;
+                    k = valid ? __ldg(dl.perm + u.trk_off + q) : 0;  // track in the stack
+                    widx = q;
+                }
+                const int m = k / cpl;                       // shift of the track within its class
+                const int64_t gid = u.trk_off + k;
+                // the track's part in this chunk: records [p0, p0 + n) of its
+                // window (stored) or 2D segments [sb0, sb1] (on the fly), and
+                // whether its first / last piece lies here (psi from psi_in /
+                // to its successor) or it continues across a chunk boundary
+                bool first_in = true, last_out = true;
+                int64_t p0 = 0;
+                int n = 0, sb0 = 0, sb1 = -1;
+                if (CHUNK && C > 1 && u.tpl_base >= 0) {
+                    const uint64_t wn = valid ? __ldg(dl.win + u.trk_off + widx) : 0ull;
+                    p0 = (int64_t)(wn & 0xffffffffffffull);
+                    n = (int)(wn >> 48);
+                    if (valid) {
+                        const int64_t *cb = dl.chunk_tab + u.cbase + C + (int64_t)(k - m * cpl) * (C + 1) + c_ch;
+                        const int64_t lo = max(p0, __ldg(cb)), hi = min(p0 + n, __ldg(cb + 1));
+                        first_in = sense == 0 ? lo == p0 : hi == p0 + n;
+                        last_out = sense == 0 ? hi == p0 + n : lo == p0;
+                        p0 = lo;
+                        n = hi > lo ? (int)(hi - lo) : 0;
+                    }
+                } else if (CHUNK && C > 1 && valid) {
+                    const StackDesc &dsk = dl.desc[(int64_t)T * Ph + ph];
+                    const int i_trk = u.i_lo + k;
+                    const int fb = first_seg(dl, dsk, i_trk), lb = last_seg(dl, dsk, i_trk);
+                    sb0 = max(fb, b0);
+                    sb1 = min(lb, b1 - 1);
+                    first_in = sense == 0 ? fb >= b0 : lb < b1;
+                    last_out = sense == 0 ? lb < b1 : fb >= b0;
+                }
+                const bool active = valid && (C == 1 || (u.tpl_base >= 0 ? n > 0 : sb0 <= sb1));
+                const int64_t lt = gid - unit_trk0;  // hand-off slot of the track
+                // psi is carried pre-multiplied by the track weight W, so that the
+                // tally contribution W (psi_in - psi_out) is the psi change itself
+                const real W = sizeof(real) == 4 ? (real)u.Wf : (real)u.W;
+                const real invW = sizeof(real) == 4 ? (real)u.invWf : (real)u.invW;
+                const int qlo = ql * GPL;                    // first group of this lane in the chunk
+                float scl[GPL];
+#pragma unroll
+                for (int c = 0; c < GPL; ++c) scl[c] = kFixed && SMEM ? s_scl[ql * GPL + c] : 1.0f;
+                // psi is carried as W S psi, S the group's fixed-point scale (1 when
+                // the tally is not in fixed point), so that the change of the
+                // carried value is the tally contribution in tally units
+                real WS[GPL], iWS[GPL], iS[GPL];
+#pragma unroll
+                for (int c = 0; c < GPL; ++c) {
+                    const real is = kFixed && SMEM ? (real)s_inv[ql * GPL + c] : (real)1;
+                    WS[c] = W * (real)scl[c];
+                    iWS[c] = invW * is;
+                    iS[c] = is;
+                }
+                real psiU[GPL], psiD[GPL];
+#pragma unroll
+                for (int c = 0; c < GPL; ++c) {
+                    psiU[c] = (real)0;
+                    psiD[c] = (real)0;
+                }
+                int64_t dstU = -1, dstD = -1;
+                if (active) {
+                    if (!first_in) {
+                        // psi left by the previous chunk of this pass
+#pragma unroll
+                        for (int c = 0; c < GPL; ++c) {
+                            const int qq = ql * GPL + c;
+                            if (qq < gc) {
+                                psiU[c] = hand[(lt * 2 + 0) * G + g0 + qq] * WS[c];
+                                psiD[c] = hand[(lt * 2 + 1) * G + g0 + qq] * WS[c];
+                            }
+                        }
+                    } else if (psi_in) {
+#pragma unroll
+                        for (int c = 0; c < GPL; ++c) {
+                            const int qq = ql * GPL + c;
+                            if (qq < gc) {
+                                psiU[c] = psi_in[(gid * 4 + 0 * 2 + sense) * G + g0 + qq] * (scale * WS[c]);
+                                psiD[c] = psi_in[(gid * 4 + 1 * 2 + sense) * G + g0 + qq] * (scale * WS[c]);
+                            }
+                        }
+                    }
+                    if (last_out && dl.dst) {
+                        dstU = dl.dst[gid * 4 + 0 * 2 + sense];
+                        dstD = dl.dst[gid * 4 + 1 * 2 + sense];
+                    }
+                }
+                // one segment of this slot's track, in tile rows rU (upward frame,
+                // row b * NL + L) and rD (mirrored frame, row b * NL + NL-1-L)
+                auto visit = [&](int rU, int rD, real len) {
+                    real tU[GPL], tD[GPL];
+                    if (SMEM) {
+                        const int eU = rU * GP + qlo, eD = rD * GP + qlo;
+                        const int tU_ = rU * TS + qlo, tD_ = rD * TS + qlo;
+                        real qU[GPL], sU[GPL], qD[GPL], sD[GPL];
+                        RowLoadS<real, GPL>::get(rows_sa + eU * (unsigned)(2 * sizeof(real)), qU, sU);
+                        RowLoadS<real, GPL>::get(rows_sa + eD * (unsigned)(2 * sizeof(real)), qD, sD);
+#pragma unroll
+                        for (int c = 0; c < GPL; ++c) {
+                            // Eq. 3 on W S psi: d = W S (psi_in - Qr),
+                            // W S (psi_in - psi_out) = d (1 - e^{-Sigma_t l})
+                            const real xU = attenuation<real>(sU[c] * len);
+                            const real xD = attenuation<real>(sD[c] * len);
+                            const real dU = fma(-WS[c], qU[c], psiU[c]), dD = fma(-WS[c], qD[c], psiD[c]);
+                            tU[c] = fma(-dU, xU, dU);
+                            tD[c] = fma(-dD, xD, dD);
+                            psiU[c] -= tU[c];
+                            psiD[c] -= tD[c];
+                        }
+                        if constexpr (kFixed) {
+                            // round to the fixed-point grid: adding 1.5 * 2^23 leaves the
+                            // integer in the low mantissa bits (|t scl| < 2^22)
+#pragma unroll
+                            for (int c = 0; c < GPL; ++c) {
+                                shared_red_add(tl_sa + (tU_ + c) * 4u,
+                                               __float2int_rn((float)tU[c]));
+                                shared_red_add(tl_sa + (tD_ + c) * 4u,
+                                               __float2int_rn((float)tD[c]));
+                            }
+                        } else {
+                            TallyAdd<real, GPL>::add(tl_s + tU_, tU, err);
+                            TallyAdd<real, GPL>::add(tl_s + tD_, tD, err);
+                        }
+                    } else {
+                        const int b = rU / NL, L = rU - b * NL, LD = NL - 1 - L;
+                        const int reg = __ldg(reg2d + b);
+                        const size_t fU = (size_t)reg * NL + L, fD = (size_t)reg * NL + LD;
+                        const int mU = __ldg(dl.fsr_mat + fU), mD = __ldg(dl.fsr_mat + fD);
+#pragma unroll
+                        for (int c = 0; c < GPL; ++c) {
+                            const int qq = qlo + c;
+                            const real qU = qq < gc ? qr_g[fU * G + g0 + qq] : (real)0;
+                            const real qD = qq < gc ? qr_g[fD * G + g0 + qq] : (real)0;
+                            const real xU = attenuation<real>(sig[mU * GP + qq] * len);
+                            const real xD = attenuation<real>(sig[mD * GP + qq] * len);
+                            const real dU = fma(-WS[c], qU, psiU[c]), dD = fma(-WS[c], qD, psiD[c]);
+                            tU[c] = fma(-dU, xU, dU);
+                            tD[c] = fma(-dD, xD, dD);
+                            if (qq < gc) {
+                                atomicAdd(st.tally + fU * G + g0 + qq, (double)tU[c]);
+                                atomicAdd(st.tally + fD * G + g0 + qq, (double)tD[c]);
+                            }
+                            psiU[c] -= tU[c];
+                            psiD[c] -= tD[c];
+                        }
+                    }
+                };
+                // four consecutive segments of the track at once (shared tally):
+                // all row loads and exponentials first, then the psi recurrence,
+                // then the tally updates, so that the loads overlap each other
+                auto visit4 = [&](const int (&rU)[4], const int (&rD)[4], const real (&len)[4]) {
+                    if constexpr (!SMEM) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) visit(rU[i], rD[i], len[i]);
+                    } else {
+                        int eU[4], eD[4], fU[4], fD[4];
+                        real qU[4][GPL], sU[4][GPL], qD[4][GPL], sD[4][GPL];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            eU[i] = rU[i] * GP + qlo;
+                            eD[i] = rD[i] * GP + qlo;
+                            fU[i] = rU[i] * TS + qlo;
+                            fD[i] = rD[i] * TS + qlo;
+                            RowLoadS<real, GPL>::get(rows_sa + eU[i] * (unsigned)(2 * sizeof(real)), qU[i], sU[i]);
+                            RowLoadS<real, GPL>::get(rows_sa + eD[i] * (unsigned)(2 * sizeof(real)), qD[i], sD[i]);
+                        }
+                        real tU[4][GPL], tD[4][GPL];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int c = 0; c < GPL; ++c) {
+                                sU[i][c] = attenuation<real>(sU[i][c] * len[i]);  // now e^{-Sigma_t l}
+                                sD[i][c] = attenuation<real>(sD[i][c] * len[i]);
+                            }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int c = 0; c < GPL; ++c) {
+                                const real dU = fma(-WS[c], qU[i][c], psiU[c]), dD = fma(-WS[c], qD[i][c], psiD[c]);
+                                tU[i][c] = fma(-dU, sU[i][c], dU);
+                                tD[i][c] = fma(-dD, sD[i][c], dD);
+                                psiU[c] -= tU[i][c];
+                                psiD[c] -= tD[i][c];
+                            }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            if constexpr (kFixed) {
+#pragma unroll
+                                for (int c = 0; c < GPL; ++c) {
+                                    shared_red_add(tl_sa + (fU[i] + c) * 4u,
+                                                   __float2int_rn((float)tU[i][c]));
+                                    shared_red_add(tl_sa + (fD[i] + c) * 4u,
+                                                   __float2int_rn((float)tD[i][c]));
+                                }
+                            } else {
+                                TallyAdd<real, GPL>::add(tl_s + fU[i], tU[i], err);
+                                TallyAdd<real, GPL>::add(tl_s + fD[i], tD[i], err);
+                            }
+                        }
+                    }
+                };
+                if (u.tpl_base >= 0) {
+                    if (!(CHUNK && C > 1)) {
+                        // stored template of class r (line i_lo + r): this track is
+                        // its pieces with template layer in [-m, NL - m), a contiguous
+                        // record range because the layer never decreases along an
+                        // upward line (per track in sweep order: count << 48 | first)
+                        const uint64_t wn = valid ? __ldg(dl.win + u.trk_off + widx) : 0ull;
+                        p0 = (int64_t)(wn & 0xffffffffffffull);
+                        n = (int)(wn >> 48);
+                    }
+                    const int64_t p1 = p0 + n;
+                    const int dir = sense == 0 ? 1 : -1;
+                    const SegRec<real> *pr = recs + (sense == 0 ? p0 : p1 - 1);
+                    // all slots step together to the longest track of the warp; a
+                    // slot past its own end repeats its last record with length 0,
+                    // which leaves psi unchanged and adds exactly 0 to the tally
+                    const int nmax = __reduce_max_sync(0xffffffffu, n);
+                    auto fetch4 = [&](SegRec<real> (&c)[4], int s0) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            if (n > 0) {
+                                c[i] = pr[min(s0 + i, n - 1) * dir];
+                                if (s0 + i >= n) c[i].len = (real)0;
+                            } else {
+                                // tile rows 0 and NL - 1 (0 and 0 for whole units)
+                                c[i].key = CHUNK ? tpl_key_seg(b0, -m) : tpl_key(-m, m);
+                                c[i].len = (real)0;
+                            }
+                        }
+                    };
+                    auto sweep4 = [&](const SegRec<real> (&c)[4]) {
+                        int ru[4], rd[4];
+                        real ln[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            if constexpr (CHUNK) {
+                                const int bN = tpl_seg(c[i].key) * NL, Lt = tpl_layer(c[i].key);
+                                ru[i] = bN + Lt + (m - rowoff);
+                                rd[i] = bN - Lt + (NL - 1 - m - rowoff);
+                            } else {
+                                ru[i] = tpl_row_up(c[i].key) + m;
+                                rd[i] = tpl_row_down(c[i].key) - m;
+                            }
+                            ln[i] = c[i].len;
+                        }
+                        if constexpr (GPL >= 4) {
+                            // eight recurrences per segment already: no batching
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) visit(ru[i], rd[i], ln[i]);
+                        } else {
+                            visit4(ru, rd, ln);
+                        }
+                    };
+                    // two sets of four records: one set in flight while the other
+                    // is swept
+                    SegRec<real> ra[4], rb[4];
+                    fetch4(ra, 0);
+                    for (int s = 0; s < nmax; s += 8) {
+                        fetch4(rb, s + 4);
+                        sweep4(ra);
+                        if (s + 4 >= nmax) break;
+                        fetch4(ra, s + 8);
+                        sweep4(rb);
+                    }
+                } else if (active) {
+                    // generated on the fly: this track's own line, layers [0, NL),
+                    // 2D segments [sb0, sb1]
+                    const StackDesc &dsk = dl.desc[(int64_t)T * Ph + ph];
+                    const int i_trk = u.i_lo + k;
+                    TplIter<real> it;
+                    if (CHUNK && C > 1) it.init(dl, dsk, i_trk, sb0, sb1, 0, NL, sense == 0 ? 1 : -1);
+                    else it.init(dl, dsk, i_trk, first_seg(dl, dsk, i_trk), last_seg(dl, dsk, i_trk), 0, NL,
+                                 sense == 0 ? 1 : -1);
+                    while (!it.done) {
+                        int b, L;
+                        real len;
+                        it.next(dl, dsk, b, L, len);
+                        visit((b - b0) * NL + L, (b - b0) * NL + NL - 1 - L, len);
+                    }
+                }
+                if (active && !last_out) {
+                    // the track goes on in the next chunk of this pass
+#pragma unroll
+                    for (int c = 0; c < GPL; ++c) {
+                        const int qq = ql * GPL + c;
+                        if (qq >= gc) continue;
+                        const real vU = psiU[c] * iWS[c], vD = psiD[c] * iWS[c];
+                        hand[(lt * 2 + 0) * G + g0 + qq] = vU;
+                        hand[(lt * 2 + 1) * G + g0 + qq] = vD;
+                        hmx[c] = fmaxf(hmx[c], fmaxf(fabsf((float)vU), fabsf((float)vD)));
+                    }
+                } else if (active) {
+#pragma unroll
+                    for (int c = 0; c < GPL; ++c) {
+                        const int qq = ql * GPL + c;
+                        if (qq >= gc) continue;
+                        if (dstU >= 0 && dstU < dl.n_slots) {
+                            const real v = psiU[c] * iWS[c];
+                            psi_out[dstU * G + g0 + qq] = v;
+                            pmax[c] = fmaxf(pmax[c], fabsf((float)v));
+                        } else {
+                            leak += psiU[c] * iS[c];
+                        }
+                        if (dstD >= 0 && dstD < dl.n_slots) {
+                            const real v = psiD[c] * iWS[c];
+                            psi_out[dstD * G + g0 + qq] = v;
+                            pmax[c] = fmaxf(pmax[c], fabsf((float)v));
+                        } else {
+                            leak += psiD[c] * iS[c];
+                        }
+                    }
+                }
+            }
+            if (track_bound && G > GP) fold_pmax(gc);  // several chunks: publish per chunk
+            if (kFixed && C > 1) {
+                // the next chunk's bound covers the psi handed over to it
+#pragma unroll
+                for (int c = 0; c < GPL; ++c) {
+                    float v = hmx[c];
+                    for (int o = GL; o < 32; o <<= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+                    if (j == 0 && ql * GPL + c < gc && v > 0.0f) atomicMax(&s_hmax[ql * GPL + c], __float_as_uint(v));
+                }
+            }
+            __syncthreads();
+            if (track_bound && G > GP && tid < gc) {
+                if (s_pmax[tid]) atomicMax(bound_out + g0 + tid, s_pmax[tid]);
+                s_pmax[tid] = 0u;  // read again only after the next chunk's barriers
+            }
+            if (SMEM) {
+                for (int bb = warp; bb < b1 - b0; bb += nwarps) {
+                    const int reg = __ldg(reg2d + b0 + bb);
+                    for (int x = lane; x < NL * GP; x += 32) {
+                        const int L = x / GP, qq = x - L * GP;
+                        if (qq >= gc) continue;
+                        const int e = (bb * NL + L) * TS + qq;
+                        const double v = kFixed ? (double)((float)tl_i[e] * s_inv[qq]) : (double)tl_s[e];
+                        if (v != 0.0) atomicAdd(st.tally + ((size_t)reg * NL + L) * G + g0 + qq, v);
+                    }
+                }
+                if (tid < 32) s_bmax[tid] = 0u;  // next chunk's bound (read only before its tasks)
+            }
+        }
+    }
+    if (track_bound && G <= GP) {
+        // one chunk: the maxima span every unit of the block, published once
+        fold_pmax(G);
+        __syncthreads();
+        if (tid < G && s_pmax[tid]) atomicMax(bound_out + tid, s_pmax[tid]);
+    }
+    double leak64 = (double)leak;
+    for (int o = 16; o > 0; o >>= 1) leak64 += __shfl_down_sync(0xffffffffu, leak64, o);
+    if (lane == 0) s_leak[warp] = leak64;
+    __syncthreads();
+    if (tid == 0) {
+        double v = 0.0;
+        for (int k = 0; k < nwarps; ++k) v += s_leak[k];
+        if (v != 0.0) atomicAdd(st.scal + SC_LEAK, v);
+    }
+}
+
+// the kernel for gl lanes per track; only shapes with gl * GPL <= 32 exist
+// (each translation unit of the sweep instantiates its share)
+template <typename real, int GPL, bool SMEM, bool CHUNK, int GL = 32 / GPL>
+const void *pick(int gl) {
+    if constexpr (GL > 1) {
+        if (gl < GL) return pick<real, GPL, SMEM, CHUNK, GL / 2>(gl);
+    }
+    return (const void *)k_sweep<real, GL, GPL, SMEM, CHUNK>;
+}
+
+template <typename real, int GPL>
+const void *pick_tally(int tally_smem, int chunk, int gl) {
+    if (!tally_smem) return pick<real, GPL, false, false>(gl);
+    return chunk ? pick<real, GPL, true, true>(gl) : pick<real, GPL, true, false>(gl);
+}
+
+// chunk: some units are swept in radial chunks (shared tally only)
+
+}  // namespace
