@@ -255,6 +255,33 @@ int moc_set_flux(moc_tracks *tracks, const double *phi, double k);
 /* Tracked FSR volumes [n_fsr] (FP64, host). */
 int moc_get_volumes(moc_tracks *tracks, double *volumes);
 
+/* A second, independent solve on the layout of `tracks` (Sec. 4.2: the
+ * stored segments, links and tables are shared, not copied): its own flux,
+ * source, boundary fluxes and scalars, in the initial state.  ext_source
+ * [M*G] (host, copied; NULL = the geometry's own) gives it a different
+ * external source, which makes it a fixed-source problem.  The returned
+ * handle is a moc_tracks and takes every call a moc_tracks takes; it holds a
+ * host copy of the layout tables.  Destroy it with moc_state_destroy (or
+ * moc_destroy_tracks); the layout's memory lives until its owner and all its
+ * states are destroyed.  Errors: MOC_ERR_INVALID_ARG (NULL, a source value
+ * negative or not finite, an owner already destroyed), MOC_ERR_OUT_OF_MEMORY,
+ * MOC_ERR_CUDA. */
+int moc_state_create(const moc_tracks *tracks, const double *ext_source, moc_tracks **state);
+void moc_state_destroy(moc_tracks *state);
+
+/* One outer iteration (source, sweep, flux / k update, Sec. 5.1) of each of n
+ * solves that share one layout (the moc_tracks and its states), with the
+ * sweeps of all of them in ONE persistent launch whose work list takes every
+ * unit of every solve, the solves' units interleaved, largest first.  Like
+ * moc_iterate(solve, 1): no convergence test, and a converged solve resumes.
+ * Layouts without the shared tally, or with radially chunked units, run one
+ * iteration per solve instead.  Enqueued on `stream` (NULL: the first
+ * solve's stream) and synchronised before returning.  Calls on solves of one
+ * layout must not overlap in time (they share the batch table).  Errors:
+ * MOC_ERR_INVALID_ARG (NULL, n < 1, a solve twice, different layouts),
+ * MOC_ERR_CUDA. */
+int moc_batch_step(moc_tracks *const *solves, int32_t n, void *stream);
+
 /* Layout counts, int64 values written to out[0..n-1]:
  *   0 n_fsr, 1 groups, 2 2D tracks, 3 z-stacks (both hemispheres), 4 3D tracks,
  *   5 3D segments, 6 segment-group integrations per sweep, 7 stored segments,

@@ -88,6 +88,9 @@ SIGNATURES = {
     "moc_generate_tracks": (C.c_int, [C.c_void_p, C.POINTER(moc_track_params),
                                       C.POINTER(C.c_void_p)]),
     "moc_destroy_tracks": (None, [C.c_void_p]),
+    "moc_state_create": (C.c_int, [C.c_void_p, f64p, C.POINTER(C.c_void_p)]),
+    "moc_state_destroy": (None, [C.c_void_p]),
+    "moc_batch_step": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p]),
     "moc_sweep": (C.c_int, [C.c_void_p, C.c_void_p]),
     "moc_update_source": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p]),
     "moc_solve_eigen": (C.c_int, [C.c_void_p, C.POINTER(moc_solve_params), C.POINTER(moc_result)]),
@@ -233,15 +236,32 @@ INFO_KEYS = ["n_fsr", "groups", "tracks2d", "stacks", "tracks3d", "segments3d",
 class Tracks:
     """moc_generate_tracks + the solve entry points."""
 
-    def __init__(self, geom: Geometry, params: moc_track_params):
+    def __init__(self, geom: Geometry, params: moc_track_params, _handle=None, _owner=None):
         self.geom = geom
         self.params = params
-        h = C.c_void_p()
-        _check(load().moc_generate_tracks(geom._h, C.byref(params), C.byref(h)))
+        if _handle is None:
+            h = C.c_void_p()
+            _check(load().moc_generate_tracks(geom._h, C.byref(params), C.byref(h)))
+        else:
+            h = _handle
         self._h = h
+        self._owner = _owner  # a state keeps its layout's Python object alive
         self.info = self._info()
         self.n_fsr = self.info["n_fsr"]
         self.G = self.info["groups"]
+
+    def state(self, ext_source=None):
+        """moc_state_create: another solve on this layout (optionally with its
+        own external source [M, G]); a Tracks object."""
+        src = None
+        if ext_source is not None:
+            src = np.ascontiguousarray(ext_source, dtype=np.float64)
+        h = C.c_void_p()
+        _check(load().moc_state_create(self._h, _ptr(src, f64p) if src is not None else f64p(),
+                                       C.byref(h)))
+        t = Tracks(self.geom, self.params, _handle=h, _owner=self)
+        t._src_keep = src
+        return t
 
     def _info(self):
         out = np.zeros(len(INFO_KEYS), dtype=np.int64)
@@ -363,6 +383,13 @@ class Tracks:
         out = np.zeros(2 * self.G)
         _check(load().moc_group_rates_static(self._h, stream, _ptr(out, f64p)))
         return out[:self.G].copy(), out[self.G:].copy()
+
+
+def batch_step(solves, stream=None):
+    """moc_batch_step: one outer iteration of every solve (a Tracks and its
+    states), their sweeps in one persistent launch."""
+    arr = (C.c_void_p * len(solves))(*[t._h for t in solves])
+    _check(load().moc_batch_step(arr, len(solves), stream))
 
 
 def measure_ex2_rate(device=0):

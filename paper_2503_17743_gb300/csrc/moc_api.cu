@@ -18,7 +18,14 @@ namespace {
 struct DevBuf {
     void *p = nullptr;
     size_t n = 0;
-    ~DevBuf() { if (p) cudaFree(p); }
+    bool borrowed = false;  // another handle's buffer (a solve state sharing a layout)
+    ~DevBuf() { release(); }
+    void release() {
+        if (p && !borrowed) cudaFree(p);
+        p = nullptr;
+        n = 0;
+        borrowed = false;
+    }
     DevBuf() = default;
     DevBuf(const DevBuf &) = delete;
     DevBuf &operator=(const DevBuf &) = delete;
@@ -36,7 +43,7 @@ struct moc_tracks {
     // device buffers
     DevBuf d_desc, d_zn, d_zf, d_zf64, d_reg2d, d_len2d, d_len2d64, d_segs, d_fsr_mat, d_order;
     DevBuf d_tpl_off, d_tpl_loff, d_tpl_lmin, d_tpl_lidx;
-    DevBuf d_dst, d_perm, d_win, d_chunk, d_hand;
+    DevBuf d_dst, d_perm, d_win, d_chunk, d_hand, d_batch;
     DevBuf d_phi, d_qr, d_tally, d_vol, d_psi[2], d_fiss, d_fiss_old, d_partial, d_scal, d_counter;
     DevBuf d_sigt, d_sigt64, d_sigs64, d_nsf64, d_chi64, d_src64, d_inv_st64, d_siga64, d_inv_vol;
     double *h_scal = nullptr;  // pinned mirror of the device scalars
@@ -70,6 +77,12 @@ struct moc_tracks {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     DevLayout dl{};
     DevState ds{};
+    // solve states sharing this handle's layout (moc_state_create): a state
+    // points at its owner; an owner destroyed while states live is freed with
+    // the last of them
+    moc_tracks *owner = nullptr;
+    int live_states = 0;
+    bool destroy_pending = false;
     ~moc_tracks() {
         for (auto &g : graph) if (g) cudaGraphExecDestroy(g);
         if (h_scal) cudaFreeHost(h_scal);
@@ -795,11 +808,126 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     return MOC_OK;
 }
 
+std::mutex g_states_mu;  // live-state counts of layout owners
+
 extern "C" void moc_destroy_tracks(moc_tracks *h) {
     if (!h) return;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
+    moc_tracks *free_owner = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_states_mu);
+        if (h->owner) {
+            moc_tracks *o = h->owner;
+            if (--o->live_states == 0 && o->destroy_pending) free_owner = o;
+        } else if (h->live_states > 0) {
+            h->destroy_pending = true;  // its states still use the layout
+            return;
+        }
+    }
     delete h;
+    if (free_owner) delete free_owner;
+}
+
+extern "C" void moc_state_destroy(moc_tracks *state) { moc_destroy_tracks(state); }
+
+namespace {
+void borrow(DevBuf &d, const DevBuf &s) {
+    d.p = s.p;
+    d.n = s.n;
+    d.borrowed = true;
+}
+}  // namespace
+
+extern "C" int moc_state_create(const moc_tracks *t, const double *ext_source, moc_tracks **out) {
+    if (!t || !out) { moc_set_error("NULL argument"); return MOC_ERR_INVALID_ARG; }
+    *out = nullptr;
+    moc_tracks *base = t->owner ? t->owner : const_cast<moc_tracks *>(t);
+    {
+        std::lock_guard<std::mutex> lk(g_states_mu);
+        if (base->destroy_pending) { moc_set_error("the layout was destroyed"); return MOC_ERR_INVALID_ARG; }
+    }
+    const int G = base->geom.G, M = base->geom.M;
+    if (ext_source)
+        for (int i = 0; i < M * G; ++i)
+            if (!(ext_source[i] >= 0.0) || !std::isfinite(ext_source[i])) {
+                moc_set_error("ext_source must be finite and non-negative");
+                return MOC_ERR_INVALID_ARG;
+            }
+    TRY(cudaSetDevice(base->device), "cudaSetDevice");
+    std::unique_ptr<moc_tracks> h(new moc_tracks());
+    h->geom = base->geom;
+    if (ext_source) h->geom.src.assign(ext_source, ext_source + (size_t)M * G);
+    h->L = base->L;
+    h->precision = base->precision;
+    h->device = base->device;
+    h->sms = base->sms;
+    h->has_psi = base->has_psi;
+    h->stack_nseg = base->stack_nseg;
+    h->order = base->order;
+    h->n_segments3d = base->n_segments3d;
+    h->n_stored = base->n_stored;
+    h->n_exp_stacks = base->n_exp_stacks;
+    h->max_nseg = base->max_nseg;
+    h->nb_max = base->nb_max;
+    h->integrations = base->integrations;
+    h->tally_smem = base->tally_smem;
+    h->gpl = base->gpl;
+    h->tally_bits = base->tally_bits;
+    h->tile_cap = base->tile_cap;
+    h->chunk_b = base->chunk_b;
+    h->hand_trk = base->hand_trk;
+    h->block = base->block;
+    h->grid = base->grid;
+    h->smem = base->smem;
+    h->red_grid = base->red_grid;
+    h->vol = base->vol;
+    // the layout: shared
+    borrow(h->d_desc, base->d_desc); borrow(h->d_zn, base->d_zn); borrow(h->d_zf, base->d_zf);
+    borrow(h->d_zf64, base->d_zf64); borrow(h->d_reg2d, base->d_reg2d); borrow(h->d_len2d, base->d_len2d);
+    borrow(h->d_len2d64, base->d_len2d64); borrow(h->d_segs, base->d_segs);
+    borrow(h->d_fsr_mat, base->d_fsr_mat); borrow(h->d_order, base->d_order);
+    borrow(h->d_tpl_off, base->d_tpl_off); borrow(h->d_tpl_loff, base->d_tpl_loff);
+    borrow(h->d_tpl_lmin, base->d_tpl_lmin); borrow(h->d_tpl_lidx, base->d_tpl_lidx);
+    borrow(h->d_dst, base->d_dst); borrow(h->d_perm, base->d_perm); borrow(h->d_win, base->d_win);
+    borrow(h->d_chunk, base->d_chunk); borrow(h->d_vol, base->d_vol); borrow(h->d_inv_vol, base->d_inv_vol);
+    borrow(h->d_sigt, base->d_sigt); borrow(h->d_sigt64, base->d_sigt64); borrow(h->d_sigs64, base->d_sigs64);
+    borrow(h->d_nsf64, base->d_nsf64); borrow(h->d_chi64, base->d_chi64);
+    borrow(h->d_inv_st64, base->d_inv_st64); borrow(h->d_siga64, base->d_siga64);
+    // the solve state: its own
+    TRY(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "stream");
+    TRY(cudaMallocHost(&h->h_scal, SC_COUNT * sizeof(double)), "pinned scalars");
+    if (ext_source) TRY(upload(h.get(), h->d_src64, h->geom.src), "upload");
+    else borrow(h->d_src64, base->d_src64);
+    const size_t nfg = (size_t)h->geom.nfsr * G, rs = real_size(h->precision);
+    TRY(dalloc(h.get(), h->d_phi, nfg * 8), "alloc flux");
+    TRY(dalloc(h.get(), h->d_qr, nfg * rs), "alloc source");
+    TRY(dalloc(h.get(), h->d_tally, nfg * 8), "alloc tally");
+    TRY(dalloc(h.get(), h->d_fiss, (size_t)h->geom.nfsr * 8), "alloc");
+    TRY(dalloc(h.get(), h->d_fiss_old, (size_t)h->geom.nfsr * 8), "alloc");
+    TRY(dalloc(h.get(), h->d_partial, (size_t)h->red_grid * 4 * 8), "alloc");
+    TRY(dalloc(h.get(), h->d_scal, SC_COUNT * 8), "alloc");
+    TRY(dalloc(h.get(), h->d_counter, 2 * sweep_block_bytes(h.get())), "alloc");
+    if (h->has_psi) {
+        TRY(dalloc(h.get(), h->d_psi[0], base->d_psi[0].n), "alloc boundary fluxes");
+        TRY(dalloc(h.get(), h->d_psi[1], base->d_psi[1].n), "alloc boundary fluxes");
+    }
+    if (h->chunk_b > 0) TRY(dalloc(h.get(), h->d_hand, base->d_hand.n), "alloc chunk hand-off");
+    fill_views(h.get());
+    std::vector<double> init(SC_COUNT, 0.0);
+    init[SC_EIGEN] = h->geom.src.empty() ? 1.0 : 0.0;
+    init[SC_SCALE] = 1.0;
+    init[SC_K] = 1.0;
+    TRY(cudaMemcpyAsync(h->d_scal.p, init.data(), SC_COUNT * 8, cudaMemcpyHostToDevice, h->stream), "upload");
+    const int rc = init_state(h.get());
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_states_mu);
+        h->owner = base;
+        ++base->live_states;
+    }
+    *out = h.release();
+    return MOC_OK;
 }
 
 extern "C" int moc_reset(moc_tracks *h) {
@@ -859,6 +987,82 @@ extern "C" int moc_enqueue_update(moc_tracks *h, void *stream) {
     TRY(clear_conv(h, s), "scalar");
     TRY(enqueue_finalize(h, s), "finalize");
     TRY(cudaMemcpyAsync(h->h_scal, h->d_scal.p, SC_COUNT * 8, cudaMemcpyDeviceToHost, s), "scalars");
+    return MOC_OK;
+}
+
+extern "C" int moc_batch_step(moc_tracks *const *solves, int32_t n, void *stream) {
+    if (!solves || n < 1) { moc_set_error("bad arguments"); return MOC_ERR_INVALID_ARG; }
+    for (int i = 0; i < n; ++i)
+        if (!solves[i]) { moc_set_error("NULL solve"); return MOC_ERR_INVALID_ARG; }
+    moc_tracks *base = solves[0]->owner ? solves[0]->owner : solves[0];
+    for (int i = 0; i < n; ++i) {
+        const moc_tracks *o = solves[i]->owner ? solves[i]->owner : solves[i];
+        if (o != base) { moc_set_error("moc_batch_step: the solves must share one layout"); return MOC_ERR_INVALID_ARG; }
+        for (int k = 0; k < i; ++k)
+            if (solves[k] == solves[i]) { moc_set_error("moc_batch_step: a solve appears twice"); return MOC_ERR_INVALID_ARG; }
+    }
+    TRY(cudaSetDevice(base->device), "cudaSetDevice");
+    cudaStream_t s = stream ? (cudaStream_t)stream : solves[0]->stream;
+    // one outer iteration each, no convergence test (like moc_iterate)
+    for (int i = 0; i < n; ++i) {
+        double *sc = (double *)solves[i]->d_scal.p;
+        TRY(cudaMemsetAsync(sc + SC_CONV, 0, sizeof(double), s), "scalar");
+        TRY(cudaMemsetAsync(sc + SC_TOLS, 0, sizeof(double), s), "scalar");
+        TRY(cudaMemsetAsync(sc + SC_TOLK, 0, sizeof(double), s), "scalar");
+    }
+    if (!base->tally_smem || base->chunk_b > 0) {
+        // the batched kernel needs whole units on the shared tally: one
+        // iteration per solve instead
+        for (int i = 0; i < n; ++i) {
+            moc_tracks *h = solves[i];
+            TRY(enqueue_iteration(h, s, h->cur), "iteration");
+            if (h->has_psi) h->cur = 1 - h->cur;
+        }
+    } else {
+        std::vector<BatchItem> it(n);
+        for (int i = 0; i < n; ++i) {
+            moc_tracks *h = solves[i];
+            const int c = h->cur;
+            it[i].qr = h->d_qr.p;
+            it[i].tally = (double *)h->d_tally.p;
+            it[i].scal = (double *)h->d_scal.p;
+            it[i].psi_in = h->has_psi ? h->d_psi[c].p : nullptr;
+            it[i].psi_out = h->has_psi ? h->d_psi[1 - c].p : nullptr;
+            it[i].bound_in = h->has_psi ? psi_bound(h, c) : nullptr;
+            it[i].bound_out = h->has_psi ? psi_bound(h, 1 - c) : nullptr;
+        }
+        if (base->d_batch.n < (size_t)n * sizeof(BatchItem)) {
+            base->bytes -= base->d_batch.n;
+            base->d_batch.release();
+            TRY(dalloc(base, base->d_batch, (size_t)n * sizeof(BatchItem)), "alloc batch table");
+        }
+        TRY(cudaMemcpyAsync(base->d_batch.p, it.data(), (size_t)n * sizeof(BatchItem), cudaMemcpyHostToDevice, s),
+            "upload");
+        for (int i = 0; i < n; ++i) {
+            moc_tracks *h = solves[i];
+            TRY(launch_source(h->precision, h->dl, h->ds, h->geom.nfsr, h->red_grid, s,
+                              h->has_psi ? psi_bound(h, 1 - h->cur) : nullptr), "source");
+        }
+        // one persistent sweep over the units of every solve
+        moc_tracks *h0 = solves[0];
+        int32_t *counter = sweep_counter(h0, h0->has_psi ? 1 - h0->cur : 0);
+        TRY(cudaMemsetAsync(counter, 0, 4, s), "memset");
+        TRY(launch_sweep_batch(base->precision, base->gpl, h0->dl, h0->ds, (const int32_t *)base->d_order.p,
+                               (int32_t)base->order.size(), base->tile_cap, counter,
+                               (const BatchItem *)base->d_batch.p, n, base->grid, base->block, base->smem, s),
+            "batched sweep");
+        for (int i = 0; i < n; ++i) {
+            moc_tracks *h = solves[i];
+            TRY(enqueue_finalize(h, s), "finalize");
+            TRY(cudaMemcpyAsync(h->h_scal, h->d_scal.p, SC_COUNT * 8, cudaMemcpyDeviceToHost, s), "scalars");
+            if (h->has_psi) h->cur = 1 - h->cur;
+        }
+    }
+    TRY(cudaStreamSynchronize(s), "batch step");
+    for (int i = 0; i < n; ++i) {
+        const int rc = check_sweep_flag(solves[i]);
+        if (rc) return rc;
+    }
     return MOC_OK;
 }
 

@@ -32,6 +32,16 @@ int sweep_lanes_per_track(int G, int gpl);
 // threads per sweep block the kernel is compiled for (its launch bound)
 int sweep_block_threads(int precision, int gpl);
 size_t sweep_smem_bytes(int precision, int tally_smem, int M, int G, int gpl, int cap);
+// The state of one solve of a batched sweep (pointers into device memory)
+struct BatchItem {
+    const void *qr;             // Q / Sigma_t, real
+    double *tally;              // FP64 tally
+    double *scal;               // device scalars
+    const void *psi_in;         // boundary fluxes in / out (null: all vacuum)
+    void *psi_out;
+    const unsigned *bound_in;   // bounds of |psi| (see launch_sweep)
+    unsigned *bound_out;
+};
 // counter: the work counter (zero at launch); bound_in: per group, a bound of
 // |psi_in| (float bits, may be null when psi_in is); bound_out: zeroed,
 // receives the bound of |psi_out| (FP32 fixed-point tally only; may be null)
@@ -40,11 +50,19 @@ cudaError_t launch_sweep(int precision, int tally_smem, int gpl, const DevLayout
                          const void *psi_in, void *psi_out, int32_t *counter,
                          const unsigned *bound_in, unsigned *bound_out, int grid, int block,
                          size_t smem, cudaStream_t s);
-// the sweep kernel for one lane shape (moc_sweep_f32g1/g2/g4.cu, moc_sweep_f64.cu)
-const void *sweep_kernel_f32_gpl1(int tally_smem, int chunk, int gl);
-const void *sweep_kernel_f32_gpl2(int tally_smem, int chunk, int gl);
-const void *sweep_kernel_f32_gpl4(int tally_smem, int chunk, int gl);
-const void *sweep_kernel_f64(int tally_smem, int chunk, int gl);
+// One sweep of n solves sharing the layout dl (shared tally, no radial
+// chunks): items[n] (device) hold their states; n_units = units in order.
+cudaError_t launch_sweep_batch(int precision, int gpl, const DevLayout &dl, const DevState &st,
+                               const int32_t *order, int32_t n_units, int32_t cap, int32_t *counter,
+                               const BatchItem *items, int32_t n, int grid, int block, size_t smem,
+                               cudaStream_t s);
+// the sweep kernel for one lane shape (moc_sweep_f32g1/g2/g4.cu, moc_sweep_f64.cu);
+// batch: the variant that sweeps several solves of one layout (shared tally,
+// units swept whole)
+const void *sweep_kernel_f32_gpl1(int tally_smem, int chunk, int batch, int gl);
+const void *sweep_kernel_f32_gpl2(int tally_smem, int chunk, int batch, int gl);
+const void *sweep_kernel_f32_gpl4(int tally_smem, int chunk, int batch, int gl);
+const void *sweep_kernel_f64(int tally_smem, int chunk, int batch, int gl);
 cudaError_t sweep_occupancy(int precision, int tally_smem, int chunk, int G, int gpl, int block,
                             size_t smem, int *blocks_per_sm);
 // threads per block of the per-FSR kernels (source, finalize, residual, init):

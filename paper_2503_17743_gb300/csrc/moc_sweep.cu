@@ -15,12 +15,12 @@ int lanes_for_groups(int G, int gpl) {
 }
 
 // chunk: some units are swept in radial chunks (shared tally only)
-const void *sweep_fn(int precision, int tally_smem, int chunk, int G, int gpl) {
+const void *sweep_fn(int precision, int tally_smem, int chunk, int G, int gpl, int batch = 0) {
     const int gl = lanes_for_groups(G, gpl);
-    if (precision == MOC_FP64) return sweep_kernel_f64(tally_smem, chunk, gl);
-    if (gpl == 4) return sweep_kernel_f32_gpl4(tally_smem, chunk, gl);
-    if (gpl == 2) return sweep_kernel_f32_gpl2(tally_smem, chunk, gl);
-    return sweep_kernel_f32_gpl1(tally_smem, chunk, gl);
+    if (precision == MOC_FP64) return sweep_kernel_f64(tally_smem, chunk, batch, gl);
+    if (gpl == 4) return sweep_kernel_f32_gpl4(tally_smem, chunk, batch, gl);
+    if (gpl == 2) return sweep_kernel_f32_gpl2(tally_smem, chunk, batch, gl);
+    return sweep_kernel_f32_gpl1(tally_smem, chunk, batch, gl);
 }
 
 }  // namespace
@@ -69,6 +69,30 @@ cudaError_t launch_sweep(int precision, int tally_smem, int gpl, const DevLayout
     void *a6 = psi_out;
     const unsigned *a7 = bound_in;
     unsigned *a8 = bound_out;
-    void *args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8};
+    const BatchItem *a9 = nullptr;
+    int32_t a10 = 0;
+    void *args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8, &a9, &a10};
+    return cudaLaunchKernel(f, dim3(grid), dim3(block), args, smem, s);
+}
+
+cudaError_t launch_sweep_batch(int precision, int gpl, const DevLayout &dl, const DevState &st,
+                               const int32_t *order, int32_t n_units, int32_t cap, int32_t *counter,
+                               const BatchItem *items, int32_t n, int grid, int block, size_t smem,
+                               cudaStream_t s) {
+    const void *f = sweep_fn(precision, 1, 0, dl.G, gpl, 1);
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    DevLayout a0 = dl;
+    DevState a1 = st;
+    a1.counter = counter;
+    const int32_t *a2 = order;
+    int32_t a3 = n_units * n, a4 = cap;
+    const void *a5 = nullptr;
+    void *a6 = nullptr;
+    const unsigned *a7 = nullptr;
+    unsigned *a8 = nullptr;
+    const BatchItem *a9 = items;
+    int32_t a10 = n;
+    void *args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8, &a9, &a10};
     return cudaLaunchKernel(f, dim3(grid), dim3(block), args, smem, s);
 }

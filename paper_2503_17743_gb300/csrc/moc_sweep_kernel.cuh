@@ -195,10 +195,14 @@ constexpr int kMaxSweepBlock = 320;
 // words per shared tally row
 __host__ __device__ constexpr int tally_stride(int GL, int GPL) { return GL * GPL + (GPL > 1 ? 1 : 0); }
 
-template <typename real, int GL, int GPL, bool SMEM, bool CHUNK>
+// BATCH: one launch sweeps several solves of one layout (their states in
+// items[n_items]); work index w is unit order[w / n_items] of solve
+// w % n_items, so the solves' units interleave, largest first.
+template <typename real, int GL, int GPL, bool SMEM, bool CHUNK, bool BATCH>
 __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(real) == 4 ? 3 : 2)
     k_sweep(DevLayout dl, DevState st, const int32_t *order, int32_t n_work, int32_t cap,
-            const real *psi_in, real *psi_out, const unsigned *bound_in, unsigned *bound_out) {
+            const real *psi_in_p, real *psi_out_p, const unsigned *bound_in_p, unsigned *bound_out_p,
+            const BatchItem *items, int32_t n_items) {
     constexpr int GP = GL * GPL;     // groups per chunk (padded)
     constexpr int SLOTS = 32 / GL;   // tracks per warp task
     extern __shared__ __align__(16) unsigned char smem[];
@@ -211,6 +215,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
     __shared__ unsigned s_pmax[32];  // max |psi_out| the block stored per group (float bits)
     __shared__ unsigned s_hmax[32];  // max |psi| handed to the next radial chunk (float bits)
     __shared__ float s_wmax;
+    __shared__ BatchItem s_item;     // BATCH: the solve of the current unit
     constexpr bool kFixed = sizeof(real) == 4;  // FP32 sweeps tally in fixed point
     const int G = dl.G, NL = dl.NL, M = dl.M, Ph = dl.Ph, cpl = dl.cpl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -220,7 +225,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
     // several groups per lane the tally rows are padded by one word so that
     // the rows of the warp's eight or more slots spread over the banks
     constexpr int TS = tally_stride(GL, GPL);
-    if (st.scal[SC_CONV] != 0.0) return;  // converged: later iterations are no-ops
+    if (!BATCH && st.scal[SC_CONV] != 0.0) return;  // converged: later iterations are no-ops
     real *sig = reinterpret_cast<real *>(smem);
     size_t off = ((size_t)M * GP * sizeof(real) + 15) & ~(size_t)15;
     real *rows = reinterpret_cast<real *>(smem + off);
@@ -230,16 +235,14 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
     const unsigned rows_sa = (unsigned)__cvta_generic_to_shared(rows);
     const unsigned tl_sa = (unsigned)__cvta_generic_to_shared(tl_s);
 
-    const real scale = (real)st.scal[SC_SCALE];
-    const real *qr_g = reinterpret_cast<const real *>(st.qr);
     const real *sig_g = reinterpret_cast<const real *>(st.sig_t);
     const SegRec<real> *recs = reinterpret_cast<const SegRec<real> *>(dl.segs);
-    double *err = st.scal + SC_ERR;
     real leak = (real)0;  // this lane's W psi leaving through vacuum faces
     // the fixed-point tally needs a bound of |psi_in| per group: the previous
     // sweep left one, and this sweep leaves one for the next (every psi_in is
-    // a psi_out of the previous sweep)
-    const bool track_bound = kFixed && SMEM && bound_out != nullptr;
+    // a psi_out of the previous sweep; the solves of a batch share the layout,
+    // so all of them have boundary fluxes or none)
+    const bool track_bound = kFixed && SMEM && (BATCH ? dl.dst != nullptr : bound_out_p != nullptr);
     float pmax[GPL];  // this lane's max |psi_out| for its groups of the current chunk
 #pragma unroll
     for (int c = 0; c < GPL; ++c) pmax[c] = 0.0f;
@@ -262,7 +265,24 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
         __syncthreads();
         const int w = s_work;
         if (w >= n_work) break;
-        const int T = order[w];
+        const int T = BATCH ? order[w / n_items] : order[w];
+        if constexpr (BATCH) {
+            if (tid < (int)(sizeof(BatchItem) / 8))
+                reinterpret_cast<uint64_t *>(&s_item)[tid] =
+                    reinterpret_cast<const uint64_t *>(items + w % n_items)[tid];
+            __syncthreads();
+            if (s_item.scal[SC_CONV] != 0.0) continue;  // that solve has converged
+        }
+        // the unit's solve (one solve unless batched)
+        const real *psi_in = BATCH ? reinterpret_cast<const real *>(s_item.psi_in) : psi_in_p;
+        real *psi_out = BATCH ? reinterpret_cast<real *>(s_item.psi_out) : psi_out_p;
+        const unsigned *bound_in = BATCH ? s_item.bound_in : bound_in_p;
+        unsigned *bound_out = BATCH ? s_item.bound_out : bound_out_p;
+        double *scal_u = BATCH ? s_item.scal : st.scal;
+        const real scale = (real)scal_u[SC_SCALE];
+        const real *qr_g = reinterpret_cast<const real *>(BATCH ? s_item.qr : st.qr);
+        double *tally_g = BATCH ? s_item.tally : st.tally;
+        double *err = scal_u + SC_ERR;
         if (tid == 0) {
             int pre = 0;
             for (int ph = 0; ph < Ph; ++ph) {
@@ -548,8 +568,8 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                             tU[c] = fma(-dU, xU, dU);
                             tD[c] = fma(-dD, xD, dD);
                             if (qq < gc) {
-                                atomicAdd(st.tally + fU * G + g0 + qq, (double)tU[c]);
-                                atomicAdd(st.tally + fD * G + g0 + qq, (double)tD[c]);
+                                atomicAdd(tally_g + fU * G + g0 + qq, (double)tU[c]);
+                                atomicAdd(tally_g + fD * G + g0 + qq, (double)tD[c]);
                             }
                             psiU[c] -= tU[c];
                             psiD[c] -= tD[c];
@@ -746,19 +766,39 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                         if (qq >= gc) continue;
                         const int e = (bb * NL + L) * TS + qq;
                         const double v = kFixed ? (double)((float)tl_i[e] * s_inv[qq]) : (double)tl_s[e];
-                        if (v != 0.0) atomicAdd(st.tally + ((size_t)reg * NL + L) * G + g0 + qq, v);
+                        if (v != 0.0) atomicAdd(tally_g + ((size_t)reg * NL + L) * G + g0 + qq, v);
                     }
                 }
                 if (tid < 32) s_bmax[tid] = 0u;  // next chunk's bound (read only before its tasks)
             }
         }
+        if constexpr (BATCH) {
+            // the next unit may belong to another solve: publish this one's
+            // psi bound and leakage now
+            if (track_bound && G <= GP) fold_pmax(G);
+            double lk = (double)leak;
+            for (int o = 16; o > 0; o >>= 1) lk += __shfl_down_sync(0xffffffffu, lk, o);
+            if (lane == 0) s_leak[warp] = lk;
+            leak = (real)0;
+            __syncthreads();
+            if (track_bound && G <= GP && tid < G) {
+                if (s_pmax[tid]) atomicMax(bound_out + tid, s_pmax[tid]);
+                s_pmax[tid] = 0u;
+            }
+            if (tid == 0) {
+                double v = 0.0;
+                for (int k = 0; k < nwarps; ++k) v += s_leak[k];
+                if (v != 0.0) atomicAdd(scal_u + SC_LEAK, v);
+            }
+        }
     }
-    if (track_bound && G <= GP) {
+    if (!BATCH && track_bound && G <= GP) {
         // one chunk: the maxima span every unit of the block, published once
         fold_pmax(G);
         __syncthreads();
-        if (tid < G && s_pmax[tid]) atomicMax(bound_out + tid, s_pmax[tid]);
+        if (tid < G && s_pmax[tid]) atomicMax(bound_out_p + tid, s_pmax[tid]);
     }
+    if (BATCH) return;
     double leak64 = (double)leak;
     for (int o = 16; o > 0; o >>= 1) leak64 += __shfl_down_sync(0xffffffffu, leak64, o);
     if (lane == 0) s_leak[warp] = leak64;
@@ -772,12 +812,12 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
 
 // the kernel for gl lanes per track; only shapes with gl * GPL <= 32 exist
 // (each translation unit of the sweep instantiates its share)
-template <typename real, int GPL, bool SMEM, bool CHUNK, int GL = 32 / GPL>
+template <typename real, int GPL, bool SMEM, bool CHUNK, bool BATCH, int GL = 32 / GPL>
 const void *pick(int gl) {
     if constexpr (GL > 1) {
-        if (gl < GL) return pick<real, GPL, SMEM, CHUNK, GL / 2>(gl);
+        if (gl < GL) return pick<real, GPL, SMEM, CHUNK, BATCH, GL / 2>(gl);
     }
-    return (const void *)k_sweep<real, GL, GPL, SMEM, CHUNK>;
+    return (const void *)k_sweep<real, GL, GPL, SMEM, CHUNK, BATCH>;
 }
 
 template <typename real, int GPL>
