@@ -120,6 +120,13 @@ def profile_traffic(src_hash):
     return int(t.group(1))
 
 
+def measured_hbm_gbs():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def sweep_source_hash():
     h = hashlib.sha256()
     for f in ("moc_sweep_kernel.cuh", "moc_device.cuh"):
@@ -129,7 +136,8 @@ def sweep_source_hash():
 
 def cpu_baseline(prob, seconds_target=10.0):
     """The oracle (as it stands) on the host cores: full FP64 sweeps of the
-    workload from a seeded source, as many as fit in about 10 s."""
+    workload from a seeded source, as many as fit in about 10 s; then on one
+    thread, the 2D tracks of one sweep in index order for about 5 s."""
     import numpy as np
 
     import oracle
@@ -143,9 +151,22 @@ def cpu_baseline(prob, seconds_target=10.0):
         t_total += time.perf_counter() - t0
         n_total += n
         sweeps += 1
+    o.set_threads(1)
+    n1, t1, t = 0, 0.0, 0
+    step = max(1, o.n_tracks2d // 32)
+    while t1 < seconds_target / 2 and t < o.n_tracks2d:
+        t_end = min(t + step, o.n_tracks2d)
+        t0 = time.perf_counter()
+        n, _ = o.sweep_sample(Q, t, t_end)
+        t1 += time.perf_counter() - t0
+        n1 += n
+        t = t_end
     return {"value": n_total / t_total, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{sweeps} full FP64 sweep(s) of {WORKLOAD} from a seeded source "
-                      f"({n_total:.4g} integrations, {t_total:.1f} s)"}
+                      f"({n_total:.4g} integrations, {t_total:.1f} s)",
+            "single_thread": {"value": n1 / t1, "unit": UNIT, "cores": 1,
+                              "sample": f"2D tracks 0-{t} of {o.n_tracks2d} of one sweep "
+                                        f"({n1:.4g} integrations, {t1:.1f} s)"}}
 
 
 def run_reference(args):
@@ -297,11 +318,21 @@ def run_ours(args):
     sw = statistics.mean(sweep_ms) * 1e-3
     ach = OPS_PER_INTEGRATION * integ / sw / 1e12
     peak = SMS * LANES_PER_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = profile_traffic(sweep_source_hash())
     roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-            "traffic": profile_traffic(sweep_source_hash()), "kernel": "k_sweep",
+            "traffic": traffic, "kernel": "k_sweep",
             "sweep_ms": sw * 1e3,
             "peak_basis": "derived: FP32 issue 128 lane-ops per SM per clock x 152 SMs x 2070 MHz; "
                           "7 FP32 ops per integration (ex2 unit measured 31.4/SM/clk, not binding)"}
+    # the HBM side of the same sweep: algorithmic bytes (boundary fluxes in
+    # and out, stored template records) and, from the committed ncu summary,
+    # the DRAM bytes moved, both per launch time, against the measured copy peak
+    alg_bytes = 2 * (info["tracks3d"] // 2) * 4 * prob.num_groups * 4 + info["stored_segments"] * 8
+    hbm_peak = measured_hbm_gbs()
+    roof["hbm"] = {"algorithmic_bytes": alg_bytes, "algorithmic_gbs": alg_bytes / sw / 1e9,
+                   "dram_gbs": traffic / sw / 1e9 if traffic else None,
+                   "peak_gbs": hbm_peak,
+                   "frac": (traffic / sw / 1e9) / hbm_peak if (traffic and hbm_peak) else None}
     clocks = parse_clocks(clk_path)
     try:
         os.remove(clk_path)

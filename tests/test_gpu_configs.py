@@ -7,7 +7,8 @@ by one:
 * the 7x7-assembly core with a reflector ring (200 cm, 100 layers,
   128 azimuths x 6 polar, all faces vacuum).
 
-For each: sampled z-stacks bit-exact, and one sweep of a sample of 2D tracks
+For each: sampled z-stacks bit-exact (10^4 on the assemblies, 500 on the
+core), and one sweep of a sample of 2D tracks
 (every polar angle, both senses, zero incoming flux) from a seeded source,
 tallies element by element against the FP64 oracle (FP32 tolerance 2e-5 of
 the largest).  The oracle runs in its light mode (tracks and segments only).
@@ -26,8 +27,8 @@ pytestmark = pytest.mark.gpu
 NTH = os.cpu_count() or 4
 
 
-@pytest.mark.parametrize("name,budget", [("asm3x3", 1 << 30), ("core7x7", -1)])
-def test_large_configuration_samples(name, budget):
+@pytest.mark.parametrize("name,budget,n_stacks", [("asm3x3", 1 << 30, 10000), ("core7x7", -1, 500)])
+def test_large_configuration_samples(name, budget, n_stacks):
     p = synth.workload(name)
     o = oracle.Oracle(p, n_threads=NTH, light=True)
     tr = Tracks(Geometry(p), track_params(p, precision=MOC_FP32, preload_budget_bytes=budget))
@@ -37,7 +38,7 @@ def test_large_configuration_samples(name, budget):
         # part stored, part generated on the fly (Sec. 4.2)
         assert 0 < info["preloaded_stacks"] < info["stacks"] // 2
     rng = np.random.default_rng(31)
-    for _ in range(30):
+    for _ in range(n_stacks):
         t = int(rng.integers(o.n_tracks2d))
         pp = int(rng.integers(p.n_polar))
         oi, on, of, ol = o.stack(t, pp)

@@ -311,3 +311,24 @@ def test_radial_chunks_power_iterations(name, prec, ktol, ftol):
     assert abs(k - ref["k"]) < ktol, (k, ref["k"])
     np.testing.assert_allclose(phi, o.flux(), rtol=ftol)
     tr.close()
+
+
+@pytest.mark.parametrize("prec,rtol", [(MOC_FP64, 1e-12), (MOC_FP32, 1e-5)])
+@pytest.mark.parametrize("k", [2, 3])
+def test_virtual_shards_sum_to_the_sweep(k, prec, rtol):
+    """Angular decomposition on one GPU: k disjoint ranges of 2D tracks
+    (whole azimuths in laydown order) swept separately from one source with
+    zero incoming flux; their tallies and leakages sum to the sweep of all
+    tracks, which is the all-reduce a sharded sweep would do."""
+    p, o, g = get("lat3_mixed")
+    tr = Tracks(g, track_params(p, precision=prec))
+    Q = np.random.default_rng(5).uniform(0.2, 1.0, size=(o.n_fsr, p.num_groups))
+    full, lf = tr.sweep_units_from_source(Q, 0, o.n_tracks2d)
+    edges = np.linspace(0, o.n_tracks2d, k + 1).astype(int)
+    parts = [tr.sweep_units_from_source(Q, int(a), int(b)) for a, b in zip(edges[:-1], edges[1:])]
+    total = sum(t for t, _ in parts)
+    np.testing.assert_allclose(total, full, rtol=rtol, atol=rtol * np.abs(full).max())
+    assert abs(sum(lk for _, lk in parts) - lf) <= rtol * abs(lf) + 1e-300
+    # and the shards partition the work: each one alone misses the others' part
+    assert all(np.abs(t).sum() < np.abs(full).sum() for t, _ in parts)
+    tr.close()
