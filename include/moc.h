@@ -137,7 +137,10 @@ typedef struct {
  *                      units whose tile does not fit in shared memory, in the
  *                      largest chunks that keep three blocks per SM.  A
  *                      track's psi passes from chunk to chunk; results equal
- *                      the whole-unit sweep up to FP rounding. */
+ *                      the whole-unit sweep up to FP rounding.
+ *   trace_on_device    1: trace the 2D tracks through the lattice on the GPU
+ *                      (one thread per track; the same pieces as the host
+ *                      tracer, bit for bit), 0: on the host (Sec. 3.1). */
 typedef struct {
     int32_t n_azim, n_polar;
     double radial_spacing, axial_spacing;
@@ -150,6 +153,7 @@ typedef struct {
     int32_t groups_per_lane;
     int32_t schedule;
     int32_t chunk_segments;
+    int32_t trace_on_device;
 } moc_track_params;
 
 /* Stopping rule of a solve: |k_n - k_(n-1)| < tol_k (eigenvalue problems
@@ -281,6 +285,14 @@ void moc_state_destroy(moc_tracks *state);
  * MOC_ERR_INVALID_ARG (NULL, n < 1, a solve twice, different layouts),
  * MOC_ERR_CUDA. */
 int moc_batch_step(moc_tracks *const *solves, int32_t n, void *stream);
+
+/* The 2D segments of 2D track t (Sec. 3.1 ray tracing, host copy): *n
+ * segments; when cap >= *n, region[*n], length[*n] (cm) and position[*n + 1]
+ * (distance of each boundary from the track's start, the last = its length)
+ * are written (each may be NULL).  Errors: MOC_ERR_INVALID_ARG (NULL n, t
+ * out of range). */
+int moc_get_segments2d(const moc_tracks *tracks, int32_t t, int64_t cap, int32_t *region,
+                       double *length, double *position, int64_t *n);
 
 /* Layout counts, int64 values written to out[0..n-1]:
  *   0 n_fsr, 1 groups, 2 2D tracks, 3 z-stacks (both hemispheres), 4 3D tracks,

@@ -55,7 +55,7 @@ class moc_track_params(C.Structure):
                 ("preload_budget_bytes", C.c_int64), ("tally_mode", C.c_int32),
                 ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("device", C.c_int32),
                 ("groups_per_lane", C.c_int32), ("schedule", C.c_int32),
-                ("chunk_segments", C.c_int32)]
+                ("chunk_segments", C.c_int32), ("trace_on_device", C.c_int32)]
 
 
 class moc_server_params(C.Structure):
@@ -89,6 +89,7 @@ SIGNATURES = {
                                       C.POINTER(C.c_void_p)]),
     "moc_destroy_tracks": (None, [C.c_void_p]),
     "moc_state_create": (C.c_int, [C.c_void_p, f64p, C.POINTER(C.c_void_p)]),
+    "moc_get_segments2d": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, i32p, f64p, f64p, i64p]),
     "moc_state_destroy": (None, [C.c_void_p]),
     "moc_batch_step": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p]),
     "moc_sweep": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -210,7 +211,7 @@ class Geometry:
 
 def track_params(prob, precision=MOC_FP32, preload_budget_bytes=-1, tally_mode=MOC_TALLY_AUTO,
                  block_threads=0, blocks_per_sm=0, device=0, groups_per_lane=0, schedule=0,
-                 chunk_segments=0):
+                 chunk_segments=0, trace_on_device=0):
     p = moc_track_params()
     p.n_azim, p.n_polar = prob.n_azim, prob.n_polar
     p.radial_spacing, p.axial_spacing = prob.radial_spacing, prob.axial_spacing
@@ -223,6 +224,7 @@ def track_params(prob, precision=MOC_FP32, preload_budget_bytes=-1, tally_mode=M
     p.groups_per_lane = groups_per_lane
     p.schedule = schedule
     p.chunk_segments = chunk_segments
+    p.trace_on_device = trace_on_device
     return p
 
 
@@ -249,6 +251,18 @@ class Tracks:
         self.info = self._info()
         self.n_fsr = self.info["n_fsr"]
         self.G = self.info["groups"]
+
+    def segments2d(self, t):
+        """moc_get_segments2d: (regions, lengths, boundary positions) of 2D track t."""
+        n = C.c_int64()
+        lib = load()
+        _check(lib.moc_get_segments2d(self._h, int(t), 0, i32p(), f64p(), f64p(), C.byref(n)))
+        reg = np.zeros(n.value, dtype=np.int32)
+        ln = np.zeros(n.value)
+        pos = np.zeros(n.value + 1)
+        _check(lib.moc_get_segments2d(self._h, int(t), n.value, _ptr(reg, i32p), _ptr(ln, f64p),
+                                      _ptr(pos, f64p), C.byref(n)))
+        return reg, ln, pos
 
     def state(self, ext_source=None):
         """moc_state_create: another solve on this layout (optionally with its

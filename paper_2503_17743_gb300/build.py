@@ -22,7 +22,9 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["moc_kernels.cu", "moc_sweep.cu", "moc_sweep_f32g1.cu", "moc_sweep_f32g2.cu",
               "moc_sweep_f32g4.cu", "moc_sweep_f64.cu", "moc_api.cu", "moc_static.cu", "moc_peak.cu",
-              "moc_server.cu", "moc_tune.cu"]
+              "moc_server.cu", "moc_tune.cu", "moc_trace.cu"]
+# per-file nvcc flags: the device 2D tracer must round like the host tracer
+CU_FLAGS = {"moc_trace.cu": ["-fmad=false"]}
 CPP_SOURCES = ["moc_host.cpp"]
 
 
@@ -55,7 +57,7 @@ def build(force: bool = False, verbose: bool = False, extra_nvcc=()) -> str:
         objs.append(o)
         jobs.append([NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC,
-                     *extra_nvcc, "-c", os.path.join(CSRC, f), "-o", o])
+                     *CU_FLAGS.get(f, []), *extra_nvcc, "-c", os.path.join(CSRC, f), "-o", o])
     for f in CPP_SOURCES:
         o = os.path.join(BUILD, f + ".o")
         objs.append(o)

@@ -362,7 +362,9 @@ extern "C" int moc_query_footprint(const moc_geometry *g, const moc_track_params
     if (!g || !p) { moc_set_error("NULL argument"); return MOC_ERR_INVALID_ARG; }
     Layout L;
     std::string err;
-    int rc = moc_build_layout(*g, *p, L, err);
+    moc_track_params hp = *p;
+    hp.trace_on_device = 0;  // a host-only query
+    int rc = moc_build_layout(*g, hp, L, err);
     if (rc) { moc_set_error(err); return rc; }
     const size_t rs = real_size(p->precision);
     const int64_t G = g->G;
@@ -1164,6 +1166,23 @@ extern "C" int moc_tracks_info(const moc_tracks *h, int64_t *out, int32_t n) {
                            (int64_t)h->smem, h->tile_cap, sweep_lanes_per_track(h->geom.G, h->gpl),
                            h->max_nseg, (int64_t)h->h2d, h->gpl, h->chunk_b};
     for (int i = 0; i < n && i < 23; ++i) out[i] = v[i];
+    return MOC_OK;
+}
+
+extern "C" int moc_get_segments2d(const moc_tracks *h, int32_t t, int64_t cap, int32_t *region,
+                                  double *length, double *position, int64_t *n) {
+    if (!h || !n) { moc_set_error("NULL argument"); return MOC_ERR_INVALID_ARG; }
+    const Layout &L = h->L;
+    if (t < 0 || t >= L.nt) { moc_set_error("2D track out of range"); return MOC_ERR_INVALID_ARG; }
+    const int64_t a = L.seg_off[t], b = L.seg_off[t + 1];
+    *n = b - a;
+    if (cap < b - a) return MOC_OK;  // sizes only
+    for (int64_t q = a; q < b; ++q) {
+        if (region) region[q - a] = L.seg_reg[q];
+        if (length) length[q - a] = L.seg_len[q];
+        if (position) position[q - a] = L.seg_pos[q + t];
+    }
+    if (position) position[b - a] = L.seg_pos[b + t];
     return MOC_OK;
 }
 

@@ -381,7 +381,19 @@ int moc_build_layout(const moc_geometry &g, const moc_track_params &prm, Layout 
     // 2D segments
     L.seg_off.assign(nt + 1, 0);
     L.seg_reg.clear(); L.seg_len.clear(); L.seg_pos.clear();
-    {
+    if (prm.trace_on_device) {
+        std::vector<double> dxs(nt), dys(nt);
+        for (int t = 0; t < nt; ++t) {
+            const int a = L.t_azim[t];
+            const int m = a < nq ? a : A / 2 - 1 - a;
+            double ux = g.Wx / (2.0 * (double)L.nx[m]), uy = g.Wy / (2.0 * (double)L.ny[m]);
+            dxs[t] = (a < nq ? ux : -ux) / L.lu[m];
+            dys[t] = uy / L.lu[m];
+        }
+        const int rc = moc_trace2d_device(g, prm.device, L.t_x0, L.t_y0, dxs, dys, L.t_len, L.seg_off,
+                                          L.seg_reg, L.seg_len, L.seg_pos, err);
+        if (rc) return rc;
+    } else {
         std::vector<Piece> pcs;
         for (int t = 0; t < nt; ++t) {
             const int a = L.t_azim[t];

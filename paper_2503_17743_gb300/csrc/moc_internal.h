@@ -104,6 +104,13 @@ struct Layout {
 
 // tracker entry points (moc_host.cpp)
 int moc_build_layout(const moc_geometry &g, const moc_track_params &p, Layout &L, std::string &err);
+// 2D ray tracing of the laydown's tracks on the device (moc_trace.cu): the
+// host tracer's pieces bit for bit (CSR offsets, regions, lengths, positions)
+int moc_trace2d_device(const moc_geometry &g, int device, const std::vector<double> &x0,
+                       const std::vector<double> &y0, const std::vector<double> &dx,
+                       const std::vector<double> &dy, const std::vector<double> &len,
+                       std::vector<int32_t> &seg_off, std::vector<int32_t> &seg_reg,
+                       std::vector<double> &seg_len, std::vector<double> &seg_pos, std::string &err);
 
 // explicit destination of (geometric track gid, variant v): gid'*4+v' or -1
 int64_t moc_layout_link(const moc_geometry &g, const Layout &L, int64_t stack, int64_t i, int v);
