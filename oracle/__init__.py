@@ -47,6 +47,7 @@ class _Input(C.Structure):
         ("n_threads", C.c_int),
         ("light", C.c_int),
         ("fuel_rings", C.c_int), ("mod_rings", C.c_int), ("sectors", C.c_int),
+        ("layer_z", f64p),
     ]
 
 
@@ -140,6 +141,8 @@ class Oracle:
         inp.fuel_rings = int(getattr(prob, "fuel_rings", 1))
         inp.mod_rings = int(getattr(prob, "moderator_rings", 0))
         inp.sectors = int(getattr(prob, "sectors", 1))
+        lz = getattr(prob, "layer_z", None)
+        inp.layer_z = _p(arr(lz, np.float64), f64p) if lz is not None else f64p()
         self.n_threads = inp.n_threads
         err = C.create_string_buffer(256)
         h = lib.orc_create(C.byref(inp), err, 256)

@@ -62,6 +62,8 @@ typedef struct {
     int light;  /* 1: tracks and segments only (no links, boundary fluxes or
                    volumes): for sampled checks of problems too large to solve */
     int fuel_rings, mod_rings, sectors;  /* pin-cell refinement (0 read as 1, 0, 1) */
+    const double *layer_z;  /* [n_layers + 1] layer planes from 0 to height, or NULL
+                               (equal layers); each a whole number of axial spacings */
 } orc_input;
 
 /* faces */
@@ -81,7 +83,8 @@ typedef struct {
     double circ_r2[130];           /* squared radii of the circles, increasing */
     int *reg_base;      /* per cell */
     int *fsr_mat;       /* per FSR */
-    int Nz, cpl;
+    int Nz, cpl;      /* cpl: lattice cells per layer (0 when the layers differ) */
+    long *lplane;     /* [nl + 1] lattice index of each layer plane */
     double dz;
     /* azimuth pairs m = 0..nq-1 */
     int nq;
@@ -506,7 +509,7 @@ static void build_stack(orc_t *o, int t, int p, stackbuf *sb) {
     stack_geom(o, t, p, sb->zeta, &nbx, &cot, &sn, &cs);
     double *zeta = sb->zeta;
     int up = cot > 0;
-    int cpl = o->cpl, NL = o->nl;
+    int NL = o->nl;
     /* track index range over the whole stack (domain 0 < u < Nz) */
     double zmx = zeta[0] > zeta[nb] ? zeta[0] : zeta[nb];
     double zmn = zeta[0] < zeta[nb] ? zeta[0] : zeta[nb];
@@ -543,7 +546,7 @@ static void build_stack(orc_t *o, int t, int p, stackbuf *sb) {
             double l2d = o->slen[off + b];
             for (int li = 0; li < NL; li++) {
                 int L = up ? li : NL - 1 - li;     /* traversal order of the layers */
-                double kmin = (double)(L * cpl), kmax = (double)((L + 1) * cpl);
+                double kmin = (double)o->lplane[L], kmax = (double)o->lplane[L + 1];
                 long i_start = (long)ceil(kmin - zhi);    /* Eq. 6 */
                 long i_end = (long)floor(kmax - zlo);     /* Eq. 7 */
                 long i_in = (long)ceil(kmin - zlo);       /* Eq. 9 */
@@ -555,7 +558,7 @@ static void build_stack(orc_t *o, int t, int p, stackbuf *sb) {
                     if (i >= i_in && i <= i_out) {
                         len = l2d / sn;                          /* Eq. 8 */
                     } else if (i_in > i_out && i > i_out && i < i_in) {
-                        len = (double)cpl * o->dz / cs;          /* Eq. 11 */
+                        len = (kmax - kmin) * o->dz / cs;        /* Eq. 11 */
                     } else {
                         double lo = (double)i + zlo, hi = (double)i + zhi;
                         if (lo < kmin) lo = kmin;
@@ -741,13 +744,32 @@ void *orc_create(const orc_input *in, char *err, int errlen) {
     }
     for (int i = 0; i < o->nfsr; i++)
         if (o->fsr_mat[i] < 0 || o->fsr_mat[i] >= M) { set_err(err, errlen, "material index out of range"); orc_destroy(o); return NULL; }
-    /* axial lattice: dz_eff = H / Nz; layers must be whole numbers of dz */
+    /* axial lattice: dz_eff = H / Nz; every layer plane must lie on it (a
+       whole number of dz from the bottom), so layers are whole numbers of
+       lattice cells (equal layers: cpl each; otherwise per the plane list) */
     double q = o->H / in->axial_spacing;
     long Nz = (fabs(q - nearbyint(q)) < 1e-9) ? (long)nearbyint(q) : (long)ceil(q);
     o->Nz = (int)Nz;
     o->dz = o->H / (double)Nz;
-    if (Nz % o->nl) { set_err(err, errlen, "layers are not whole numbers of axial spacings"); orc_destroy(o); return NULL; }
-    o->cpl = (int)(Nz / o->nl);
+    o->lplane = malloc(sizeof(long) * (size_t)(o->nl + 1));
+    if (!in->layer_z) {
+        if (Nz % o->nl) { set_err(err, errlen, "layers are not whole numbers of axial spacings"); orc_destroy(o); return NULL; }
+        o->cpl = (int)(Nz / o->nl);
+        for (int L = 0; L <= o->nl; L++) o->lplane[L] = (long)L * o->cpl;
+    } else {
+        o->cpl = 0;
+        for (int L = 0; L <= o->nl; L++) {
+            double u = in->layer_z[L] / o->dz;
+            long k = (long)nearbyint(u);
+            if (fabs(u - (double)k) > 1e-9 || (L > 0 && k <= o->lplane[L - 1]) || (L == 0 && k != 0) ||
+                (L == o->nl && k != Nz)) {
+                set_err(err, errlen, "layer planes must rise from 0 to the height on the axial lattice");
+                orc_destroy(o);
+                return NULL;
+            }
+            o->lplane[L] = k;
+        }
+    }
     /* azimuths */
     o->nq = o->A / 4;
     int nq = o->nq;
@@ -869,7 +891,7 @@ void *orc_create(const orc_input *in, char *err, int errlen) {
 void orc_destroy(void *h) {
     orc_t *o = (orc_t *)h;
     if (!o) return;
-    void *ptrs[] = {o->has_pin, o->mat_in, o->mat_out, o->st, o->ss, o->nsf, o->chi, o->src,
+    void *ptrs[] = {o->lplane, o->has_pin, o->mat_in, o->mat_out, o->st, o->ss, o->nsf, o->chi, o->src,
                     o->reg_base, o->fsr_mat, o->nx, o->ny, o->gg, o->Mcyc, o->phi_eff, o->span,
                     o->deff, o->lu, o->mu_gl, o->w_gl, o->cpol, o->cot, o->sinp, o->cosp,
                     o->a_off, o->t_azim, o->t_sface, o->t_sk, o->t_eface, o->t_ek, o->t_steps,

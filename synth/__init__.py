@@ -22,8 +22,9 @@ Conventions shared by both consumers (they are inputs, not arithmetic):
   ``mat_out``.  With the defaults (1, 0, 1) a pin cell has two regions
   (circle, then moderator).  Every other cell is one region; radial regions
   are numbered cell by cell;
-* a flat source region (FSR) is ``region * n_layers + layer`` (axially
-  uniform layers, layer 0 at z = 0);
+* a flat source region (FSR) is ``region * n_layers + layer`` (layer 0 at
+  z = 0); layers are equal unless ``layer_z`` lists the n_layers + 1 planes
+  from 0 to the height, each a whole number of axial spacings;
 * ``bc`` lists the faces xmin, xmax, ymin, ymax, zmin, zmax with 1 =
   reflective and 0 = vacuum;
 * ``sigma_s[m, g, h]`` is the scattering cross section from group g into
@@ -72,6 +73,7 @@ class Problem:
     fuel_rings: int = 1
     moderator_rings: int = 0
     sectors: int = 1
+    layer_z: Optional[np.ndarray] = None   # float64 [n_layers + 1] planes, or None: equal layers
     meta: dict = field(default_factory=dict)
 
     @property
@@ -321,6 +323,7 @@ def workload(name: str, seed: int = 1) -> Problem:
                        and 8 sectors per pin cell
     * ``pin_cell_rings`` - the pin cell with 3 fuel rings, 2 moderator rings
                        and 4 sectors
+    * ``lattice5_axial`` - lattice5 with unequal layers (0.5, 1, 1.5, 1 cm)
     * ``asm3x3``     - 3x3 assemblies + reflector on two sides, 64 cm
     * ``core7x7``    - 7x7 assemblies + reflector ring, 200 cm
     """
@@ -341,6 +344,11 @@ def workload(name: str, seed: int = 1) -> Problem:
         return replace(lattice(seed, n=5, n_azim=16, n_polar=4, radial_spacing=0.1,
                                axial_spacing=0.5, height=4.0, n_layers=4, name="lattice5_rings"),
                        fuel_rings=3, moderator_rings=1, sectors=8)
+    if name == "lattice5_axial":
+        # unequal layers on the 0.5 cm axial lattice: 0.5, 1.0, 1.5 and 1.0 cm
+        return replace(lattice(seed, n=5, n_azim=16, n_polar=4, radial_spacing=0.1,
+                               axial_spacing=0.5, height=4.0, n_layers=4, name="lattice5_axial"),
+                       layer_z=np.array([0.0, 0.5, 1.5, 3.0, 4.0]))
     if name == "pin_cell_rings":
         return replace(pin_cell(seed), name="pin_cell_rings", fuel_rings=3, moderator_rings=2,
                        sectors=4)

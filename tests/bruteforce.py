@@ -131,7 +131,11 @@ def ray_fsrs_3d(prob, x0, y0, dx, dy, L, z_start, cot, n_samples=200000):
     inside = (z > 0) & (z < prob.height)
     s, z = s[inside], z[inside]
     reg = region_ids(prob, x0 + s * dx, y0 + s * dy)
-    layer = np.floor(z / (prob.height / prob.n_layers)).astype(np.int64)
+    lz = getattr(prob, "layer_z", None)
+    if lz is None:
+        layer = np.floor(z / (prob.height / prob.n_layers)).astype(np.int64)
+    else:
+        layer = np.searchsorted(np.asarray(lz), z, side="right") - 1
     fsr = reg * prob.n_layers + layer
     sin = 1.0 / math.sqrt(1.0 + cot * cot)
     ids, lens = rle(fsr, h / sin)

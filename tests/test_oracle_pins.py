@@ -40,6 +40,16 @@ def lat3r(oracle_mod):
 
 
 @pytest.fixture(scope="module")
+def lat3z(oracle_mod):
+    """lat3 with unequal layers on the axial lattice: 0.5, 1.0, 1.5, 1.0 cm."""
+    p = synth.lattice(3, n=3, G=3, height=4.0, n_layers=4, n_azim=8, n_polar=4,
+                      radial_spacing=0.15, axial_spacing=0.5, bc=(1, 1, 1, 1, 1, 1),
+                      n_gt=2, name="lat3z")
+    p = p.with_tracks(layer_z=np.array([0.0, 0.5, 1.5, 3.0, 4.0]))
+    return p, oracle_mod.Oracle(p, n_threads=2)
+
+
+@pytest.fixture(scope="module")
 def lat3(oracle_mod):
     p = synth.lattice(3, n=3, G=3, height=4.0, n_layers=4, n_azim=8, n_polar=4,
                       radial_spacing=0.15, axial_spacing=0.5, bc=(1, 1, 1, 1, 1, 1),
@@ -219,8 +229,8 @@ def _stack_checks(p, o, t, p_idx):
         assert abs(l.sum() - (s_hi - s_lo) / sin) < 1e-9
 
 
-def test_3d_segments_bruteforce(pin, lat3, lat3r):
-    for p, o in (pin, lat3, lat3r):
+def test_3d_segments_bruteforce(pin, lat3, lat3r, lat3z):
+    for p, o in (pin, lat3, lat3r, lat3z):
         for t in range(0, o.n_tracks2d, max(1, o.n_tracks2d // 8)):
             for p_idx in range(p.n_polar):
                 _stack_checks(p, o, t, p_idx)
@@ -394,9 +404,14 @@ def test_eq3_flat_source_equilibrium(oracle_mod):
 
 # --------------------------------------------------------------- iteration
 
-def test_infinite_medium_k_closed_form(oracle_mod):
+@pytest.mark.parametrize("layers", ["equal", "unequal"])
+def test_infinite_medium_k_closed_form(oracle_mod, layers):
     for G, seed in ((2, 1), (4, 7)):
-        p = synth.pin_cell(seed, G=G, homogeneous=True)
+        if layers == "unequal":
+            p = synth.pin_cell(seed, G=G, homogeneous=True, n_layers=3).with_tracks(
+                layer_z=np.array([0.0, 0.5, 1.5, 2.0]))
+        else:
+            p = synth.pin_cell(seed, G=G, homogeneous=True)
         o = oracle_mod.Oracle(p, n_threads=2)
         r = o.solve(tol_k=1e-13, tol_src=1e-12, max_iter=20000)
         assert r["converged"]
@@ -448,3 +463,26 @@ def test_pin_cell_axial_mirror_symmetry(pin):
     V = o.volumes().reshape(2, p.n_layers)
     np.testing.assert_allclose(V, V[:, ::-1], rtol=1e-12)
     assert abs(r["production"] / r["k"] - r["absorption"]) < 1e-9 * r["absorption"]
+
+
+def test_unequal_layer_volumes_match_analytic(oracle_mod):
+    """Unequal layers (0.5, 1.0, 0.5 cm on the 0.5 cm axial lattice): each
+    FSR's tracked volume is its radial area times its layer's height, the
+    area from the same per-azimuth chord sums in every layer."""
+    p = synth.pin_cell(1, radial_spacing=0.02, n_azim=32, n_layers=3).with_tracks(
+        layer_z=np.array([0.0, 0.5, 1.5, 2.0]))
+    o = oracle_mod.Oracle(p, n_threads=4)
+    V = o.volumes().reshape(2, 3)
+    h = np.diff(p.layer_z)
+    fuel = math.pi * p.fuel_radius ** 2
+    np.testing.assert_allclose(V[0] / h, fuel, rtol=0.005)
+    np.testing.assert_allclose(V[1] / h, p.pitch ** 2 - fuel, rtol=0.005)
+    # every layer sees the same radial areas: the ratios are exact up to rounding
+    np.testing.assert_allclose(V[:, 1] / V[:, 0], h[1] / h[0], rtol=1e-9)
+    assert abs(V.sum() - p.pitch ** 2 * p.height) < 1e-9 * p.pitch ** 2 * p.height
+
+
+def test_unequal_layers_off_the_lattice_rejected(oracle_mod):
+    p = synth.pin_cell(1, n_layers=3).with_tracks(layer_z=np.array([0.0, 0.6, 1.5, 2.0]))
+    with pytest.raises(ValueError):
+        oracle_mod.Oracle(p, n_threads=1)
