@@ -85,7 +85,11 @@ typedef struct moc_tracks moc_tracks;
  * ring * sectors + sector, rings from the centre outwards and the region
  * outside every circle last.  Rings inside the fuel circle take mat_in, the
  * others mat_out.  With 1, 0, 1 a pin cell has two regions (circle, then
- * moderator).  Cells without a pin stay one region. */
+ * moderator).  Cells without a pin stay one region.
+ *   layer_z       NULL (n_layers equal layers) or [n_layers + 1] layer planes
+ *                 rising from 0 to height: unequal layers (a local axial
+ *                 mesh); each plane must be a whole number of axial spacings
+ *                 (moc_generate_tracks returns MOC_ERR_UNSUPPORTED otherwise). */
 typedef struct {
     int32_t ncx, ncy;
     double pitch, fuel_radius, height;
@@ -95,6 +99,7 @@ typedef struct {
     const int32_t *mat_out;
     int32_t bc[6];
     int32_t fuel_rings, moderator_rings, sectors;
+    const double *layer_z;
 } moc_geometry_desc;
 
 /* Multigroup macroscopic cross sections (1/cm), host arrays:

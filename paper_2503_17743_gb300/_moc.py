@@ -40,7 +40,8 @@ class moc_geometry_desc(C.Structure):
     _fields_ = [("ncx", C.c_int32), ("ncy", C.c_int32), ("pitch", C.c_double),
                 ("fuel_radius", C.c_double), ("height", C.c_double), ("n_layers", C.c_int32),
                 ("has_pin", i32p), ("mat_in", i32p), ("mat_out", i32p), ("bc", C.c_int32 * 6),
-                ("fuel_rings", C.c_int32), ("moderator_rings", C.c_int32), ("sectors", C.c_int32)]
+                ("fuel_rings", C.c_int32), ("moderator_rings", C.c_int32), ("sectors", C.c_int32),
+                ("layer_z", f64p)]
 
 
 class moc_materials(C.Structure):
@@ -182,6 +183,8 @@ class Geometry:
         d.fuel_rings = int(getattr(prob, "fuel_rings", 1))
         d.moderator_rings = int(getattr(prob, "moderator_rings", 0))
         d.sectors = int(getattr(prob, "sectors", 1))
+        lz = getattr(prob, "layer_z", None)
+        d.layer_z = _ptr(arr(lz, np.float64), f64p) if lz is not None else f64p()
         m = moc_materials()
         m.num_materials, m.num_groups = prob.num_materials, prob.num_groups
         m.sigma_t = _ptr(arr(prob.sigma_t, np.float64), f64p)

@@ -43,7 +43,7 @@ struct moc_tracks {
     // device buffers
     DevBuf d_desc, d_zn, d_zf, d_zf64, d_reg2d, d_len2d, d_len2d64, d_segs, d_fsr_mat, d_order;
     DevBuf d_tpl_off, d_tpl_loff, d_tpl_lmin, d_tpl_lidx;
-    DevBuf d_dst, d_perm, d_win, d_chunk, d_hand, d_batch;
+    DevBuf d_dst, d_perm, d_win, d_chunk, d_hand, d_batch, d_lmap;
     DevBuf d_phi, d_qr, d_tally, d_vol, d_psi[2], d_fiss, d_fiss_old, d_partial, d_scal, d_counter;
     DevBuf d_sigt, d_sigt64, d_sigs64, d_nsf64, d_chi64, d_src64, d_inv_st64, d_siga64, d_inv_vol;
     double *h_scal = nullptr;  // pinned mirror of the device scalars
@@ -143,7 +143,9 @@ void fill_views(moc_tracks *h) {
     dl.Ph = h->L.Ph;
     dl.Nz = h->L.Nz;
     dl.cpl = h->L.cpl;
-    dl.NL = h->geom.nl;
+    dl.NL = h->L.nlv;
+    dl.NLr = h->geom.nl;
+    dl.lmap = (const int32_t *)h->d_lmap.p;
     dl.G = h->geom.G;
     dl.M = h->geom.M;
     dl.bc_zmin = h->geom.bc[FACE_ZMIN];
@@ -425,7 +427,7 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     if (L.Ph > 16) { moc_set_error("at most 32 polar angles"); return MOC_ERR_UNSUPPORTED; }
     // tally mode: a shared tile of every (2D segment, layer) row of one unit
     // when it fits
-    h->tile_cap = h->nb_max * geo.nl;
+    h->tile_cap = h->nb_max * L.nlv;
     if (prm->groups_per_lane < 0 || prm->groups_per_lane > 4 || prm->groups_per_lane == 3 ||
         (prm->groups_per_lane > 1 && h->precision == MOC_FP64)) {
         moc_set_error("groups_per_lane must be 0, 1, 2 or 4 (2 and 4 for FP32 sweeps only)");
@@ -448,14 +450,14 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
              sweep_smem_bytes(h->precision, 1, geo.M, G, h->gpl, h->tile_cap) > kWholeTile)) {
             int cb = 0;
             while (cb < h->nb_max &&
-                   sweep_smem_bytes(h->precision, 1, geo.M, G, h->gpl, (cb + 1) * geo.nl) <= kChunkTile)
+                   sweep_smem_bytes(h->precision, 1, geo.M, G, h->gpl, (cb + 1) * L.nlv) <= kChunkTile)
                 ++cb;
             if (prm->chunk_segments > 0) cb = std::min(cb, (int)prm->chunk_segments);
             if (cb >= h->nb_max) {
                 cb = 0;  // every unit fits whole
             } else if (cb >= 1) {
                 h->chunk_b = cb;
-                h->tile_cap = cb * geo.nl;
+                h->tile_cap = cb * L.nlv;
             } else {
                 mode = MOC_TALLY_GLOBAL;
             }
@@ -501,6 +503,7 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     std::vector<float> len2d(L.seg_len.begin(), L.seg_len.end());
     TRY(upload(h.get(), h->d_zn, L.zn), "upload");
     TRY(upload(h.get(), h->d_zf, L.zf), "upload");
+    if (!L.lmap.empty()) TRY(upload(h.get(), h->d_lmap, L.lmap), "upload");
     TRY(upload(h.get(), h->d_reg2d, reg2d), "upload");
     TRY(upload(h.get(), h->d_len2d, len2d), "upload");
     TRY(upload(h.get(), h->d_fsr_mat, geo.fsr_mat), "upload");
@@ -618,7 +621,7 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
                 ok = ok && tlmin[q] > -32768 && tlmin[q] + tnlay[q] < 32767;
                 if (h->chunk_b == 0)
                     ok = ok && tlmin[q] > -2000 && tlmin[q] + tnlay[q] < 2000 &&
-                         (int64_t)(L.desc[s].nb + 1) * geo.nl + 2000 < 32768;
+                         (int64_t)(L.desc[s].nb + 1) * L.nlv + 2000 < 32768;
             }
         }
         ok = ok && h->max_nseg < 65536;  // record windows hold the count in 16 bits
@@ -896,6 +899,7 @@ extern "C" int moc_state_create(const moc_tracks *t, const double *ext_source, m
     borrow(h->d_sigt, base->d_sigt); borrow(h->d_sigt64, base->d_sigt64); borrow(h->d_sigs64, base->d_sigs64);
     borrow(h->d_nsf64, base->d_nsf64); borrow(h->d_chi64, base->d_chi64);
     borrow(h->d_inv_st64, base->d_inv_st64); borrow(h->d_siga64, base->d_siga64);
+    borrow(h->d_lmap, base->d_lmap);
     // the solve state: its own
     TRY(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "stream");
     TRY(cudaMallocHost(&h->h_scal, SC_COUNT * sizeof(double)), "pinned scalars");
@@ -1229,7 +1233,7 @@ extern "C" int moc_get_stack_segments(moc_tracks *h, int32_t t, int32_t p, int64
     }
     TRY(cudaStreamSynchronize(h->stream), "copy");
     h->bytes -= d_offs.n + d_f.n + d_l.n;
-    const int NL = h->geom.nl;
+    const int NL = L.nlv, NLr = h->geom.nl;
     const bool zero = L.zf[d.zoff] == 0.0f && L.zn[d.zoff] == 0;
     int64_t q = 0;
     for (int kk = 0; kk < d.n_trk; ++kk) {
@@ -1239,12 +1243,11 @@ extern "C" int moc_get_stack_segments(moc_tracks *h, int32_t t, int32_t p, int64
         track_index[kk] = frame == 0 ? j : (int64_t)L.Nz - j - (zero ? 0 : 1);
         n_seg[kk] = (int32_t)(offs[k + 1] - offs[k]);
         for (int64_t a = offs[k]; a < offs[k + 1]; ++a, ++q) {
-            int32_t ff = f[a];
-            if (frame == 1) {
-                const int reg = ff / NL, Lr = ff % NL;
-                ff = reg * NL + (NL - 1 - Lr);
-            }
-            fsr[q] = ff;
+            // the device lists (region, sweep layer) of the upward frame; the
+            // mirrored frame flips the layer, then the geometry's layer
+            const int reg = f[a] / NL, Lv = f[a] % NL;
+            const int Lm = frame == 1 ? NL - 1 - Lv : Lv;
+            fsr[q] = reg * NLr + (L.lmap.empty() ? Lm : L.lmap[Lm]);
             length[q] = l[a];
         }
     }

@@ -27,7 +27,9 @@ struct DevLayout {
     const uint64_t *win;     // [n_gtrk] stored stacks: each track's record window, in perm order
     const int32_t *perm;     // [n_gtrk] per stack, its track indices by decreasing segment
                              // count (ties: class by class, then by index)
-    int32_t Nz, cpl, NL, G, M, Ph;
+    int32_t Nz, cpl, NL, G, M, Ph;  // NL: the sweep's (uniform) layers
+    int32_t NLr;             // the geometry's layers (FSR = region * NLr + layer)
+    const int32_t *lmap;     // the geometry's layer of each sweep layer, or null (the same)
     int32_t bc_zmin, bc_zmax;
     int32_t tally_bits;      // FP32 shared tally: fixed-point bits per unit bound (0: not used)
     int64_t n_slots;         // geometric tracks * 4 variants (bound of every link)
@@ -87,6 +89,12 @@ enum ScalarSlot {
 // layer, cpl * dz / cos) or a partial lattice interval times dz / cos.
 // `visit(b, layer, len)` is called for every segment in traversal order:
 // along the 2D track for sense 0, against it for sense 1.
+
+// FSR of (radial region, sweep layer L): unequal geometry layers are split
+// into uniform sweep layers, each mapped to the geometry layer holding it
+__device__ __forceinline__ int64_t fsr_of(const DevLayout &dl, int reg, int L) {
+    return (int64_t)reg * dl.NLr + (dl.lmap ? __ldg(dl.lmap + L) : L);
+}
 
 // A stored template piece: key (see tpl_key) and its length.
 template <typename real>

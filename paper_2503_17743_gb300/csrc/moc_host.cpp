@@ -198,13 +198,45 @@ int moc_build_layout(const moc_geometry &g, const moc_track_params &prm, Layout 
         err = "axial spacing out of range";
         return MOC_ERR_INVALID_ARG;
     }
-    if (Nz % g.nl) {
-        err = "layer height is not a whole number of axial spacings";
-        return MOC_ERR_UNSUPPORTED;
-    }
     L.Nz = (int)Nz;
-    L.cpl = (int)(Nz / g.nl);
     L.dz = g.H / (double)Nz;
+    L.lmap.clear();
+    if (g.layer_z.empty()) {
+        if (Nz % g.nl) {
+            err = "layer height is not a whole number of axial spacings";
+            return MOC_ERR_UNSUPPORTED;
+        }
+        L.cpl = (int)(Nz / g.nl);
+        L.nlv = g.nl;
+    } else {
+        // every plane on the axial lattice; the sweep's layers are the
+        // coarsest uniform grid that holds them all
+        std::vector<int64_t> P(g.nl + 1);
+        int64_t h = 0;
+        for (int l = 0; l <= g.nl; ++l) {
+            const double u = g.layer_z[l] / L.dz;
+            P[l] = (int64_t)std::nearbyint(u);
+            if (std::fabs(u - (double)P[l]) > 1e-9) {
+                err = "layer planes must lie on the axial lattice (whole numbers of axial spacings)";
+                return MOC_ERR_UNSUPPORTED;
+            }
+            if (l > 0) h = gcd64(h, P[l] - P[l - 1]);
+        }
+        if (P[0] != 0 || P[g.nl] != Nz || h < 1) {
+            err = "layer planes must rise from 0 to the height";
+            return MOC_ERR_UNSUPPORTED;
+        }
+        L.cpl = (int)h;
+        L.nlv = (int)(Nz / h);
+        if (L.nlv != g.nl) {
+            L.lmap.resize(L.nlv);
+            int l = 0;
+            for (int v = 0; v < L.nlv; ++v) {
+                while ((int64_t)v * h >= P[l + 1]) ++l;
+                L.lmap[v] = l;
+            }
+        }
+    }
     // azimuth pairs
     const int nq = L.nq, A = L.A, Ph = L.Ph;
     L.nx.resize(nq); L.ny.resize(nq); L.gg.resize(nq); L.Mcyc.resize(nq);
@@ -585,6 +617,17 @@ extern "C" int moc_create_geometry(const moc_geometry_desc *d, const moc_materia
         moc_set_error("geometry: bad lattice description (sizes, pitch, radius < pitch/2, arrays)");
         return MOC_ERR_INVALID_ARG;
     }
+    if (d->layer_z) {
+        for (int l = 0; l <= d->n_layers; ++l)
+            if (!std::isfinite(d->layer_z[l]) || (l > 0 && !(d->layer_z[l] > d->layer_z[l - 1]))) {
+                moc_set_error("geometry: layer_z must rise strictly");
+                return MOC_ERR_INVALID_ARG;
+            }
+        if (std::fabs(d->layer_z[0]) > 1e-12 || std::fabs(d->layer_z[d->n_layers] - d->height) > 1e-9 * d->height) {
+            moc_set_error("geometry: layer_z must run from 0 to the height");
+            return MOC_ERR_INVALID_ARG;
+        }
+    }
     if ((int64_t)d->ncx * d->ncy > (1 << 26) || d->n_layers > 65535) {
         moc_set_error("geometry: lattice too large");
         return MOC_ERR_UNSUPPORTED;
@@ -606,6 +649,7 @@ extern "C" int moc_create_geometry(const moc_geometry_desc *d, const moc_materia
     g->has_pin.assign(d->has_pin, d->has_pin + nc);
     g->mat_in.assign(d->mat_in, d->mat_in + nc * g->nl);
     g->mat_out.assign(d->mat_out, d->mat_out + nc * g->nl);
+    if (d->layer_z) g->layer_z.assign(d->layer_z, d->layer_z + g->nl + 1);
     for (int f = 0; f < 6; ++f) g->bc[f] = d->bc[f] ? 1 : 0;
     g->M = mt->num_materials;
     g->G = mt->num_groups;

@@ -25,6 +25,7 @@ struct moc_geometry {
     // angular sectors; a pin cell has (circles + 1) * sectors regions
     std::vector<double> ring_r2;
     int fuel_rings = 1, sectors = 1;
+    std::vector<double> layer_z;    // unequal layers: the nl + 1 planes (empty: equal layers)
     std::vector<int32_t> fsr_mat;   // material of each FSR
 };
 
@@ -72,6 +73,11 @@ struct Layout {
     int A = 0, P = 0, Ph = 0, nq = 0;
     double dz = 0;
     int Nz = 0, cpl = 0;
+    // the sweep's layers: uniform, cpl lattice cells each (the coarsest such
+    // grid that holds every plane of the geometry); lmap gives the
+    // geometry's layer of each (empty when they are the same layers)
+    int nlv = 0;
+    std::vector<int32_t> lmap;
     // azimuth pairs m = 0..nq-1
     std::vector<int64_t> nx, ny, gg, Mcyc;
     std::vector<double> phi, span, deff, lu;

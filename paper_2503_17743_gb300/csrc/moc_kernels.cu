@@ -203,14 +203,15 @@ __global__ void k_links(DevLayout dl, int64_t n_stacks, int32_t *dst) {
 
 template <typename real>
 struct VolVisit {
+    const DevLayout *dl;
     const int32_t *reg2d;
     int NL;
     double *vol;
     double c;
     __device__ void operator()(int b, int L, real len) {
         const int reg = __ldg(reg2d + b);
-        atomicAdd(vol + (size_t)reg * NL + L, c * (double)len);
-        atomicAdd(vol + (size_t)reg * NL + (NL - 1 - L), c * (double)len);
+        atomicAdd(vol + fsr_of(*dl, reg, L), c * (double)len);
+        atomicAdd(vol + fsr_of(*dl, reg, NL - 1 - L), c * (double)len);
     }
 };
 
@@ -219,7 +220,7 @@ __global__ void k_volumes(DevLayout dl, int64_t n_stacks, double *vol) {
     for (int64_t s = blockIdx.x; s < n_stacks; s += gridDim.x) {
         const StackDesc d = dl.desc[s];
         // each stored track carries two directions of equal weight, in two frames
-        VolVisit<real> v{dl.reg2d + d.seg2d_off, dl.NL, vol, 2.0 * d.W / (4.0 * MOC_PI)};
+        VolVisit<real> v{&dl, dl.reg2d + d.seg2d_off, dl.NL, vol, 2.0 * d.W / (4.0 * MOC_PI)};
         for (int k = threadIdx.x; k < d.n_trk; k += blockDim.x) walk_otf<real>(dl, d, d.i_lo + k, 0, v);
     }
 }

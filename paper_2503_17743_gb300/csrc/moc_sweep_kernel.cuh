@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                     const int reg = __ldg(reg2d + b);
                     for (int x = lane; x < NL * GP; x += 32) {
                         const int L = x / GP, qq = x - L * GP;
-                        const int f = reg * NL + L;
+                        const int64_t f = fsr_of(dl, reg, L);
                         const int e = (bb * NL + L) * GP + qq;
                         const int et = (bb * NL + L) * TS + qq;
                         real q = (real)0, sg = (real)0;
@@ -555,7 +555,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                     } else {
                         const int b = rU / NL, L = rU - b * NL, LD = NL - 1 - L;
                         const int reg = __ldg(reg2d + b);
-                        const size_t fU = (size_t)reg * NL + L, fD = (size_t)reg * NL + LD;
+                        const size_t fU = (size_t)fsr_of(dl, reg, L), fD = (size_t)fsr_of(dl, reg, LD);
                         const int mU = __ldg(dl.fsr_mat + fU), mD = __ldg(dl.fsr_mat + fD);
 #pragma unroll
                         for (int c = 0; c < GPL; ++c) {
@@ -766,7 +766,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                         if (qq >= gc) continue;
                         const int e = (bb * NL + L) * TS + qq;
                         const double v = kFixed ? (double)((float)tl_i[e] * s_inv[qq]) : (double)tl_s[e];
-                        if (v != 0.0) atomicAdd(tally_g + ((size_t)reg * NL + L) * G + g0 + qq, v);
+                        if (v != 0.0) atomicAdd(tally_g + (size_t)fsr_of(dl, reg, L) * G + g0 + qq, v);
                     }
                 }
                 if (tid < 32) s_bmax[tid] = 0u;  // next chunk's bound (read only before its tasks)

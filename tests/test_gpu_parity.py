@@ -332,3 +332,70 @@ def test_virtual_shards_sum_to_the_sweep(k, prec, rtol):
     # and the shards partition the work: each one alone misses the others' part
     assert all(np.abs(t).sum() < np.abs(full).sum() for t, _ in parts)
     tr.close()
+
+
+# --------------------------------------------------------------- unequal layers
+
+def _lat3z(seed=6):
+    """Unequal layers on the 0.5 cm axial lattice (0.5, 1.0, 1.5, 1.0 cm),
+    mixed faces; the sweep runs on 0.5 cm layers mapped to these four."""
+    p = synth.lattice(seed, n=3, G=3, height=4.0, n_layers=4, n_azim=8, n_polar=4,
+                      radial_spacing=0.15, axial_spacing=0.5, bc=(1, 0, 1, 1, 0, 1), n_gt=2,
+                      name="lat3z")
+    return p.with_tracks(layer_z=np.array([0.0, 0.5, 1.5, 3.0, 4.0]))
+
+
+def _merge_runs(fsr, ln):
+    """Consecutive pieces in one FSR as one segment (the sweep's layers split
+    a segment where the geometry's do not)."""
+    if len(fsr) == 0:
+        return fsr, ln
+    keep = np.concatenate([[True], fsr[1:] != fsr[:-1]])
+    idx = np.cumsum(keep) - 1
+    return fsr[keep], np.bincount(idx, weights=ln)
+
+
+UNEQUAL = {"lat3z": _lat3z, "lattice5_axial": lambda: synth.workload("lattice5_axial")}
+
+
+@pytest.mark.parametrize("name", list(UNEQUAL))
+def test_unequal_layers_segments_and_volumes(name):
+    p = UNEQUAL[name]()
+    o = oracle.Oracle(p, n_threads=NTH)
+    tr = Tracks(Geometry(p), track_params(p))
+    assert tr.info["n_fsr"] == o.n_fsr
+    np.testing.assert_allclose(tr.volumes(), o.volumes(), rtol=1e-6)
+    for t in range(0, o.n_tracks2d, max(1, o.n_tracks2d // 30)):
+        for pp in range(p.n_polar):
+            oi, on, of, ol = o.stack(t, pp)
+            gi, gn, gf, gl = tr.stack_segments(t, pp)
+            np.testing.assert_array_equal(gi, oi)
+            go = np.concatenate([[0], np.cumsum(gn)])
+            oo = np.concatenate([[0], np.cumsum(on)])
+            for k in range(len(oi)):
+                f, l = _merge_runs(gf[go[k]:go[k + 1]], gl[go[k]:go[k + 1]])
+                np.testing.assert_array_equal(f, of[oo[k]:oo[k + 1]], err_msg=f"t={t} p={pp} k={k}")
+                np.testing.assert_allclose(l, ol[oo[k]:oo[k + 1]], rtol=2e-6, atol=2e-6)
+    tr.close()
+
+
+@pytest.mark.parametrize("prec,ktol,ftol", [(MOC_FP64, 1e-11, 1e-10), (MOC_FP32, 1e-5, 1e-4)])
+@pytest.mark.parametrize("name", list(UNEQUAL))
+def test_unequal_layers_power_iterations(name, prec, ktol, ftol):
+    p = UNEQUAL[name]()
+    o = oracle.Oracle(p, n_threads=NTH)
+    tr = Tracks(Geometry(p), track_params(p, precision=prec))
+    o.reset()
+    ref = o.iterate(15)
+    tr.iterate(15)
+    phi, k = tr.flux()
+    assert abs(k - ref["k"]) < ktol, (k, ref["k"])
+    np.testing.assert_allclose(phi, o.flux(), rtol=ftol)
+    tr.close()
+
+
+def test_layer_planes_off_the_axial_lattice_rejected():
+    p = _lat3z().with_tracks(layer_z=np.array([0.0, 0.6, 1.5, 3.0, 4.0]))
+    from paper_2503_17743_gb300 import MocError
+    with pytest.raises(MocError):
+        Tracks(Geometry(p), track_params(p))
