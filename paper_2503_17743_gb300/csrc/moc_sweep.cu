@@ -23,6 +23,24 @@ const void *sweep_fn(int precision, int tally_smem, int chunk, int G, int gpl, i
     return sweep_kernel_f32_gpl1(tally_smem, chunk, batch, gl);
 }
 
+// The kernel's dynamic shared-memory limit is per function and shared by
+// every thread of the process: solves of different tile sizes launched from
+// several threads (the serving engine) would race on it.  So every caller
+// sets the same value, the device's opt-in maximum, and checks its own size.
+cudaError_t allow_dynamic_smem(const void *f, size_t smem) {
+    int dev = 0, cap = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (smem > (size_t)cap) return cudaErrorInvalidValue;
+    // the opt-in maximum less the kernel's static shared memory
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, cap - (int)fa.sharedSizeBytes);
+}
+
 }  // namespace
 
 // two groups per lane in FP32 (half the per-segment bookkeeping per
@@ -47,7 +65,7 @@ size_t sweep_smem_bytes(int precision, int tally_smem, int M, int G, int gpl, in
 cudaError_t sweep_occupancy(int precision, int tally_smem, int chunk, int G, int gpl, int block,
                             size_t smem, int *blocks_per_sm) {
     const void *f = sweep_fn(precision, tally_smem, chunk, G, gpl);
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(f, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, block, smem);
 }
@@ -58,7 +76,7 @@ cudaError_t launch_sweep(int precision, int tally_smem, int gpl, const DevLayout
                          const unsigned *bound_in, unsigned *bound_out, int grid, int block,
                          size_t smem, cudaStream_t s) {
     const void *f = sweep_fn(precision, tally_smem, tally_smem && dl.chunk_b > 0, dl.G, gpl);
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(f, smem);
     if (e != cudaSuccess) return e;
     DevLayout a0 = dl;
     DevState a1 = st;
@@ -80,7 +98,7 @@ cudaError_t launch_sweep_batch(int precision, int gpl, const DevLayout &dl, cons
                                const BatchItem *items, int32_t n, int grid, int block, size_t smem,
                                cudaStream_t s) {
     const void *f = sweep_fn(precision, 1, 0, dl.G, gpl, 1);
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(f, smem);
     if (e != cudaSuccess) return e;
     DevLayout a0 = dl;
     DevState a1 = st;

@@ -129,11 +129,13 @@ struct RowLoadS<float, 1> {
         asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(q[0]), "=f"(s[0]) : "r"(a));
     }
 };
+// (with two or more groups per lane a row keeps each pair of groups as
+// Qr_0 Qr_1 Sigma_0 Sigma_1, so that the pairs load as packed operands)
 template <>
 struct RowLoadS<float, 2> {
     static __device__ __forceinline__ void get(unsigned a, float (&q)[2], float (&s)[2]) {
         asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                     : "=f"(q[0]), "=f"(s[0]), "=f"(q[1]), "=f"(s[1])
+                     : "=f"(q[0]), "=f"(q[1]), "=f"(s[0]), "=f"(s[1])
                      : "r"(a));
     }
 };
@@ -141,13 +143,43 @@ template <>
 struct RowLoadS<float, 4> {
     static __device__ __forceinline__ void get(unsigned a, float (&q)[4], float (&s)[4]) {
         asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                     : "=f"(q[0]), "=f"(s[0]), "=f"(q[1]), "=f"(s[1])
+                     : "=f"(q[0]), "=f"(q[1]), "=f"(s[0]), "=f"(s[1])
                      : "r"(a));
         asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                     : "=f"(q[2]), "=f"(s[2]), "=f"(q[3]), "=f"(s[3])
+                     : "=f"(q[2]), "=f"(q[3]), "=f"(s[2]), "=f"(s[3])
                      : "r"(a + 16u));
     }
 };
+
+// Packed FP32 pairs (two groups of a lane) for the sm_100-family f32x2
+// instructions: one issue slot for two operations
+__device__ __forceinline__ uint64_t pk2(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(uint64_t r, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// (Qr_0, Qr_1) and (Sigma_0, Sigma_1) of one row as two packed pairs
+__device__ __forceinline__ void row_load_pairs(unsigned a, uint64_t &q, uint64_t &s) {
+    asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(q), "=l"(s) : "r"(a));
+}
 template <>
 struct RowLoadS<double, 1> {
     static __device__ __forceinline__ void get(unsigned a, double (&q)[1], double (&s)[1]) {
@@ -369,8 +401,14 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                             if (sizeof(real) == 4) sg = (real)((float)sg * kLog2e);
                             q = qr_g[(size_t)f * G + g0 + qq];
                         }
-                        rows[2 * e] = q;
-                        rows[2 * e + 1] = sg;
+                        if constexpr (GPL >= 2) {
+                            const int pe = 2 * (e - (qq & 1));  // the pair's Qr_0 Qr_1 Sigma_0 Sigma_1
+                            rows[pe + (qq & 1)] = q;
+                            rows[pe + 2 + (qq & 1)] = sg;
+                        } else {
+                            rows[2 * e] = q;
+                            rows[2 * e + 1] = sg;
+                        }
                         tl_s[et] = (real)0;
                         if (kFixed) bmax = fmaxf(bmax, fabsf((float)q));
                     }
@@ -585,6 +623,64 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                         for (int i = 0; i < 4; ++i) visit(rU[i], rD[i], len[i]);
                     } else {
                         int eU[4], eD[4], fU[4], fD[4];
+                        if constexpr (kFixed && GPL == 2) {
+                            // both groups of the lane as packed pairs: per frame and
+                            // piece one mul (-Sigma l), two ex2, then
+                            // d = psi - W S Qr, t = d (1 - e^{-tau}) (1 - x is exact in
+                            // FP32 for x >= 1/2), psi -= t in three paired operations
+                            uint64_t QU[4], SU[4], QD[4], SD[4];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                eU[i] = rU[i] * GP + qlo;
+                                eD[i] = rD[i] * GP + qlo;
+                                fU[i] = rU[i] * TS + qlo;
+                                fD[i] = rD[i] * TS + qlo;
+                                row_load_pairs(rows_sa + eU[i] * 8u, QU[i], SU[i]);
+                                row_load_pairs(rows_sa + eD[i] * 8u, QD[i], SD[i]);
+                            }
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const uint64_t nl = pk2(-(float)len[i], -(float)len[i]);
+                                float a0, a1, b0, b1;
+                                upk2(mul2(SU[i], nl), a0, a1);
+                                upk2(mul2(SD[i], nl), b0, b1);
+                                SU[i] = pk2(fast_exp2(a0), fast_exp2(a1));  // now e^{-Sigma_t l}
+                                SD[i] = pk2(fast_exp2(b0), fast_exp2(b1));
+                            }
+                            const uint64_t nws = pk2(-(float)WS[0], -(float)WS[1]), one = pk2(1.0f, 1.0f);
+                            uint64_t PU = pk2((float)psiU[0], (float)psiU[1]);
+                            uint64_t PD = pk2((float)psiD[0], (float)psiD[1]);
+                            int vU[4][2], vD[4][2];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const uint64_t TU = mul2(fma2(nws, QU[i], PU), sub2(one, SU[i]));
+                                const uint64_t TD = mul2(fma2(nws, QD[i], PD), sub2(one, SD[i]));
+                                PU = sub2(PU, TU);
+                                PD = sub2(PD, TD);
+                                float t0, t1;
+                                upk2(TU, t0, t1);
+                                vU[i][0] = __float2int_rn(t0);
+                                vU[i][1] = __float2int_rn(t1);
+                                upk2(TD, t0, t1);
+                                vD[i][0] = __float2int_rn(t0);
+                                vD[i][1] = __float2int_rn(t1);
+                            }
+                            float p0, p1;
+                            upk2(PU, p0, p1);
+                            psiU[0] = (real)p0;
+                            psiU[1] = (real)p1;
+                            upk2(PD, p0, p1);
+                            psiD[0] = (real)p0;
+                            psiD[1] = (real)p1;
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                shared_red_add(tl_sa + fU[i] * 4u, vU[i][0]);
+                                shared_red_add(tl_sa + (fU[i] + 1) * 4u, vU[i][1]);
+                                shared_red_add(tl_sa + fD[i] * 4u, vD[i][0]);
+                                shared_red_add(tl_sa + (fD[i] + 1) * 4u, vD[i][1]);
+                            }
+                            return;
+                        }
                         real qU[4][GPL], sU[4][GPL], qD[4][GPL], sD[4][GPL];
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
