@@ -87,3 +87,42 @@ def test_bad_track_params(lib):
         g.footprint(_moc.track_params(p.with_tracks(n_azim=6)))
     with pytest.raises(_moc.MocError):
         g.footprint(_moc.track_params(p.with_tracks(n_polar=3)))
+
+
+def test_unequal_layers_host_checks(lib):
+    """Layer planes: rising from 0 to the height (geometry), and on the axial
+    lattice (layout); the footprint query runs the layout on the host."""
+    p = synth.pin_cell(1, n_layers=3)
+    ok = p.with_tracks(layer_z=np.array([0.0, 0.5, 1.5, 2.0]))
+    g = _moc.Geometry(ok)
+    res, _ = g.footprint(_moc.track_params(ok))
+    assert res > 0
+    with pytest.raises(_moc.MocError) as e:
+        _moc.Geometry(p.with_tracks(layer_z=np.array([0.0, 1.5, 0.5, 2.0])))
+    assert e.value.code == _moc.MOC_ERR_INVALID_ARG
+    with pytest.raises(_moc.MocError):
+        _moc.Geometry(p.with_tracks(layer_z=np.array([0.0, 0.5, 1.5, 2.5])))  # not the height
+    off = p.with_tracks(layer_z=np.array([0.0, 0.6, 1.5, 2.0]))  # 0.6 is off the 0.5 cm lattice
+    with pytest.raises(_moc.MocError) as e:
+        _moc.Geometry(off).footprint(_moc.track_params(off))
+    assert e.value.code == _moc.MOC_ERR_UNSUPPORTED
+
+
+def test_ring_and_sector_counts_host(lib):
+    """Rings and sectors multiply a pin cell's regions; out-of-range counts
+    are rejected."""
+    p = synth.workload("lattice5_rings")
+    g = _moc.Geometry(p)
+    assert g._h
+    with pytest.raises(_moc.MocError):
+        _moc.Geometry(p.with_tracks(sectors=65))
+    with pytest.raises(_moc.MocError):
+        _moc.Geometry(p.with_tracks(fuel_rings=-1))
+
+
+def test_negative_chunk_segments_rejected(lib):
+    p = synth.pin_cell(1)
+    g = _moc.Geometry(p)
+    with pytest.raises(_moc.MocError) as e:
+        _moc.Tracks(g, _moc.track_params(p, chunk_segments=-1))
+    assert e.value.code == _moc.MOC_ERR_INVALID_ARG  # checked before any device work
