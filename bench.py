@@ -343,12 +343,19 @@ def run_ours(args):
     fp64 = None
     if rank == 0 and args.fp64_steps > 0:
         from paper_2503_17743_gb300 import MOC_FP64
-        t64 = Tracks(geom, track_params(prob, precision=MOC_FP64, device=local))
+        p64 = track_params(prob, precision=MOC_FP64, device=local)
+        sched64 = None
+        if not args.no_tune:
+            p64, t64_best, _ = autotune(geom, p64, iterations=3)
+            sched64 = {"tally_mode": int(p64.tally_mode), "preload_budget_bytes": int(p64.preload_budget_bytes),
+                       "tuned_ms_per_iteration": t64_best * 1e3}
+        t64 = Tracks(geom, p64)
         t64.iterate(3, use_graph=True)
         r64 = t64.iterate(args.fp64_steps, use_graph=True)
         fp64 = {"value": r64["integrations"] / r64["seconds"], "unit": UNIT,
                 "ms_per_step": r64["seconds"] / args.fp64_steps * 1e3, "steps": args.fp64_steps,
-                "dtype": "f64", "timing": "CUDA events around the graph launches of the steps"}
+                "dtype": "f64", "timing": "CUDA events around the graph launches of the steps",
+                "schedule": sched64}
         t64.close()
     serving = None
     if args.serving_requests > 0:

@@ -55,7 +55,7 @@ extern "C" {
 #define MOC_FP64 1
 
 /* FSR tally strategy of the sweep kernel */
-#define MOC_TALLY_AUTO 0   /* shared-memory tile when it fits, else global */
+#define MOC_TALLY_AUTO 0   /* FP32: shared-memory tile (radial chunks if needed); FP64: global */
 #define MOC_TALLY_SHARED 1 /* per-stack tile privatised in shared memory, flushed in FP64 */
 #define MOC_TALLY_GLOBAL 2 /* atomics straight into the FP64 global tally */
 

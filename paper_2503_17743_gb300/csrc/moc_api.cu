@@ -444,7 +444,9 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
             moc_set_error("chunk_segments must be >= 0");
             return MOC_ERR_INVALID_ARG;
         }
-        if (mode == MOC_TALLY_AUTO) mode = MOC_TALLY_SHARED;
+        // FP64 sweeps: a shared tile would add with compare-and-swap loops,
+        // which measured slower than the native FP64 adds of the global tally
+        if (mode == MOC_TALLY_AUTO) mode = h->precision == MOC_FP64 ? MOC_TALLY_GLOBAL : MOC_TALLY_SHARED;
         if (mode == MOC_TALLY_SHARED &&
             (prm->chunk_segments > 0 ||
              sweep_smem_bytes(h->precision, 1, geo.M, G, h->gpl, h->tile_cap) > kWholeTile)) {
