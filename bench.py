@@ -342,10 +342,10 @@ def run_ours(args):
     # the same workload with FP64 sweeps (parity precision), device-resident
     fp64 = None
     if rank == 0 and args.fp64_steps > 0:
-        from paper_2503_17743_gb300 import MOC_FP64
+        from paper_2503_17743_gb300 import MOC_FP64, autotune
         p64 = track_params(prob, precision=MOC_FP64, device=local)
         sched64 = None
-        if not args.no_tune:
+        if args.tune:
             p64, t64_best, _ = autotune(geom, p64, iterations=3)
             sched64 = {"tally_mode": int(p64.tally_mode), "preload_budget_bytes": int(p64.preload_budget_bytes),
                        "tuned_ms_per_iteration": t64_best * 1e3}

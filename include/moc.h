@@ -376,6 +376,19 @@ int moc_group_rates_static(moc_tracks *tracks, void *stream, double *rates);
  * Errors: MOC_ERR_INVALID_ARG for NULL, MOC_ERR_CUDA. */
 int moc_measure_ex2_rate(int32_t device, double *ex2_per_second, double *sm_count);
 
+/* The attenuation factor e^{-x} of Eq. 3 as the FP64 sweep computes it
+ * (table-driven: 2^{j/64} in hi + lo parts, degree-5 polynomial on
+ * |r| <= ln2/128; within 1 ulp for |x| < 700, 0 for x >= 700), evaluated on
+ * the device next to CUDA's exp(-x) for comparison.  Synchronous; allocates
+ * and frees 24 n bytes of device memory.
+ *   x      host [n]: arguments (optical lengths Sigma_t l)
+ *   n      0 <= n <= 2^28
+ *   y      host out [n]: the sweep's e^{-x}
+ *   y_lib  host out [n]: CUDA's exp(-x)
+ * Errors: MOC_ERR_INVALID_ARG for NULL pointers with n > 0 or n out of
+ * range, MOC_ERR_CUDA. */
+int moc_eval_attenuation_f64(int32_t device, const double *x, int64_t n, double *y, double *y_lib);
+
 /* Autotuner of the sweep's launch schedule: generates the tracks of `geom`
  * under every candidate schedule (energy groups per lane 1, 2, 4 for FP32
  * sweeps; shared-memory or global tally; preload budget: everything stored,

@@ -112,6 +112,7 @@ SIGNATURES = {
     "moc_sweep_units_from_source": (C.c_int, [C.c_void_p, f64p, C.c_int32, C.c_int32, f64p, f64p]),
     "moc_group_rates_static": (C.c_int, [C.c_void_p, C.c_void_p, f64p]),
     "moc_measure_ex2_rate": (C.c_int, [C.c_int32, f64p, f64p]),
+    "moc_eval_attenuation_f64": (C.c_int, [C.c_int32, f64p, C.c_int64, f64p, f64p]),
     "moc_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, f64p, C.c_int32,
                                f64p, i32p]),
     "moc_server_create": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -415,6 +416,15 @@ def measure_ex2_rate(device=0):
     rate, sms = C.c_double(), C.c_double()
     _check(load().moc_measure_ex2_rate(device, C.byref(rate), C.byref(sms)))
     return rate.value, int(sms.value)
+
+
+def eval_attenuation_f64(x, device=0):
+    """(the FP64 sweep's e^{-x}, CUDA's exp(-x)) for a float64 array x,
+    both evaluated on the device."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y, y_lib = np.empty_like(x), np.empty_like(x)
+    _check(load().moc_eval_attenuation_f64(device, _ptr(x, f64p), x.size, _ptr(y, f64p), _ptr(y_lib, f64p)))
+    return y, y_lib
 
 
 SERVER_STATS = ["queued", "resident", "admitted", "retired", "bytes_resident", "budget",

@@ -6,9 +6,22 @@
 // sustained ex2 rate of the whole device.
 #include <cuda_runtime.h>
 
+#include "moc_exp64.cuh"
 #include "moc_internal.h"
 
 namespace {
+
+// one element per thread: the sweep's FP64 attenuation factor and CUDA's exp
+__global__ void __launch_bounds__(256) k_eval_exp64(const double *x, int64_t n, double *y, double *y_lib) {
+    __shared__ double2 tab[64];
+    for (int i = threadIdx.x; i < 64; i += blockDim.x)
+        tab[i] = make_double2(moc_exp64::kTable[i].hi, moc_exp64::kTable[i].lo);
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    y[i] = moc_exp64::exp_neg(x[i], tab);
+    y_lib[i] = exp(-x[i]);
+}
 
 __global__ void __launch_bounds__(256) k_ex2_rate(int iters, float c, float *sink) {
     float x[8];
@@ -63,5 +76,29 @@ extern "C" int moc_measure_ex2_rate(int32_t device, double *ex2_per_second, doub
     }
     *ex2_per_second = (double)blocks * threads * iters * 8.0 / (ms * 1e-3);
     if (sm_count) *sm_count = sms;
+    return MOC_OK;
+}
+
+extern "C" int moc_eval_attenuation_f64(int32_t device, const double *x, int64_t n, double *y,
+                                        double *y_lib) {
+    if (n < 0 || (n > 0 && (!x || !y || !y_lib))) { moc_set_error("NULL argument or n < 0"); return MOC_ERR_INVALID_ARG; }
+    if (n == 0) return MOC_OK;
+    if (n > ((int64_t)1 << 28)) { moc_set_error("n above 2^28"); return MOC_ERR_INVALID_ARG; }
+    if (cudaSetDevice(device) != cudaSuccess) { moc_set_error("cudaSetDevice failed"); return MOC_ERR_CUDA; }
+    double *d = nullptr;
+    const size_t bytes = (size_t)n * sizeof(double);
+    cudaError_t e = cudaMalloc(&d, 3 * bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(d, x, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_eval_exp64<<<(unsigned)((n + 255) / 256), 256>>>(d, n, d + n, d + 2 * n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(y, d + n, bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(y_lib, d + 2 * n, bytes, cudaMemcpyDeviceToHost);
+    if (d) cudaFree(d);
+    if (e != cudaSuccess) {
+        moc_set_error(std::string("attenuation probe: ") + cudaGetErrorString(e));
+        return MOC_ERR_CUDA;
+    }
     return MOC_OK;
 }

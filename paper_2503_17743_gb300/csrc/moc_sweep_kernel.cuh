@@ -36,6 +36,7 @@
 #include <type_traits>
 
 #include "moc_device.cuh"
+#include "moc_exp64.cuh"
 #include "moc_kernels.h"
 
 namespace {
@@ -43,16 +44,17 @@ namespace {
 constexpr float kLog2e = 1.4426950408889634f;
 
 // e^{-Sigma_t l} from x = Sigma_t l: FP32 on the MUFU pipe (Sigma_t pre-scaled
-// by log2 e, the negation folds into the multiply), FP64 exp
+// by log2 e, the negation folds into the multiply), FP64 by the table-driven
+// method of moc_exp64.cuh (tab: its table in shared memory)
 template <typename real>
-__device__ __forceinline__ real attenuation(real x);
+__device__ __forceinline__ real attenuation(real x, const double2 *tab);
 template <>
-__device__ __forceinline__ float attenuation<float>(float x) {
+__device__ __forceinline__ float attenuation<float>(float x, const double2 *) {
     return fast_exp2(-x);
 }
 template <>
-__device__ __forceinline__ double attenuation<double>(double x) {
-    return exp(-x);
+__device__ __forceinline__ double attenuation<double>(double x, const double2 *tab) {
+    return moc_exp64::exp_neg(x, tab);
 }
 
 // per polar stack of the work unit, cached in shared memory
@@ -248,6 +250,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
     __shared__ unsigned s_hmax[32];  // max |psi| handed to the next radial chunk (float bits)
     __shared__ float s_wmax;
     __shared__ BatchItem s_item;     // BATCH: the solve of the current unit
+    __shared__ double2 s_exp[sizeof(real) == 8 ? 64 : 1];  // FP64: 2^{j/64} as hi, lo
     constexpr bool kFixed = sizeof(real) == 4;  // FP32 sweeps tally in fixed point
     const int G = dl.G, NL = dl.NL, M = dl.M, Ph = dl.Ph, cpl = dl.cpl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -280,6 +283,8 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
     for (int c = 0; c < GPL; ++c) pmax[c] = 0.0f;
     if (tid < 32) s_pmax[tid] = 0u;
     if (tid < 32) s_hmax[tid] = 0u;
+    if constexpr (sizeof(real) == 8)
+        for (int i = tid; i < 64; i += blockDim.x) s_exp[i] = make_double2(moc_exp64::kTable[i].hi, moc_exp64::kTable[i].lo);
     // lanes with the same groups (one per slot) fold their maxima into s_pmax
     auto fold_pmax = [&](int gc_) {
 #pragma unroll
@@ -568,8 +573,8 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                         for (int c = 0; c < GPL; ++c) {
                             // Eq. 3 on W S psi: d = W S (psi_in - Qr),
                             // W S (psi_in - psi_out) = d (1 - e^{-Sigma_t l})
-                            const real xU = attenuation<real>(sU[c] * len);
-                            const real xD = attenuation<real>(sD[c] * len);
+                            const real xU = attenuation<real>(sU[c] * len, s_exp);
+                            const real xD = attenuation<real>(sD[c] * len, s_exp);
                             const real dU = fma(-WS[c], qU[c], psiU[c]), dD = fma(-WS[c], qD[c], psiD[c]);
                             tU[c] = fma(-dU, xU, dU);
                             tD[c] = fma(-dD, xD, dD);
@@ -600,8 +605,8 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                             const int qq = qlo + c;
                             const real qU = qq < gc ? qr_g[fU * G + g0 + qq] : (real)0;
                             const real qD = qq < gc ? qr_g[fD * G + g0 + qq] : (real)0;
-                            const real xU = attenuation<real>(sig[mU * GP + qq] * len);
-                            const real xD = attenuation<real>(sig[mD * GP + qq] * len);
+                            const real xU = attenuation<real>(sig[mU * GP + qq] * len, s_exp);
+                            const real xD = attenuation<real>(sig[mD * GP + qq] * len, s_exp);
                             const real dU = fma(-WS[c], qU, psiU[c]), dD = fma(-WS[c], qD, psiD[c]);
                             tU[c] = fma(-dU, xU, dU);
                             tD[c] = fma(-dD, xD, dD);
@@ -696,8 +701,8 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                         for (int i = 0; i < 4; ++i)
 #pragma unroll
                             for (int c = 0; c < GPL; ++c) {
-                                sU[i][c] = attenuation<real>(sU[i][c] * len[i]);  // now e^{-Sigma_t l}
-                                sD[i][c] = attenuation<real>(sD[i][c] * len[i]);
+                                sU[i][c] = attenuation<real>(sU[i][c] * len[i], s_exp);  // now e^{-Sigma_t l}
+                                sD[i][c] = attenuation<real>(sD[i][c] * len[i], s_exp);
                             }
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
