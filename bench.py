@@ -129,7 +129,7 @@ def measured_hbm_gbs():
 
 def sweep_source_hash():
     h = hashlib.sha256()
-    for f in ("moc_sweep_kernel.cuh", "moc_device.cuh"):
+    for f in ("moc_sweep_kernel.cuh", "moc_device.cuh", "moc_exp64.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2503_17743_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
@@ -381,11 +381,12 @@ def run_profile_driver(args):
     outer iterations, then 2 more (the 4th and 5th sweeps are the ones a
     capture with -s 3 selects)."""
     import synth
-    from paper_2503_17743_gb300 import Geometry, Tracks, track_params
+    from paper_2503_17743_gb300 import MOC_FP32, MOC_FP64, Geometry, Tracks, track_params
     prob = synth.workload(args.workload)
     tr = Tracks(Geometry(prob), track_params(prob, preload_budget_bytes=args.budget,
                                              groups_per_lane=args.gpl,
-                                             chunk_segments=args.chunk))
+                                             chunk_segments=args.chunk,
+                                             precision=MOC_FP64 if args.fp64 else MOC_FP32))
     tr.iterate(3, use_graph=False)
     r = tr.iterate(2, use_graph=False)
     print(json.dumps({"info": tr.info, "ms_per_iteration": r["seconds"] * 1e3 / 2}), flush=True)
@@ -525,6 +526,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--budget", type=int, default=-1, help="preload budget bytes (--profile)")
     ap.add_argument("--gpl", type=int, default=0, help="groups per lane (--profile)")
+    ap.add_argument("--fp64", action="store_true", help="FP64 sweeps (--profile)")
     ap.add_argument("--chunk", type=int, default=0,
                     help="2D segments per radial chunk, 0 = automatic (--profile)")
     args = ap.parse_args()
