@@ -389,6 +389,18 @@ int moc_measure_ex2_rate(int32_t device, double *ex2_per_second, double *sm_coun
  * range, MOC_ERR_CUDA. */
 int moc_eval_attenuation_f64(int32_t device, const double *x, int64_t n, double *y, double *y_lib);
 
+/* The attenuation factor e^{-tau} of Eq. 3 as the FP32 sweep computes it:
+ * 2^{-b} with b = tau log2 e (the sweep pre-scales Sigma_t by log2 e) on the
+ * hardware ex2.approx.ftz.f32; the sweep's escape fraction is 1 minus this
+ * value.  Evaluated on the device.  Synchronous; allocates and frees 8 n
+ * bytes of device memory.
+ *   b  host [n]: tau log2 e, >= 0
+ *   n  0 <= n <= 2^28
+ *   e  host out [n]: 2^{-b}
+ * Errors: MOC_ERR_INVALID_ARG for NULL pointers with n > 0 or n out of
+ * range, MOC_ERR_CUDA. */
+int moc_eval_attenuation_f32(int32_t device, const float *b, int64_t n, float *e);
+
 /* Autotuner of the sweep's launch schedule: generates the tracks of `geom`
  * under every candidate schedule (energy groups per lane 1, 2, 4 for FP32
  * sweeps; shared-memory or global tally; preload budget: everything stored,

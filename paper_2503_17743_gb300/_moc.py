@@ -113,6 +113,7 @@ SIGNATURES = {
     "moc_group_rates_static": (C.c_int, [C.c_void_p, C.c_void_p, f64p]),
     "moc_measure_ex2_rate": (C.c_int, [C.c_int32, f64p, f64p]),
     "moc_eval_attenuation_f64": (C.c_int, [C.c_int32, f64p, C.c_int64, f64p, f64p]),
+    "moc_eval_attenuation_f32": (C.c_int, [C.c_int32, f32p, C.c_int64, f32p]),
     "moc_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, f64p, C.c_int32,
                                f64p, i32p]),
     "moc_server_create": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -425,6 +426,15 @@ def eval_attenuation_f64(x, device=0):
     y, y_lib = np.empty_like(x), np.empty_like(x)
     _check(load().moc_eval_attenuation_f64(device, _ptr(x, f64p), x.size, _ptr(y, f64p), _ptr(y_lib, f64p)))
     return y, y_lib
+
+
+def eval_attenuation_f32(b, device=0):
+    """The FP32 sweep's e^{-tau} = 2^{-b} for a float32 array b = tau log2 e,
+    evaluated on the device."""
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    e = np.empty_like(b)
+    _check(load().moc_eval_attenuation_f32(device, _ptr(b, f32p), b.size, _ptr(e, f32p)))
+    return e
 
 
 SERVER_STATS = ["queued", "resident", "admitted", "retired", "bytes_resident", "budget",

@@ -6,6 +6,7 @@
 // sustained ex2 rate of the whole device.
 #include <cuda_runtime.h>
 
+#include "moc_device.cuh"
 #include "moc_exp64.cuh"
 #include "moc_internal.h"
 
@@ -39,6 +40,12 @@ __global__ void __launch_bounds__(256) k_ex2_rate(int iters, float c, float *sin
 #pragma unroll
     for (int j = 0; j < 8; ++j) s += x[j];
     if (s == -1.0f) sink[blockIdx.x] = s;  // never true; keeps the chains alive
+}
+
+// the FP32 sweep's attenuation factor e^{-tau} = 2^{-b}, b = tau log2 e
+__global__ void __launch_bounds__(256) k_eval_exp32(const float *b, int64_t n, float *e) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) e[i] = fast_exp2(-b[i]);
 }
 
 }  // namespace
@@ -98,6 +105,28 @@ extern "C" int moc_eval_attenuation_f64(int32_t device, const double *x, int64_t
     if (d) cudaFree(d);
     if (e != cudaSuccess) {
         moc_set_error(std::string("attenuation probe: ") + cudaGetErrorString(e));
+        return MOC_ERR_CUDA;
+    }
+    return MOC_OK;
+}
+
+extern "C" int moc_eval_attenuation_f32(int32_t device, const float *b, int64_t n, float *e) {
+    if (n < 0 || (n > 0 && (!b || !e))) { moc_set_error("NULL argument or n < 0"); return MOC_ERR_INVALID_ARG; }
+    if (n == 0) return MOC_OK;
+    if (n > ((int64_t)1 << 28)) { moc_set_error("n above 2^28"); return MOC_ERR_INVALID_ARG; }
+    if (cudaSetDevice(device) != cudaSuccess) { moc_set_error("cudaSetDevice failed"); return MOC_ERR_CUDA; }
+    float *d = nullptr;
+    const size_t bytes = (size_t)n * sizeof(float);
+    cudaError_t err = cudaMalloc(&d, 2 * bytes);
+    if (err == cudaSuccess) err = cudaMemcpy(d, b, bytes, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) {
+        k_eval_exp32<<<(unsigned)((n + 255) / 256), 256>>>(d, n, d + n);
+        err = cudaGetLastError();
+    }
+    if (err == cudaSuccess) err = cudaMemcpy(e, d + n, bytes, cudaMemcpyDeviceToHost);
+    if (d) cudaFree(d);
+    if (err != cudaSuccess) {
+        moc_set_error(std::string("attenuation probe: ") + cudaGetErrorString(err));
         return MOC_ERR_CUDA;
     }
     return MOC_OK;
