@@ -43,6 +43,11 @@ OPS_PER_INTEGRATION = 7
 # (31.4 ex2 per SM per clock, measured by moc_measure_ex2_rate) would allow
 # 9.9e12 integrations/s, so it is not the binding unit.
 SMS, LANES_PER_CLK, SM_MAX_MHZ = 152, 128, 2070.0
+# FP64 sweeps are bound by the FP64 pipe: 2 lane operations per SM per clock
+# (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on peak_sustained).  Each
+# integration takes 15 FP64 operations as written: Sigma_t l (1), the
+# table-driven e^{-x} (11), d = psi - W S Qr, d (1 - e), psi -= (3)
+FP64_LANES_PER_CLK, FP64_OPS_PER_INTEGRATION = 2, 15
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -352,10 +357,18 @@ def run_ours(args):
         t64 = Tracks(geom, p64)
         t64.iterate(3, use_graph=True)
         r64 = t64.iterate(args.fp64_steps, use_graph=True)
-        fp64 = {"value": r64["integrations"] / r64["seconds"], "unit": UNIT,
+        rate64 = r64["integrations"] / r64["seconds"]
+        peak64 = SMS * FP64_LANES_PER_CLK * SM_MAX_MHZ * 1e6 / 1e12
+        fp64 = {"value": rate64, "unit": UNIT,
                 "ms_per_step": r64["seconds"] / args.fp64_steps * 1e3, "steps": args.fp64_steps,
                 "dtype": "f64", "timing": "CUDA events around the graph launches of the steps",
-                "schedule": sched64}
+                "schedule": sched64,
+                "roofline": {"bound": "alu", "achieved": rate64 * FP64_OPS_PER_INTEGRATION / 1e12,
+                             "peak": peak64, "unit": "TFLOP/s",
+                             "frac": rate64 * FP64_OPS_PER_INTEGRATION / 1e12 / peak64,
+                             "peak_basis": "derived: FP64 pipe 2 lane operations per SM per clock x "
+                                           "152 SMs x 2070 MHz; 15 FP64 operations per integration "
+                                           "(whole step timed: the sweep is most of it)"}}
         t64.close()
     serving = None
     if args.serving_requests > 0:
