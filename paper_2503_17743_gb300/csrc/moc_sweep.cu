@@ -58,7 +58,9 @@ size_t sweep_smem_bytes(int precision, int tally_smem, int M, int G, int gpl, in
     const size_t gp = (size_t)lanes_for_groups(G, gpl) * gpl;
     size_t b = ((size_t)M * gp * rs + 15) & ~(size_t)15;
     if (tally_smem)  // (Qr, Sigma_t) rows + tally rows
-        b += (size_t)cap * gp * rs * 2 + (size_t)cap * tally_stride((int)(gp / gpl), gpl) * rs;
+        b += (size_t)cap * gp * rs * 2 +
+             (precision == MOC_FP64 ? (size_t)cap * tally_stride((int)(gp / gpl), gpl)
+                                    : (size_t)tally_rows(cap, (int)(gp / gpl), gpl) * gp) * rs;
     return b;
 }
 

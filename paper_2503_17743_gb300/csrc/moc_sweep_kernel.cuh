@@ -226,8 +226,17 @@ __host__ __device__ constexpr int sweep_block(bool fp32, int GPL) {
 }
 constexpr int kMaxSweepBlock = 320;
 
-// words per shared tally row
+// words per shared tally row (FP64 tally tile: row-major, [row][TS])
 __host__ __device__ constexpr int tally_stride(int GL, int GPL) { return GL * GPL + (GPL > 1 ? 1 : 0); }
+
+// FP32 fixed-point tally tile: group-major, [group][RS] with RS >= cap rows
+// and RS GPL = 32 / GL (mod 32), so that the GL lanes of a slot, whose
+// groups are GPL apart, land 32 / GL banks apart: two slots of a warp then
+// meet in a bank only when their rows agree modulo 32 / GL (row-major rows
+// of GL GPL words collide whenever their windows overlap)
+__host__ __device__ constexpr int tally_rows(int cap, int GL, int GPL) {
+    return cap + ((((32 / (GL * GPL)) % (32 / GPL)) - cap % (32 / GPL)) + (32 / GPL)) % (32 / GPL);
+}
 
 // BATCH: one launch sweeps several solves of one layout (their states in
 // items[n_items]); work index w is unit order[w / n_items] of solve
@@ -256,10 +265,15 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int j = lane / GL;         // slot: track of the warp task
     const int ql = lane & (GL - 1);  // lane of the slot: groups ql * GPL + c, c < GPL
-    // shared layout: sig [M][GP] | rows [cap][GP][2] (Qr, Sigma_t) | tally [cap][TS]; with
-    // several groups per lane the tally rows are padded by one word so that
-    // the rows of the warp's eight or more slots spread over the banks
+    // shared layout: sig [M][GP] | rows [cap][GP][2] (Qr, Sigma_t) | tally:
+    // FP32 fixed point [GP][RS] (tally_rows), FP64 [cap][TS] with rows padded by
+    // one word when a lane holds several groups
     constexpr int TS = tally_stride(GL, GPL);
+    // tally word of (tile row, group q): FP32 group-major, FP64 row-major;
+    // CS = words from group q to q + 1 of the same row
+    const int RS = kFixed ? tally_rows(cap, GL, GPL) : 0;
+    const int CS = kFixed ? RS : 1;
+    auto tix = [&](int row, int q) { return kFixed ? q * RS + row : row * TS + q; };
     if (!BATCH && st.scal[SC_CONV] != 0.0) return;  // converged: later iterations are no-ops
     real *sig = reinterpret_cast<real *>(smem);
     size_t off = ((size_t)M * GP * sizeof(real) + 15) & ~(size_t)15;
@@ -398,7 +412,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                         const int L = x / GP, qq = x - L * GP;
                         const int64_t f = fsr_of(dl, reg, L);
                         const int e = (bb * NL + L) * GP + qq;
-                        const int et = (bb * NL + L) * TS + qq;
+                        const int et = tix(bb * NL + L, qq);
                         real q = (real)0, sg = (real)0;
                         if (qq < gc) {
                             const int m = __ldg(dl.fsr_mat + f);
@@ -565,7 +579,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                     real tU[GPL], tD[GPL];
                     if (SMEM) {
                         const int eU = rU * GP + qlo, eD = rD * GP + qlo;
-                        const int tU_ = rU * TS + qlo, tD_ = rD * TS + qlo;
+                        const int tU_ = tix(rU, qlo), tD_ = tix(rD, qlo);
                         real qU[GPL], sU[GPL], qD[GPL], sD[GPL];
                         RowLoadS<real, GPL>::get(rows_sa + eU * (unsigned)(2 * sizeof(real)), qU, sU);
                         RowLoadS<real, GPL>::get(rows_sa + eD * (unsigned)(2 * sizeof(real)), qD, sD);
@@ -586,9 +600,9 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                             // integer in the low mantissa bits (|t scl| < 2^22)
 #pragma unroll
                             for (int c = 0; c < GPL; ++c) {
-                                shared_red_add(tl_sa + (tU_ + c) * 4u,
+                                shared_red_add(tl_sa + (tU_ + c * CS) * 4u,
                                                __float2int_rn((float)tU[c]));
-                                shared_red_add(tl_sa + (tD_ + c) * 4u,
+                                shared_red_add(tl_sa + (tD_ + c * CS) * 4u,
                                                __float2int_rn((float)tD[c]));
                             }
                         } else {
@@ -638,8 +652,8 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                             for (int i = 0; i < 4; ++i) {
                                 eU[i] = rU[i] * GP + qlo;
                                 eD[i] = rD[i] * GP + qlo;
-                                fU[i] = rU[i] * TS + qlo;
-                                fD[i] = rD[i] * TS + qlo;
+                                fU[i] = tix(rU[i], qlo);
+                                fD[i] = tix(rD[i], qlo);
                                 row_load_pairs(rows_sa + eU[i] * 8u, QU[i], SU[i]);
                                 row_load_pairs(rows_sa + eD[i] * 8u, QD[i], SD[i]);
                             }
@@ -680,9 +694,9 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
 #pragma unroll
                             for (int i = 0; i < 4; ++i) {
                                 shared_red_add(tl_sa + fU[i] * 4u, vU[i][0]);
-                                shared_red_add(tl_sa + (fU[i] + 1) * 4u, vU[i][1]);
+                                shared_red_add(tl_sa + (fU[i] + CS) * 4u, vU[i][1]);
                                 shared_red_add(tl_sa + fD[i] * 4u, vD[i][0]);
-                                shared_red_add(tl_sa + (fD[i] + 1) * 4u, vD[i][1]);
+                                shared_red_add(tl_sa + (fD[i] + CS) * 4u, vD[i][1]);
                             }
                             return;
                         }
@@ -691,8 +705,8 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                         for (int i = 0; i < 4; ++i) {
                             eU[i] = rU[i] * GP + qlo;
                             eD[i] = rD[i] * GP + qlo;
-                            fU[i] = rU[i] * TS + qlo;
-                            fD[i] = rD[i] * TS + qlo;
+                            fU[i] = tix(rU[i], qlo);
+                            fD[i] = tix(rD[i], qlo);
                             RowLoadS<real, GPL>::get(rows_sa + eU[i] * (unsigned)(2 * sizeof(real)), qU[i], sU[i]);
                             RowLoadS<real, GPL>::get(rows_sa + eD[i] * (unsigned)(2 * sizeof(real)), qD[i], sD[i]);
                         }
@@ -719,9 +733,9 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                             if constexpr (kFixed) {
 #pragma unroll
                                 for (int c = 0; c < GPL; ++c) {
-                                    shared_red_add(tl_sa + (fU[i] + c) * 4u,
+                                    shared_red_add(tl_sa + (fU[i] + c * CS) * 4u,
                                                    __float2int_rn((float)tU[i][c]));
-                                    shared_red_add(tl_sa + (fD[i] + c) * 4u,
+                                    shared_red_add(tl_sa + (fD[i] + c * CS) * 4u,
                                                    __float2int_rn((float)tD[i][c]));
                                 }
                             } else {
@@ -865,7 +879,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                     for (int x = lane; x < NL * GP; x += 32) {
                         const int L = x / GP, qq = x - L * GP;
                         if (qq >= gc) continue;
-                        const int e = (bb * NL + L) * TS + qq;
+                        const int e = tix(bb * NL + L, qq);
                         const double v = kFixed ? (double)((float)tl_i[e] * s_inv[qq]) : (double)tl_s[e];
                         if (v != 0.0) atomicAdd(tally_g + (size_t)fsr_of(dl, reg, L) * G + g0 + qq, v);
                     }
