@@ -449,10 +449,10 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
         if (mode == MOC_TALLY_AUTO) mode = h->precision == MOC_FP64 ? MOC_TALLY_GLOBAL : MOC_TALLY_SHARED;
         if (mode == MOC_TALLY_SHARED &&
             (prm->chunk_segments > 0 ||
-             sweep_smem_bytes(h->precision, 1, geo.M, G, h->gpl, h->tile_cap) > kWholeTile)) {
+             sweep_smem_bytes(h->precision, 1, 0, geo.M, G, h->gpl, h->tile_cap) > kWholeTile)) {
             int cb = 0;
             while (cb < h->nb_max &&
-                   sweep_smem_bytes(h->precision, 1, geo.M, G, h->gpl, (cb + 1) * L.nlv) <= kChunkTile)
+                   sweep_smem_bytes(h->precision, 1, 1, geo.M, G, h->gpl, (cb + 1) * L.nlv) <= kChunkTile)
                 ++cb;
             if (prm->chunk_segments > 0) cb = std::min(cb, (int)prm->chunk_segments);
             if (cb >= h->nb_max) {
@@ -792,7 +792,7 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     TRY(upload(h.get(), h->d_order, h->order), "upload");
     fill_views(h.get());
     // sweep launch shape (tally mode chosen above)
-    h->smem = sweep_smem_bytes(h->precision, h->tally_smem, geo.M, G, h->gpl, h->tile_cap);
+    h->smem = sweep_smem_bytes(h->precision, h->tally_smem, h->chunk_b > 0, geo.M, G, h->gpl, h->tile_cap);
     {
         const int bmax = sweep_block_threads(h->precision, h->gpl);
         h->block = prm->block_threads > 0 ? std::max(32, std::min(prm->block_threads, bmax) / 32 * 32) : bmax;

@@ -31,7 +31,7 @@ int sweep_default_gpl(int precision, int G);
 int sweep_lanes_per_track(int G, int gpl);
 // threads per sweep block the kernel is compiled for (its launch bound)
 int sweep_block_threads(int precision, int gpl);
-size_t sweep_smem_bytes(int precision, int tally_smem, int M, int G, int gpl, int cap);
+size_t sweep_smem_bytes(int precision, int tally_smem, int chunk, int M, int G, int gpl, int cap);
 // The state of one solve of a batched sweep (pointers into device memory)
 struct BatchItem {
     const void *qr;             // Q / Sigma_t, real

@@ -53,14 +53,14 @@ int sweep_lanes_per_track(int G, int gpl) { return lanes_for_groups(G, gpl); }
 
 int sweep_block_threads(int precision, int gpl) { return sweep_block(precision != MOC_FP64, gpl); }
 
-size_t sweep_smem_bytes(int precision, int tally_smem, int M, int G, int gpl, int cap) {
+size_t sweep_smem_bytes(int precision, int tally_smem, int chunk, int M, int G, int gpl, int cap) {
     const size_t rs = precision == MOC_FP64 ? 8 : 4;
     const size_t gp = (size_t)lanes_for_groups(G, gpl) * gpl;
     size_t b = ((size_t)M * gp * rs + 15) & ~(size_t)15;
     if (tally_smem)  // (Qr, Sigma_t) rows + tally rows
         b += (size_t)cap * gp * rs * 2 +
-             (precision == MOC_FP64 ? (size_t)cap * tally_stride((int)(gp / gpl), gpl)
-                                    : (size_t)tally_rows(cap, (int)(gp / gpl), gpl) * gp) * rs;
+             (precision == MOC_FP64 || chunk ? (size_t)cap * tally_stride((int)(gp / gpl), gpl)
+                                             : (size_t)tally_rows(cap, (int)(gp / gpl), gpl) * gp) * rs;
     return b;
 }
 

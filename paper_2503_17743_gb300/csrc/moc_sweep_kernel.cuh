@@ -229,7 +229,8 @@ constexpr int kMaxSweepBlock = 320;
 // words per shared tally row (FP64 tally tile: row-major, [row][TS])
 __host__ __device__ constexpr int tally_stride(int GL, int GPL) { return GL * GPL + (GPL > 1 ? 1 : 0); }
 
-// FP32 fixed-point tally tile: group-major, [group][RS] with RS >= cap rows
+// FP32 fixed-point tally tile of units swept whole: group-major, [group][RS]
+// with RS >= cap rows
 // and RS GPL = 32 / GL (mod 32), so that the GL lanes of a slot, whose
 // groups are GPL apart, land 32 / GL banks apart: two slots of a warp then
 // meet in a bank only when their rows agree modulo 32 / GL (row-major rows
@@ -266,14 +267,17 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
     const int j = lane / GL;         // slot: track of the warp task
     const int ql = lane & (GL - 1);  // lane of the slot: groups ql * GPL + c, c < GPL
     // shared layout: sig [M][GP] | rows [cap][GP][2] (Qr, Sigma_t) | tally:
-    // FP32 fixed point [GP][RS] (tally_rows), FP64 [cap][TS] with rows padded by
-    // one word when a lane holds several groups
+    // [GP][RS] (tally_rows) or [cap][TS] with rows padded by one word when a
+    // lane holds several groups
     constexpr int TS = tally_stride(GL, GPL);
-    // tally word of (tile row, group q): FP32 group-major, FP64 row-major;
+    // tally word of (tile row, group q): group-major for the FP32 fixed-point
+    // tile of units swept whole, row-major otherwise (FP64; and radial
+    // chunks, whose kernel is short of registers for the stride);
     // CS = words from group q to q + 1 of the same row
-    const int RS = kFixed ? tally_rows(cap, GL, GPL) : 0;
-    const int CS = kFixed ? RS : 1;
-    auto tix = [&](int row, int q) { return kFixed ? q * RS + row : row * TS + q; };
+    constexpr bool kGM = kFixed && !CHUNK;
+    const int RS = kGM ? tally_rows(cap, GL, GPL) : 0;
+    const int CS = kGM ? RS : 1;
+    auto tix = [&](int row, int q) { return kGM ? q * RS + row : row * TS + q; };
     if (!BATCH && st.scal[SC_CONV] != 0.0) return;  // converged: later iterations are no-ops
     real *sig = reinterpret_cast<real *>(smem);
     size_t off = ((size_t)M * GP * sizeof(real) + 15) & ~(size_t)15;
