@@ -399,3 +399,41 @@ def test_layer_planes_off_the_axial_lattice_rejected():
     from paper_2503_17743_gb300 import MocError
     with pytest.raises(MocError):
         Tracks(Geometry(p), track_params(p))
+
+
+# --------------------------------------------------------------- group counts
+
+def _lat2(G):
+    return synth.lattice(6, n=2, G=G, height=2.0, n_layers=2, n_azim=8, n_polar=4,
+                         radial_spacing=0.2, axial_spacing=0.5, bc=(1, 0, 1, 1, 0, 1),
+                         n_gt=1, name=f"lat2_g{G}")
+
+
+@pytest.mark.parametrize("prec,rtol,ktol,ftol", [(MOC_FP64, 1e-11, 1e-11, 1e-10),
+                                                 (MOC_FP32, 2e-5, 1e-5, 1e-4)])
+@pytest.mark.parametrize("G", [1, 12, 40])
+def test_group_counts_against_oracle(G, prec, rtol, ktol, ftol):
+    """One group, and more groups than the usual lane shape holds (12: eight
+    lanes per track in FP32; 40: two chunks of 32 groups): two sweeps from a
+    seeded source, then power iterations, like the oracle."""
+    p = _lat2(G)
+    o = oracle.Oracle(p, n_threads=NTH)
+    tr = Tracks(Geometry(p), track_params(p, precision=prec))
+    Q = np.random.default_rng(G).uniform(0.2, 1.0, size=(o.n_fsr, G))
+    o.reset()
+    for sweep in range(2):
+        ot, ol = o.sweep_once(Q)
+        gt, gl = tr.sweep_from_source(Q)
+        scale = np.abs(ot).max()
+        assert np.abs(gt - ot).max() <= rtol * scale, (sweep, np.abs(gt - ot).max() / scale)
+        assert abs(gl - ol) <= rtol * max(abs(ol), 1e-300) + 1e-300
+    o.reset()
+    tr.reset()
+    n = 10
+    ref = o.iterate(n)
+    res = tr.iterate(n, use_graph=True)
+    phi, k = tr.flux()
+    assert res["iterations"] == n
+    assert abs(k - ref["k"]) < ktol, (k, ref["k"])
+    np.testing.assert_allclose(phi, o.flux(), rtol=ftol)
+    tr.close()
