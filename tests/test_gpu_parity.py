@@ -437,3 +437,33 @@ def test_group_counts_against_oracle(G, prec, rtol, ktol, ftol):
     assert abs(k - ref["k"]) < ktol, (k, ref["k"])
     np.testing.assert_allclose(phi, o.flux(), rtol=ftol)
     tr.close()
+
+
+@pytest.mark.parametrize("prec,rtol,ktol,ftol", [(MOC_FP64, 1e-11, 1e-11, 1e-10),
+                                                 (MOC_FP32, 2e-5, 1e-5, 1e-4)])
+def test_all_vacuum_against_oracle(prec, rtol, ktol, ftol):
+    """Vacuum on all six faces (no boundary flux is stored or read: the
+    fixed-point bound comes from the source alone): sweeps and power
+    iterations like the oracle, and every track leaks."""
+    p = _lat3(bc=(0, 0, 0, 0, 0, 0), seed=9)
+    o = oracle.Oracle(p, n_threads=NTH)
+    tr = Tracks(Geometry(p), track_params(p, precision=prec))
+    Q = np.random.default_rng(9).uniform(0.2, 1.0, size=(o.n_fsr, p.num_groups))
+    o.reset()
+    for sweep in range(2):
+        ot, ol = o.sweep_once(Q)
+        gt, gl = tr.sweep_from_source(Q)
+        scale = np.abs(ot).max()
+        assert np.abs(gt - ot).max() <= rtol * scale, (sweep, np.abs(gt - ot).max() / scale)
+        assert ol > 0.0 and abs(gl - ol) <= rtol * abs(ol)
+    # an empty range of 2D tracks sweeps nothing
+    et, el = tr.sweep_units_from_source(Q, 3, 3)
+    assert not et.any() and el == 0.0
+    o.reset()
+    tr.reset()
+    ref = o.iterate(12)
+    res = tr.iterate(12, use_graph=True)
+    phi, k = tr.flux()
+    assert abs(k - ref["k"]) < ktol, (k, ref["k"])
+    np.testing.assert_allclose(phi, o.flux(), rtol=ftol)
+    tr.close()
