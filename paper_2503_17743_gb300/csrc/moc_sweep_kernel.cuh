@@ -702,49 +702,49 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                                 shared_red_add(tl_sa + fD[i] * 4u, vD[i][0]);
                                 shared_red_add(tl_sa + (fD[i] + CS) * 4u, vD[i][1]);
                             }
-                            return;
-                        }
-                        real qU[4][GPL], sU[4][GPL], qD[4][GPL], sD[4][GPL];
+                        } else {
+                            real qU[4][GPL], sU[4][GPL], qD[4][GPL], sD[4][GPL];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            eU[i] = rU[i] * GP + qlo;
-                            eD[i] = rD[i] * GP + qlo;
-                            fU[i] = tix(rU[i], qlo);
-                            fD[i] = tix(rD[i], qlo);
-                            RowLoadS<real, GPL>::get(rows_sa + eU[i] * (unsigned)(2 * sizeof(real)), qU[i], sU[i]);
-                            RowLoadS<real, GPL>::get(rows_sa + eD[i] * (unsigned)(2 * sizeof(real)), qD[i], sD[i]);
-                        }
-                        real tU[4][GPL], tD[4][GPL];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-#pragma unroll
-                            for (int c = 0; c < GPL; ++c) {
-                                sU[i][c] = attenuation<real>(sU[i][c] * len[i], s_exp);  // now e^{-Sigma_t l}
-                                sD[i][c] = attenuation<real>(sD[i][c] * len[i], s_exp);
+                            for (int i = 0; i < 4; ++i) {
+                                eU[i] = rU[i] * GP + qlo;
+                                eD[i] = rD[i] * GP + qlo;
+                                fU[i] = tix(rU[i], qlo);
+                                fD[i] = tix(rD[i], qlo);
+                                RowLoadS<real, GPL>::get(rows_sa + eU[i] * (unsigned)(2 * sizeof(real)), qU[i], sU[i]);
+                                RowLoadS<real, GPL>::get(rows_sa + eD[i] * (unsigned)(2 * sizeof(real)), qD[i], sD[i]);
                             }
+                            real tU[4][GPL], tD[4][GPL];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i)
-#pragma unroll
-                            for (int c = 0; c < GPL; ++c) {
-                                const real dU = fma(-WS[c], qU[i][c], psiU[c]), dD = fma(-WS[c], qD[i][c], psiD[c]);
-                                tU[i][c] = fma(-dU, sU[i][c], dU);
-                                tD[i][c] = fma(-dD, sD[i][c], dD);
-                                psiU[c] -= tU[i][c];
-                                psiD[c] -= tD[i][c];
-                            }
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            if constexpr (kFixed) {
+                            for (int i = 0; i < 4; ++i)
 #pragma unroll
                                 for (int c = 0; c < GPL; ++c) {
-                                    shared_red_add(tl_sa + (fU[i] + c * CS) * 4u,
-                                                   __float2int_rn((float)tU[i][c]));
-                                    shared_red_add(tl_sa + (fD[i] + c * CS) * 4u,
-                                                   __float2int_rn((float)tD[i][c]));
+                                    sU[i][c] = attenuation<real>(sU[i][c] * len[i], s_exp);  // now e^{-Sigma_t l}
+                                    sD[i][c] = attenuation<real>(sD[i][c] * len[i], s_exp);
                                 }
-                            } else {
-                                TallyAdd<real, GPL>::add(tl_s + fU[i], tU[i], err);
-                                TallyAdd<real, GPL>::add(tl_s + fD[i], tD[i], err);
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                                for (int c = 0; c < GPL; ++c) {
+                                    const real dU = fma(-WS[c], qU[i][c], psiU[c]), dD = fma(-WS[c], qD[i][c], psiD[c]);
+                                    tU[i][c] = fma(-dU, sU[i][c], dU);
+                                    tD[i][c] = fma(-dD, sD[i][c], dD);
+                                    psiU[c] -= tU[i][c];
+                                    psiD[c] -= tD[i][c];
+                                }
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                if constexpr (kFixed) {
+#pragma unroll
+                                    for (int c = 0; c < GPL; ++c) {
+                                        shared_red_add(tl_sa + (fU[i] + c * CS) * 4u,
+                                                       __float2int_rn((float)tU[i][c]));
+                                        shared_red_add(tl_sa + (fD[i] + c * CS) * 4u,
+                                                       __float2int_rn((float)tD[i][c]));
+                                    }
+                                } else {
+                                    TallyAdd<real, GPL>::add(tl_s + fU[i], tU[i], err);
+                                    TallyAdd<real, GPL>::add(tl_s + fD[i], tD[i], err);
+                                }
                             }
                         }
                     }
