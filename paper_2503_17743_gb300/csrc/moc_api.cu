@@ -817,23 +817,33 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
 
 std::mutex g_states_mu;  // live-state counts of layout owners
 
+namespace {
+// drop one state's hold on a layout owner; frees the owner when it was
+// destroyed while states lived and this was the last of them
+void release_owner(moc_tracks *o) {
+    bool free_it = false;
+    {
+        std::lock_guard<std::mutex> lk(g_states_mu);
+        free_it = --o->live_states == 0 && o->destroy_pending;
+    }
+    if (free_it) delete o;
+}
+}  // namespace
+
 extern "C" void moc_destroy_tracks(moc_tracks *h) {
     if (!h) return;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
-    moc_tracks *free_owner = nullptr;
-    {
+    moc_tracks *owner = h->owner;
+    if (!owner) {
         std::lock_guard<std::mutex> lk(g_states_mu);
-        if (h->owner) {
-            moc_tracks *o = h->owner;
-            if (--o->live_states == 0 && o->destroy_pending) free_owner = o;
-        } else if (h->live_states > 0) {
+        if (h->live_states > 0) {
             h->destroy_pending = true;  // its states still use the layout
             return;
         }
     }
     delete h;
-    if (free_owner) delete free_owner;
+    if (owner) release_owner(owner);
 }
 
 extern "C" void moc_state_destroy(moc_tracks *state) { moc_destroy_tracks(state); }
@@ -851,9 +861,19 @@ extern "C" int moc_state_create(const moc_tracks *t, const double *ext_source, m
     *out = nullptr;
     moc_tracks *base = t->owner ? t->owner : const_cast<moc_tracks *>(t);
     {
+        // hold the layout from here on, so that a concurrent destroy of its
+        // owner cannot free the buffers this state borrows while it is built
         std::lock_guard<std::mutex> lk(g_states_mu);
         if (base->destroy_pending) { moc_set_error("the layout was destroyed"); return MOC_ERR_INVALID_ARG; }
+        ++base->live_states;
     }
+    struct Hold {
+        moc_tracks *o;
+        bool kept = false;
+        ~Hold() {
+            if (!kept) release_owner(o);
+        }
+    } hold{base};
     const int G = base->geom.G, M = base->geom.M;
     if (ext_source)
         for (int i = 0; i < M * G; ++i)
@@ -929,11 +949,8 @@ extern "C" int moc_state_create(const moc_tracks *t, const double *ext_source, m
     TRY(cudaMemcpyAsync(h->d_scal.p, init.data(), SC_COUNT * 8, cudaMemcpyHostToDevice, h->stream), "upload");
     const int rc = init_state(h.get());
     if (rc) return rc;
-    {
-        std::lock_guard<std::mutex> lk(g_states_mu);
-        h->owner = base;
-        ++base->live_states;
-    }
+    h->owner = base;  // the hold taken above now belongs to the state
+    hold.kept = true;
     *out = h.release();
     return MOC_OK;
 }

@@ -39,8 +39,11 @@ def test_state_is_an_independent_solve(prec, tol):
         assert r["iterations"] == 12
         assert abs(k - ref["k"]) < tol
         np.testing.assert_allclose(phi, o.flux(), rtol=10 * tol)
-    # the layout outlives its owner's handle while a state uses it
+    # the layout outlives its owner's handle while a state uses it, but takes
+    # no new states once the owner is closed
     base.close()
+    with pytest.raises(MocError):
+        st.state()
     r3 = st.iterate(3)
     assert r3["iterations"] == 3
     st.close()
