@@ -140,3 +140,70 @@ def ray_fsrs_3d(prob, x0, y0, dx, dy, L, z_start, cot, n_samples=200000):
     sin = 1.0 / math.sqrt(1.0 + cot * cot)
     ids, lens = rle(fsr, h / sin)
     return ids, lens, h / sin
+
+
+def layer_of(prob, z):
+    """Axial layer of heights z (equal layers, or the listed planes)."""
+    lz = getattr(prob, "layer_z", None)
+    if lz is None:
+        return np.minimum(prob.n_layers - 1,
+                          np.floor(z / (prob.height / prob.n_layers)).astype(np.int64))
+    return np.minimum(prob.n_layers - 1, np.searchsorted(np.asarray(lz), z, side="right") - 1)
+
+
+def point_material(prob, x, y, z):
+    """Material at points (x, y, z) by direct location, without any region
+    numbering: the cell's mat_in inside its pin's fuel circle (radius
+    fuel_radius about the cell centre), mat_out elsewhere in the cell; the
+    layer from z."""
+    cx = np.clip(np.floor(x / prob.pitch).astype(np.int64), 0, prob.ncx - 1)
+    cy = np.clip(np.floor(y / prob.pitch).astype(np.int64), 0, prob.ncy - 1)
+    c = cy * prob.ncx + cx
+    L = layer_of(prob, z)
+    ux = x - (cx + 0.5) * prob.pitch
+    uy = y - (cy + 0.5) * prob.pitch
+    inside = (prob.has_pin[c] != 0) & (ux ** 2 + uy ** 2 < prob.fuel_radius ** 2)
+    mi = np.asarray(prob.mat_in)[c * prob.n_layers + L]
+    mo = np.asarray(prob.mat_out)[c * prob.n_layers + L]
+    return np.where(inside, mi, mo)
+
+
+def fsr_materials(prob):
+    """Material of every FSR from the documented numbering alone: radial
+    regions cell by cell, a pin cell's region = ring * sectors + sector with
+    the rings inside the fuel circle (the first fuel_rings) holding mat_in and
+    the others mat_out; FSR = region * n_layers + layer."""
+    F = max(1, getattr(prob, "fuel_rings", 1))
+    S = max(1, getattr(prob, "sectors", 1))
+    rings = F + getattr(prob, "moderator_rings", 0) + 1
+    NL = prob.n_layers
+    out = []
+    for c in range(prob.ncx * prob.ncy):
+        mi = np.asarray(prob.mat_in)[c * NL:(c + 1) * NL]
+        mo = np.asarray(prob.mat_out)[c * NL:(c + 1) * NL]
+        if prob.has_pin[c]:
+            for ring in range(rings):
+                for _ in range(S):
+                    out.append(mi if ring < F else mo)
+        else:
+            out.append(mo)
+    return np.concatenate(out).astype(np.int32)
+
+
+def fsr_centres(prob):
+    """(x, y, z) of the centre of every FSR's cell and layer, from the
+    documented numbering (regions cell by cell, FSR = region * n_layers +
+    layer)."""
+    R = prob.pin_regions
+    NL = prob.n_layers
+    cells = np.concatenate([np.full(R if prob.has_pin[c] else 1, c)
+                            for c in range(prob.ncx * prob.ncy)])
+    cx = (cells % prob.ncx + 0.5) * prob.pitch
+    cy = (cells // prob.ncx + 0.5) * prob.pitch
+    lz = getattr(prob, "layer_z", None)
+    planes = np.asarray(lz) if lz is not None else np.linspace(0.0, prob.height, NL + 1)
+    zc = 0.5 * (planes[:-1] + planes[1:])
+    x = np.repeat(cx, NL)
+    y = np.repeat(cy, NL)
+    z = np.tile(zc, cells.size)
+    return x, y, z

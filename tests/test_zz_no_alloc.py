@@ -9,9 +9,9 @@ the first call and reused).
 import numpy as np
 import pytest
 
-import oracle
 import synth
 from paper_2503_17743_gb300 import Geometry, Tracks, track_params
+from tests import bruteforce as bf
 
 pytestmark = pytest.mark.gpu
 
@@ -30,7 +30,8 @@ def test_group_rates_static_two_calls_in_a_row(fixed):
                           radial_spacing=0.2, axial_spacing=0.5, fixed_source=True)
     else:
         p = synth.workload("lattice5")
-    fsr_mat = oracle.Oracle(p, n_threads=1).fsr_materials()
+    # the FSR -> material map from the problem's documented numbering
+    fsr_mat = bf.fsr_materials(p)
     tr = Tracks(Geometry(p), track_params(p))
     vol = tr.volumes()
     for _ in range(2):
