@@ -258,6 +258,25 @@ int moc_read_result(moc_tracks *tracks, void *stream, moc_result *res);
 /* Copy the normalised scalar flux [n_fsr*G] (FP64, host) and k. */
 int moc_get_flux(moc_tracks *tracks, double *phi, double *k);
 
+/* The scalar flux where it lives on the device, without a copy: for a
+ * consumer on the same device (a PyTorch tensor made from the pointer, a
+ * caller's kernel) that should not round-trip through host memory.
+ *   phi    out: device pointer to phi[n_fsr*G] (FP64, group fastest), the
+ *          flux iterate of the Eq. 4 update before normalisation
+ *   scale  out (may be NULL): device pointer to one FP64 value; the
+ *          normalised flux (what moc_get_flux returns) is phi * (*scale)
+ *          (1 for fixed-source problems, 1 / production for eigenvalue
+ *          problems)
+ *   n_fsr, G  out (may be NULL): the array's shape
+ * Both buffers are owned by the library and READ-ONLY for the caller.  They
+ * stay allocated until the handle is destroyed; their values change with
+ * every outer iteration, so read them on the handle's stream (or after
+ * synchronising it) and before the next iteration is enqueued.  No GPU work
+ * and no synchronisation happen in the call.  Errors: MOC_ERR_INVALID_ARG for
+ * NULL tracks or phi. */
+int moc_get_flux_device(moc_tracks *tracks, const double **phi, const double **scale,
+                        int64_t *n_fsr, int32_t *G);
+
 /* Set the scalar flux [n_fsr*G] and k (host FP64 input). */
 int moc_set_flux(moc_tracks *tracks, const double *phi, double k);
 
@@ -360,9 +379,10 @@ int moc_sweep_units_from_source(moc_tracks *tracks, const double *Q, int32_t t0,
  * device) instead of an allocation; nothing in it has to start at zero.  Limit:
  * G <= 32 (MOC_ERR_UNSUPPORTED beyond).  The first call on each device
  * resolves the scratch address (cudaGetSymbolAddress, with that device
- * current); make that first call before any stream capture.  Calls that
- * overlap in time (two streams or two host threads) share the scratch and
- * race: serialise them.  Errors: MOC_ERR_INVALID_ARG for NULL,
+ * current); make that first call before any stream capture begins.  Every
+ * call synchronises `stream` and copies the rates into host memory before
+ * it returns.  Calls that overlap in time (two streams or two host threads)
+ * share the scratch and race: serialise them.  Errors: MOC_ERR_INVALID_ARG for NULL,
  * MOC_ERR_UNSUPPORTED, MOC_ERR_CUDA. */
 int moc_group_rates_static(moc_tracks *tracks, void *stream, double *rates);
 
@@ -375,6 +395,27 @@ int moc_group_rates_static(moc_tracks *tracks, void *stream, double *rates);
  *   sm_count        out (may be NULL): multiprocessors of the device
  * Errors: MOC_ERR_INVALID_ARG for NULL, MOC_ERR_CUDA. */
 int moc_measure_ex2_rate(int32_t device, double *ex2_per_second, double *sm_count);
+
+/* Sustained throughput of the other units the FP32 sweep issues to, each
+ * probed by its own kernel (8 independent operations per thread and step,
+ * 8 blocks of 256 threads on every SM, the last of three runs timed with
+ * CUDA events).  Measurement support for the sweep's roofline; the paper has
+ * no counterpart.  Allocates and frees a small device buffer.
+ *   out[0]  multiprocessors of the device
+ *   out[1]  SM clock (MHz) during the scalar FMA run (clock64 over its time)
+ *   out[2]  FP32 fused multiply-adds per second, scalar (fma.rn.f32),
+ *           counted as lane operations
+ *   out[3]  FP32 lane operations per second as packed pairs
+ *           (fma.rn.f32x2, two per lane and instruction)
+ *   out[4]  conflict-free shared-memory 32-bit integer reductions per second
+ *           (red.shared.add.s32, 32 banks per warp instruction)
+ *   out[5]  conflict-free shared-memory load bytes per second (16-byte loads,
+ *           512 contiguous bytes per warp instruction)
+ *   out[6]  float-to-integer conversions with rounding per second
+ *           (cvt.rni.s32.f32)
+ *   n       entries of out to write (at most 7)
+ * Errors: MOC_ERR_INVALID_ARG for NULL or n < 1, MOC_ERR_CUDA. */
+int moc_measure_unit_rates(int32_t device, double *out, int32_t n);
 
 /* The attenuation factor e^{-x} of Eq. 3 as the FP64 sweep computes it
  * (table-driven: 2^{j/64} in hi + lo parts, degree-5 polynomial on
@@ -427,8 +468,12 @@ int moc_autotune(const moc_geometry *geom, const moc_track_params *base, int32_t
  *
  * Requests queue in arrival order and are admitted while a slot is free and
  * their device footprint (moc_query_footprint: resident state plus stored
- * templates) fits next to the resident solves in the memory budget; the
- * oldest request is always admitted into an empty engine.  Each resident solve
+ * templates) fits next to the resident solves in the memory budget; a
+ * request whose footprint alone exceeds the budget is not admitted and
+ * finishes with MOC_ERR_OUT_OF_MEMORY.  A request that fails (track
+ * generation, for example MOC_ERR_UNSUPPORTED for an axial mesh off the
+ * lattice; an enqueue; a kernel) finishes with its own status while the other
+ * resident solves go on.  Each resident solve
  * owns a stream and captured iteration graphs; a step enqueues a quantum of
  * outer iterations on every idle solve (their kernels overlap on the device),
  * waits for the oldest quantum in flight and retires every solve whose
@@ -459,9 +504,12 @@ int moc_server_submit(moc_server *server, const moc_geometry *geom, const moc_tr
                       const moc_solve_params *solve, int64_t *ticket);
 
 /* One engine step: admit, enqueue, wait for the oldest quantum in flight,
- * retire finished solves, admit and enqueue again.  *finished = solves
- * retired by this call, *pending = queued + resident requests left (either may
- * be NULL).  Blocks at most until one quantum completes. */
+ * retire finished solves, admit and enqueue again.  *finished = requests
+ * finished by this call (retired or failed), *pending = queued + resident
+ * requests left (either may be NULL; both are written also on failure).
+ * Blocks at most until one quantum completes.  Errors: MOC_ERR_INVALID_ARG
+ * for NULL; MOC_ERR_CUDA only when the device context reports a sticky error
+ * (one failing solve is reported through its own ticket instead). */
 int moc_server_step(moc_server *server, int32_t *finished, int32_t *pending);
 
 /* Result of a ticket: *ready = 0 while it is queued or resident.  Once ready,

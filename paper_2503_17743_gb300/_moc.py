@@ -101,6 +101,8 @@ SIGNATURES = {
     "moc_reset": (C.c_int, [C.c_void_p]),
     "moc_iterate": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(moc_result)]),
     "moc_get_flux": (C.c_int, [C.c_void_p, f64p, f64p]),
+    "moc_get_flux_device": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                      i64p, i32p]),
     "moc_set_flux": (C.c_int, [C.c_void_p, f64p, C.c_double]),
     "moc_get_volumes": (C.c_int, [C.c_void_p, f64p]),
     "moc_tracks_info": (C.c_int, [C.c_void_p, i64p, C.c_int32]),
@@ -112,6 +114,7 @@ SIGNATURES = {
     "moc_sweep_units_from_source": (C.c_int, [C.c_void_p, f64p, C.c_int32, C.c_int32, f64p, f64p]),
     "moc_group_rates_static": (C.c_int, [C.c_void_p, C.c_void_p, f64p]),
     "moc_measure_ex2_rate": (C.c_int, [C.c_int32, f64p, f64p]),
+    "moc_measure_unit_rates": (C.c_int, [C.c_int32, f64p, C.c_int32]),
     "moc_eval_attenuation_f64": (C.c_int, [C.c_int32, f64p, C.c_int64, f64p, f64p]),
     "moc_eval_attenuation_f32": (C.c_int, [C.c_int32, f32p, C.c_int64, f32p]),
     "moc_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, f64p, C.c_int32,
@@ -347,6 +350,19 @@ class Tracks:
         _check(load().moc_get_flux(self._h, _ptr(phi, f64p), C.byref(k)))
         return phi.reshape(self.n_fsr, self.G), k.value
 
+    def flux_device(self):
+        """moc_get_flux_device: (phi, scale) as read-only device arrays that
+        expose ``__cuda_array_interface__`` (``torch.as_tensor(phi,
+        device="cuda")`` views them without a copy): phi [n_fsr, G] FP64, the
+        flux iterate, and scale [1], its normalisation (the normalised flux
+        is phi * scale).  The library owns the memory: the views are valid
+        until this handle is closed and change with every iteration."""
+        p, sc = C.c_void_p(), C.c_void_p()
+        n, g = C.c_int64(), C.c_int32()
+        _check(load().moc_get_flux_device(self._h, C.byref(p), C.byref(sc), C.byref(n), C.byref(g)))
+        return (DeviceArray(p.value, (n.value, g.value), self),
+                DeviceArray(sc.value, (1,), self))
+
     def set_flux(self, phi, k):
         phi = np.ascontiguousarray(phi, dtype=np.float64).ravel()
         _check(load().moc_set_flux(self._h, _ptr(phi, f64p), float(k)))
@@ -404,6 +420,22 @@ class Tracks:
         return out[:self.G].copy(), out[self.G:].copy()
 
 
+class DeviceArray:
+    """A read-only FP64 device array owned by the library, described by
+    ``__cuda_array_interface__`` (version 3) so that PyTorch or any other
+    consumer can view it in place; keeps its owner handle alive."""
+
+    def __init__(self, ptr, shape, owner):
+        self.ptr = int(ptr)
+        self.shape = tuple(int(s) for s in shape)
+        self._owner = owner
+
+    @property
+    def __cuda_array_interface__(self):
+        return {"shape": self.shape, "typestr": "<f8", "data": (self.ptr, True),
+                "version": 3, "strides": None}
+
+
 def batch_step(solves, stream=None):
     """moc_batch_step: one outer iteration of every solve (a Tracks and its
     states), their sweeps in one persistent launch."""
@@ -417,6 +449,23 @@ def measure_ex2_rate(device=0):
     rate, sms = C.c_double(), C.c_double()
     _check(load().moc_measure_ex2_rate(device, C.byref(rate), C.byref(sms)))
     return rate.value, int(sms.value)
+
+
+UNIT_RATES = ["sm_count", "sm_mhz", "fp32_fma_scalar_per_s", "fp32_fma_packed_lane_ops_per_s",
+              "smem_red_s32_per_s", "smem_load_bytes_per_s", "f2i_per_s"]
+
+
+def measure_unit_rates(device=0):
+    """Measured throughput of the units the FP32 sweep issues to (dict, see
+    moc_measure_unit_rates): SM count and clock, FP32 FMA lane operations per
+    second scalar and as packed pairs, conflict-free shared-memory integer
+    reductions and load bytes per second, float-to-integer conversions per
+    second."""
+    out = np.zeros(len(UNIT_RATES))
+    _check(load().moc_measure_unit_rates(device, _ptr(out, f64p), len(UNIT_RATES)))
+    d = dict(zip(UNIT_RATES, out.tolist()))
+    d["sm_count"] = int(d["sm_count"])
+    return d
 
 
 def eval_attenuation_f64(x, device=0):
@@ -462,8 +511,8 @@ class Server:
         t = C.c_int64()
         _check(load().moc_server_submit(self._h, geom._h, C.byref(params), C.byref(sp), C.byref(t)))
         prob = geom.prob
-        n_fsr = int(np.sum(np.where(np.asarray(prob.has_pin) != 0, 2, 1))) * prob.n_layers
-        self._shape[t.value] = (n_fsr, prob.num_groups)
+        # every FSR of the geometry: rings and sectors of the pin cells included
+        self._shape[t.value] = (int(prob.n_fsr), prob.num_groups)
         return t.value
 
     def step(self):

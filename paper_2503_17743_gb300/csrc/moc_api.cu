@@ -1151,6 +1151,18 @@ extern "C" int moc_get_flux(moc_tracks *h, double *phi, double *k) {
     return MOC_OK;
 }
 
+extern "C" int moc_get_flux_device(moc_tracks *h, const double **phi, const double **scale,
+                                   int64_t *n_fsr, int32_t *G) {
+    if (!h || !phi) { moc_set_error("NULL argument"); return MOC_ERR_INVALID_ARG; }
+    // no copy, no synchronisation: the library's own buffers, read-only for
+    // the caller (phi is the flux iterate of Eq. 4; scale its normalisation)
+    *phi = static_cast<const double *>(h->d_phi.p);
+    if (scale) *scale = static_cast<const double *>(h->d_scal.p) + SC_SCALE;
+    if (n_fsr) *n_fsr = h->geom.nfsr;
+    if (G) *G = h->geom.G;
+    return MOC_OK;
+}
+
 extern "C" int moc_set_flux(moc_tracks *h, const double *phi, double k) {
     if (!h || !phi) { moc_set_error("NULL argument"); return MOC_ERR_INVALID_ARG; }
     TRY(cudaSetDevice(h->device), "cudaSetDevice");
