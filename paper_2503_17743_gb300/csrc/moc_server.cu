@@ -5,8 +5,10 @@
 //
 // * Requests queue in arrival order.  A request is admitted when a slot is
 //   free and its device footprint (moc_query_footprint: resident state plus
-//   stored templates) fits the memory budget next to the resident solves; the
-//   oldest request is always admitted into an empty engine.
+//   stored templates) fits the memory budget next to the resident solves; a
+//   request larger than the whole budget finishes with MOC_ERR_OUT_OF_MEMORY.
+// * A solve that fails (generation, an enqueue, a kernel) finishes with its
+//   own error status; the other resident solves go on.
 // * Every resident solve owns its stream and its captured iteration graphs.
 //   One engine step enqueues a quantum of outer iterations on every resident
 //   solve that is idle, so the kernels of different solves overlap on the
@@ -168,10 +170,31 @@ struct moc_server {
         ++n_finished;
     }
 
+    // a queued request that can never be admitted: finished with its error
+    void reject(Request &&r, int status, const std::string &err) {
+        Finished f;
+        f.status = status;
+        f.error = err;
+        f.t_submit = r.t_submit;
+        f.t_start = f.t_finish = now_seconds();
+        done[r.ticket] = std::move(f);
+        ++n_finished;
+    }
+
     // admit queued requests while a slot and the memory allow; their tracks
-    // are generated on the worker threads
-    void admit() {
-        int added = 0;
+    // are generated on the worker threads.  A request whose footprint alone
+    // exceeds the budget finishes with MOC_ERR_OUT_OF_MEMORY (its neighbours
+    // are not disturbed).  Returns the requests rejected.
+    int admit() {
+        int added = 0, rejected = 0;
+        while (!queue.empty() && queue.front().bytes > budget) {
+            Request r = std::move(queue.front());
+            queue.pop_front();
+            const std::string msg = "request footprint " + std::to_string(r.bytes) +
+                                    " bytes exceeds the memory budget of " + std::to_string(budget);
+            reject(std::move(r), MOC_ERR_OUT_OF_MEMORY, msg);
+            ++rejected;
+        }
         while (!queue.empty() && (int)active.size() + generating < max_active &&
                ((active.empty() && generating == 0) || bytes_resident + queue.front().bytes <= budget)) {
             auto s = std::make_unique<Slot>();
@@ -185,8 +208,15 @@ struct moc_server {
             gen_tickets.insert(s->req.ticket);
             std::lock_guard<std::mutex> lk(mu);
             to_gen.push_back(std::move(s));
+            while (!queue.empty() && queue.front().bytes > budget) {
+                Request r = std::move(queue.front());
+                queue.pop_front();
+                reject(std::move(r), MOC_ERR_OUT_OF_MEMORY, "request footprint exceeds the memory budget");
+                ++rejected;
+            }
         }
         if (added) cv_work.notify_all();
+        return rejected;
     }
 
     // generated requests become resident (or finish with their error); with
@@ -211,17 +241,28 @@ struct moc_server {
         }
     }
 
-    // a quantum of iterations on every idle resident solve
+    // a quantum of iterations on every idle resident solve; a solve whose
+    // enqueue fails finishes with that error and the others go on.  Returns
+    // the solves finished here.
     int launch() {
-        for (auto &s : active) {
-            if (s->in_flight) continue;
-            const int n = std::min(quantum, s->req.sp.max_iter - s->enqueued);
-            int rc = tracks_enqueue_iterations(s->tr, n, s->ev);
-            if (rc != MOC_OK) return rc;
-            s->enqueued += n;
-            s->in_flight = true;
+        int nf = 0;
+        for (size_t i = 0; i < active.size();) {
+            auto &s = active[i];
+            if (!s->in_flight) {
+                const int n = std::min(quantum, s->req.sp.max_iter - s->enqueued);
+                const int rc = tracks_enqueue_iterations(s->tr, n, s->ev);
+                if (rc != MOC_OK) {
+                    finish(s, rc, moc_last_error());
+                    active.erase(active.begin() + i);
+                    ++nf;
+                    continue;
+                }
+                s->enqueued += n;
+                s->in_flight = true;
+            }
+            ++i;
         }
-        return MOC_OK;
+        return nf;
     }
 
     // retire the solves whose quantum has completed and whose stopping rule
@@ -305,28 +346,34 @@ extern "C" int moc_server_submit(moc_server *s, const moc_geometry *g, const moc
 }
 
 extern "C" int moc_server_step(moc_server *s, int32_t *finished, int32_t *pending) {
+    if (finished) *finished = 0;
     if (!s) { moc_set_error("NULL argument"); return MOC_ERR_INVALID_ARG; }
+    if (pending) *pending = (int32_t)(s->queue.size() + s->active.size() + s->generating);
     if (cudaSetDevice(s->device) != cudaSuccess) { moc_set_error("cudaSetDevice failed"); return MOC_ERR_CUDA; }
-    int nf = 0;
-    s->admit();
+    int nf = s->admit();
     s->take_generated(s->active.empty());
-    int rc = s->launch();
-    if (rc) return rc;
+    nf += s->launch();
     // wait for the oldest quantum in flight, then retire what is done and
-    // keep the rest busy
-    if (!s->active.empty()) {
-        if (cudaEventSynchronize(s->active.front()->ev) != cudaSuccess) {
-            moc_set_error("moc_server_step: a solve failed on the device");
-            return MOC_ERR_CUDA;
-        }
+    // keep the rest busy.  A solve that failed on the device is finished with
+    // its error by collect(); the step itself fails only when the error is
+    // sticky (the device context is lost for every solve).
+    bool sticky = false;
+    if (!s->active.empty() && cudaEventSynchronize(s->active.front()->ev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        sticky = cudaGetLastError() != cudaSuccess;
     }
     s->collect(&nf);
-    s->admit();
-    s->take_generated(false);
-    rc = s->launch();
-    if (rc) return rc;
+    if (!sticky) {
+        nf += s->admit();
+        s->take_generated(false);
+        nf += s->launch();
+    }
     if (finished) *finished = nf;
     if (pending) *pending = (int32_t)(s->queue.size() + s->active.size() + s->generating);
+    if (sticky) {
+        moc_set_error("moc_server_step: the device context reported a sticky error");
+        return MOC_ERR_CUDA;
+    }
     return MOC_OK;
 }
 

@@ -1,11 +1,14 @@
 """The serving engine (moc_server_*): every solve gives the same answer alone
-and in a mix of resident solves, admission respects the memory budget, and
-requests submitted while others run are served (continuous batching)."""
+and in a mix of resident solves, admission respects the memory budget,
+requests submitted while others run are served (continuous batching), and a
+request that fails (not converged, over the memory budget, an unsupported
+mesh) gets its own error status without disturbing its neighbours."""
 import numpy as np
 import pytest
 
 import synth
 from paper_2503_17743_gb300 import Geometry, Server, Tracks, track_params
+from paper_2503_17743_gb300 import _moc
 
 pytestmark = pytest.mark.gpu
 
@@ -130,4 +133,85 @@ def test_requests_arriving_while_others_run():
     out.update({t: r for t, r in drain(srv, [t for t in tickets if t not in out]).items()})
     for t, (r0, phi0) in zip(tickets, ref):
         check_same(out[t][0], out[t][1], r0, phi0)
+    srv.close()
+
+
+def test_failing_requests_do_not_disturb_neighbours():
+    good = requests(3, seed=17)
+    ref = [alone(p) for p in good]
+    # a ringed, sectored lattice: its flux array is larger than 2 regions a pin
+    rings = synth.workload("lattice5_rings")
+    ref_rings = alone(rings)
+    # an axial mesh off the lattice (a plane at 0.6 cm with 0.5 cm spacing)
+    off = synth.pin_cell(1, n_layers=3).with_tracks(layer_z=np.array([0.0, 0.6, 1.5, 2.0]))
+    srv = Server(max_active=4, iterations_per_poll=8)
+    geoms = {}
+    tickets = {}
+    for i, p in enumerate(good):
+        geoms[f"good{i}"] = Geometry(p)
+        tickets[f"good{i}"] = srv.submit(geoms[f"good{i}"], track_params(p), **TOL)
+    geoms["few"] = Geometry(good[0])
+    tickets["few"] = srv.submit(geoms["few"], track_params(good[0]), tol_k=1e-12, tol_src=1e-12,
+                                max_iter=3)
+    geoms["off"] = Geometry(off)
+    with pytest.raises(_moc.MocError) as e:  # refused when it is queued
+        srv.submit(geoms["off"], track_params(off), **TOL)
+    assert e.value.code == _moc.MOC_ERR_UNSUPPORTED
+    geoms["rings"] = Geometry(rings)
+    tickets["rings"] = srv.submit(geoms["rings"], track_params(rings), **TOL)
+    out = {}
+    order = list(tickets)
+    for _ in range(100000):
+        srv.step()
+        for name in order:
+            if name not in out:
+                r = srv.result(tickets[name], check=False)
+                if r is not None:
+                    out[name] = r
+        if len(out) == len(order):
+            break
+    assert len(out) == len(order)
+    # max_iter reached first: NOT_CONVERGED with the last k of 3 iterations
+    r, phi, _, _, rc = out["few"]
+    assert rc == _moc.MOC_ERR_NOT_CONVERGED and r["iterations"] == 3 and np.isfinite(r["k"])
+    tr = Tracks(Geometry(good[0]), track_params(good[0]))
+    r3 = tr.iterate(3)
+    assert abs(r["k"] - r3["k"]) < 1e-5
+    tr.close()
+    assert out["rings"][4] == 0 and out["rings"][1].shape == (rings.n_fsr, rings.num_groups)
+    check_same(out["rings"][0], out["rings"][1], *ref_rings)
+    for i in range(len(good)):
+        r, phi, _, _, rc = out[f"good{i}"]
+        assert rc == 0
+        check_same(r, phi, *ref[i])
+    srv.close()
+
+
+def test_request_over_the_budget_is_rejected():
+    probs = requests(3, seed=19)
+    geoms = [Geometry(p) for p in probs]
+    params = [track_params(p) for p in probs]
+    foot = [sum(g.footprint(tp)) for g, tp in zip(geoms, params)]
+    big = int(np.argmax(foot))
+    budget = max(f for i, f in enumerate(foot) if i != big) if foot.count(max(foot)) == 1 else None
+    if budget is None or budget >= foot[big]:
+        pytest.skip("no request is larger than the others")
+    ref = {i: alone(p) for i, p in enumerate(probs) if i != big}
+    srv = Server(max_active=3, memory_budget_bytes=budget)
+    tickets = [srv.submit(g, tp, **TOL) for g, tp in zip(geoms, params)]
+    out = {}
+    for _ in range(100000):
+        srv.step()
+        for i, t in enumerate(tickets):
+            if i not in out:
+                r = srv.result(t, check=False)
+                if r is not None:
+                    out[i] = r
+        if len(out) == len(tickets):
+            break
+    assert out[big][4] == _moc.MOC_ERR_OUT_OF_MEMORY
+    for i, (r0, phi0) in ref.items():
+        assert out[i][4] == 0
+        check_same(out[i][0], out[i][1], r0, phi0)
+    assert srv.stats()["retired"] == len(tickets)
     srv.close()
