@@ -3,8 +3,12 @@
 benchmark times (FP32 sweep, every template stored, default lane shape).
 
 * FSR-id sequences and segment counts of sampled z-stacks: bit-exact.
-* One sweep from a seeded source (both hemispheres, every track): tallies
-  within 2e-5 of the largest, element by element, against the FP64 oracle.
+* One sweep from a seeded source (uniform, and peaked at the centre), both
+  hemispheres, every track: tallies element by element against the FP64
+  oracle (1e-4 relative above 1e-3 of the largest, 2e-5 of the largest
+  below), and the flux they give within 1e-4 on every FSR-group.
+* The converged FP32 flux within 1e-4 relative of the oracle's converged flux
+  on every FSR-group (the metric's own condition).
 * Converged k-eff within 1e-5 of the oracle's converged value (stored in
   tests/golden/oracle_k.json by tests/golden/make_golden.py, which runs the
   oracle only), with neutron balance P / k = absorption + leakage.
@@ -18,6 +22,8 @@ import pytest
 import oracle
 import synth
 from paper_2503_17743_gb300 import MOC_FP32, Geometry, Tracks, track_params
+
+from tests.parity import check_flux, check_tally, shaped_source
 
 pytestmark = pytest.mark.gpu
 
@@ -52,18 +58,57 @@ def test_sampled_stacks_bit_exact(l17):
         assert np.all(np.abs(gl - ol) <= 1e-6 * ol + 1e-6)
 
 
-def test_one_sweep_against_oracle(l17):
+@pytest.mark.parametrize("source", ["uniform", "shaped"])
+def test_one_sweep_against_oracle(l17, source):
+    """One full sweep from a seeded source (uniform, or peaked at the centre
+    and falling to 1e-3 of the peak at the edges): tallies element by element
+    (1e-4 relative above 1e-3 of the largest, 2e-5 of the largest below) and
+    the flux they give (Eq. 4) within 1e-4 on every FSR-group."""
     p, o, tr = l17
-    Q = np.random.default_rng(23).uniform(0.2, 1.0, size=(o.n_fsr, p.num_groups))
+    if source == "uniform":
+        Q = np.random.default_rng(23).uniform(0.2, 1.0, size=(o.n_fsr, p.num_groups))
+    else:
+        Q = shaped_source(p, p.num_groups, seed=29)
     o.reset()
     tr.reset()
     ot, ol = o.sweep_once(Q)
     gt, gl = tr.sweep_from_source(Q)
-    scale = np.abs(ot).max()
-    assert np.abs(gt - ot).max() <= 2e-5 * scale, np.abs(gt - ot).max() / scale
+    check_tally(gt, ot, what=f"lattice17 {source}")
+    check_flux(gt, ot, Q, o.volumes(), p.sigma_t[o.fsr_materials()], what=f"lattice17 {source}")
     assert abs(gl - ol) <= 2e-5 * abs(ol)
     o.reset()
     tr.reset()
+
+
+@pytest.mark.parametrize("name", ["lattice17", "lattice17_small", "lattice5"])
+def test_converged_flux_per_element_against_oracle(name, l17):
+    """The metric's condition: the converged FP32 flux within 1e-4 relative of
+    the oracle's converged flux on EVERY FSR-group (the stored oracle flux of
+    tests/golden/make_golden.py, converged to a residual below 1e-9).  The
+    GPU runs 30% more outer iterations than the oracle needed (a fixed count,
+    no stopping test), so that what remains is the FP32 sweep's error."""
+    gold = np.load(os.path.join(HERE, "golden", f"oracle_flux_{name}.npz"))
+    if name == "lattice17":
+        p, _, tr = l17
+        tr.reset()
+    else:
+        p = synth.workload(name)
+        tr = Tracks(Geometry(p), track_params(p, precision=MOC_FP32))
+    n_it = int(1.3 * int(gold["iterations"])) + 20
+    res = tr.iterate(n_it, use_graph=True)
+    phi, k = tr.flux()
+    ref = gold["phi"]
+    assert phi.shape == ref.shape and np.all(ref > 0)
+    r = np.abs(phi / ref - 1)
+    worst = np.unravel_index(np.argmax(r), r.shape)
+    print(name, "converged flux max relative error", float(r.max()), "at fsr, group", worst,
+          "k error", abs(k - float(gold["k"])), "iterations", res["iterations"])
+    assert r.max() <= 1e-4, (float(r.max()), worst)
+    assert abs(k - float(gold["k"])) < 1e-5
+    if name != "lattice17":
+        tr.close()
+    else:
+        tr.reset()
 
 
 @pytest.mark.parametrize("name", ["lattice17", "lattice17_small"])

@@ -15,6 +15,8 @@ import synth
 from paper_2503_17743_gb300 import (MOC_FP32, MOC_FP64, MOC_TALLY_GLOBAL, MOC_TALLY_SHARED,
                                     Geometry, Tracks, track_params)
 
+from tests.parity import check_flux, check_tally
+
 pytestmark = pytest.mark.gpu
 
 NTH = os.cpu_count() or 4
@@ -76,21 +78,31 @@ def test_volumes(name):
     tr.close()
 
 
-@pytest.mark.parametrize("prec,rtol", [(MOC_FP64, 1e-11), (MOC_FP32, 2e-5)])
+def sweep_bars(prec):
+    """(relative bar above the floor, absolute bar over the largest tally,
+    flux bar) of one sweep's tallies in each precision."""
+    return (1e-9, 1e-11, 1e-10) if prec == MOC_FP64 else (1e-4, 2e-5, 1e-4)
+
+
+@pytest.mark.parametrize("prec", [MOC_FP64, MOC_FP32])
 @pytest.mark.parametrize("name", ["pin", "lat3", "lat3_mixed", "l17_small", "lat3_rings"])
-def test_two_sweeps_from_source(name, prec, rtol):
+def test_two_sweeps_from_source(name, prec):
     """Seeded source, zero incoming fluxes, two sweeps: the second one runs on
-    the boundary fluxes the first one passed through the links."""
+    the boundary fluxes the first one passed through the links.  Tallies
+    element by element (relative above a floor of 1e-3 of the largest,
+    absolute below it) and the flux they give on every FSR-group."""
     p, o, tr = make(name, precision=prec)
+    rel, absb, frel = sweep_bars(prec)
     rng = np.random.default_rng(11)
     Q = rng.uniform(0.2, 1.0, size=(o.n_fsr, p.num_groups))
+    sigt = p.sigma_t[o.fsr_materials()]
     o.reset()
     for sweep in range(2):
         ot, ol = o.sweep_once(Q)
         gt, gl = tr.sweep_from_source(Q)
-        scale = np.abs(ot).max()
-        assert np.abs(gt - ot).max() <= rtol * scale, (sweep, np.abs(gt - ot).max() / scale)
-        assert abs(gl - ol) <= rtol * max(abs(ol), 1e-300) + 1e-300
+        check_tally(gt, ot, rel=rel, abs_frac=absb, what=f"{name} sweep {sweep}")
+        check_flux(gt, ot, Q, o.volumes(), sigt, rel=frel, what=f"{name} sweep {sweep}")
+        assert abs(gl - ol) <= absb * max(abs(ol), 1e-300) + 1e-300
     o.reset()
     tr.close()
 
