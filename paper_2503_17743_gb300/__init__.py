@@ -9,9 +9,9 @@ ctypes binding (argument marshalling only) plus the build script.
 from ._moc import (MOC_FP32, MOC_FP64, MOC_SCHED_TRACKS_NATURAL, MOC_SCHED_UNITS_NATURAL,
                    MOC_TALLY_AUTO, MOC_TALLY_GLOBAL, MOC_TALLY_SHARED,
                    Geometry, MocError, Server, Tracks, autotune, batch_step, load,
-                   measure_ex2_rate, eval_attenuation_f64, eval_attenuation_f32, track_params)
+                   measure_ex2_rate, measure_unit_rates, eval_attenuation_f64, eval_attenuation_f32, track_params)
 
 __all__ = ["Geometry", "Tracks", "Server", "MocError", "autotune", "batch_step", "load",
-           "track_params", "measure_ex2_rate", "eval_attenuation_f64", "eval_attenuation_f32",
+           "track_params", "measure_ex2_rate", "measure_unit_rates", "eval_attenuation_f64", "eval_attenuation_f32",
            "MOC_FP32", "MOC_FP64", "MOC_TALLY_AUTO", "MOC_TALLY_SHARED", "MOC_TALLY_GLOBAL",
            "MOC_SCHED_UNITS_NATURAL", "MOC_SCHED_TRACKS_NATURAL"]
