@@ -37,17 +37,21 @@ WORKLOAD_DESC = ("17x17 pin lattice (264 fuel pins, 25 seeded guide tubes), 3 ma
                  "radial spacing 0.05 cm, axial spacing 0.5 cm; FP32 sweep, templates stored")
 # algorithmic work of one integration: 7 FP32 operations, one of them the exponential
 OPS_PER_INTEGRATION = 7
-# ALU roofline: FP32 instruction issue, 4 schedulers x 32 lanes = 128 lane
-# operations per SM per clock (152 SMs at the 2070 MHz maximum clock):
-# 40.3e12 operations/s = 5.75e12 integrations/s.  The exponential unit
-# (31.4 ex2 per SM per clock, measured by moc_measure_ex2_rate) would allow
-# 9.9e12 integrations/s, so it is not the binding unit.
-SMS, LANES_PER_CLK, SM_MAX_MHZ = 152, 128, 2070.0
+# shared-memory bytes of one integration in the privatised-tally design: Qr and
+# Sigma_t of the FSR-group (4 + 4) and the tally word (4)
+SMEM_BYTES_PER_INTEGRATION = 12
+# ALU roofline: the FP32 lane-operation rate MEASURED on the device at the
+# start of the run (moc_measure_unit_rates: fused multiply-adds, scalar and as
+# packed pairs, every SM filled); the SM count is the device's.  The
+# exponential unit (moc_measure_ex2_rate, ~31 ex2 per SM per clock) would
+# allow 1.4x more integrations per second than the FP32 pipe, so it does not bind.
 # FP64 sweeps are bound by the FP64 pipe: 2 lane operations per SM per clock
 # (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on peak_sustained).  Each
 # integration takes 15 FP64 operations as written: Sigma_t l (1), the
 # table-driven e^{-x} (11), d = psi - W S Qr, d (1 - e), psi -= (3)
+SM_MAX_MHZ = 2070.0
 FP64_LANES_PER_CLK, FP64_OPS_PER_INTEGRATION = 2, 15
+STEP_DESC = "one outer power iteration: source, sweep, flux/k/residual update"
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -174,6 +178,12 @@ def cpu_baseline(prob, seconds_target=10.0):
                                         f"({n1:.4g} integrations, {t1:.1f} s)"}}
 
 
+def bench_config():
+    """The `config` of both arms' lines: the workload and the step (the same
+    keys and values, so that the two lines are like for like)."""
+    return {"workload": WORKLOAD_DESC, "step": STEP_DESC}
+
+
 def run_reference(args):
     import synth
     rank, world, _ = dist_env()
@@ -200,7 +210,8 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD_DESC, "step": "one outer power iteration (FP64 oracle)"},
+            "config": bench_config(),
+            "details": {"arm": "FP64 oracle on the host cores, as it stands"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} outer iterations of {WORKLOAD}"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -221,6 +232,9 @@ def run_ours(args):
     torch.cuda.set_device(local)
     libbuild.build()
     load()
+    # the device's unit rates (FP32 pipe, shared memory): the roofline peaks
+    from paper_2503_17743_gb300 import measure_unit_rates
+    rates = measure_unit_rates(local)
     prob = synth.workload(WORKLOAD)
     geom = Geometry(prob)
     params = track_params(prob, precision=MOC_FP32, device=local)
@@ -232,10 +246,12 @@ def run_ours(args):
         from paper_2503_17743_gb300 import autotune
         params, t_best, table = autotune(geom, params, iterations=5)
         schedule = {"groups_per_lane": params.groups_per_lane, "tally_mode": params.tally_mode,
-                    "preload_budget_bytes": params.preload_budget_bytes,
+                    "preload_budget_bytes": params.preload_budget_bytes, "sync_block": params.sync_block,
                     "tuned_ms_per_iteration": t_best * 1e3,
-                    "candidates": [[int(r[0]), int(r[1]), int(r[2]), round(r[4] * 1e3, 4)] for r in table],
-                    "candidate_columns": ["groups_per_lane", "tally_mode", "preload_budget", "ms_per_iteration"]}
+                    "candidates": [[int(r[0]), int(r[1]), int(r[2]), int(r[5]), round(r[4] * 1e3, 4)]
+                                   for r in table],
+                    "candidate_columns": ["groups_per_lane", "tally_mode", "preload_budget", "sync_block",
+                                          "ms_per_iteration"]}
     tr = Tracks(geom, params)
     info = tr.info
     integ = info["integrations_per_sweep"]
@@ -321,14 +337,9 @@ def run_ours(args):
     if rank != 0:
         return
     sw = statistics.mean(sweep_ms) * 1e-3
-    ach = OPS_PER_INTEGRATION * integ / sw / 1e12
-    peak = SMS * LANES_PER_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    roof = alu_roofline(integ, sw, rates)
     traffic = profile_traffic(sweep_source_hash())
-    roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-            "traffic": traffic, "kernel": "k_sweep",
-            "sweep_ms": sw * 1e3,
-            "peak_basis": "derived: FP32 issue 128 lane-ops per SM per clock x 152 SMs x 2070 MHz; "
-                          "7 FP32 ops per integration (ex2 unit measured 31.4/SM/clk, not binding)"}
+    roof["traffic"] = traffic
     # the HBM side of the same sweep: algorithmic bytes (boundary fluxes in
     # and out, stored template records) and, from the committed ncu summary,
     # the DRAM bytes moved, both per launch time, against the measured copy peak
@@ -358,7 +369,7 @@ def run_ours(args):
         t64.iterate(3, use_graph=True)
         r64 = t64.iterate(args.fp64_steps, use_graph=True)
         rate64 = r64["integrations"] / r64["seconds"]
-        peak64 = SMS * FP64_LANES_PER_CLK * SM_MAX_MHZ * 1e6 / 1e12
+        peak64 = rates["sm_count"] * FP64_LANES_PER_CLK * SM_MAX_MHZ * 1e6 / 1e12
         fp64 = {"value": rate64, "unit": UNIT,
                 "ms_per_step": r64["seconds"] / args.fp64_steps * 1e3, "steps": args.fp64_steps,
                 "dtype": "f64", "timing": "CUDA events around the graph launches of the steps",
@@ -366,27 +377,142 @@ def run_ours(args):
                 "roofline": {"bound": "alu", "achieved": rate64 * FP64_OPS_PER_INTEGRATION / 1e12,
                              "peak": peak64, "unit": "TFLOP/s",
                              "frac": rate64 * FP64_OPS_PER_INTEGRATION / 1e12 / peak64,
-                             "peak_basis": "derived: FP64 pipe 2 lane operations per SM per clock x "
-                                           "152 SMs x 2070 MHz; 15 FP64 operations per integration "
-                                           "(whole step timed: the sweep is most of it)"}}
+                             "peak_basis": f"derived: FP64 pipe 2 lane operations per SM per clock x "
+                                           f"{rates['sm_count']} SMs x 2070 MHz; 15 FP64 operations per "
+                                           "integration (whole step timed: the sweep is most of it)"}}
         t64.close()
+    tr.close()
+    ablation = run_ablation_rows(WORKLOAD, local) if (rank == 0 and args.ablation_leg) else None
+    large = None
+    if rank == 0 and args.large:
+        large = [run_large(name, local, rates, oracle_seconds=args.large_oracle_seconds)
+                 for name in ("asm3x3", "core7x7")]
     serving = None
-    if args.serving_requests > 0:
-        tr.close()
-        serving = run_serving(args.serving_requests, device=local)
+    if rank == 0 and args.serving_requests > 0:
+        serving = run_serving_rates(args.serving_requests, device=local,
+                                    load_factors=tuple(float(x) for x in args.serving_loads.split(",")))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_s / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC, "parallelism": f"replicas x{world}",
-                       "step": "one outer power iteration: source, sweep, flux/k/residual update",
-                       "integrations_per_step": integ, "segments3d": info["segments3d"],
-                       "l2": "flushed between timed steps (256 MiB write outside the events)",
-                       "k_after_steps": res["k"], "schedule": schedule},
+            "config": bench_config(),
+            "details": {"parallelism": f"replicas x{world}",
+                        "integrations_per_step": integ, "segments3d": info["segments3d"],
+                        "l2": "flushed between timed steps (256 MiB write outside the events)",
+                        "k_after_steps": res["k"], "schedule": schedule,
+                        "sync_block": info.get("sync_block"), "unit_rates": rates},
             "roofline": roof, "clocks": clocks, "cpu_baseline": cpu, "e2e": e2e, "fp64": fp64,
-            "serving": serving,
+            "large": large, "serving": serving, "ablation": ablation,
             "gpu_launches": 6 * args.steps}
     print(json.dumps(line), flush=True)
+
+
+def alu_roofline(integrations, sweep_s, rates):
+    """Roofline of one sweep launch against the device's MEASURED FP32 rate
+    (7 FP32 operations per integration), with the shared-memory side of the
+    same launch (12 algorithmic bytes per integration against the measured
+    conflict-free shared-memory load rate)."""
+    peak_ops = max(rates["fp32_fma_scalar_per_s"], rates["fp32_fma_packed_lane_ops_per_s"])
+    ach = OPS_PER_INTEGRATION * integrations / sweep_s / 1e12
+    peak = peak_ops / 1e12
+    smem_peak = rates["smem_load_bytes_per_s"] / 1e9
+    smem_ach = SMEM_BYTES_PER_INTEGRATION * integrations / sweep_s / 1e9
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "kernel": "k_sweep", "sweep_ms": sweep_s * 1e3,
+            "peak_basis": f"of measured: FP32 lane operations per second on this device "
+                          f"(moc_measure_unit_rates, {rates['sm_count']} SMs at {rates['sm_mhz']:.0f} MHz; "
+                          "scalar and packed f32x2 FMAs measure the same rate); "
+                          "7 FP32 operations per integration",
+            "smem": {"algorithmic_bytes_per_integration": SMEM_BYTES_PER_INTEGRATION,
+                     "achieved_gbs": smem_ach, "peak_gbs": smem_peak, "frac": smem_ach / smem_peak,
+                     "peak_basis": "of measured: conflict-free 16-byte shared-memory loads"}}
+
+
+def run_large(name, device, rates, iters=3, oracle_seconds=6.0):
+    """One of the large configurations (3x3 assemblies + reflector, 64 cm,
+    64 x 6 directions, a preload budget below the full template set; the 7x7
+    core with a reflector ring, 200 cm, 128 x 6, all vacuum), FP32: track
+    generation, one warm-up and `iters` graph-launched outer iterations timed
+    with CUDA events, clocks sampled during them; the roofline against the
+    same measured FP32 peak; the FP64 oracle on the host cores timed on a
+    sample of 2D tracks of one sweep and extrapolated (labelled as such)."""
+    import numpy as np
+
+    import oracle
+    import synth
+    from paper_2503_17743_gb300 import MOC_FP32, Geometry, Tracks, track_params
+    p = synth.workload(name)
+    budget = (1 << 30) if name == "asm3x3" else -1
+    t0 = time.perf_counter()
+    tr = Tracks(Geometry(p), track_params(p, precision=MOC_FP32, device=device,
+                                          preload_budget_bytes=budget, trace_on_device=1))
+    gen_s = time.perf_counter() - t0
+    info = tr.info
+    tr.iterate(1, use_graph=True)
+    clk_path = os.path.join(tempfile.gettempdir(), f"moc_large_clocks_{os.getpid()}.csv")
+    sampler, clk_file = clock_sampler(device, clk_path)
+    time.sleep(0.3)
+    r = tr.iterate(iters, use_graph=True)
+    if sampler is not None:
+        sampler.terminate()
+        sampler.wait()
+        clk_file.close()
+    clocks = parse_clocks(clk_path)
+    try:
+        os.remove(clk_path)
+    except OSError:
+        pass
+    rate = r["integrations"] / r["seconds"]
+    integ = info["integrations_per_sweep"]
+    tr.close()
+    # the oracle on a sample: 2D tracks from four places of the laydown
+    o = oracle.Oracle(p, n_threads=os.cpu_count() or 1, light=True)
+    Q = np.random.default_rng(3).uniform(0.2, 1.0, size=(o.n_fsr, p.num_groups))
+    n_s, t_s, tracks = 0, 0.0, 0
+    k = max(1, o.n_tracks2d // 400)
+    for frac in (0.125, 0.375, 0.625, 0.875, 0.0625, 0.3125, 0.5625, 0.8125):
+        a = int(frac * o.n_tracks2d)
+        t1 = time.perf_counter()
+        n, _ = o.sweep_sample(Q, a, min(a + k, o.n_tracks2d))
+        t_s += time.perf_counter() - t1
+        n_s += n
+        tracks += min(a + k, o.n_tracks2d) - a
+        if t_s > oracle_seconds:
+            break
+    del o
+    roof = alu_roofline(integ, r["seconds"] / iters, rates)
+    roof["sweep_ms"] = None
+    roof["timing"] = "whole outer iteration (the sweep is nearly all of it)"
+    return {"workload": name, "integrations_per_sweep": integ, "value": rate, "unit": UNIT,
+            "ms_per_iteration": r["seconds"] / iters * 1e3, "iterations": iters,
+            "generation_s": gen_s, "preloaded_stacks": info["preloaded_stacks"], "stacks": info["stacks"],
+            "stored_segments": info["stored_segments"], "chunk_segments": info["chunk_segments"],
+            "device_bytes": info["device_bytes"], "clocks": clocks, "roofline": roof,
+            "cpu_baseline": {"value": n_s / t_s, "unit": UNIT, "cores": os.cpu_count() or 1,
+                             "kind": "oracle",
+                             "sample": f"extrapolated: {tracks} of {p.name}'s 2D tracks of one FP64 sweep "
+                                       f"({n_s:.4g} integrations, {t_s:.1f} s); a full sweep would take "
+                                       f"about {integ / (n_s / t_s):.0f} s"}}
+
+
+def run_serving_rates(n_requests, device=0, load_factors=(0.5, 1.0, 2.0), seed=1):
+    """The serving stream at several arrival rates: the requests solved one at
+    a time once (the sequential rate R), then arriving as a Poisson process at
+    each load factor x R into the serving engine."""
+    seq = sequential_solves(n_requests, device, seed)
+    rows = [run_serving(n_requests, seed=seed, load_factor=lf, device=device, seq=seq)
+            for lf in load_factors]
+    return {"requests": n_requests, "sequential_solves_per_s": seq[0], "rates": rows}
+
+
+def run_ablation_rows(workload, device):
+    """The ablation table (see run_ablation) as a list of rows."""
+    class A:
+        pass
+    a = A()
+    a.workload = workload
+    a.device = device
+    return run_ablation(a, emit=False)
 
 
 def run_profile_driver(args):
@@ -409,32 +535,42 @@ def run_profile_driver(args):
 SERVE_TOL = dict(tol_k=1e-7, tol_src=1e-6, max_iter=4000)
 
 
-def run_serving(n_requests, seed=1, load_factor=2.0, device=0):
-    """Serving stream (seeded serving_request mix: n x n lattices, 2-7 groups,
-    2-20 cm, 16-64 azimuths x 2-4 polar, half eigenvalue, half fixed source).
-    First every request is solved one at a time in arrival order (sequential
-    rate R); then the same requests arrive as a Poisson process at
-    load_factor x R into the serving engine.  Latency = completion time minus
-    scheduled arrival time."""
-    import numpy as np
-
+def sequential_solves(n_requests, device=0, seed=1):
+    """Every request of the serving stream solved one at a time, end to end
+    through the C ABI: (solves per second, k of each, flux of each)."""
     import synth
-    from paper_2503_17743_gb300 import Geometry, Server, Tracks, track_params
+    from paper_2503_17743_gb300 import Geometry, Tracks, track_params
     probs = [synth.serving_request(seed, i) for i in range(n_requests)]
-    # sequential: one solve at a time, end to end through the C ABI
     t0 = time.perf_counter()
-    ks = []
+    ks, phis = [], []
     for p in probs:
         tr = Tracks(Geometry(p), track_params(p, device=device))
         if p.ext_source is None:
             r = tr.solve_eigen(**SERVE_TOL)
         else:
             r = tr.solve_fixed_source(tol_src=SERVE_TOL["tol_src"], max_iter=SERVE_TOL["max_iter"])
-        tr.flux()
+        phi, _ = tr.flux()
         ks.append(r["k"])
+        phis.append(phi)
         tr.close()
-    t_seq = time.perf_counter() - t0
-    rate_seq = n_requests / t_seq
+    return n_requests / (time.perf_counter() - t0), ks, phis
+
+
+def run_serving(n_requests, seed=1, load_factor=2.0, device=0, seq=None):
+    """Serving stream (seeded serving_request mix: n x n lattices, 2-7 groups,
+    2-20 cm, 16-64 azimuths x 2-4 polar, half eigenvalue, half fixed source).
+    First every request is solved one at a time in arrival order (sequential
+    rate R, unless `seq` gives it); then the same requests arrive as a
+    Poisson process at load_factor x R into the serving engine.  Latency =
+    completion time minus scheduled arrival time."""
+    import numpy as np
+
+    import synth
+    from paper_2503_17743_gb300 import Geometry, Server, track_params
+    probs = [synth.serving_request(seed, i) for i in range(n_requests)]
+    if seq is None:
+        seq = sequential_solves(n_requests, device, seed)
+    rate_seq, ks, phis = seq
     # batched: Poisson arrivals into the engine
     rng = np.random.default_rng(seed + 1000)
     arrivals = np.cumsum(rng.exponential(1.0 / (load_factor * rate_seq), size=n_requests))
@@ -462,19 +598,22 @@ def run_serving(n_requests, seed=1, load_factor=2.0, device=0):
     t_end = max(v[0] for v in done.values())
     lat = np.array([done[i][0] - arrivals[i] for i in range(n_requests)])
     kerr = max(abs(done[i][1][0]["k"] - ks[i]) for i in range(n_requests))
+    ferr = max(float(np.max(np.abs(done[i][1][1] - phis[i]) / np.maximum(np.abs(phis[i]), 1e-300)))
+               for i in range(n_requests))
     st = srv.stats()
     srv.close()
     return {"requests": n_requests, "load_factor": load_factor,
             "sequential_solves_per_s": rate_seq, "solves_per_s": n_requests / (t_end - arrivals[0]),
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "max_resident": st["max_resident"], "max_k_diff_vs_sequential": kerr,
+            "max_flux_rel_diff_vs_sequential": ferr,
             "tolerance": "tol_k 1e-7, tol_src 1e-6, FP32 sweeps",
             "workload": f"seeded serving_request mix, seed {seed}: n x n pin lattices (n 1-17), 2-7 groups, "
                         "2-20 cm, 16-64 azimuths x 2-4 polar, half eigenvalue / half fixed source, "
                         "Poisson arrivals at load_factor x the sequential rate"}
 
 
-def run_ablation(args):
+def run_ablation(args, emit=True):
     """The paper's two optimisations measured on this sweep (Sec. 4.2, 4.3;
     Figs. 6 and 7): the stored (EXP) share of the segment templates from 0 to
     100%, and load balancing off (work units and tracks in index order) or on.
@@ -485,13 +624,14 @@ def run_ablation(args):
                                         Tracks, track_params)
     prob = synth.workload(args.workload)
     geom = Geometry(prob)
-    full = Tracks(geom, track_params(prob, preload_budget_bytes=-1))
+    dev = getattr(args, "device", 0)
+    full = Tracks(geom, track_params(prob, preload_budget_bytes=-1, device=dev))
     tpl_bytes = full.info["stored_segments"] * 8
     full.close()
     rows = []
 
     def measure(label, **kw):
-        tr = Tracks(geom, track_params(prob, **kw))
+        tr = Tracks(geom, track_params(prob, device=dev, **kw))
         tr.iterate(3, use_graph=True)
         r = tr.iterate(10, use_graph=True)
         info = tr.info
@@ -508,7 +648,10 @@ def run_ablation(args):
     measure("units largest first, tracks in index order", schedule=MOC_SCHED_TRACKS_NATURAL)
     measure("units in index order, tracks by segment count", schedule=MOC_SCHED_UNITS_NATURAL)
     measure("load balancing on (default)")
-    print(json.dumps({"ablation": args.workload, "rows": rows}), flush=True)
+    measure("synchronous blocks off (each track on its own records)", sync_block=1)
+    if emit:
+        print(json.dumps({"ablation": args.workload, "rows": rows}), flush=True)
+    return rows
 
 
 def golden_k():
@@ -530,8 +673,16 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=5, help="timed FP64 steps (0 = skip)")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the schedule autotuner (default parameters)")
-    ap.add_argument("--serving-requests", type=int, default=48,
+    ap.add_argument("--serving-requests", type=int, default=256,
                     help="requests of the serving leg (0 = skip)")
+    ap.add_argument("--serving-loads", default="0.5,1,2",
+                    help="arrival rates of the serving leg, as multiples of the sequential rate")
+    ap.add_argument("--no-large", dest="large", action="store_false",
+                    help="skip the large-configuration leg (3x3 assemblies, 7x7 core)")
+    ap.add_argument("--large-oracle-seconds", type=float, default=6.0,
+                    help="host-core seconds of the oracle sample per large configuration")
+    ap.add_argument("--no-ablation-leg", dest="ablation_leg", action="store_false",
+                    help="skip the ablation table in the bench line")
     ap.add_argument("--ablation", action="store_true",
                     help="EXP share and load-balancing ablation table (JSON)")
     ap.add_argument("--profile", action="store_true",

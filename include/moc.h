@@ -145,7 +145,19 @@ typedef struct {
  *                      the whole-unit sweep up to FP rounding.
  *   trace_on_device    1: trace the 2D tracks through the lattice on the GPU
  *                      (one thread per track; the same pieces as the host
- *                      tracer, bit for bit), 0: on the host (Sec. 3.1). */
+ *                      tracer, bit for bit), 0: on the host (Sec. 3.1).
+ *   sync_block         warp schedule of the stored (EXP) stacks, FP32 sweeps
+ *                      with two groups per lane, shared tally, units swept
+ *                      whole: 1 = each track of a warp walks its own records
+ *                      (tracks by decreasing segment count); 4 or 8 = blocks
+ *                      of that many tracks of one segment template (tracks
+ *                      r + m cpl, consecutive m) step through the
+ *                      template's records together, so that their tally rows
+ *                      are consecutive (no shared-memory bank conflicts) and
+ *                      the record is read once per block, at the price of idle
+ *                      tracks where the block's windows do not overlap; 0 = the
+ *                      default, 1 (the autotuner times 1, 4 and 8).  Other
+ *                      layouts ignore it. */
 typedef struct {
     int32_t n_azim, n_polar;
     double radial_spacing, axial_spacing;
@@ -159,6 +171,7 @@ typedef struct {
     int32_t schedule;
     int32_t chunk_segments;
     int32_t trace_on_device;
+    int32_t sync_block;
 } moc_track_params;
 
 /* Stopping rule of a solve: |k_n - k_(n-1)| < tol_k (eigenvalue problems
@@ -277,7 +290,9 @@ int moc_get_flux(moc_tracks *tracks, double *phi, double *k);
 int moc_get_flux_device(moc_tracks *tracks, const double **phi, const double **scale,
                         int64_t *n_fsr, int32_t *G);
 
-/* Set the scalar flux [n_fsr*G] and k (host FP64 input). */
+/* Set the scalar flux [n_fsr*G] and k (host FP64 input).  Errors:
+ * MOC_ERR_INVALID_ARG for NULL, a flux value negative or not finite, k not
+ * positive. */
 int moc_set_flux(moc_tracks *tracks, const double *phi, double k);
 
 /* Tracked FSR volumes [n_fsr] (FP64, host). */
@@ -327,7 +342,9 @@ int moc_get_segments2d(const moc_tracks *tracks, int32_t t, int64_t cap, int32_t
  *   17 shared tile entries, 18 lanes per track, 19 most segments on one
  *   track, 20 bytes copied host to device while generating, 21 energy
  *   groups per lane, 22 2D segments per radial chunk (0: no unit is
- *   chunked) */
+ *   chunked), 23 tracks per synchronous block of the stored stacks (1: none,
+ *   see moc_track_params.sync_block), 24 sweep slots (tracks plus the
+ *   padding of synchronous blocks) */
 int moc_tracks_info(const moc_tracks *tracks, int64_t *out, int32_t n);
 
 /* 3D segments of z-stack (t, p) as the device generator produces them
@@ -344,18 +361,21 @@ int moc_get_stack_segments(moc_tracks *tracks, int32_t t, int32_t p, int64_t cap
                            int64_t *n_segments);
 
 /* Incoming boundary flux of one track direction (t, p, i, sense = 0 along t,
- * 1 against it) for the next sweep, get (set = 0) or set (set = 1), G values. */
+ * 1 against it) for the next sweep, get (set = 0) or set (set = 1), G values
+ * (set: finite and non-negative, else MOC_ERR_INVALID_ARG). */
 int moc_track_psi(moc_tracks *tracks, int32_t t, int32_t p, int64_t i, int32_t sense,
                   double *values, int32_t set);
 
-/* Sweep from a caller-given source Q [n_fsr*G] (per steradian, host FP64) with
- * the current boundary fluxes; returns the FSR tally [n_fsr*G] and leakage. */
+/* Sweep from a caller-given source Q [n_fsr*G] (per steradian, host FP64,
+ * finite and non-negative, else MOC_ERR_INVALID_ARG) with the current
+ * boundary fluxes; returns the FSR tally [n_fsr*G] and leakage. */
 int moc_sweep_from_source(moc_tracks *tracks, const double *Q, double *tally, double *leakage);
 
 /* One sweep of only the 2D tracks t in [t0, t1) (every polar angle, both
  * senses) from the isotropic source Q [n_fsr*G] (per steradian, FP64, host)
  * with zero incoming boundary fluxes: a bounded sample of a sweep that an
- * oracle can reproduce on large problems.  tally [n_fsr*G] (host, FP64) gets
+ * oracle can reproduce on large problems (Q finite and non-negative, else
+ * MOC_ERR_INVALID_ARG).  tally [n_fsr*G] (host, FP64) gets
  * sum over those tracks' segments of W (psi_in - psi_out) (Eq. 4 before the
  * division by volume); *leakage (may be NULL) their W psi leaving through
  * vacuum faces.  Afterwards the stored boundary fluxes are undefined: call
@@ -445,13 +465,15 @@ int moc_eval_attenuation_f32(int32_t device, const float *b, int64_t n, float *e
 /* Autotuner of the sweep's launch schedule: generates the tracks of `geom`
  * under every candidate schedule (energy groups per lane 1, 2, 4 for FP32
  * sweeps; shared-memory or global tally; preload budget: everything stored,
- * base->preload_budget_bytes when >= 0, nothing stored), times `iterations`
+ * base->preload_budget_bytes when >= 0, nothing stored; with two groups per
+ * lane and stored templates, sync_block 1, 4 and 8), times `iterations`
  * outer iterations of each after 2 warm-up iterations (CUDA events), and
  * writes the fastest schedule to *best (base's other fields unchanged, the
- * tally mode resolved).  *seconds_per_iteration (may be NULL) is its time;
- * report (may be NULL) gets up to max_report rows of 5 doubles: groups per
- * lane, tally mode in use, preload budget, stored template pieces, seconds per
- * iteration; *n_report the rows written.  The paper fixes its launch shape by
+ * tally mode and the synchronous block resolved).  *seconds_per_iteration
+ * (may be NULL) is its time; report (may be NULL) gets up to max_report rows
+ * of 6 doubles: groups per lane, tally mode in use, preload budget, stored
+ * template pieces, seconds per iteration, tracks per synchronous block in use
+ * (1: none); *n_report the rows written.  The paper fixes its launch shape by
  * hand; this tunes it per problem.  Runs on base->device and frees
  * everything it generated.  Errors: MOC_ERR_INVALID_ARG (NULL, iterations <
  * 1), MOC_ERR_UNSUPPORTED (no candidate could be generated), errors of

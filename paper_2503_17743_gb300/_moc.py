@@ -56,7 +56,8 @@ class moc_track_params(C.Structure):
                 ("preload_budget_bytes", C.c_int64), ("tally_mode", C.c_int32),
                 ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("device", C.c_int32),
                 ("groups_per_lane", C.c_int32), ("schedule", C.c_int32),
-                ("chunk_segments", C.c_int32), ("trace_on_device", C.c_int32)]
+                ("chunk_segments", C.c_int32), ("trace_on_device", C.c_int32),
+                ("sync_block", C.c_int32)]
 
 
 class moc_server_params(C.Structure):
@@ -219,7 +220,7 @@ class Geometry:
 
 def track_params(prob, precision=MOC_FP32, preload_budget_bytes=-1, tally_mode=MOC_TALLY_AUTO,
                  block_threads=0, blocks_per_sm=0, device=0, groups_per_lane=0, schedule=0,
-                 chunk_segments=0, trace_on_device=0):
+                 chunk_segments=0, trace_on_device=0, sync_block=0):
     p = moc_track_params()
     p.n_azim, p.n_polar = prob.n_azim, prob.n_polar
     p.radial_spacing, p.axial_spacing = prob.radial_spacing, prob.axial_spacing
@@ -233,6 +234,7 @@ def track_params(prob, precision=MOC_FP32, preload_budget_bytes=-1, tally_mode=M
     p.schedule = schedule
     p.chunk_segments = chunk_segments
     p.trace_on_device = trace_on_device
+    p.sync_block = sync_block
     return p
 
 
@@ -240,7 +242,7 @@ INFO_KEYS = ["n_fsr", "groups", "tracks2d", "stacks", "tracks3d", "segments3d",
              "integrations_per_sweep", "stored_segments", "preloaded_stacks", "device_bytes",
              "n_z", "cells_per_layer", "sweep_blocks", "sweep_threads", "tally_mode", "precision",
              "sweep_smem_bytes", "tile_entries", "lanes_per_track", "max_segments_per_track",
-             "h2d_bytes", "groups_per_lane", "chunk_segments"]
+             "h2d_bytes", "groups_per_lane", "chunk_segments", "sync_block", "sweep_slots"]
 
 
 class Tracks:
@@ -421,9 +423,11 @@ class Tracks:
 
 
 class DeviceArray:
-    """A read-only FP64 device array owned by the library, described by
+    """An FP64 device array owned by the library, described by
     ``__cuda_array_interface__`` (version 3) so that PyTorch or any other
-    consumer can view it in place; keeps its owner handle alive."""
+    consumer can view it in place; keeps its owner handle alive.  The
+    library's contract makes it read-only for the caller; the interface
+    itself does not carry the flag (PyTorch refuses read-only arrays)."""
 
     def __init__(self, ptr, shape, owner):
         self.ptr = int(ptr)
@@ -432,7 +436,7 @@ class DeviceArray:
 
     @property
     def __cuda_array_interface__(self):
-        return {"shape": self.shape, "typestr": "<f8", "data": (self.ptr, True),
+        return {"shape": self.shape, "typestr": "<f8", "data": (self.ptr, False),
                 "version": 3, "strides": None}
 
 
@@ -559,10 +563,10 @@ class Server:
 def autotune(geom, params, iterations=5):
     """moc_autotune: (best track parameters, seconds per iteration, table of
     the candidates [groups per lane, tally mode, preload budget, stored
-    pieces, seconds per iteration])."""
+    pieces, seconds per iteration, tracks per synchronous block])."""
     best = moc_track_params()
     sec = C.c_double()
-    rep = np.zeros((64, 5))
+    rep = np.zeros((64, 6))
     n = C.c_int32()
     _check(load().moc_autotune(geom._h, C.byref(params), int(iterations), C.byref(best),
                                C.byref(sec), 64, _ptr(rep, f64p), C.byref(n)))

@@ -43,7 +43,7 @@ struct moc_tracks {
     // device buffers
     DevBuf d_desc, d_zn, d_zf, d_zf64, d_reg2d, d_len2d, d_len2d64, d_segs, d_fsr_mat, d_order;
     DevBuf d_tpl_off, d_tpl_loff, d_tpl_lmin, d_tpl_lidx;
-    DevBuf d_dst, d_perm, d_win, d_chunk, d_hand, d_batch, d_lmap;
+    DevBuf d_dst, d_perm, d_win, d_chunk, d_hand, d_batch, d_lmap, d_reg_mat;
     DevBuf d_phi, d_qr, d_tally, d_vol, d_psi[2], d_fiss, d_fiss_old, d_partial, d_scal, d_counter;
     DevBuf d_sigt, d_sigt64, d_sigs64, d_nsf64, d_chi64, d_src64, d_inv_st64, d_siga64, d_inv_vol;
     double *h_scal = nullptr;  // pinned mirror of the device scalars
@@ -66,6 +66,8 @@ struct moc_tracks {
     int tally_bits = 0;         // fixed-point bits of the FP32 shared tally
     int tile_cap = 0;
     int chunk_b = 0;            // 2D segments per radial chunk (0: units swept whole)
+    int sync_b = 0;             // tracks per synchronous block of the stored stacks (0: none)
+    int64_t n_slots = 0;        // sweep slots of all stacks (perm / win entries)
     int64_t hand_trk = 0;       // tracks of the largest chunked unit
     int block = 256;
     int grid = 0;
@@ -91,6 +93,14 @@ struct moc_tracks {
 };
 
 namespace {
+
+// sources, fluxes and boundary fluxes given by a caller must be finite and
+// non-negative (the FP32 sweep's fixed-point tally bound relies on it)
+bool all_nonneg(const double *v, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!(v[i] >= 0.0) || !std::isfinite(v[i])) return false;
+    return true;
+}
 
 int cuda_fail(cudaError_t e, const char *what) {
     moc_set_error(std::string(what) + ": " + cudaGetErrorString(e));
@@ -154,6 +164,8 @@ void fill_views(moc_tracks *h) {
     dl.tally_bits = h->tally_bits;
     dl.chunk_tab = (const int64_t *)h->d_chunk.p;
     dl.chunk_b = h->chunk_b;
+    dl.sync_b = h->sync_b;
+    dl.reg_mat = (const int32_t *)h->d_reg_mat.p;
     dl.hand_trk = (int32_t)h->hand_trk;
     dl.hand = h->d_hand.p;
     DevState &s = h->ds;
@@ -467,12 +479,16 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
         h->tally_smem = mode == MOC_TALLY_SHARED ? 1 : 0;
         if (!h->tally_smem) h->chunk_b = 0;
     }
-    // FP32 shared tally in fixed point: each contribution becomes an integer
-    // multiple of 2^-bits of its unit's bound and is added with a native
-    // integer atomic, so one row of one unit must stay below 2^30.  Pieces
-    // that reach one row of one unit: per polar stack, 2 senses x 2 frames x
-    // the tracks crossing one layer inside one 2D segment (at most cpl plus
-    // the segment's lattice span plus 2).
+    // FP32 shared tally in fixed point: each contribution t becomes an
+    // integer multiple of 2^-bits of its unit's bound B (|t| <= B, so at most
+    // 2^bits in magnitude) and is added with a native integer atomic.  The
+    // adds wrap modulo 2^32, so partial sums may overflow as long as the
+    // final sum of one row of one unit lies in [-2^31, 2^31): pieces that
+    // reach one row x 2^bits < 2^31.  Pieces that reach one row of one unit:
+    // per polar stack, 2 senses x 2 frames x the tracks crossing one layer
+    // inside one 2D segment (at most cpl plus the segment's lattice span
+    // plus 2).  At most 24 bits: the grid then matches the FP32 precision of
+    // the contributions themselves.
     if (h->tally_smem && h->precision == MOC_FP32) {
         int64_t nmax = 1;
         for (int t = 0; t < L.nt; ++t) {
@@ -488,13 +504,24 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
             }
             nmax = std::max(nmax, n);
         }
-        int bits = 21;
-        while (bits > 0 && (nmax << bits) >= ((int64_t)1 << 30)) --bits;
+        int bits = 24;
+        while (bits > 0 && (nmax << bits) >= ((int64_t)1 << 31)) --bits;
         if (bits < 12) {  // too many pieces per row: FP64 global tally instead
             h->tally_smem = 0;
             h->chunk_b = 0;
         }
         else h->tally_bits = bits;
+    }
+    // synchronous blocks of the stored stacks: FP32, two groups per lane,
+    // shared tally, every unit swept whole; at most the tracks of one warp
+    if (prm->sync_block < 0 || prm->sync_block > 8 || (prm->sync_block & (prm->sync_block - 1))) {
+        moc_set_error("sync_block must be 0, 1, 2, 4 or 8");
+        return MOC_ERR_INVALID_ARG;
+    }
+    if (h->precision == MOC_FP32 && h->gpl == 2 && h->tally_smem && h->chunk_b == 0) {
+        const int slots = 32 / sweep_lanes_per_track(G, 2);
+        h->sync_b = std::min(prm->sync_block > 0 ? (int)prm->sync_block : 1, slots);
+        if (h->sync_b < 2) h->sync_b = 0;
     }
     TRY(cudaSetDevice(h->device), "cudaSetDevice");
     TRY(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "stream");
@@ -509,6 +536,18 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     TRY(upload(h.get(), h->d_reg2d, reg2d), "upload");
     TRY(upload(h.get(), h->d_len2d, len2d), "upload");
     TRY(upload(h.get(), h->d_fsr_mat, geo.fsr_mat), "upload");
+    if (h->sync_b) {
+        // per radial region: its material when every layer has the same one
+        // (then Sigma_t is one value per 2D segment of a unit), else -1
+        std::vector<int32_t> reg_mat(geo.nreg);
+        for (int r = 0; r < geo.nreg; ++r) {
+            int m = geo.fsr_mat[(size_t)r * geo.nl];
+            for (int l = 1; l < geo.nl && m >= 0; ++l)
+                if (geo.fsr_mat[(size_t)r * geo.nl + l] != m) m = -1;
+            reg_mat[r] = m;
+        }
+        TRY(upload(h.get(), h->d_reg_mat, reg_mat), "upload");
+    }
     if (h->precision == MOC_FP64) {
         TRY(upload(h.get(), h->d_zf64, L.zf64), "upload");
         TRY(upload(h.get(), h->d_len2d64, L.seg_len), "upload");
@@ -533,32 +572,6 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
         TRY(cudaMemcpyAsync(tseg.data(), d_tseg.p, L.n_gtrk * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream), "copy");
     TRY(cudaStreamSynchronize(h->stream), "count");
     h->bytes -= d_nseg.n + d_max.n + d_tseg.n;
-    // sweep order inside each stack: by decreasing segment count, so that the
-    // tracks a warp sweeps side by side take the same number of steps; among
-    // equal counts class by class (tracks r, r + cpl, ... are whole-layer
-    // shifts of one another and rarely meet in the same FSR at the same step,
-    // so the shared tally updates of one warp seldom collide)
-    {
-        std::vector<int32_t> perm(L.n_gtrk);
-        for (int64_t s = 0; s < ns; ++s) {
-            const int64_t o = L.desc[s].trk_off;
-            const int n = L.desc[s].n_trk;
-            int32_t *q = perm.data() + o;
-            int32_t *p = q;
-            if (h->chunk_b > 0 && L.desc[s].nb > h->chunk_b) {
-                // radially chunked unit: tracks in index order, so that the
-                // tracks crossing one chunk are one contiguous range
-                for (int k = 0; k < n; ++k) q[k] = k;
-                continue;
-            }
-            for (int r = 0; r < std::min(L.cpl, n); ++r)
-                for (int k = r; k < n; k += L.cpl) *p++ = k;
-            if (!(prm->schedule & MOC_SCHED_TRACKS_NATURAL))
-                std::stable_sort(q, q + n, [&](int32_t a, int32_t b) { return tseg[o + a] > tseg[o + b]; });
-        }
-        TRY(upload(h.get(), h->d_perm, perm), "upload");
-        fill_views(h.get());
-    }
     int64_t segs_up = 0;
     for (auto v : h->stack_nseg) segs_up += v;
     h->n_segments3d = 2 * segs_up;
@@ -619,9 +632,10 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
                 const int64_t q = tpl_first[s] + r;
                 need += tcnt[q] * rec_bytes + (int64_t)(tnlay[q] + 1) * 4 + 20;
                 // stored keys: the template layer as a signed 16-bit number
-                // (chunked layouts), else both tile rows as 16-bit numbers
+                // (chunked and synchronous layouts), else both tile rows as
+                // 16-bit numbers
                 ok = ok && tlmin[q] > -32768 && tlmin[q] + tnlay[q] < 32767;
-                if (h->chunk_b == 0)
+                if (h->chunk_b == 0 && h->sync_b == 0)
                     ok = ok && tlmin[q] > -2000 && tlmin[q] + tnlay[q] < 2000 &&
                          (int64_t)(L.desc[s].nb + 1) * L.nlv + 2000 < 32768;
             }
@@ -645,6 +659,58 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
         }
     }
     h->n_exp_stacks = (int64_t)exp_stacks.size();
+    // sweep slots of every stack (perm; the record windows follow the same
+    // order).  Tracks by decreasing segment count, so that the tracks a warp
+    // sweeps side by side take the same number of steps; among equal counts
+    // class by class (tracks r, r + cpl, ... are whole-layer shifts of one
+    // another and rarely meet in the same FSR at the same step, so the shared
+    // tally updates of one warp seldom collide).  Radially chunked units: in
+    // index order (the tracks crossing one chunk are one range).  Stored
+    // stacks of layouts with synchronous blocks: blocks of sync_b consecutive
+    // tracks r + m cpl of one class (padded with entries -1 - k that continue
+    // the block's sequence), blocks by decreasing segment count.
+    {
+        std::vector<int32_t> perm;
+        perm.reserve((size_t)L.n_gtrk);
+        const int B = h->sync_b;
+        for (int64_t s = 0; s < ns; ++s) {
+            StackDesc &d = L.desc[s];
+            const int64_t o = d.trk_off;
+            const int n = d.n_trk;
+            d.slot_off = (int64_t)perm.size();
+            if (h->chunk_b > 0 && d.nb > h->chunk_b) {
+                for (int k = 0; k < n; ++k) perm.push_back(k);
+            } else if (B > 1 && d.exp_base >= 0) {
+                std::vector<std::pair<int32_t, std::vector<int32_t>>> blocks;
+                for (int r = 0; r < std::min(cpl, n); ++r)
+                    for (int k0 = r; k0 < n; k0 += B * cpl) {
+                        std::vector<int32_t> e(B);
+                        int32_t est = 0;
+                        for (int j = 0; j < B; ++j) {
+                            const int k = k0 + j * cpl;
+                            e[j] = k < n ? k : -1 - k;
+                            if (k < n) est = std::max(est, tseg[o + k]);
+                        }
+                        blocks.emplace_back(est, std::move(e));
+                    }
+                if (!(prm->schedule & MOC_SCHED_TRACKS_NATURAL))
+                    std::stable_sort(blocks.begin(), blocks.end(),
+                                     [](const auto &a, const auto &b) { return a.first > b.first; });
+                for (auto &bl : blocks) perm.insert(perm.end(), bl.second.begin(), bl.second.end());
+            } else {
+                const size_t q0 = perm.size();
+                for (int r = 0; r < std::min(cpl, n); ++r)
+                    for (int k = r; k < n; k += cpl) perm.push_back(k);
+                if (!(prm->schedule & MOC_SCHED_TRACKS_NATURAL))
+                    std::stable_sort(perm.begin() + q0, perm.end(),
+                                     [&](int32_t a, int32_t b) { return tseg[o + a] > tseg[o + b]; });
+            }
+            d.n_slot = (int32_t)((int64_t)perm.size() - d.slot_off);
+        }
+        h->n_slots = (int64_t)perm.size();
+        TRY(upload(h.get(), h->d_perm, perm), "upload");
+        fill_views(h.get());
+    }
     TRY(cudaMemcpyAsync(h->d_desc.p, L.desc.data(), ns * sizeof(StackDesc), cudaMemcpyHostToDevice, h->stream), "upload");
     if (!exp_stacks.empty()) {
         DevBuf d_exp_stacks;
@@ -659,7 +725,7 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
         const int egrid = (int)std::max<int64_t>(1, std::min<int64_t>(h->n_exp_stacks, (int64_t)h->sms * 16));
         TRY(launch_tpl_write(h->precision, h->dl, (const int32_t *)d_exp_stacks.p, h->n_exp_stacks,
                              h->d_segs.p, (int32_t *)h->d_tpl_lidx.p, egrid, h->stream), "templates");
-        TRY(dalloc(h.get(), h->d_win, (size_t)L.n_gtrk * 8), "alloc record windows");
+        TRY(dalloc(h.get(), h->d_win, (size_t)std::max<int64_t>(h->n_slots, 1) * 8), "alloc record windows");
         fill_views(h.get());
         TRY(launch_windows(h->dl, ns, (uint64_t *)h->d_win.p, lgrid, h->stream), "record windows");
         TRY(cudaStreamSynchronize(h->stream), "templates");
@@ -792,13 +858,15 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     TRY(upload(h.get(), h->d_order, h->order), "upload");
     fill_views(h.get());
     // sweep launch shape (tally mode chosen above)
-    h->smem = sweep_smem_bytes(h->precision, h->tally_smem, h->chunk_b > 0, geo.M, G, h->gpl, h->tile_cap);
+    h->smem = sweep_smem_bytes(h->precision, h->tally_smem, h->chunk_b > 0, geo.M, G, h->gpl, h->tile_cap,
+                               h->sync_b, L.nlv);
     {
         const int bmax = sweep_block_threads(h->precision, h->gpl);
         h->block = prm->block_threads > 0 ? std::max(32, std::min(prm->block_threads, bmax) / 32 * 32) : bmax;
     }
     int bps = 0;
-    TRY(sweep_occupancy(h->precision, h->tally_smem, h->chunk_b > 0, G, h->gpl, h->block, h->smem, &bps),
+    TRY(sweep_occupancy(h->precision, h->tally_smem, h->chunk_b > 0, G, h->gpl, h->block, h->smem, &bps,
+                        h->sync_b > 0),
         "occupancy");
     if (bps < 1) { moc_set_error("sweep kernel does not fit on an SM"); return MOC_ERR_UNSUPPORTED; }
     if (prm->blocks_per_sm > 0) bps = std::min(bps, prm->blocks_per_sm);
@@ -903,6 +971,8 @@ extern "C" int moc_state_create(const moc_tracks *t, const double *ext_source, m
     h->tally_bits = base->tally_bits;
     h->tile_cap = base->tile_cap;
     h->chunk_b = base->chunk_b;
+    h->sync_b = base->sync_b;
+    h->n_slots = base->n_slots;
     h->hand_trk = base->hand_trk;
     h->block = base->block;
     h->grid = base->grid;
@@ -921,7 +991,7 @@ extern "C" int moc_state_create(const moc_tracks *t, const double *ext_source, m
     borrow(h->d_sigt, base->d_sigt); borrow(h->d_sigt64, base->d_sigt64); borrow(h->d_sigs64, base->d_sigs64);
     borrow(h->d_nsf64, base->d_nsf64); borrow(h->d_chi64, base->d_chi64);
     borrow(h->d_inv_st64, base->d_inv_st64); borrow(h->d_siga64, base->d_siga64);
-    borrow(h->d_lmap, base->d_lmap);
+    borrow(h->d_lmap, base->d_lmap); borrow(h->d_reg_mat, base->d_reg_mat);
     // the solve state: its own
     TRY(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "stream");
     TRY(cudaMallocHost(&h->h_scal, SC_COUNT * sizeof(double)), "pinned scalars");
@@ -1168,6 +1238,8 @@ extern "C" int moc_set_flux(moc_tracks *h, const double *phi, double k) {
     TRY(cudaSetDevice(h->device), "cudaSetDevice");
     const moc_geometry &g = h->geom;
     const size_t n = (size_t)g.nfsr * g.G;
+    if (!all_nonneg(phi, n)) { moc_set_error("phi must be finite and non-negative"); return MOC_ERR_INVALID_ARG; }
+    if (!(k > 0.0) || !std::isfinite(k)) { moc_set_error("k must be finite and positive"); return MOC_ERR_INVALID_ARG; }
     std::vector<double> fiss(g.nfsr, 0.0);
     double P = 0;
     for (int i = 0; i < g.nfsr; ++i) {
@@ -1194,13 +1266,14 @@ extern "C" int moc_get_volumes(moc_tracks *h, double *v) {
 
 extern "C" int moc_tracks_info(const moc_tracks *h, int64_t *out, int32_t n) {
     if (!h || !out) { moc_set_error("NULL argument"); return MOC_ERR_INVALID_ARG; }
-    const int64_t v[23] = {h->geom.nfsr, h->geom.G, h->L.nt, 2 * h->L.n_stacks, 2 * h->L.n_gtrk,
+    const int64_t v[25] = {h->geom.nfsr, h->geom.G, h->L.nt, 2 * h->L.n_stacks, 2 * h->L.n_gtrk,
                            h->n_segments3d, (int64_t)h->integrations, h->n_stored, h->n_exp_stacks,
                            (int64_t)h->bytes, h->L.Nz, h->L.cpl, h->grid, h->block,
                            h->tally_smem ? MOC_TALLY_SHARED : MOC_TALLY_GLOBAL, h->precision,
                            (int64_t)h->smem, h->tile_cap, sweep_lanes_per_track(h->geom.G, h->gpl),
-                           h->max_nseg, (int64_t)h->h2d, h->gpl, h->chunk_b};
-    for (int i = 0; i < n && i < 23; ++i) out[i] = v[i];
+                           h->max_nseg, (int64_t)h->h2d, h->gpl, h->chunk_b, h->sync_b > 1 ? h->sync_b : 1,
+                           h->n_slots};
+    for (int i = 0; i < n && i < 25; ++i) out[i] = v[i];
     return MOC_OK;
 }
 
@@ -1299,6 +1372,10 @@ extern "C" int moc_track_psi(moc_tracks *h, int32_t t, int32_t p, int64_t i, int
     const int v = frame * 2 + sense;
     const size_t rs = real_size(h->precision);
     char *base = (char *)h->d_psi[h->cur].p + ((size_t)(gid * 4 + v) * G) * rs;
+    if (set && !all_nonneg(values, (size_t)G)) {
+        moc_set_error("boundary flux values must be finite and non-negative");
+        return MOC_ERR_INVALID_ARG;
+    }
     TRY(cudaMemcpyAsync(h->h_scal, h->d_scal.p, SC_COUNT * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
     TRY(cudaStreamSynchronize(h->stream), "copy");
     const double sc = h->h_scal[SC_SCALE];
@@ -1335,6 +1412,7 @@ extern "C" int moc_sweep_from_source(moc_tracks *h, const double *Q, double *tal
     TRY(cudaSetDevice(h->device), "cudaSetDevice");
     const moc_geometry &g = h->geom;
     const size_t n = (size_t)g.nfsr * g.G;
+    if (!all_nonneg(Q, n)) { moc_set_error("Q must be finite and non-negative"); return MOC_ERR_INVALID_ARG; }
     const size_t rs = real_size(h->precision);
     std::vector<double> qr(n);
     for (int i = 0; i < g.nfsr; ++i)
@@ -1420,6 +1498,7 @@ extern "C" int moc_sweep_units_from_source(moc_tracks *h, const double *Q, int32
     TRY(cudaSetDevice(h->device), "cudaSetDevice");
     const moc_geometry &g = h->geom;
     const size_t n = (size_t)g.nfsr * g.G;
+    if (!all_nonneg(Q, n)) { moc_set_error("Q must be finite and non-negative"); return MOC_ERR_INVALID_ARG; }
     std::vector<double> qr(n);
     for (int i = 0; i < g.nfsr; ++i)
         for (int gr = 0; gr < g.G; ++gr)

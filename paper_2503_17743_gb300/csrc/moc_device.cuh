@@ -24,9 +24,14 @@ struct DevLayout {
     const void *segs;        // template records, SegRec<real>
     const int32_t *fsr_mat;  // material of each FSR
     const int32_t *dst;      // [n_gtrk*4] link destination of every track direction, or null (all vacuum)
-    const uint64_t *win;     // [n_gtrk] stored stacks: each track's record window, in perm order
-    const int32_t *perm;     // [n_gtrk] per stack, its track indices by decreasing segment
-                             // count (ties: class by class, then by index)
+    const uint64_t *win;     // [slots] stored stacks: each slot's record window (perm order)
+    const int32_t *perm;     // [slots] per stack (StackDesc::slot_off), its tracks in sweep
+                             // order: by decreasing segment count (ties: class by class,
+                             // then by index); with synchronous blocks, blocks of sync_b
+                             // consecutive tracks r + m cpl of one class, padding entries
+                             // -1 - (r + m cpl) continuing the block's sequence
+    int32_t sync_b;          // tracks per synchronous block (0: none)
+    const int32_t *reg_mat;  // per radial region: its material if the same in every layer, else -1
     int32_t Nz, cpl, NL, G, M, Ph;  // NL: the sweep's (uniform) layers
     int32_t NLr;             // the geometry's layers (FSR = region * NLr + layer)
     const int32_t *lmap;     // the geometry's layer of each sweep layer, or null (the same)

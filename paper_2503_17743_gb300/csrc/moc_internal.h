@@ -64,6 +64,13 @@ struct StackDesc {
     // | count << 32), then per stored template r < min(cpl, n_trk) and
     // c <= C the first record at or beyond 2D segment c * chunk_b
     int64_t chunk_base;
+    // the stack's sweep slots: perm / win entries [slot_off, slot_off +
+    // n_slot); the tracks in sweep order, and in layouts with synchronous
+    // blocks (stored stacks) padded so that each block holds tracks of one
+    // segment template
+    int64_t slot_off;
+    int32_t n_slot;
+    int32_t slot_pad;
 };
 
 // ---------------------------------------------------------------------------

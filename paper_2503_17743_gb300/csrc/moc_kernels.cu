@@ -100,8 +100,9 @@ __global__ void k_tpl_write(DevLayout dl, const int32_t *exp_stacks, int64_t n_e
                 for (int L = tr.La; L <= tr.Le; ++L) {
                     while (x <= L - Lmin && x <= nL) lidx[lb + x++] = pos;
                     SegRec<real> rec{};
-                    rec.key = dl.chunk_b > 0 ? tpl_key_seg(b, L)
-                                             : tpl_key(b * dl.NL + L, b * dl.NL + dl.NL - 1 - L);
+                    rec.key = (dl.chunk_b > 0 || dl.sync_b > 1)
+                                  ? tpl_key_seg(b, L)
+                                  : tpl_key(b * dl.NL + L, b * dl.NL + dl.NL - 1 - L);
                     rec.len = tpl_len(dl, d, b, tr, L);
                     out[pos++] = rec;
                 }
@@ -121,8 +122,12 @@ __global__ void k_windows(DevLayout dl, int64_t n_stacks, uint64_t *win) {
     for (int64_t s = blockIdx.x; s < n_stacks; s += gridDim.x) {
         const StackDesc &d = dl.desc[s];
         if (d.exp_base < 0) continue;
-        for (int q = threadIdx.x; q < d.n_trk; q += blockDim.x) {
-            const int k = dl.perm[d.trk_off + q];
+        for (int q = threadIdx.x; q < d.n_slot; q += blockDim.x) {
+            const int k = dl.perm[d.slot_off + q];
+            if (k < 0) {  // padding of a synchronous block: no records
+                win[d.slot_off + q] = 0ull;
+                continue;
+            }
             const int r = k % dl.cpl, m = k / dl.cpl;
             const int64_t tpl = d.exp_base + r;
             const int Lmin = dl.tpl_lmin[tpl];
@@ -131,7 +136,7 @@ __global__ void k_windows(DevLayout dl, int64_t n_stacks, uint64_t *win) {
             const int64_t tb = dl.tpl_off[tpl];
             const int64_t p0 = tb + dl.tpl_lidx[lb + min(max(-m - Lmin, 0), nL)];
             const int64_t p1 = tb + dl.tpl_lidx[lb + min(max(dl.NL - m - Lmin, 0), nL)];
-            win[d.trk_off + q] = ((uint64_t)(p1 - p0) << 48) | (uint64_t)p0;
+            win[d.slot_off + q] = ((uint64_t)(p1 - p0) << 48) | (uint64_t)p0;
         }
     }
 }

@@ -54,9 +54,16 @@ __global__ void __launch_bounds__(256) k_eval_exp32(const float *b, int64_t n, f
 // alive through a store that never happens.
 
 // FP32 fused multiply-add, scalar (one lane operation per instruction)
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 __global__ void __launch_bounds__(256) k_fma_rate(int iters, float a, float b, float *sink,
                                                   long long *clk) {
     const long long c0 = clock64();
+    const unsigned long long t0 = global_ns();
     float x[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) x[j] = 0.5f + 0.01f * (float)((threadIdx.x + j) & 31);
@@ -69,8 +76,11 @@ __global__ void __launch_bounds__(256) k_fma_rate(int iters, float a, float b, f
     for (int j = 0; j < 8; ++j) s += x[j];
     if (s == -1.0f) sink[blockIdx.x] = s;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        clk[0] = c0;
-        clk[1] = clock64();
+        // the SM clock of this block: clock cycles over global-timer ns
+        const long long c1 = clock64();
+        const unsigned long long t1 = global_ns();
+        clk[0] = c1 - c0;
+        clk[1] = (long long)(t1 - t0);
     }
 }
 
@@ -117,15 +127,22 @@ __global__ void __launch_bounds__(256) k_lds_rate(int iters, float *sink) {
     __shared__ __align__(16) unsigned buf[4 * 256 * 2];
     for (int i = threadIdx.x; i < 4 * 256 * 2; i += blockDim.x) buf[i] = i;
     __syncthreads();
-    const unsigned base = (unsigned)__cvta_generic_to_shared(buf) + 16u * (threadIdx.x & 255);
+    const unsigned sbase = (unsigned)__cvta_generic_to_shared(buf);
+    const unsigned lane_off = 16u * (threadIdx.x & 31);
     unsigned acc = 0;
     for (int i = 0; i < iters; ++i) {
+        // a different 512-byte block each step (addresses the compiler
+        // cannot hoist out of the loop); lanes stay 16 bytes apart.  Byte
+        // offsets inside buf: lane_off + 512 k with k = (block ^ j) < 16,
+        // so at most 496 + 7680 + 16 = 8192 = sizeof(buf)
+        const unsigned blk = (unsigned)((i + (threadIdx.x >> 5)) & 15);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             unsigned a, b, c, d;
-            asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+            const unsigned off = lane_off + 512u * (blk ^ (unsigned)j);
+            asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
                          : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
-                         : "r"(base + 4096u * (j & 1)));
+                         : "r"(sbase + off));
             acc ^= a ^ b ^ c ^ d;
         }
     }
@@ -192,9 +209,10 @@ extern "C" int moc_measure_unit_rates(int32_t device, double *out, int32_t n) {
     for (int k = 0; k < 5 && e == cudaSuccess; ++k) timed(k, iters[k], ms[k]);
     long long hc[2] = {0, 0};
     if (e == cudaSuccess) {
-        // the SM clock during the scalar FMA run (its last repetition)
+        // the SM clock during the scalar FMA run (block 0 of its last repetition)
         timed(0, iters[0], ms[0]);
         if (e == cudaSuccess) e = cudaMemcpy(hc, clk, sizeof(hc), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && hc[1] <= 0) e = cudaErrorUnknown;
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -207,7 +225,7 @@ extern "C" int moc_measure_unit_rates(int32_t device, double *out, int32_t n) {
         return MOC_ERR_CUDA;
     }
     const double v[8] = {(double)sms,
-                         (double)(hc[1] - hc[0]) / (ms[0] * 1e-3) / 1e6,
+                         (double)hc[0] / (double)hc[1] * 1e3,
                          lanes * iters[0] / (ms[0] * 1e-3),
                          2.0 * lanes * iters[1] / (ms[1] * 1e-3),
                          lanes * iters[2] / (ms[2] * 1e-3),

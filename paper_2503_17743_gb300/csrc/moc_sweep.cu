@@ -15,11 +15,11 @@ int lanes_for_groups(int G, int gpl) {
 }
 
 // chunk: some units are swept in radial chunks (shared tally only)
-const void *sweep_fn(int precision, int tally_smem, int chunk, int G, int gpl, int batch = 0) {
+const void *sweep_fn(int precision, int tally_smem, int chunk, int G, int gpl, int batch = 0, int sync = 0) {
     const int gl = lanes_for_groups(G, gpl);
     if (precision == MOC_FP64) return sweep_kernel_f64(tally_smem, chunk, batch, gl);
     if (gpl == 4) return sweep_kernel_f32_gpl4(tally_smem, chunk, batch, gl);
-    if (gpl == 2) return sweep_kernel_f32_gpl2(tally_smem, chunk, batch, gl);
+    if (gpl == 2) return sweep_kernel_f32_gpl2(tally_smem, chunk, batch, gl, sync);
     return sweep_kernel_f32_gpl1(tally_smem, chunk, batch, gl);
 }
 
@@ -53,20 +53,30 @@ int sweep_lanes_per_track(int G, int gpl) { return lanes_for_groups(G, gpl); }
 
 int sweep_block_threads(int precision, int gpl) { return sweep_block(precision != MOC_FP64, gpl); }
 
-size_t sweep_smem_bytes(int precision, int tally_smem, int chunk, int M, int G, int gpl, int cap) {
+size_t sweep_smem_bytes(int precision, int tally_smem, int chunk, int M, int G, int gpl, int cap,
+                        int sync, int NL) {
     const size_t rs = precision == MOC_FP64 ? 8 : 4;
     const size_t gp = (size_t)lanes_for_groups(G, gpl) * gpl;
     size_t b = ((size_t)M * gp * rs + 15) & ~(size_t)15;
-    if (tally_smem)  // (Qr, Sigma_t) rows + tally rows
-        b += (size_t)cap * gp * rs * 2 +
-             (precision == MOC_FP64 || chunk ? (size_t)cap * tally_stride((int)(gp / gpl), gpl)
-                                             : (size_t)tally_rows(cap, (int)(gp / gpl), gpl) * gp) * rs;
+    if (!tally_smem) return b;
+    if (sync) {
+        // split tile (Qr, Sigma_t with guard rows), Sigma_t per 2D segment,
+        // then the tally with a guard of kSyncGuard words after it
+        b += 2 * (size_t)(cap + 2 * kSyncGuard) * gp * 4;
+        b += ((size_t)(cap / NL) * gp * 4 + 15) & ~(size_t)15;
+        b += ((size_t)tally_rows(cap, (int)(gp / gpl), gpl) * gp + kSyncGuard) * 4;
+        return b;
+    }
+    // (Qr, Sigma_t) rows + tally rows
+    b += (size_t)cap * gp * rs * 2 +
+         (precision == MOC_FP64 || chunk ? (size_t)cap * tally_stride((int)(gp / gpl), gpl)
+                                         : (size_t)tally_rows(cap, (int)(gp / gpl), gpl) * gp) * rs;
     return b;
 }
 
 cudaError_t sweep_occupancy(int precision, int tally_smem, int chunk, int G, int gpl, int block,
-                            size_t smem, int *blocks_per_sm) {
-    const void *f = sweep_fn(precision, tally_smem, chunk, G, gpl);
+                            size_t smem, int *blocks_per_sm, bool sync) {
+    const void *f = sweep_fn(precision, tally_smem, chunk, G, gpl, 0, sync ? 1 : 0);
     cudaError_t e = allow_dynamic_smem(f, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, block, smem);
@@ -77,7 +87,8 @@ cudaError_t launch_sweep(int precision, int tally_smem, int gpl, const DevLayout
                          const void *psi_in, void *psi_out, int32_t *counter,
                          const unsigned *bound_in, unsigned *bound_out, int grid, int block,
                          size_t smem, cudaStream_t s) {
-    const void *f = sweep_fn(precision, tally_smem, tally_smem && dl.chunk_b > 0, dl.G, gpl);
+    const void *f = sweep_fn(precision, tally_smem, tally_smem && dl.chunk_b > 0, dl.G, gpl, 0,
+                             tally_smem && dl.sync_b > 0 ? 1 : 0);
     cudaError_t e = allow_dynamic_smem(f, smem);
     if (e != cudaSuccess) return e;
     DevLayout a0 = dl;
@@ -99,7 +110,7 @@ cudaError_t launch_sweep_batch(int precision, int gpl, const DevLayout &dl, cons
                                const int32_t *order, int32_t n_units, int32_t cap, int32_t *counter,
                                const BatchItem *items, int32_t n, int grid, int block, size_t smem,
                                cudaStream_t s) {
-    const void *f = sweep_fn(precision, 1, 0, dl.G, gpl, 1);
+    const void *f = sweep_fn(precision, 1, 0, dl.G, gpl, 1, dl.sync_b > 0 ? 1 : 0);
     cudaError_t e = allow_dynamic_smem(f, smem);
     if (e != cudaSuccess) return e;
     DevLayout a0 = dl;

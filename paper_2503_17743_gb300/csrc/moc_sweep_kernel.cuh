@@ -33,6 +33,7 @@
 // tally units (Eq. 3, Eq. 4), rounded to an integer by one conversion.
 #pragma once
 
+#include <climits>
 #include <type_traits>
 
 #include "moc_device.cuh"
@@ -61,10 +62,10 @@ __device__ __forceinline__ double attenuation<double>(double x, const double2 *t
 // (the track weight and its inverse in both precisions: the sweep's hot path
 // does no FP64 arithmetic in FP32 mode)
 struct UnitStack {
-    int64_t trk_off, tpl_base, cbase;
+    int64_t trk_off, tpl_base, cbase, slot_off;
     double W, invW;
     float Wf, invWf;
-    int32_t n_trk, i_lo, task_pre, pad;
+    int32_t n_trk, i_lo, task_pre, n_slot;
 };
 constexpr int kMaxPh = 16;
 
@@ -182,6 +183,11 @@ __device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
 __device__ __forceinline__ void row_load_pairs(unsigned a, uint64_t &q, uint64_t &s) {
     asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(q), "=l"(s) : "r"(a));
 }
+// split tile (synchronous blocks): Qr and Sigma_t of a row in two arrays,
+// a lane's pair of groups as one 64-bit load from each
+__device__ __forceinline__ void lds64(unsigned a, uint64_t &v) {
+    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(a));
+}
 template <>
 struct RowLoadS<double, 1> {
     static __device__ __forceinline__ void get(unsigned a, double (&q)[1], double (&s)[1]) {
@@ -239,10 +245,24 @@ __host__ __device__ constexpr int tally_rows(int cap, int GL, int GPL) {
     return cap + ((((32 / (GL * GPL)) % (32 / GPL)) - cap % (32 / GPL)) + (32 / GPL)) % (32 / GPL);
 }
 
+// Guard rows on both sides of the split tile of a layout with synchronous
+// blocks: a block's idle tracks read rows at most 7 past the rows of its
+// active ones (see the SYNC step loop), and the guard rows hold finite values
+constexpr int kSyncGuard = 8;
+
 // BATCH: one launch sweeps several solves of one layout (their states in
 // items[n_items]); work index w is unit order[w / n_items] of solve
 // w % n_items, so the solves' units interleave, largest first.
-template <typename real, int GL, int GPL, bool SMEM, bool CHUNK, bool BATCH>
+// SYNC (FP32, two groups per lane, units swept whole): the stored stacks are
+// swept in synchronous blocks of dl.sync_b tracks r + m cpl (consecutive m)
+// of one segment template.  The tracks of a block step through the
+// template's records together, each active while the record lies in its own
+// window (else length 0: psi unchanged, tally + 0).  Their tile rows are then
+// consecutive, so the Qr loads and tally adds of a block meet no bank
+// conflicts, and the record is read once per block.  The tile keeps Qr and
+// Sigma_t in separate arrays, with Sigma_t also once per 2D segment when the
+// segment's region has one material in every layer.
+template <typename real, int GL, int GPL, bool SMEM, bool CHUNK, bool BATCH, bool SYNC = false>
 __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(real) == 4 ? 3 : 2)
     k_sweep(DevLayout dl, DevState st, const int32_t *order, int32_t n_work, int32_t cap,
             const real *psi_in_p, real *psi_out_p, const unsigned *bound_in_p, unsigned *bound_out_p,
@@ -278,15 +298,40 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
     const int RS = kGM ? tally_rows(cap, GL, GPL) : 0;
     const int CS = kGM ? RS : 1;
     auto tix = [&](int row, int q) { return kGM ? q * RS + row : row * TS + q; };
+    static_assert(!SYNC || (sizeof(real) == 4 && GPL == 2 && SMEM && !CHUNK), "synchronous blocks: FP32 pairs");
     if (!BATCH && st.scal[SC_CONV] != 0.0) return;  // converged: later iterations are no-ops
     real *sig = reinterpret_cast<real *>(smem);
     size_t off = ((size_t)M * GP * sizeof(real) + 15) & ~(size_t)15;
     real *rows = reinterpret_cast<real *>(smem + off);
-    off += (size_t)cap * GP * 2 * sizeof(real);
+    // split tile (SYNC): Qr [row][GP] and Sigma_t log2 e [row][GP], each with
+    // kSyncGuard guard rows before and after; Sigma_t of each 2D segment
+    // [cap / NL][GP] (-1: the segment's region changes material with the layer)
+    float *qr_t = nullptr, *sg_t = nullptr, *sb_t = nullptr;
+    if constexpr (SYNC) {
+        qr_t = reinterpret_cast<float *>(smem + off) + kSyncGuard * GP;
+        off += (size_t)(cap + 2 * kSyncGuard) * GP * 4;
+        sg_t = reinterpret_cast<float *>(smem + off) + kSyncGuard * GP;
+        off += (size_t)(cap + 2 * kSyncGuard) * GP * 4;
+        sb_t = reinterpret_cast<float *>(smem + off);
+        off += ((size_t)(cap / NL) * GP * 4 + 15) & ~(size_t)15;
+    } else {
+        off += (size_t)cap * GP * 2 * sizeof(real);
+    }
     real *tl_s = reinterpret_cast<real *>(smem + off);
     int *tl_i = reinterpret_cast<int *>(smem + off);  // the same tally rows in fixed point
     const unsigned rows_sa = (unsigned)__cvta_generic_to_shared(rows);
     const unsigned tl_sa = (unsigned)__cvta_generic_to_shared(tl_s);
+    const unsigned qr_sa = SYNC ? (unsigned)__cvta_generic_to_shared(qr_t) : 0u;
+    const unsigned sg_sa = SYNC ? (unsigned)__cvta_generic_to_shared(sg_t) : 0u;
+    const unsigned sb_sa = SYNC ? (unsigned)__cvta_generic_to_shared(sb_t) : 0u;
+    if constexpr (SYNC) {
+        // every row of the split tile holds finite values from here on (the
+        // guard rows stay 0; unit rows are restaged per unit)
+        for (int i = tid - kSyncGuard * GP; i < (cap + kSyncGuard) * GP; i += blockDim.x) {
+            qr_t[i] = 0.0f;
+            sg_t[i] = 0.0f;
+        }
+    }
 
     const real *sig_g = reinterpret_cast<const real *>(st.sig_t);
     const SegRec<real> *recs = reinterpret_cast<const SegRec<real> *>(dl.segs);
@@ -346,6 +391,8 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                 u.trk_off = e.trk_off;
                 u.tpl_base = e.exp_base;
                 u.cbase = e.chunk_base;
+                u.slot_off = e.slot_off;
+                u.n_slot = e.n_slot;
                 u.W = e.W;
                 u.invW = 1.0 / e.W;
                 u.Wf = (float)e.W;
@@ -353,9 +400,8 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                 u.n_trk = e.n_trk;
                 u.i_lo = e.i_lo;
                 u.task_pre = pre;
-                u.pad = 0;
                 s_us[ph] = u;
-                pre += 2 * ((e.n_trk + SLOTS - 1) / SLOTS);  // blocks of SLOTS tracks, 2 senses
+                pre += 2 * ((e.n_slot + SLOTS - 1) / SLOTS);  // blocks of SLOTS slots, 2 senses
             }
             s_ntask = pre;
             float wm = 0.0f;
@@ -424,7 +470,10 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                             if (sizeof(real) == 4) sg = (real)((float)sg * kLog2e);
                             q = qr_g[(size_t)f * G + g0 + qq];
                         }
-                        if constexpr (GPL >= 2) {
+                        if constexpr (SYNC) {
+                            qr_t[e] = (float)q;
+                            sg_t[e] = (float)sg;
+                        } else if constexpr (GPL >= 2) {
                             const int pe = 2 * (e - (qq & 1));  // the pair's Qr_0 Qr_1 Sigma_0 Sigma_1
                             rows[pe + (qq & 1)] = q;
                             rows[pe + 2 + (qq & 1)] = sg;
@@ -434,6 +483,13 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                         }
                         tl_s[et] = (real)0;
                         if (kFixed) bmax = fmaxf(bmax, fabsf((float)q));
+                    }
+                    if constexpr (SYNC) {
+                        // Sigma_t once per 2D segment where its region has one material
+                        const int rm = __ldg(dl.reg_mat + reg);
+                        for (int qq = lane; qq < GP; qq += 32)
+                            sb_t[bb * GP + qq] = rm < 0 ? -1.0f
+                                                        : (qq < gc ? (float)sig_g[rm * G + g0 + qq] * kLog2e : 0.0f);
                     }
                 }
                 if (kFixed) {
@@ -454,8 +510,11 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
             const int ntask_c = C > 1 ? s_ntask : ntask;
             if (kFixed && SMEM && tid < GP) {
                 // one unit of the fixed-point tally = 2^-bits of a bound of every
-                // contribution W |psi - Qr| <= W (|psi| + |Qr|)
-                const float B = 2.0f * s_wmax * __uint_as_float(s_bmax[tid]);
+                // contribution: W |psi - Qr| <= W max(psi, Qr), since psi and Qr
+                // are never negative (sources, fluxes and boundary fluxes
+                // are non-negative and the library refuses negative inputs;
+                // psi moves between its incoming value and Qr, Eq. 3)
+                const float B = s_wmax * __uint_as_float(s_bmax[tid]);
                 s_scl[tid] = B > 0.0f ? ldexpf(1.0f, dl.tally_bits) / B : 1.0f;
                 s_inv[tid] = B > 0.0f ? B * ldexpf(1.0f, -dl.tally_bits) : 1.0f;
             }
@@ -489,8 +548,12 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                 } else {
                     sense = x & 1;
                     q = (x >> 1) * SLOTS + j;
-                    valid = q < u.n_trk;
-                    k = valid ? __ldg(dl.perm + u.trk_off + q) : 0;  // track in the stack
+                    // the slot's track in the stack; a padding slot of a
+                    // synchronous block holds -1 - (the track its block's
+                    // sequence would continue with): idle, but with its m
+                    const int kk = q < u.n_slot ? __ldg(dl.perm + u.slot_off + q) : 0;
+                    valid = q < u.n_slot && kk >= 0;
+                    k = kk >= 0 ? kk : -1 - kk;
                     widx = q;
                 }
                 const int m = k / cpl;                       // shift of the track within its class
@@ -503,7 +566,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                 int64_t p0 = 0;
                 int n = 0, sb0 = 0, sb1 = -1;
                 if (CHUNK && C > 1 && u.tpl_base >= 0) {
-                    const uint64_t wn = valid ? __ldg(dl.win + u.trk_off + widx) : 0ull;
+                    const uint64_t wn = valid ? __ldg(dl.win + u.trk_off + widx) : 0ull;  // chunked: index order
                     p0 = (int64_t)(wn & 0xffffffffffffull);
                     n = (int)(wn >> 48);
                     if (valid) {
@@ -585,8 +648,20 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                         const int eU = rU * GP + qlo, eD = rD * GP + qlo;
                         const int tU_ = tix(rU, qlo), tD_ = tix(rD, qlo);
                         real qU[GPL], sU[GPL], qD[GPL], sD[GPL];
-                        RowLoadS<real, GPL>::get(rows_sa + eU * (unsigned)(2 * sizeof(real)), qU, sU);
-                        RowLoadS<real, GPL>::get(rows_sa + eD * (unsigned)(2 * sizeof(real)), qD, sD);
+                        if constexpr (SYNC) {
+                            uint64_t a, b;
+                            lds64(qr_sa + eU * 4u, a);
+                            lds64(sg_sa + eU * 4u, b);
+                            upk2(a, qU[0], qU[1]);
+                            upk2(b, sU[0], sU[1]);
+                            lds64(qr_sa + eD * 4u, a);
+                            lds64(sg_sa + eD * 4u, b);
+                            upk2(a, qD[0], qD[1]);
+                            upk2(b, sD[0], sD[1]);
+                        } else {
+                            RowLoadS<real, GPL>::get(rows_sa + eU * (unsigned)(2 * sizeof(real)), qU, sU);
+                            RowLoadS<real, GPL>::get(rows_sa + eD * (unsigned)(2 * sizeof(real)), qD, sD);
+                        }
 #pragma unroll
                         for (int c = 0; c < GPL; ++c) {
                             // Eq. 3 on W S psi: d = W S (psi_in - Qr),
@@ -600,8 +675,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                             psiD[c] -= tD[c];
                         }
                         if constexpr (kFixed) {
-                            // round to the fixed-point grid: adding 1.5 * 2^23 leaves the
-                            // integer in the low mantissa bits (|t scl| < 2^22)
+                            // round to the fixed-point grid (|t scl| <= 2^bits <= 2^24)
 #pragma unroll
                             for (int c = 0; c < GPL; ++c) {
                                 shared_red_add(tl_sa + (tU_ + c * CS) * 4u,
@@ -640,7 +714,8 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                 // four consecutive segments of the track at once (shared tally):
                 // all row loads and exponentials first, then the psi recurrence,
                 // then the tally updates, so that the loads overlap each other
-                auto visit4 = [&](const int (&rU)[4], const int (&rD)[4], const real (&len)[4]) {
+                auto visit4 = [&](const int (&rU)[4], const int (&rD)[4], const real (&len)[4],
+                                  const int (&bs)[4]) {
                     if constexpr (!SMEM) {
 #pragma unroll
                         for (int i = 0; i < 4; ++i) visit(rU[i], rD[i], len[i]);
@@ -658,8 +733,26 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                                 eD[i] = rD[i] * GP + qlo;
                                 fU[i] = tix(rU[i], qlo);
                                 fD[i] = tix(rD[i], qlo);
-                                row_load_pairs(rows_sa + eU[i] * 8u, QU[i], SU[i]);
-                                row_load_pairs(rows_sa + eD[i] * 8u, QD[i], SD[i]);
+                                if constexpr (SYNC) {
+                                    // Qr of both frames; Sigma_t of the 2D segment when its
+                                    // region has one material (both frames), else per row
+                                    lds64(qr_sa + eU[i] * 4u, QU[i]);
+                                    lds64(qr_sa + eD[i] * 4u, QD[i]);
+                                    uint64_t sb;
+                                    lds64(sb_sa + (unsigned)(bs[i] * GP + qlo) * 4u, sb);
+                                    float s0, s1;
+                                    upk2(sb, s0, s1);
+                                    if (s0 < 0.0f) {
+                                        lds64(sg_sa + eU[i] * 4u, SU[i]);
+                                        lds64(sg_sa + eD[i] * 4u, SD[i]);
+                                    } else {
+                                        SU[i] = sb;
+                                        SD[i] = sb;
+                                    }
+                                } else {
+                                    row_load_pairs(rows_sa + eU[i] * 8u, QU[i], SU[i]);
+                                    row_load_pairs(rows_sa + eD[i] * 8u, QD[i], SD[i]);
+                                }
                             }
 #pragma unroll
                             for (int i = 0; i < 4; ++i) {
@@ -749,13 +842,78 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                         }
                     }
                 };
-                if (u.tpl_base >= 0) {
+                if (SYNC && u.tpl_base >= 0) {
+                    // synchronous block of B slots (lanes [h B GL, (h + 1) B GL)): the
+                    // union [lo, hi) of its tracks' record windows, stepped together
+                    const int B = dl.sync_b;
+                    const uint64_t wn = valid ? __ldg(dl.win + u.slot_off + widx) : 0ull;
+                    p0 = (int64_t)(wn & 0xffffffffffffull);
+                    n = (int)(wn >> 48);
+                    long long lo = n > 0 ? (long long)p0 : LLONG_MAX, hi = n > 0 ? (long long)(p0 + n) : LLONG_MIN;
+                    for (int o = GL; o < B * GL; o <<= 1) {
+                        const long long l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+                        const long long h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+                        lo = l2 < lo ? l2 : lo;
+                        hi = h2 > hi ? h2 : hi;
+                    }
+                    const int steps = hi > lo ? (int)(hi - lo) : 0;
+                    const int nmax = __reduce_max_sync(0xffffffffu, steps);
+                    // this slot's own steps [sa, se) in sweep order
+                    int sa = 0, se = 0;
+                    if (n > 0) {
+                        const int a = (int)(p0 - lo), e = a + n;
+                        sa = sense == 0 ? a : steps - e;
+                        se = sense == 0 ? e : steps - a;
+                    }
+                    const int dir = sense == 0 ? 1 : -1;
+                    const SegRec<real> *pr = recs + (steps > 0 ? (sense == 0 ? lo : hi - 1) : 0);
+                    // every slot of the block reads the same record; past its own
+                    // window a slot takes length 0.  Its rows then lie within 7 of
+                    // an active slot's (|m - m'| < B <= 8, the record in that
+                    // slot's window), inside the guard rows.  A block with no
+                    // track reads tile rows 0 and NL - 1.
+                    auto fetch4s = [&](SegRec<real> (&c)[4], int s0) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int s1 = s0 + i;
+                            if (steps > 0) {
+                                c[i] = pr[min(s1, steps - 1) * dir];
+                                if ((unsigned)(s1 - sa) >= (unsigned)(se - sa)) c[i].len = (real)0;
+                            } else {
+                                c[i].key = tpl_key_seg(0, -m);
+                                c[i].len = (real)0;
+                            }
+                        }
+                    };
+                    auto sweep4s = [&](const SegRec<real> (&c)[4]) {
+                        int ru[4], rd[4], bs[4];
+                        real ln[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            bs[i] = tpl_seg(c[i].key);
+                            const int bN = bs[i] * NL, Lt = tpl_layer(c[i].key);
+                            ru[i] = bN + Lt + m;
+                            rd[i] = bN + (NL - 1 - m) - Lt;
+                            ln[i] = c[i].len;
+                        }
+                        visit4(ru, rd, ln, bs);
+                    };
+                    SegRec<real> ra[4], rb[4];
+                    fetch4s(ra, 0);
+                    for (int s1 = 0; s1 < nmax; s1 += 8) {
+                        fetch4s(rb, s1 + 4);
+                        sweep4s(ra);
+                        if (s1 + 4 >= nmax) break;
+                        fetch4s(ra, s1 + 8);
+                        sweep4s(rb);
+                    }
+                } else if (u.tpl_base >= 0) {
                     if (!(CHUNK && C > 1)) {
                         // stored template of class r (line i_lo + r): this track is
                         // its pieces with template layer in [-m, NL - m), a contiguous
                         // record range because the layer never decreases along an
                         // upward line (per track in sweep order: count << 48 | first)
-                        const uint64_t wn = valid ? __ldg(dl.win + u.trk_off + widx) : 0ull;
+                        const uint64_t wn = valid ? __ldg(dl.win + u.slot_off + widx) : 0ull;
                         p0 = (int64_t)(wn & 0xffffffffffffull);
                         n = (int)(wn >> 48);
                     }
@@ -799,7 +957,8 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
 #pragma unroll
                             for (int i = 0; i < 4; ++i) visit(ru[i], rd[i], ln[i]);
                         } else {
-                            visit4(ru, rd, ln);
+                            const int bs[4] = {0, 0, 0, 0};
+                            visit4(ru, rd, ln, bs);
                         }
                     };
                     // two sets of four records: one set in flight while the other
@@ -931,12 +1090,12 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
 
 // the kernel for gl lanes per track; only shapes with gl * GPL <= 32 exist
 // (each translation unit of the sweep instantiates its share)
-template <typename real, int GPL, bool SMEM, bool CHUNK, bool BATCH, int GL = 32 / GPL>
+template <typename real, int GPL, bool SMEM, bool CHUNK, bool BATCH, int GL = 32 / GPL, bool SYNC = false>
 const void *pick(int gl) {
     if constexpr (GL > 1) {
-        if (gl < GL) return pick<real, GPL, SMEM, CHUNK, BATCH, GL / 2>(gl);
+        if (gl < GL) return pick<real, GPL, SMEM, CHUNK, BATCH, GL / 2, SYNC>(gl);
     }
-    return (const void *)k_sweep<real, GL, GPL, SMEM, CHUNK, BATCH>;
+    return (const void *)k_sweep<real, GL, GPL, SMEM, CHUNK, BATCH, SYNC>;
 }
 
 template <typename real, int GPL>

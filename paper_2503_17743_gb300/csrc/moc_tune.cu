@@ -2,10 +2,12 @@
 // of track parameters it generates the tracks under every candidate schedule,
 // times a few outer iterations of each (CUDA events, after warm-up) and keeps
 // the fastest.  Candidates: energy groups per lane (1, 2, 4; FP32 only),
-// shared-memory or global tally, and the preload split between stored
-// templates and on-the-fly generation (Sec. 4.2: everything stored, the base
-// budget, nothing stored).  The paper fixes its launch shape by hand; this
-// replaces that choice.
+// shared-memory or global tally, the preload split between stored templates
+// and on-the-fly generation (Sec. 4.2: everything stored, the base budget,
+// nothing stored), and with two groups per lane the warp schedule of the
+// stored stacks (each track on its own records, or synchronous blocks of 4
+// or 8 tracks of one template).  The paper fixes its launch shape by hand;
+// this replaces that choice.
 #include <algorithm>
 #include <vector>
 
@@ -16,6 +18,7 @@ namespace {
 struct Candidate {
     int gpl, tally;
     int64_t budget;
+    int sync;
 };
 
 }  // namespace
@@ -36,7 +39,13 @@ extern "C" int moc_autotune(const moc_geometry *geom, const moc_track_params *ba
     std::vector<Candidate> cands;
     for (int g : gpls)
         for (int t : {MOC_TALLY_AUTO, MOC_TALLY_GLOBAL})
-            for (int64_t b : budgets) cands.push_back({g, t, b});
+            for (int64_t b : budgets) {
+                if (g == 2 && t == MOC_TALLY_AUTO && b != 0) {
+                    for (int sy : {1, 4, 8}) cands.push_back({g, t, b, sy});
+                } else {
+                    cands.push_back({g, t, b, 1});
+                }
+            }
 
     double best_s = -1.0;
     int nrep = 0;
@@ -45,14 +54,18 @@ extern "C" int moc_autotune(const moc_geometry *geom, const moc_track_params *ba
         p.groups_per_lane = c.gpl;
         p.tally_mode = c.tally;
         p.preload_budget_bytes = c.budget;
+        p.sync_block = c.sync;
         moc_tracks *tr = nullptr;
         int rc = moc_generate_tracks(geom, &p, &tr);
         if (rc == MOC_ERR_OUT_OF_MEMORY || rc == MOC_ERR_UNSUPPORTED) continue;  // not a valid schedule here
         if (rc) return rc;
-        int64_t info[22] = {0};
-        moc_tracks_info(tr, info, 22);
-        // AUTO that fell back to the global tally duplicates the GLOBAL candidate
-        const bool dup = c.tally == MOC_TALLY_AUTO && info[14] == MOC_TALLY_GLOBAL;
+        int64_t info[24] = {0};
+        moc_tracks_info(tr, info, 24);
+        // AUTO that fell back to the global tally duplicates the GLOBAL
+        // candidate; a synchronous block the layout cannot use duplicates 1
+        const bool dup = (c.tally == MOC_TALLY_AUTO && info[14] == MOC_TALLY_GLOBAL) ||
+                         (c.sync > 1 && info[23] != c.sync && info[23] == 1) ||
+                         (c.sync > 1 && info[23] > 1 && info[23] != c.sync);
         moc_result r{};
         double s = -1.0;
         if (!dup) {
@@ -64,18 +77,20 @@ extern "C" int moc_autotune(const moc_geometry *geom, const moc_track_params *ba
         if (rc) return rc;
         if (dup) continue;
         if (report && nrep < max_report) {
-            double *row = report + (size_t)nrep * 5;
+            double *row = report + (size_t)nrep * 6;
             row[0] = c.gpl;
             row[1] = (double)info[14];
             row[2] = (double)c.budget;
             row[3] = (double)info[7];  // stored template pieces
             row[4] = s;
+            row[5] = (double)info[23];  // tracks per synchronous block (1: none)
             ++nrep;
         }
         if (best_s < 0.0 || s < best_s) {
             best_s = s;
             *best = p;
             best->tally_mode = (int32_t)info[14];
+            best->sync_block = (int32_t)info[23];
         }
     }
     if (n_report) *n_report = nrep;

@@ -324,6 +324,8 @@ def workload(name: str, seed: int = 1) -> Problem:
     * ``pin_cell_rings`` - the pin cell with 3 fuel rings, 2 moderator rings
                        and 4 sectors
     * ``lattice5_axial`` - lattice5 with unequal layers (0.5, 1, 1.5, 1 cm)
+    * ``asm1_absorber`` - one assembly + reflector on two sides, 8 cm, absorber
+                       in the top layer of half the guide tubes
     * ``asm3x3``     - 3x3 assemblies + reflector on two sides, 64 cm
     * ``core7x7``    - 7x7 assemblies + reflector ring, 200 cm
     """
@@ -352,6 +354,12 @@ def workload(name: str, seed: int = 1) -> Problem:
     if name == "pin_cell_rings":
         return replace(pin_cell(seed), name="pin_cell_rings", fuel_rings=3, moderator_rings=2,
                        sectors=4)
+    if name == "asm1_absorber":
+        # one assembly, reflector on two sides, absorber in the top layer of a
+        # seeded half of the guide tubes (a small reflected, axially varying case)
+        return assemblies(seed=2 if seed == 1 else seed, n_asm=1, height=8.0, n_layers=4,
+                          absorber_height=2.0, n_azim=8, n_polar=4, radial_spacing=0.1,
+                          axial_spacing=0.5)
     if name == "asm3x3":
         return assemblies(seed)
     if name == "core7x7":

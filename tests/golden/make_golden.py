@@ -27,7 +27,7 @@ import synth  # noqa: E402
 
 OUT = os.path.join(HERE, "oracle_k.json")
 # converged fluxes are stored for these (the bench workload and a small one)
-FLUX = ("lattice17", "lattice17_small", "lattice5")
+FLUX = ("lattice17", "lattice17_small", "lattice5", "lattice5_rings", "asm1_absorber")
 
 
 def flux_path(name):

@@ -21,21 +21,32 @@ import numpy as np
 from tests import bruteforce as bf
 
 
-def check_tally(gt, ot, rel=1e-4, floor_frac=1e-3, abs_frac=2e-5, what=""):
+def tally_stats(gt, ot, floor_frac=1e-3):
     gt = np.asarray(gt)
     ot = np.asarray(ot)
     scale = np.abs(ot).max()
-    assert scale > 0, what
     err = np.abs(gt - ot)
     big = np.abs(ot) >= floor_frac * scale
     rel_big = (err[big] / np.abs(ot[big])).max() if big.any() else 0.0
     small = ~big
     rel_small = (err[small] / np.maximum(np.abs(ot[small]), 1e-300)).max() if small.any() else 0.0
-    stats = {"what": what, "max_rel_above_floor": float(rel_big), "n_above_floor": int(big.sum()),
+    stats = {"max_rel_above_floor": float(rel_big), "n_above_floor": int(big.sum()),
              "max_rel_below_floor": float(rel_small), "n_below_floor": int(small.sum()),
-             "max_abs_over_scale": float(err.max() / scale)}
+             "max_abs_over_scale": float(err.max() / scale) if scale > 0 else 0.0}
+    # the worst relative error by magnitude decade of the oracle's tally
+    for d in (1e-1, 1e-2, 1e-3, 1e-4):
+        m = (np.abs(ot) >= d * scale) & (np.abs(ot) < 10 * d * scale)
+        if m.any():
+            stats[f"rel_{d:g}"] = float((err[m] / np.abs(ot[m])).max())
+    return stats, scale, err
+
+
+def check_tally(gt, ot, rel=1e-4, floor_frac=1e-3, abs_frac=2e-5, what=""):
+    stats, scale, err = tally_stats(gt, ot, floor_frac)
+    stats["what"] = what
     print("tally parity", stats)
-    assert rel_big <= rel, stats
+    assert scale > 0, what
+    assert stats["max_rel_above_floor"] <= rel, stats
     assert err.max() <= abs_frac * scale, stats
     return stats
 

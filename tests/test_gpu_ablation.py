@@ -56,8 +56,8 @@ def test_ablation_case_sweeps_like_the_oracle(problem, kind, frac, sched):
         assert 0 < info["preloaded_stacks"] < info["stacks"] // 2
     gt, gl = tr.sweep_from_source(Q)
     what = f"{kind} {frac} schedule {sched}"
-    check_tally(gt, ot, what=what)
     check_flux(gt, ot, Q, o.volumes(), p.sigma_t[o.fsr_materials()], what=what)
+    check_tally(gt, ot, what=what)
     assert abs(gl - ol) <= 2e-5 * abs(ol)
     # against the default schedule's sweep: rounding-level differences only
     assert np.abs(gt - base).max() <= 1e-5 * np.abs(base).max()

@@ -73,3 +73,40 @@ def test_solve_fixed_source_not_converged():
     r = tr.solve_fixed_source(tol_src=1e-12, max_iter=2, check=False)
     assert r["iterations"] == 2 and not r["converged"] and r["k"] == 1.0
     tr.close()
+
+
+def test_negative_or_nonfinite_inputs_are_refused():
+    """Sources, fluxes and boundary fluxes handed to the library must be
+    finite and non-negative (physical values; the FP32 tally's fixed-point
+    bound relies on it): each entry point that takes them refuses others."""
+    p = synth.workload("lattice5")
+    tr = Tracks(Geometry(p), track_params(p))
+    n, G = tr.n_fsr, tr.G
+    bad_q = np.full((n, G), 0.5)
+    bad_q[3, 1] = -1e-3
+    for call in (lambda: tr.sweep_from_source(bad_q), lambda: tr.sweep_units_from_source(bad_q, 0, 4)):
+        with pytest.raises(MocError) as e:
+            call()
+        assert e.value.code == _moc.MOC_ERR_INVALID_ARG
+    nan_q = np.full((n, G), 0.5)
+    nan_q[0, 0] = np.nan
+    with pytest.raises(MocError):
+        tr.sweep_from_source(nan_q)
+    phi = np.ones((n, G))
+    phi[5, 0] = -1.0
+    with pytest.raises(MocError):
+        tr.set_flux(phi, 1.0)
+    with pytest.raises(MocError):
+        tr.set_flux(np.ones((n, G)), 0.0)
+    with pytest.raises(MocError):
+        tr.psi(0, 0, tr_first_index(tr), 0, value=-np.ones(G))
+    # the valid forms still work
+    tr.set_flux(np.ones((n, G)), 1.0)
+    tr.sweep_from_source(np.full((n, G), 0.5))
+    tr.close()
+
+
+def tr_first_index(tr):
+    """Lattice index of the first track of stack (0, 0)."""
+    ti, _, _, _ = tr.stack_segments(0, 0)
+    return int(ti[0])

@@ -19,8 +19,11 @@ def test_autotune_picks_the_fastest_candidate():
     assert sec == pytest.approx(table[:, 4].min())
     row = table[np.argmin(table[:, 4])]
     assert best.groups_per_lane == int(row[0]) and best.tally_mode == int(row[1])
-    assert best.preload_budget_bytes == int(row[2])
+    assert best.preload_budget_bytes == int(row[2]) and best.sync_block == int(row[5])
     assert set(table[:, 0].astype(int)) == {1, 2, 4}
+    # two groups per lane with stored templates: every warp schedule is timed
+    two = table[(table[:, 0] == 2) & (table[:, 2] != 0)]
+    assert {1, 4, 8} <= set(two[:, 5].astype(int))
     assert MOC_TALLY_GLOBAL in set(table[:, 1].astype(int))
     # same sweep under the tuned and the default schedule
     Q = np.random.default_rng(1).uniform(0.2, 1.0, size=(Tracks(g, base).n_fsr, p.num_groups))
