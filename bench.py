@@ -524,7 +524,7 @@ def run_profile_driver(args):
     prob = synth.workload(args.workload)
     tr = Tracks(Geometry(prob), track_params(prob, preload_budget_bytes=args.budget,
                                              groups_per_lane=args.gpl,
-                                             chunk_segments=args.chunk,
+                                             chunk_segments=args.chunk, sync_block=args.sync,
                                              precision=MOC_FP64 if args.fp64 else MOC_FP32))
     tr.iterate(3, use_graph=False)
     r = tr.iterate(2, use_graph=False)
@@ -693,6 +693,8 @@ def main():
     ap.add_argument("--fp64", action="store_true", help="FP64 sweeps (--profile)")
     ap.add_argument("--chunk", type=int, default=0,
                     help="2D segments per radial chunk, 0 = automatic (--profile)")
+    ap.add_argument("--sync", type=int, default=0,
+                    help="tracks per synchronous block, 0 = default (--profile)")
     args = ap.parse_args()
     if args.profile:
         run_profile_driver(args)

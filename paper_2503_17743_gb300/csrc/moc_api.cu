@@ -162,6 +162,7 @@ void fill_views(moc_tracks *h) {
     dl.bc_zmax = h->geom.bc[FACE_ZMAX];
     dl.n_slots = h->L.n_gtrk * 4;
     dl.tally_bits = h->tally_bits;
+    dl.tally3 = (h->precision == MOC_FP32 && h->tally_smem) ? 1 : 0;
     dl.chunk_tab = (const int64_t *)h->d_chunk.p;
     dl.chunk_b = h->chunk_b;
     dl.sync_b = h->sync_b;
@@ -202,30 +203,23 @@ cudaError_t set_scalar(moc_tracks *h, int slot, double v) {
                            h->stream);
 }
 
-// Per psi buffer p, one small block of d_counter: the work counter of the
-// sweep that writes buffer p, then the bound of |psi| over buffer p per group
-// (float bits; written by that sweep, read by the next one to size its
-// fixed-point tally)
-size_t sweep_block_bytes(const moc_tracks *h) { return 16 + (((size_t)h->geom.G * 4 + 15) & ~(size_t)15); }
+// Per psi buffer p, one 16-byte block of d_counter: the work counter of the
+// sweep that writes buffer p
+size_t sweep_block_bytes(const moc_tracks *) { return 16; }
 int32_t *sweep_counter(moc_tracks *h, int p) {
     return (int32_t *)((char *)h->d_counter.p + (size_t)p * sweep_block_bytes(h));
 }
-unsigned *psi_bound(moc_tracks *h, int p) { return (unsigned *)((char *)sweep_counter(h, p) + 16); }
 
-// one sweep into the other psi buffer (no source update, no finalize).
-// zero_bound = false: the output bound was zeroed by the source kernel just
-// before (outer iterations, where a converged solve's iterations are no-ops
-// and the bound of a psi buffer that is not rewritten must survive)
-cudaError_t enqueue_sweep(moc_tracks *h, cudaStream_t s, int cur, bool zero_bound = true) {
+// one sweep into the other psi buffer (no source update, no finalize)
+cudaError_t enqueue_sweep(moc_tracks *h, cudaStream_t s, int cur) {
     const int out = h->has_psi ? 1 - cur : 0;
-    cudaError_t e = cudaMemsetAsync(sweep_counter(h, out), 0, zero_bound ? sweep_block_bytes(h) : 4, s);
+    cudaError_t e = cudaMemsetAsync(sweep_counter(h, out), 0, 4, s);
     if (e != cudaSuccess) return e;
     const void *pin = h->has_psi ? h->d_psi[cur].p : nullptr;
     void *pout = h->has_psi ? h->d_psi[1 - cur].p : nullptr;
     return launch_sweep(h->precision, h->tally_smem, h->gpl, h->dl, h->ds, (const int32_t *)h->d_order.p,
-                        (int32_t)h->order.size(), h->tile_cap, pin, pout, sweep_counter(h, out),
-                        h->has_psi ? psi_bound(h, cur) : nullptr, h->has_psi ? psi_bound(h, out) : nullptr,
-                        h->grid, h->block, h->smem, s);
+                        (int32_t)h->order.size(), h->tile_cap, pin, pout, sweep_counter(h, out), h->grid,
+                        h->block, h->smem, s);
 }
 
 cudaError_t enqueue_finalize(moc_tracks *h, cudaStream_t s) {
@@ -238,10 +232,9 @@ cudaError_t enqueue_finalize(moc_tracks *h, cudaStream_t s) {
 // one outer iteration: source, sweep, flux update, k / residual; the scalars
 // are copied to the pinned host mirror at the end
 cudaError_t enqueue_iteration(moc_tracks *h, cudaStream_t s, int cur) {
-    cudaError_t e = launch_source(h->precision, h->dl, h->ds, h->geom.nfsr, h->red_grid, s,
-                                  h->has_psi ? psi_bound(h, 1 - cur) : nullptr);
+    cudaError_t e = launch_source(h->precision, h->dl, h->ds, h->geom.nfsr, h->red_grid, s);
     if (e != cudaSuccess) return e;
-    e = enqueue_sweep(h, s, cur, false);
+    e = enqueue_sweep(h, s, cur);
     if (e != cudaSuccess) return e;
     e = enqueue_finalize(h, s);
     if (e != cudaSuccess) return e;
@@ -281,14 +274,39 @@ void fill_result(moc_tracks *h, moc_result *r, double seconds, int iters) {
     r->converged = s[SC_CONV] != 0.0 ? 1 : 0;
 }
 
-// the sweep sets SC_ERR when a shared tally update gave up after its retry
-// limit (never expected: it needs that many consecutive lost races)
+// the sweep sets SC_ERR to 1 when a shared tally update gave up after its
+// retry limit (never expected: it needs that many consecutive lost races), to
+// 2 when a unit's tally scale lay outside the fixed-point tally's range
 int check_sweep_flag(moc_tracks *h) {
+    if (h->h_scal[SC_ERR] == 2.0) {
+        moc_set_error("sweep: a tally contribution beyond 2^51 (fixed-point tally range); results are invalid");
+        return MOC_ERR_CUDA;
+    }
     if (h->h_scal[SC_ERR] != 0.0) {
         moc_set_error("sweep: a shared tally update exceeded its retry limit; results are invalid");
         return MOC_ERR_CUDA;
     }
     return MOC_OK;
+}
+
+// bytes of one FSR-group's tally entry: the three 64-bit fixed-point words
+// of FP32 shared-tally layouts, else FP64
+size_t tally_entry_bytes(const moc_tracks *h) {
+    return (h->precision == MOC_FP32 && h->tally_smem) ? 24 : 8;
+}
+
+// the tally [n] copied to host FP64 values (synchronises the stream)
+cudaError_t tally_to_host(moc_tracks *h, double *out, size_t n) {
+    if (tally_entry_bytes(h) == 8) {
+        cudaError_t e = cudaMemcpyAsync(out, h->d_tally.p, n * 8, cudaMemcpyDeviceToHost, h->stream);
+        return e == cudaSuccess ? cudaStreamSynchronize(h->stream) : e;
+    }
+    std::vector<long long> w(3 * n);
+    cudaError_t e = cudaMemcpyAsync(w.data(), h->d_tally.p, n * 24, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return e;
+    for (size_t i = 0; i < n; ++i) out[i] = tally3_value(w[3 * i], w[3 * i + 1], w[3 * i + 2]);
+    return cudaSuccess;
 }
 
 // Runs up to n outer iterations.  With stop_on_conv the scalars are checked
@@ -800,7 +818,7 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     const size_t rs = real_size(h->precision);
     TRY(dalloc(h.get(), h->d_phi, nfg * 8), "alloc flux");
     TRY(dalloc(h.get(), h->d_qr, nfg * rs), "alloc source");
-    TRY(dalloc(h.get(), h->d_tally, nfg * 8), "alloc tally");
+    TRY(dalloc(h.get(), h->d_tally, nfg * tally_entry_bytes(h.get())), "alloc tally");
     TRY(dalloc(h.get(), h->d_vol, (size_t)geo.nfsr * 8), "alloc volumes");
     TRY(dalloc(h.get(), h->d_fiss, (size_t)geo.nfsr * 8), "alloc");
     TRY(dalloc(h.get(), h->d_fiss_old, (size_t)geo.nfsr * 8), "alloc");
@@ -842,11 +860,16 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     init[SC_SCALE] = 1.0;
     init[SC_K] = 1.0;
     TRY(cudaMemcpyAsync(h->d_scal.p, init.data(), SC_COUNT * 8, cudaMemcpyHostToDevice, h->stream), "upload");
-    TRY(cudaMemsetAsync(h->d_vol.p, 0, h->d_vol.n, h->stream), "memset");
-    TRY(launch_volumes(h->precision, h->dl, ns, (double *)h->d_vol.p, lgrid, h->stream), "volumes");
-    h->vol.resize(geo.nfsr);
-    TRY(cudaMemcpyAsync(h->vol.data(), h->d_vol.p, geo.nfsr * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
-    TRY(cudaStreamSynchronize(h->stream), "volumes");
+    {
+        DevBuf d_vacc;  // exact sums, freed once the volumes are read
+        TRY(dalloc(h.get(), d_vacc, (size_t)geo.nfsr * 4 * 8), "alloc volume sums");
+        TRY(launch_volumes(h->precision, h->dl, ns, geo.nfsr, (unsigned long long *)d_vacc.p,
+                           (double *)h->d_vol.p, lgrid, h->stream), "volumes");
+        h->vol.resize(geo.nfsr);
+        TRY(cudaMemcpyAsync(h->vol.data(), h->d_vol.p, geo.nfsr * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
+        TRY(cudaStreamSynchronize(h->stream), "volumes");
+        h->bytes -= d_vacc.n;
+    }
     {
         std::vector<double> inv_vol(geo.nfsr);
         for (int i = 0; i < geo.nfsr; ++i) inv_vol[i] = h->vol[i] > 0.0 ? 1.0 / h->vol[i] : 0.0;
@@ -1000,7 +1023,7 @@ extern "C" int moc_state_create(const moc_tracks *t, const double *ext_source, m
     const size_t nfg = (size_t)h->geom.nfsr * G, rs = real_size(h->precision);
     TRY(dalloc(h.get(), h->d_phi, nfg * 8), "alloc flux");
     TRY(dalloc(h.get(), h->d_qr, nfg * rs), "alloc source");
-    TRY(dalloc(h.get(), h->d_tally, nfg * 8), "alloc tally");
+    TRY(dalloc(h.get(), h->d_tally, nfg * tally_entry_bytes(h.get())), "alloc tally");
     TRY(dalloc(h.get(), h->d_fiss, (size_t)h->geom.nfsr * 8), "alloc");
     TRY(dalloc(h.get(), h->d_fiss_old, (size_t)h->geom.nfsr * 8), "alloc");
     TRY(dalloc(h.get(), h->d_partial, (size_t)h->red_grid * 4 * 8), "alloc");
@@ -1123,8 +1146,6 @@ extern "C" int moc_batch_step(moc_tracks *const *solves, int32_t n, void *stream
             it[i].scal = (double *)h->d_scal.p;
             it[i].psi_in = h->has_psi ? h->d_psi[c].p : nullptr;
             it[i].psi_out = h->has_psi ? h->d_psi[1 - c].p : nullptr;
-            it[i].bound_in = h->has_psi ? psi_bound(h, c) : nullptr;
-            it[i].bound_out = h->has_psi ? psi_bound(h, 1 - c) : nullptr;
         }
         if (base->d_batch.n < (size_t)n * sizeof(BatchItem)) {
             base->bytes -= base->d_batch.n;
@@ -1135,8 +1156,7 @@ extern "C" int moc_batch_step(moc_tracks *const *solves, int32_t n, void *stream
             "upload");
         for (int i = 0; i < n; ++i) {
             moc_tracks *h = solves[i];
-            TRY(launch_source(h->precision, h->dl, h->ds, h->geom.nfsr, h->red_grid, s,
-                              h->has_psi ? psi_bound(h, 1 - h->cur) : nullptr), "source");
+            TRY(launch_source(h->precision, h->dl, h->ds, h->geom.nfsr, h->red_grid, s), "source");
         }
         // one persistent sweep over the units of every solve
         moc_tracks *h0 = solves[0];
@@ -1388,11 +1408,6 @@ extern "C" int moc_track_psi(moc_tracks *h, int32_t t, int32_t p, int64_t i, int
             std::vector<float> tmp(G);
             for (int g = 0; g < G; ++g) tmp[g] = (float)(values[g] / sc);
             TRY(cudaMemcpy(base, tmp.data(), G * 4, cudaMemcpyHostToDevice), "copy");
-            // keep the bound of |psi| over this buffer a bound
-            std::vector<float> bnd(G);
-            TRY(cudaMemcpy(bnd.data(), psi_bound(h, h->cur), G * 4, cudaMemcpyDeviceToHost), "copy");
-            for (int g = 0; g < G; ++g) bnd[g] = std::max(bnd[g], std::fabs(tmp[g]));
-            TRY(cudaMemcpy(psi_bound(h, h->cur), bnd.data(), G * 4, cudaMemcpyHostToDevice), "copy");
         }
     } else {
         if (rs == 8) {
@@ -1426,17 +1441,17 @@ extern "C" int moc_sweep_from_source(moc_tracks *h, const double *Q, double *tal
         TRY(cudaMemcpyAsync(h->d_qr.p, q32.data(), n * 4, cudaMemcpyHostToDevice, h->stream), "upload");
         TRY(cudaStreamSynchronize(h->stream), "upload");
     }
-    TRY(cudaMemsetAsync(h->d_tally.p, 0, n * 8, h->stream), "memset");
+    TRY(cudaMemsetAsync(h->d_tally.p, 0, h->d_tally.n, h->stream), "memset");
     TRY(set_scalar(h, SC_LEAK, 0.0), "scalar");
     TRY(clear_conv(h, h->stream), "scalar");
     TRY(enqueue_sweep(h, h->stream, h->cur), "sweep");
     if (h->has_psi) h->cur = 1 - h->cur;
-    if (tally) TRY(cudaMemcpyAsync(tally, h->d_tally.p, n * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
+    if (tally) TRY(tally_to_host(h, tally, n), "copy");
     TRY(cudaMemcpyAsync(h->h_scal, h->d_scal.p, SC_COUNT * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
     TRY(cudaStreamSynchronize(h->stream), "sweep");
     if (leakage) *leakage = h->h_scal[SC_LEAK];
     if (check_sweep_flag(h)) return MOC_ERR_CUDA;
-    TRY(cudaMemsetAsync(h->d_tally.p, 0, n * 8, h->stream), "memset");
+    TRY(cudaMemsetAsync(h->d_tally.p, 0, h->d_tally.n, h->stream), "memset");
     TRY(set_scalar(h, SC_LEAK, 0.0), "scalar");
     // the outgoing fluxes are physical values: the next sweep reads them as is
     TRY(set_scalar(h, SC_SCALE, 1.0), "scalar");
@@ -1516,24 +1531,24 @@ extern "C" int moc_sweep_units_from_source(moc_tracks *h, const double *Q, int32
         if (t >= t0 && t < t1) units.push_back(t);
     DevBuf d_units;
     TRY(upload(h, d_units, units.empty() ? std::vector<int32_t>(1, 0) : units), "upload");
-    TRY(cudaMemsetAsync(h->d_tally.p, 0, n * 8, h->stream), "memset");
+    TRY(cudaMemsetAsync(h->d_tally.p, 0, h->d_tally.n, h->stream), "memset");
     TRY(set_scalar(h, SC_LEAK, 0.0), "scalar");
     TRY(set_scalar(h, SC_SCALE, 1.0), "scalar");
     TRY(clear_conv(h, h->stream), "scalar");
     const int out = h->has_psi ? 1 - h->cur : 0;
-    TRY(cudaMemsetAsync(sweep_counter(h, out), 0, sweep_block_bytes(h), h->stream), "memset");
+    TRY(cudaMemsetAsync(sweep_counter(h, out), 0, 4, h->stream), "memset");
     void *pout = h->has_psi ? h->d_psi[1 - h->cur].p : nullptr;
     TRY(launch_sweep(h->precision, h->tally_smem, h->gpl, h->dl, h->ds, (const int32_t *)d_units.p,
-                     (int32_t)units.size(), h->tile_cap, nullptr, pout, sweep_counter(h, out), nullptr,
-                     h->has_psi ? psi_bound(h, out) : nullptr, h->grid, h->block, h->smem, h->stream),
+                     (int32_t)units.size(), h->tile_cap, nullptr, pout, sweep_counter(h, out), h->grid,
+                     h->block, h->smem, h->stream),
         "sweep");
-    TRY(cudaMemcpyAsync(tally, h->d_tally.p, n * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
+    TRY(tally_to_host(h, tally, n), "copy");
     TRY(cudaMemcpyAsync(h->h_scal, h->d_scal.p, SC_COUNT * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
     TRY(cudaStreamSynchronize(h->stream), "sweep");
     h->bytes -= d_units.n;
     if (leakage) *leakage = h->h_scal[SC_LEAK];
     if (check_sweep_flag(h)) return MOC_ERR_CUDA;
-    TRY(cudaMemsetAsync(h->d_tally.p, 0, n * 8, h->stream), "memset");
+    TRY(cudaMemsetAsync(h->d_tally.p, 0, h->d_tally.n, h->stream), "memset");
     TRY(set_scalar(h, SC_LEAK, 0.0), "scalar");
     TRY(cudaStreamSynchronize(h->stream), "sweep");
     return MOC_OK;

@@ -31,6 +31,8 @@ struct DevLayout {
                              // consecutive tracks r + m cpl of one class, padding entries
                              // -1 - (r + m cpl) continuing the block's sequence
     int32_t sync_b;          // tracks per synchronous block (0: none)
+    int32_t tally3;          // 1: the FSR tally is three 64-bit fixed-point words per
+                             // FSR-group (FP32 sweeps with the shared tally), else FP64
     const int32_t *reg_mat;  // per radial region: its material if the same in every layer, else -1
     int32_t Nz, cpl, NL, G, M, Ph;  // NL: the sweep's (uniform) layers
     int32_t NLr;             // the geometry's layers (FSR = region * NLr + layer)
@@ -261,6 +263,40 @@ __device__ __forceinline__ int64_t exit_dest(const DevLayout &dl, const StackDes
     const int dst = dg->rad_dst[v];
     const int j = (int)dg->rad_sign[v] * i + dg->rad_shift[v];
     return (descs[dst].trk_off + (j - descs[dst].i_lo)) * 4 + dg->rad_var[v];
+}
+
+// The FSR tally of FP32 sweeps with the shared tally: per FSR-group three
+// signed 64-bit words (A0, A1, A2) holding (A0 + A1 2^42 + A2 2^84) 2^-64.
+// A unit flushes each tile word as an integer w times its power-of-two
+// fixed-point unit 2^(sh - 64); w 2^sh is split at 42-bit boundaries into a
+// non-negative low part and a signed high part, each added with a native
+// 64-bit integer atomic (no carry between the words; fewer than 2^21 adds per
+// word keep every word in range).  Integer adds are exact and associative, so
+// the tally does not depend on the order in which units finish: a solve gives
+// the same tallies on every run and in any mix of solves.  Returns false for
+// a unit beyond the representable range (|value| >= 2^51).
+__device__ __forceinline__ bool tally3_add(long long *acc, int w, int sh) {
+    unsigned long long *a = reinterpret_cast<unsigned long long *>(acc);
+    const long long v = w;
+    if (sh < 0) {  // below 2^-64: truncated
+        atomicAdd(a, (unsigned long long)(v >> min(-sh, 63)));
+        return true;
+    }
+    if (sh >= 84) {
+        if (sh > 115) return false;
+        atomicAdd(a + 2, (unsigned long long)(v << (sh - 84)));
+        return true;
+    }
+    const int k = sh >= 42 ? 1 : 0, r = sh - 42 * k, s2 = 42 - r;
+    const long long hi = v >> s2;                          // floor(w 2^r / 2^42)
+    const long long lo = (v & ((1ll << s2) - 1)) << r;     // w 2^r - hi 2^42, in [0, 2^42)
+    if (lo) atomicAdd(a + k, (unsigned long long)lo);
+    if (hi) atomicAdd(a + k + 1, (unsigned long long)hi);
+    return true;
+}
+__host__ __device__ __forceinline__ double tally3_value(long long a0, long long a1, long long a2) {
+    // 2^-64, 2^-22, 2^20
+    return (double)a0 * 5.421010862427522e-20 + (double)a1 * 2.384185791015625e-07 + (double)a2 * 1048576.0;
 }
 
 __device__ __forceinline__ float fast_exp2(float x) {

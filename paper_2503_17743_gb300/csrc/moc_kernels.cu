@@ -206,27 +206,69 @@ __global__ void k_links(DevLayout dl, int64_t n_stacks, int32_t *dst) {
     }
 }
 
+// Tracked volumes are summed exactly, so that they do not depend on the order
+// in which threads finish (every handle built from the same geometry and track
+// parameters gets the same bits): each contribution v >= 0 is an integer
+// number of 2^-64 units (bits below 2^-64 dropped), held as 32-bit chunks in
+// four unsigned 64-bit words per FSR, value sum_k A_k 2^(32 k - 64).  Chunks
+// are below 2^32, so a word takes 2^32 adds before it could wrap.
+__device__ __forceinline__ void fix4_add(unsigned long long *a, double v) {
+    if (!(v > 0.0)) return;
+    int e = 0;
+    const double m = frexp(v, &e);                                  // v = m 2^e, 1/2 <= m < 1
+    unsigned long long M = (unsigned long long)ldexp(m, 53);        // exact, below 2^53
+    int S = e + 11;                                                 // v = M 2^(S - 64)
+    if (S < 0) {
+        M = S > -64 ? M >> -S : 0ull;
+        S = 0;
+    }
+    const int w = S >> 5;
+    const unsigned __int128 x = (unsigned __int128)M << (S & 31);   // below 2^84
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const unsigned long long c = (unsigned long long)(x >> (32 * k)) & 0xffffffffull;
+        if (c && w + k < 4) atomicAdd(a + w + k, c);
+    }
+}
+
 template <typename real>
 struct VolVisit {
     const DevLayout *dl;
     const int32_t *reg2d;
     int NL;
-    double *vol;
+    unsigned long long *acc;
     double c;
     __device__ void operator()(int b, int L, real len) {
         const int reg = __ldg(reg2d + b);
-        atomicAdd(vol + fsr_of(*dl, reg, L), c * (double)len);
-        atomicAdd(vol + fsr_of(*dl, reg, NL - 1 - L), c * (double)len);
+        fix4_add(acc + 4 * fsr_of(*dl, reg, L), c * (double)len);
+        fix4_add(acc + 4 * fsr_of(*dl, reg, NL - 1 - L), c * (double)len);
     }
 };
 
 template <typename real>
-__global__ void k_volumes(DevLayout dl, int64_t n_stacks, double *vol) {
+__global__ void k_volumes(DevLayout dl, int64_t n_stacks, unsigned long long *acc) {
     for (int64_t s = blockIdx.x; s < n_stacks; s += gridDim.x) {
         const StackDesc d = dl.desc[s];
         // each stored track carries two directions of equal weight, in two frames
-        VolVisit<real> v{&dl, dl.reg2d + d.seg2d_off, dl.NL, vol, 2.0 * d.W / (4.0 * MOC_PI)};
+        VolVisit<real> v{&dl, dl.reg2d + d.seg2d_off, dl.NL, acc, 2.0 * d.W / (4.0 * MOC_PI)};
         for (int k = threadIdx.x; k < d.n_trk; k += blockDim.x) walk_otf<real>(dl, d, d.i_lo + k, 0, v);
+    }
+}
+
+// the volumes from their exact sums: carries first, then one fixed-order sum
+__global__ void k_vol_value(const unsigned long long *acc, int64_t nfsr, double *vol) {
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nfsr;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long w[4];
+        unsigned long long carry = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const unsigned long long x = acc[4 * f + k] + carry;
+            carry = k < 3 ? x >> 32 : 0ull;
+            w[k] = k < 3 ? x & 0xffffffffull : x;
+        }
+        vol[f] = (((double)w[3] * 4294967296.0 + (double)w[2]) + (double)w[1] * 2.3283064365386963e-10) +
+                 (double)w[0] * 5.421010862427522e-20;
     }
 }
 
@@ -259,11 +301,9 @@ __global__ void k_stack_segments(DevLayout dl, int64_t s, const int64_t *offs, i
 // Q = (sum_h Sigma_s[h->g] phi_h + chi_g / k sum_h nuSigma_f,h phi_h + S_g) / 4pi, with
 // phi normalised on the fly by the latest scale; qr = Q / Sigma_t.
 template <typename real>
-__global__ void k_source(DevLayout dl, DevState st, int32_t nfsr, unsigned *zero_bound) {
+__global__ void k_source(DevLayout dl, DevState st, int32_t nfsr) {
     if (st.scal[SC_CONV] != 0.0) return;  // converged: later iterations are no-ops
     const int G = dl.G;
-    if (zero_bound && blockIdx.x == 0)
-        for (int g = threadIdx.x; g < G; g += blockDim.x) zero_bound[g] = 0u;
     const double scale = st.scal[SC_SCALE];
     const bool eig = st.scal[SC_EIGEN] != 0.0;
     // chi / k of the normalised flux; 1 / (4 pi) per steradian.  Divisions are
@@ -305,8 +345,18 @@ __global__ void k_finalize(DevLayout dl, DevState st, int32_t nfsr) {
         for (int g = 0; g < G; ++g) {
             const size_t q = (size_t)i * G + g;
             // Eq. 4: phi = 4 pi Qr + tally / (V Sigma_t)
-            const double phi = 4.0 * MOC_PI * (double)qr[q] + st.tally[q] * iV * st.inv_st64[m * G + g];
-            st.tally[q] = 0.0;
+            double t;
+            if (dl.tally3) {
+                long long *a = reinterpret_cast<long long *>(st.tally) + 3 * q;
+                t = tally3_value(a[0], a[1], a[2]);
+                a[0] = 0;
+                a[1] = 0;
+                a[2] = 0;
+            } else {
+                t = st.tally[q];
+                st.tally[q] = 0.0;
+            }
+            const double phi = 4.0 * MOC_PI * (double)qr[q] + t * iV * st.inv_st64[m * G + g];
             if (!eig && phi > 0.0) {
                 double rr = (phi - st.phi[q]) / phi;
                 r2 += rr * rr;
@@ -405,7 +455,14 @@ __global__ void k_init_state(DevLayout dl, DevState st, int32_t nfsr) {
         double fis = 0.0;
         for (int g = 0; g < G; ++g) {
             st.phi[(size_t)i * G + g] = 1.0;
-            st.tally[(size_t)i * G + g] = 0.0;
+            if (dl.tally3) {
+                long long *a = reinterpret_cast<long long *>(st.tally) + 3 * ((size_t)i * G + g);
+                a[0] = 0;
+                a[1] = 0;
+                a[2] = 0;
+            } else {
+                st.tally[(size_t)i * G + g] = 0.0;
+            }
             fis += st.nsf64[m * G + g];
         }
         st.fiss[i] = fis;
@@ -505,10 +562,13 @@ cudaError_t launch_links(const DevLayout &dl, int64_t n_stacks, int32_t *dst, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_volumes(int precision, const DevLayout &dl, int64_t n_stacks, double *vol,
-                           int grid, cudaStream_t s) {
-    if (precision == MOC_FP64) k_volumes<double><<<grid, 128, 0, s>>>(dl, n_stacks, vol);
-    else k_volumes<float><<<grid, 128, 0, s>>>(dl, n_stacks, vol);
+cudaError_t launch_volumes(int precision, const DevLayout &dl, int64_t n_stacks, int64_t nfsr,
+                           unsigned long long *acc, double *vol, int grid, cudaStream_t s) {
+    CK(cudaMemsetAsync(acc, 0, (size_t)nfsr * 4 * sizeof(unsigned long long), s));
+    if (precision == MOC_FP64) k_volumes<double><<<grid, 128, 0, s>>>(dl, n_stacks, acc);
+    else k_volumes<float><<<grid, 128, 0, s>>>(dl, n_stacks, acc);
+    CK(cudaGetLastError());
+    k_vol_value<<<grid, 256, 0, s>>>(acc, nfsr, vol);
     return cudaGetLastError();
 }
 
@@ -520,9 +580,9 @@ cudaError_t launch_stack_segments(int precision, const DevLayout &dl, int64_t st
 }
 
 cudaError_t launch_source(int precision, const DevLayout &dl, const DevState &st, int32_t nfsr,
-                          int grid, cudaStream_t s, unsigned *zero_bound) {
-    if (precision == MOC_FP64) k_source<double><<<grid, kSmallBlock, 0, s>>>(dl, st, nfsr, zero_bound);
-    else k_source<float><<<grid, kSmallBlock, 0, s>>>(dl, st, nfsr, zero_bound);
+                          int grid, cudaStream_t s) {
+    if (precision == MOC_FP64) k_source<double><<<grid, kSmallBlock, 0, s>>>(dl, st, nfsr);
+    else k_source<float><<<grid, kSmallBlock, 0, s>>>(dl, st, nfsr);
     return cudaGetLastError();
 }
 

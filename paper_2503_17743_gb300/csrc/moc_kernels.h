@@ -22,8 +22,10 @@ cudaError_t launch_chunk_tables(int precision, const DevLayout &dl, const int32_
                                 int64_t *tab, int grid, cudaStream_t s);
 cudaError_t launch_links(const DevLayout &dl, int64_t n_stacks, int32_t *dst, int grid,
                          cudaStream_t s);
-cudaError_t launch_volumes(int precision, const DevLayout &dl, int64_t n_stacks, double *vol,
-                           int grid, cudaStream_t s);
+// tracked volumes, summed exactly in acc (scratch of nfsr * 4 words) and
+// written to vol [nfsr]
+cudaError_t launch_volumes(int precision, const DevLayout &dl, int64_t n_stacks, int64_t nfsr,
+                           unsigned long long *acc, double *vol, int grid, cudaStream_t s);
 cudaError_t launch_stack_segments(int precision, const DevLayout &dl, int64_t stack,
                                   const int64_t *offs, int32_t *fsr, double *len, cudaStream_t s);
 // the sweep (moc_sweep.cu); gpl = energy groups per lane (1 or 2, FP32 only)
@@ -41,16 +43,11 @@ struct BatchItem {
     double *scal;               // device scalars
     const void *psi_in;         // boundary fluxes in / out (null: all vacuum)
     void *psi_out;
-    const unsigned *bound_in;   // bounds of |psi| (see launch_sweep)
-    unsigned *bound_out;
 };
-// counter: the work counter (zero at launch); bound_in: per group, a bound of
-// |psi_in| (float bits, may be null when psi_in is); bound_out: zeroed,
-// receives the bound of |psi_out| (FP32 fixed-point tally only; may be null)
+// counter: the work counter (zero at launch)
 cudaError_t launch_sweep(int precision, int tally_smem, int gpl, const DevLayout &dl,
                          const DevState &st, const int32_t *order, int32_t n_work, int32_t cap,
-                         const void *psi_in, void *psi_out, int32_t *counter,
-                         const unsigned *bound_in, unsigned *bound_out, int grid, int block,
+                         const void *psi_in, void *psi_out, int32_t *counter, int grid, int block,
                          size_t smem, cudaStream_t s);
 // One sweep of n solves sharing the layout dl (shared tally, no radial
 // chunks): items[n] (device) hold their states; n_units = units in order.
@@ -71,10 +68,8 @@ cudaError_t sweep_occupancy(int precision, int tally_smem, int chunk, int G, int
 // threads per block of the per-FSR kernels (source, finalize, residual, init):
 // small blocks spread a few thousand FSRs over many SMs
 constexpr int kSmallBlock = 64;
-// zero_bound (may be null): G words set to 0 unless the solve has converged
-// (the bound of the psi buffer the following sweep writes)
 cudaError_t launch_source(int precision, const DevLayout &dl, const DevState &st, int32_t nfsr,
-                          int grid, cudaStream_t s, unsigned *zero_bound = nullptr);
+                          int grid, cudaStream_t s);
 cudaError_t launch_finalize(int precision, const DevLayout &dl, const DevState &st, int32_t nfsr,
                             int grid, double integrations, cudaStream_t s);
 cudaError_t launch_finalize_fixed(int precision, const DevLayout &dl, const DevState &st,

@@ -84,8 +84,7 @@ cudaError_t sweep_occupancy(int precision, int tally_smem, int chunk, int G, int
 
 cudaError_t launch_sweep(int precision, int tally_smem, int gpl, const DevLayout &dl,
                          const DevState &st, const int32_t *order, int32_t n_work, int32_t cap,
-                         const void *psi_in, void *psi_out, int32_t *counter,
-                         const unsigned *bound_in, unsigned *bound_out, int grid, int block,
+                         const void *psi_in, void *psi_out, int32_t *counter, int grid, int block,
                          size_t smem, cudaStream_t s) {
     const void *f = sweep_fn(precision, tally_smem, tally_smem && dl.chunk_b > 0, dl.G, gpl, 0,
                              tally_smem && dl.sync_b > 0 ? 1 : 0);
@@ -98,11 +97,9 @@ cudaError_t launch_sweep(int precision, int tally_smem, int gpl, const DevLayout
     int32_t a3 = n_work, a4 = tally_smem ? cap : 0;
     const void *a5 = psi_in;
     void *a6 = psi_out;
-    const unsigned *a7 = bound_in;
-    unsigned *a8 = bound_out;
-    const BatchItem *a9 = nullptr;
-    int32_t a10 = 0;
-    void *args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8, &a9, &a10};
+    const BatchItem *a7 = nullptr;
+    int32_t a8 = 0;
+    void *args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8};
     return cudaLaunchKernel(f, dim3(grid), dim3(block), args, smem, s);
 }
 
@@ -120,10 +117,8 @@ cudaError_t launch_sweep_batch(int precision, int gpl, const DevLayout &dl, cons
     int32_t a3 = n_units * n, a4 = cap;
     const void *a5 = nullptr;
     void *a6 = nullptr;
-    const unsigned *a7 = nullptr;
-    unsigned *a8 = nullptr;
-    const BatchItem *a9 = items;
-    int32_t a10 = n;
-    void *args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8, &a9, &a10};
+    const BatchItem *a7 = items;
+    int32_t a8 = n;
+    void *args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8};
     return cudaLaunchKernel(f, dim3(grid), dim3(block), args, smem, s);
 }

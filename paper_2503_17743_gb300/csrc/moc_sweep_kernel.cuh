@@ -155,39 +155,19 @@ struct RowLoadS<float, 4> {
 };
 
 // Packed FP32 pairs (two groups of a lane) for the sm_100-family f32x2
-// instructions: one issue slot for two operations
-__device__ __forceinline__ uint64_t pk2(float a, float b) {
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
+// instructions (one issue slot for two operations): the rows keep each pair
+// of groups as Qr_0 Qr_1 Sigma_0 Sigma_1, loaded as two float2 values
+// the same pairs as float2 values (for the packed-pair intrinsics)
+__device__ __forceinline__ void row_load_f2(unsigned a, float2 &q, float2 &s) {
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(q.x), "=f"(q.y), "=f"(s.x), "=f"(s.y)
+                 : "r"(a));
 }
-__device__ __forceinline__ void upk2(uint64_t r, float &a, float &b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+__device__ __forceinline__ void lds_f2(unsigned a, float2 &v) {
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
 }
-__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
-    uint64_t d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
-    uint64_t d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
-    uint64_t d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-// (Qr_0, Qr_1) and (Sigma_0, Sigma_1) of one row as two packed pairs
-__device__ __forceinline__ void row_load_pairs(unsigned a, uint64_t &q, uint64_t &s) {
-    asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(q), "=l"(s) : "r"(a));
-}
-// split tile (synchronous blocks): Qr and Sigma_t of a row in two arrays,
-// a lane's pair of groups as one 64-bit load from each
-__device__ __forceinline__ void lds64(unsigned a, uint64_t &v) {
-    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(a));
-}
+// (split tile of synchronous blocks: Qr and Sigma_t of a row in two arrays,
+// a lane's pair of groups as one float2 load from each)
 template <>
 struct RowLoadS<double, 1> {
     static __device__ __forceinline__ void get(unsigned a, double (&q)[1], double (&s)[1]) {
@@ -265,8 +245,7 @@ constexpr int kSyncGuard = 8;
 template <typename real, int GL, int GPL, bool SMEM, bool CHUNK, bool BATCH, bool SYNC = false>
 __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(real) == 4 ? 3 : 2)
     k_sweep(DevLayout dl, DevState st, const int32_t *order, int32_t n_work, int32_t cap,
-            const real *psi_in_p, real *psi_out_p, const unsigned *bound_in_p, unsigned *bound_out_p,
-            const BatchItem *items, int32_t n_items) {
+            const real *psi_in_p, real *psi_out_p, const BatchItem *items, int32_t n_items) {
     constexpr int GP = GL * GPL;     // groups per chunk (padded)
     constexpr int SLOTS = 32 / GL;   // tracks per warp task
     extern __shared__ __align__(16) unsigned char smem[];
@@ -275,8 +254,9 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
     __shared__ double s_leak[kMaxSweepBlock / 32];
     __shared__ float s_scl[32];      // FP32 fixed-point tally: scale of each group of the chunk
     __shared__ float s_inv[32];      // and its inverse
+    __shared__ int s_sh[32];         // the tally unit s_inv = 2^(s_sh - 64)
     __shared__ unsigned s_bmax[32];  // bound of |W psi| and |W Qr| per group (float bits)
-    __shared__ unsigned s_pmax[32];  // max |psi_out| the block stored per group (float bits)
+    __shared__ unsigned s_ubnd[32];  // max |psi_in| over the unit's tracks per group (float bits)
     __shared__ unsigned s_hmax[32];  // max |psi| handed to the next radial chunk (float bits)
     __shared__ float s_wmax;
     __shared__ BatchItem s_item;     // BATCH: the solve of the current unit
@@ -336,28 +316,9 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
     const real *sig_g = reinterpret_cast<const real *>(st.sig_t);
     const SegRec<real> *recs = reinterpret_cast<const SegRec<real> *>(dl.segs);
     real leak = (real)0;  // this lane's W psi leaving through vacuum faces
-    // the fixed-point tally needs a bound of |psi_in| per group: the previous
-    // sweep left one, and this sweep leaves one for the next (every psi_in is
-    // a psi_out of the previous sweep; the solves of a batch share the layout,
-    // so all of them have boundary fluxes or none)
-    const bool track_bound = kFixed && SMEM && (BATCH ? dl.dst != nullptr : bound_out_p != nullptr);
-    float pmax[GPL];  // this lane's max |psi_out| for its groups of the current chunk
-#pragma unroll
-    for (int c = 0; c < GPL; ++c) pmax[c] = 0.0f;
-    if (tid < 32) s_pmax[tid] = 0u;
     if (tid < 32) s_hmax[tid] = 0u;
     if constexpr (sizeof(real) == 8)
         for (int i = tid; i < 64; i += blockDim.x) s_exp[i] = make_double2(moc_exp64::kTable[i].hi, moc_exp64::kTable[i].lo);
-    // lanes with the same groups (one per slot) fold their maxima into s_pmax
-    auto fold_pmax = [&](int gc_) {
-#pragma unroll
-        for (int c = 0; c < GPL; ++c) {
-            float v = pmax[c];
-            for (int o = GL; o < 32; o <<= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-            if (j == 0 && ql * GPL + c < gc_ && v > 0.0f) atomicMax(&s_pmax[ql * GPL + c], __float_as_uint(v));
-            pmax[c] = 0.0f;
-        }
-    };
 
     for (;;) {
         __syncthreads();
@@ -376,8 +337,6 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
         // the unit's solve (one solve unless batched)
         const real *psi_in = BATCH ? reinterpret_cast<const real *>(s_item.psi_in) : psi_in_p;
         real *psi_out = BATCH ? reinterpret_cast<real *>(s_item.psi_out) : psi_out_p;
-        const unsigned *bound_in = BATCH ? s_item.bound_in : bound_in_p;
-        unsigned *bound_out = BATCH ? s_item.bound_out : bound_out_p;
         double *scal_u = BATCH ? s_item.scal : st.scal;
         const real scale = (real)scal_u[SC_SCALE];
         const real *qr_g = reinterpret_cast<const real *>(BATCH ? s_item.qr : st.qr);
@@ -453,6 +412,24 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                 if (lane < Ph) s_us[lane].task_pre = incl - cnt;
                 if (lane == 31) s_ntask = incl;
             }
+            if (kFixed && SMEM && pass == 0 && ci == 0) {
+                // the unit's incoming fluxes psi_in[(gid 4 + v) G + g], its tracks
+                // gid one contiguous range: threads take a fixed group each
+                // (stride a multiple of G)
+                if (tid < 32) s_ubnd[tid] = 0u;
+                __syncthreads();
+                if (psi_in) {
+                    const int S = (blockDim.x / G) * G;
+                    const int64_t trk_end = s_us[Ph - 1].trk_off + s_us[Ph - 1].n_trk;
+                    const int64_t e0 = unit_trk0 * 4 * G, e1 = trk_end * 4 * G;
+                    const int gq = tid % G - g0;
+                    float um = 0.0f;
+                    if (tid < S && gq >= 0 && gq < gc)
+                        for (int64_t e = e0 + tid; e < e1; e += S) um = fmaxf(um, fabsf((float)psi_in[e]));
+                    if (um > 0.0f) atomicMax(&s_ubnd[gq], __float_as_uint(um));
+                }
+                __syncthreads();
+            }
             if (SMEM) {
                 // rows of the (2D segment, layer) FSRs the unit (chunk) crosses
                 for (int bb = warp; bb < b1 - b0; bb += nwarps) {
@@ -494,11 +471,11 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                 }
                 if (kFixed) {
                     // incoming fluxes enter the bound too (psi along a track stays
-                    // between its incoming value and Qr): the previous sweep's
-                    // bound of every psi it stored
+                    // between its incoming value and Qr): the largest |psi_in| of
+                    // the unit's own tracks, so that a unit far from the peak flux
+                    // gets a fine grid
                     const int qq = tid % GP;
-                    if (bound_in && psi_in && qq < gc)
-                        bmax = fmaxf(bmax, __uint_as_float(__ldg(bound_in + g0 + qq)) * fabsf((float)scale));
+                    if (psi_in && qq < gc) bmax = fmaxf(bmax, __uint_as_float(s_ubnd[qq]) * fabsf((float)scale));
                     // and psi handed over from the previous chunk of this pass
                     if (C > 1 && ci > 0) bmax = fmaxf(bmax, __uint_as_float(s_hmax[qq]));
                     atomicMax(&s_bmax[qq], __float_as_uint(bmax));
@@ -513,10 +490,15 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                 // contribution: W |psi - Qr| <= W max(psi, Qr), since psi and Qr
                 // are never negative (sources, fluxes and boundary fluxes
                 // are non-negative and the library refuses negative inputs;
-                // psi moves between its incoming value and Qr, Eq. 3)
+                // psi moves between its incoming value and Qr, Eq. 3).  The
+                // bound is rounded up to a power of two 2^e, so that scaling by
+                // the unit is exact and a flushed word is an exact shift.
                 const float B = s_wmax * __uint_as_float(s_bmax[tid]);
-                s_scl[tid] = B > 0.0f ? ldexpf(1.0f, dl.tally_bits) / B : 1.0f;
-                s_inv[tid] = B > 0.0f ? B * ldexpf(1.0f, -dl.tally_bits) : 1.0f;
+                int e = 0;
+                if (B > 0.0f) frexpf(B, &e);
+                s_scl[tid] = B > 0.0f ? ldexpf(1.0f, dl.tally_bits - e) : 1.0f;
+                s_inv[tid] = B > 0.0f ? ldexpf(1.0f, e - dl.tally_bits) : 1.0f;
+                s_sh[tid] = B > 0.0f ? e - dl.tally_bits + 64 : 64;
             }
             __syncthreads();
 
@@ -649,15 +631,13 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                         const int tU_ = tix(rU, qlo), tD_ = tix(rD, qlo);
                         real qU[GPL], sU[GPL], qD[GPL], sD[GPL];
                         if constexpr (SYNC) {
-                            uint64_t a, b;
-                            lds64(qr_sa + eU * 4u, a);
-                            lds64(sg_sa + eU * 4u, b);
-                            upk2(a, qU[0], qU[1]);
-                            upk2(b, sU[0], sU[1]);
-                            lds64(qr_sa + eD * 4u, a);
-                            lds64(sg_sa + eD * 4u, b);
-                            upk2(a, qD[0], qD[1]);
-                            upk2(b, sD[0], sD[1]);
+                            float2 a, b;
+                            lds_f2(qr_sa + eU * 4u, a);
+                            lds_f2(sg_sa + eU * 4u, b);
+                            qU[0] = a.x; qU[1] = a.y; sU[0] = b.x; sU[1] = b.y;
+                            lds_f2(qr_sa + eD * 4u, a);
+                            lds_f2(sg_sa + eD * 4u, b);
+                            qD[0] = a.x; qD[1] = a.y; sD[0] = b.x; sD[1] = b.y;
                         } else {
                             RowLoadS<real, GPL>::get(rows_sa + eU * (unsigned)(2 * sizeof(real)), qU, sU);
                             RowLoadS<real, GPL>::get(rows_sa + eD * (unsigned)(2 * sizeof(real)), qD, sD);
@@ -711,6 +691,55 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                         }
                     }
                 };
+                // the packed-pair body of four consecutive pieces (two groups per
+                // lane, FP32 fixed-point tally): per frame and piece one mul
+                // (-Sigma l), two ex2, then d = psi - W S Qr, t = d (1 - e^{-tau})
+                // (1 - x is exact in FP32 for x >= 1/2), psi -= t in three paired
+                // operations; aTU / aTD: byte addresses of the group-0 tally words
+                // (group 1 lies cs4 bytes further)
+                const unsigned cs4 = (unsigned)CS * 4u;
+                auto packed_core = [&](float2 (&QU)[4], float2 (&SU)[4], float2 (&QD)[4], float2 (&SD)[4],
+                                       const real (&len)[4], const unsigned (&aTU)[4],
+                                       const unsigned (&aTD)[4]) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float nl = -(float)len[i];
+                        const float2 xu = __fmul2_rn(SU[i], make_float2(nl, nl));
+                        const float2 xd = __fmul2_rn(SD[i], make_float2(nl, nl));
+                        SU[i] = make_float2(fast_exp2(xu.x), fast_exp2(xu.y));  // now e^{-Sigma_t l}
+                        SD[i] = make_float2(fast_exp2(xd.x), fast_exp2(xd.y));
+                    }
+                    const float2 nws = make_float2(-(float)WS[0], -(float)WS[1]);
+                    float2 PU = make_float2((float)psiU[0], (float)psiU[1]);
+                    float2 PD = make_float2((float)psiD[0], (float)psiD[1]);
+                    int vU[4][2], vD[4][2];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        // d = W S (psi - Qr); t = d (1 - e) as d - d e with one
+                        // rounding; psi -= t
+                        const float2 dU = __ffma2_rn(nws, QU[i], PU);
+                        const float2 dD = __ffma2_rn(nws, QD[i], PD);
+                        const float2 tU = __ffma2_rn(make_float2(-dU.x, -dU.y), SU[i], dU);
+                        const float2 tD = __ffma2_rn(make_float2(-dD.x, -dD.y), SD[i], dD);
+                        PU = __fadd2_rn(PU, make_float2(-tU.x, -tU.y));
+                        PD = __fadd2_rn(PD, make_float2(-tD.x, -tD.y));
+                        vU[i][0] = __float2int_rn(tU.x);
+                        vU[i][1] = __float2int_rn(tU.y);
+                        vD[i][0] = __float2int_rn(tD.x);
+                        vD[i][1] = __float2int_rn(tD.y);
+                    }
+                    psiU[0] = (real)PU.x;
+                    psiU[1] = (real)PU.y;
+                    psiD[0] = (real)PD.x;
+                    psiD[1] = (real)PD.y;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        shared_red_add(aTU[i], vU[i][0]);
+                        shared_red_add(aTU[i] + cs4, vU[i][1]);
+                        shared_red_add(aTD[i], vD[i][0]);
+                        shared_red_add(aTD[i] + cs4, vD[i][1]);
+                    }
+                };
                 // four consecutive segments of the track at once (shared tally):
                 // all row loads and exponentials first, then the psi recurrence,
                 // then the tally updates, so that the loads overlap each other
@@ -726,7 +755,8 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                             // piece one mul (-Sigma l), two ex2, then
                             // d = psi - W S Qr, t = d (1 - e^{-tau}) (1 - x is exact in
                             // FP32 for x >= 1/2), psi -= t in three paired operations
-                            uint64_t QU[4], SU[4], QD[4], SD[4];
+                            float2 QU[4], SU[4], QD[4], SD[4];
+                            unsigned aTU[4], aTD[4];
 #pragma unroll
                             for (int i = 0; i < 4; ++i) {
                                 eU[i] = rU[i] * GP + qlo;
@@ -736,65 +766,28 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                                 if constexpr (SYNC) {
                                     // Qr of both frames; Sigma_t of the 2D segment when its
                                     // region has one material (both frames), else per row
-                                    lds64(qr_sa + eU[i] * 4u, QU[i]);
-                                    lds64(qr_sa + eD[i] * 4u, QD[i]);
-                                    uint64_t sb;
-                                    lds64(sb_sa + (unsigned)(bs[i] * GP + qlo) * 4u, sb);
-                                    float s0, s1;
-                                    upk2(sb, s0, s1);
-                                    if (s0 < 0.0f) {
-                                        lds64(sg_sa + eU[i] * 4u, SU[i]);
-                                        lds64(sg_sa + eD[i] * 4u, SD[i]);
+                                    lds_f2(qr_sa + eU[i] * 4u, QU[i]);
+                                    lds_f2(qr_sa + eD[i] * 4u, QD[i]);
+                                    float2 sb;
+                                    lds_f2(sb_sa + (unsigned)(bs[i] * GP + qlo) * 4u, sb);
+                                    if (sb.x < 0.0f) {
+                                        lds_f2(sg_sa + eU[i] * 4u, SU[i]);
+                                        lds_f2(sg_sa + eD[i] * 4u, SD[i]);
                                     } else {
                                         SU[i] = sb;
                                         SD[i] = sb;
                                     }
                                 } else {
-                                    row_load_pairs(rows_sa + eU[i] * 8u, QU[i], SU[i]);
-                                    row_load_pairs(rows_sa + eD[i] * 8u, QD[i], SD[i]);
+                                    row_load_f2(rows_sa + eU[i] * 8u, QU[i], SU[i]);
+                                    row_load_f2(rows_sa + eD[i] * 8u, QD[i], SD[i]);
                                 }
                             }
 #pragma unroll
                             for (int i = 0; i < 4; ++i) {
-                                const uint64_t nl = pk2(-(float)len[i], -(float)len[i]);
-                                float a0, a1, b0, b1;
-                                upk2(mul2(SU[i], nl), a0, a1);
-                                upk2(mul2(SD[i], nl), b0, b1);
-                                SU[i] = pk2(fast_exp2(a0), fast_exp2(a1));  // now e^{-Sigma_t l}
-                                SD[i] = pk2(fast_exp2(b0), fast_exp2(b1));
+                                aTU[i] = tl_sa + (unsigned)fU[i] * 4u;
+                                aTD[i] = tl_sa + (unsigned)fD[i] * 4u;
                             }
-                            const uint64_t nws = pk2(-(float)WS[0], -(float)WS[1]), one = pk2(1.0f, 1.0f);
-                            uint64_t PU = pk2((float)psiU[0], (float)psiU[1]);
-                            uint64_t PD = pk2((float)psiD[0], (float)psiD[1]);
-                            int vU[4][2], vD[4][2];
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) {
-                                const uint64_t TU = mul2(fma2(nws, QU[i], PU), sub2(one, SU[i]));
-                                const uint64_t TD = mul2(fma2(nws, QD[i], PD), sub2(one, SD[i]));
-                                PU = sub2(PU, TU);
-                                PD = sub2(PD, TD);
-                                float t0, t1;
-                                upk2(TU, t0, t1);
-                                vU[i][0] = __float2int_rn(t0);
-                                vU[i][1] = __float2int_rn(t1);
-                                upk2(TD, t0, t1);
-                                vD[i][0] = __float2int_rn(t0);
-                                vD[i][1] = __float2int_rn(t1);
-                            }
-                            float p0, p1;
-                            upk2(PU, p0, p1);
-                            psiU[0] = (real)p0;
-                            psiU[1] = (real)p1;
-                            upk2(PD, p0, p1);
-                            psiD[0] = (real)p0;
-                            psiD[1] = (real)p1;
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) {
-                                shared_red_add(tl_sa + fU[i] * 4u, vU[i][0]);
-                                shared_red_add(tl_sa + (fU[i] + CS) * 4u, vU[i][1]);
-                                shared_red_add(tl_sa + fD[i] * 4u, vD[i][0]);
-                                shared_red_add(tl_sa + (fD[i] + CS) * 4u, vD[i][1]);
-                            }
+                            packed_core(QU, SU, QD, SD, len, aTU, aTD);
                         } else {
                             real qU[4][GPL], sU[4][GPL], qD[4][GPL], sD[4][GPL];
 #pragma unroll
@@ -1004,24 +997,13 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                     for (int c = 0; c < GPL; ++c) {
                         const int qq = ql * GPL + c;
                         if (qq >= gc) continue;
-                        if (dstU >= 0 && dstU < dl.n_slots) {
-                            const real v = psiU[c] * iWS[c];
-                            psi_out[dstU * G + g0 + qq] = v;
-                            pmax[c] = fmaxf(pmax[c], fabsf((float)v));
-                        } else {
-                            leak += psiU[c] * iS[c];
-                        }
-                        if (dstD >= 0 && dstD < dl.n_slots) {
-                            const real v = psiD[c] * iWS[c];
-                            psi_out[dstD * G + g0 + qq] = v;
-                            pmax[c] = fmaxf(pmax[c], fabsf((float)v));
-                        } else {
-                            leak += psiD[c] * iS[c];
-                        }
+                        if (dstU >= 0 && dstU < dl.n_slots) psi_out[dstU * G + g0 + qq] = psiU[c] * iWS[c];
+                        else leak += psiU[c] * iS[c];
+                        if (dstD >= 0 && dstD < dl.n_slots) psi_out[dstD * G + g0 + qq] = psiD[c] * iWS[c];
+                        else leak += psiD[c] * iS[c];
                     }
                 }
             }
-            if (track_bound && G > GP) fold_pmax(gc);  // several chunks: publish per chunk
             if (kFixed && C > 1) {
                 // the next chunk's bound covers the psi handed over to it
 #pragma unroll
@@ -1032,10 +1014,6 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                 }
             }
             __syncthreads();
-            if (track_bound && G > GP && tid < gc) {
-                if (s_pmax[tid]) atomicMax(bound_out + g0 + tid, s_pmax[tid]);
-                s_pmax[tid] = 0u;  // read again only after the next chunk's barriers
-            }
             if (SMEM) {
                 for (int bb = warp; bb < b1 - b0; bb += nwarps) {
                     const int reg = __ldg(reg2d + b0 + bb);
@@ -1043,8 +1021,17 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                         const int L = x / GP, qq = x - L * GP;
                         if (qq >= gc) continue;
                         const int e = tix(bb * NL + L, qq);
-                        const double v = kFixed ? (double)((float)tl_i[e] * s_inv[qq]) : (double)tl_s[e];
-                        if (v != 0.0) atomicAdd(tally_g + (size_t)fsr_of(dl, reg, L) * G + g0 + qq, v);
+                        const size_t gi = (size_t)fsr_of(dl, reg, L) * G + g0 + qq;
+                        if constexpr (kFixed) {
+                            // into the three-word fixed-point tally: exact, so the
+                            // order of the units does not matter
+                            const int iv = tl_i[e];
+                            if (iv != 0 && !tally3_add(reinterpret_cast<long long *>(tally_g) + 3 * gi, iv, s_sh[qq]))
+                                *err = 2.0;
+                        } else {
+                            const double v = (double)tl_s[e];
+                            if (v != 0.0) atomicAdd(tally_g + gi, v);
+                        }
                     }
                 }
                 if (tid < 32) s_bmax[tid] = 0u;  // next chunk's bound (read only before its tasks)
@@ -1052,29 +1039,18 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
         }
         if constexpr (BATCH) {
             // the next unit may belong to another solve: publish this one's
-            // psi bound and leakage now
-            if (track_bound && G <= GP) fold_pmax(G);
+            // leakage now
             double lk = (double)leak;
             for (int o = 16; o > 0; o >>= 1) lk += __shfl_down_sync(0xffffffffu, lk, o);
             if (lane == 0) s_leak[warp] = lk;
             leak = (real)0;
             __syncthreads();
-            if (track_bound && G <= GP && tid < G) {
-                if (s_pmax[tid]) atomicMax(bound_out + tid, s_pmax[tid]);
-                s_pmax[tid] = 0u;
-            }
             if (tid == 0) {
                 double v = 0.0;
                 for (int k = 0; k < nwarps; ++k) v += s_leak[k];
                 if (v != 0.0) atomicAdd(scal_u + SC_LEAK, v);
             }
         }
-    }
-    if (!BATCH && track_bound && G <= GP) {
-        // one chunk: the maxima span every unit of the block, published once
-        fold_pmax(G);
-        __syncthreads();
-        if (tid < G && s_pmax[tid]) atomicMax(bound_out_p + tid, s_pmax[tid]);
     }
     if (BATCH) return;
     double leak64 = (double)leak;
