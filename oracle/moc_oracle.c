@@ -84,7 +84,11 @@ typedef struct {
     int *reg_base;      /* per cell */
     int *fsr_mat;       /* per FSR */
     int Nz, cpl;      /* cpl: lattice cells per layer (0 when the layers differ) */
-    long *lplane;     /* [nl + 1] lattice index of each layer plane */
+    long *lplane;     /* [nl + 1] integer part of each layer plane in lattice units, z / dz */
+    double *kplane;   /* [nl + 1] each layer plane in lattice units (any mesh) */
+    double *qplane;   /* [nl + 1] its fractional part, the pfrac entry itself when nonzero */
+    double *pfrac;    /* distinct fractional parts of the planes, ascending */
+    int npfrac;
     double dz;
     /* azimuth pairs m = 0..nq-1 */
     int nq;
@@ -153,6 +157,27 @@ static void gauss_legendre(int n, double *x, double *w) {
 static double snap(double z) {
     double r = nearbyint(z);
     return fabs(z - r) <= TIE_EPS ? r : z;
+}
+
+/* Layer planes off the axial lattice (a local axial mesh, Sec. 2.2).  A
+ * lattice coordinate u is kept as its integer part n and fractional part f,
+ * and a fraction within TIE_EPS of a plane's fractional part is replaced by
+ * that plane's fraction (the same double), so that "u lies on the plane" and
+ * "u lies below it" are exact comparisons of integers and of equal doubles,
+ * decided the same way by any implementation of the same arithmetic and for
+ * integer parts of any size. */
+static void split_coord(const double *pfrac, int npfrac, double z, long *n, double *f) {
+    z = snap(z);
+    double fl = floor(z), fr = z - fl;
+    for (int q = 0; q < npfrac; q++)
+        if (fabs(fr - pfrac[q]) <= TIE_EPS) { fr = pfrac[q]; break; }
+    *n = (long)fl;
+    *f = fr;
+}
+
+/* u < v for split coordinates */
+static int coord_lt(long un, double uf, long vn, double vf) {
+    return un < vn || (un == vn && uf < vf);
 }
 
 /* ------------------------------------------------------------------------
@@ -454,7 +479,7 @@ static int build_2d_segments(orc_t *o) {
  * an exact rational.  Every reflective link then lands on a track.
  * ---------------------------------------------------------------------- */
 
-static void stack_geom(orc_t *o, int t, int p, double *zeta, int *nb_out,
+static void stack_geom(orc_t *o, int t, int p, long *zn, double *zf, int *nb_out,
                        double *cot_out, double *sin_out, double *cos_out) {
     int a = o->t_azim[t];
     int m = a < o->nq ? a : o->A / 2 - 1 - a;
@@ -469,7 +494,7 @@ static void stack_geom(orc_t *o, int t, int p, double *zeta, int *nb_out,
     int nb = (int)(o->soff[t + 1] - off);
     for (int j = 0; j <= nb; j++) {
         double s = o->spos[off + t + j];
-        zeta[j] = snap(z0 + s * slope);
+        split_coord(o->pfrac, o->npfrac, z0 + s * slope, zn + j, zf + j);
     }
     *nb_out = nb;
     *cot_out = cot;
@@ -487,34 +512,43 @@ typedef struct {
     long cap_seg;
     int cap_trk;
     int *cursor;
-    double *zeta;
+    long *zn;       /* lattice coordinates at the 2D boundaries: integer parts */
+    double *zf;     /* and fractional parts */
     int zcap;
 } stackbuf;
 
 static void sb_free(stackbuf *sb) {
-    free(sb->nseg); free(sb->off); free(sb->fsr); free(sb->len); free(sb->cursor); free(sb->zeta);
+    free(sb->nseg); free(sb->off); free(sb->fsr); free(sb->len); free(sb->cursor); free(sb->zn); free(sb->zf);
     memset(sb, 0, sizeof *sb);
 }
 
 /* Segments of every track of stack (t, p), collectively for the whole
  * z-stack (Sec. 2.2): per (2D segment b, layer L) the range of track indices
  * crossing it (Eqs. 6-7), classified by Eqs. 9-10.  All index arithmetic is
- * done in lattice units (z / dz), where the layer planes are integers. */
+ * done in lattice units (z / dz) on split coordinates n + f (split_coord):
+ * track i at boundary j lies at (i + zn[j]) + zf[j], a plane at
+ * lplane[L] + qplane[L]. */
 static void build_stack(orc_t *o, int t, int p, stackbuf *sb) {
     long off = o->soff[t];
     int nb = (int)(o->soff[t + 1] - off);
-    if (sb->zcap < nb + 1) { free(sb->zeta); sb->zcap = nb + 1; sb->zeta = malloc(sizeof(double) * (size_t)sb->zcap); }
+    if (sb->zcap < nb + 1) {
+        free(sb->zn); free(sb->zf);
+        sb->zcap = nb + 1;
+        sb->zn = malloc(sizeof(long) * (size_t)sb->zcap);
+        sb->zf = malloc(sizeof(double) * (size_t)sb->zcap);
+    }
     double cot, sn, cs;
     int nbx;
-    stack_geom(o, t, p, sb->zeta, &nbx, &cot, &sn, &cs);
-    double *zeta = sb->zeta;
+    stack_geom(o, t, p, sb->zn, sb->zf, &nbx, &cot, &sn, &cs);
+    const long *zn = sb->zn;
+    const double *zf = sb->zf;
     int up = cot > 0;
     int NL = o->nl;
-    /* track index range over the whole stack (domain 0 < u < Nz) */
-    double zmx = zeta[0] > zeta[nb] ? zeta[0] : zeta[nb];
-    double zmn = zeta[0] < zeta[nb] ? zeta[0] : zeta[nb];
-    long imin = (long)floor(-zmx) + 1;
-    long imax = (long)ceil((double)o->Nz - zmn) - 1;
+    /* track index range over the whole stack (domain 0 < u < Nz): the
+       highest end above 0, the lowest below Nz */
+    int e_hi = coord_lt(zn[0], zf[0], zn[nb], zf[nb]) ? nb : 0, e_lo = nb - e_hi;
+    long imin = -zn[e_hi] + (zf[e_hi] > 0.0 ? 0 : 1);
+    long imax = (long)o->Nz - 1 - zn[e_lo];
     int ntrk = (int)(imax - imin + 1);
     if (ntrk < 0) ntrk = 0;
     if (sb->cap_trk < ntrk) {
@@ -540,31 +574,46 @@ static void build_stack(orc_t *o, int t, int p, stackbuf *sb) {
             }
         }
         for (int b = 0; b < nb; b++) {
-            double za = zeta[b], zb = zeta[b + 1];
-            double zhi = za > zb ? za : zb, zlo = za < zb ? za : zb;
+            /* the segment's higher and lower end */
+            int jh = coord_lt(zn[b], zf[b], zn[b + 1], zf[b + 1]) ? b + 1 : b, jl = 2 * b + 1 - jh;
+            long nhi = zn[jh], nlo = zn[jl];
+            double fhi = zf[jh], flo = zf[jl];
             int reg = o->sreg[off + b];
             double l2d = o->slen[off + b];
             for (int li = 0; li < NL; li++) {
                 int L = up ? li : NL - 1 - li;     /* traversal order of the layers */
-                double kmin = (double)o->lplane[L], kmax = (double)o->lplane[L + 1];
-                long i_start = (long)ceil(kmin - zhi);    /* Eq. 6 */
-                long i_end = (long)floor(kmax - zlo);     /* Eq. 7 */
-                long i_in = (long)ceil(kmin - zlo);       /* Eq. 9 */
-                long i_out = (long)floor(kmax - zhi);     /* Eq. 10 */
+                long pmin = o->lplane[L], pmax = o->lplane[L + 1];
+                double qmin = o->qplane[L], qmax = o->qplane[L + 1];
+                /* Eq. 6: the smallest i with i + zhi >= kmin */
+                long i_start = (pmin - nhi) + (qmin > fhi ? 1 : 0);
+                /* Eq. 7: the largest i with i + zlo <= kmax */
+                long i_end = (pmax - nlo) - (qmax >= flo ? 0 : 1);
+                /* Eq. 9: the smallest i with i + zlo >= kmin */
+                long i_in = (pmin - nlo) + (qmin > flo ? 1 : 0);
+                /* Eq. 10: the largest i with i + zhi <= kmax */
+                long i_out = (pmax - nhi) - (qmax >= fhi ? 0 : 1);
                 if (i_start < imin) i_start = imin;
                 if (i_end > imax) i_end = imax;
                 for (long i = i_start; i <= i_end; i++) {
                     double len;
                     if (i >= i_in && i <= i_out) {
-                        len = l2d / sn;                          /* Eq. 8 */
+                        len = l2d / sn;                                                    /* Eq. 8 */
                     } else if (i_in > i_out && i > i_out && i < i_in) {
-                        len = (kmax - kmin) * o->dz / cs;        /* Eq. 11 */
+                        len = ((double)(pmax - pmin) + (qmax - qmin)) * o->dz / cs;         /* Eq. 11 */
                     } else {
-                        double lo = (double)i + zlo, hi = (double)i + zhi;
-                        if (lo < kmin) lo = kmin;
-                        if (hi > kmax) hi = kmax;
-                        double du = hi - lo;
-                        if (du <= 0.0) continue;                 /* touching only */
+                        /* a partial crossing; touching a plane only (zero
+                           length) is no segment: i + zhi == kmin (i = i_start
+                           with equal parts) or i + zlo == kmax (i = i_end) */
+                        if ((i == pmin - nhi && qmin == fhi) || (i == pmax - nlo && qmax == flo))
+                            continue;
+                        /* the part inside the layer: from max(i + zlo, kmin)
+                           to min(i + zhi, kmax) */
+                        long an = i + nlo, bn = i + nhi;
+                        double af = flo, bf = fhi;
+                        if (coord_lt(an, af, pmin, qmin)) { an = pmin; af = qmin; }
+                        if (coord_lt(pmax, qmax, bn, bf)) { bn = pmax; bf = qmax; }
+                        double du = (double)(bn - an) + (bf - af);
+                        if (du <= 0.0) continue;                                          /* (rounding) */
                         len = du * o->dz / cs;
                     }
                     int k = (int)(i - imin);
@@ -744,30 +793,65 @@ void *orc_create(const orc_input *in, char *err, int errlen) {
     }
     for (int i = 0; i < o->nfsr; i++)
         if (o->fsr_mat[i] < 0 || o->fsr_mat[i] >= M) { set_err(err, errlen, "material index out of range"); orc_destroy(o); return NULL; }
-    /* axial lattice: dz_eff = H / Nz; every layer plane must lie on it (a
-       whole number of dz from the bottom), so layers are whole numbers of
-       lattice cells (equal layers: cpl each; otherwise per the plane list) */
+    /* axial lattice: dz_eff = H / Nz.  Equal layers of cpl lattice cells
+       each when the height divides; otherwise layer planes in lattice units,
+       anywhere (the local axial mesh of Sec. 2.2), with exact plane ties
+       (split_coord) */
     double q = o->H / in->axial_spacing;
     long Nz = (fabs(q - nearbyint(q)) < 1e-9) ? (long)nearbyint(q) : (long)ceil(q);
     o->Nz = (int)Nz;
     o->dz = o->H / (double)Nz;
     o->lplane = malloc(sizeof(long) * (size_t)(o->nl + 1));
-    if (!in->layer_z) {
-        if (Nz % o->nl) { set_err(err, errlen, "layers are not whole numbers of axial spacings"); orc_destroy(o); return NULL; }
+    o->kplane = malloc(sizeof(double) * (size_t)(o->nl + 1));
+    o->qplane = malloc(sizeof(double) * (size_t)(o->nl + 1));
+    o->pfrac = malloc(sizeof(double) * (size_t)(o->nl + 1));
+    o->npfrac = 0;
+    if (!in->layer_z && Nz % o->nl == 0) {
         o->cpl = (int)(Nz / o->nl);
-        for (int L = 0; L <= o->nl; L++) o->lplane[L] = (long)L * o->cpl;
+        for (int L = 0; L <= o->nl; L++) {
+            o->lplane[L] = (long)L * o->cpl;
+            o->kplane[L] = (double)o->lplane[L];
+            o->qplane[L] = 0.0;
+        }
     } else {
+        /* planes in lattice units (equal layers off the lattice: the planes
+           L H / n_layers); a plane within 1e-9 of a lattice index is that
+           index; the first is 0 and the last the height, increasing */
         o->cpl = 0;
         for (int L = 0; L <= o->nl; L++) {
-            double u = in->layer_z[L] / o->dz;
-            long k = (long)nearbyint(u);
-            if (fabs(u - (double)k) > 1e-9 || (L > 0 && k <= o->lplane[L - 1]) || (L == 0 && k != 0) ||
-                (L == o->nl && k != Nz)) {
-                set_err(err, errlen, "layer planes must rise from 0 to the height on the axial lattice");
+            double zl = in->layer_z ? in->layer_z[L] : (double)L * o->H / (double)o->nl;
+            double u = zl / o->dz;
+            double k = nearbyint(u);
+            if (fabs(u - k) <= 1e-9) u = k;
+            if ((L == 0 && u != 0.0) || (L == o->nl && u != (double)Nz) ||
+                (L > 0 && !(u > o->kplane[L - 1] + 1e-6)) || !isfinite(u)) {
+                set_err(err, errlen, "layer planes must rise from 0 to the height");
                 orc_destroy(o);
                 return NULL;
             }
-            o->lplane[L] = k;
+            o->kplane[L] = u;
+            o->lplane[L] = (long)floor(u);
+        }
+        /* distinct fractional parts of the interior planes, ascending */
+        for (int L = 1; L < o->nl; L++) {
+            double f = o->kplane[L] - floor(o->kplane[L]);
+            if (f == 0.0) continue;
+            int seen = 0;
+            for (int q = 0; q < o->npfrac; q++) seen |= fabs(o->pfrac[q] - f) <= TIE_EPS;
+            if (!seen) o->pfrac[o->npfrac++] = f;
+        }
+        for (int a = 1; a < o->npfrac; a++)
+            for (int b = a; b > 0 && o->pfrac[b - 1] > o->pfrac[b]; b--) {
+                double t = o->pfrac[b]; o->pfrac[b] = o->pfrac[b - 1]; o->pfrac[b - 1] = t;
+            }
+        /* each plane's fraction is its pfrac entry (planes whose fractions
+           tie within TIE_EPS share one) */
+        for (int L = 0; L <= o->nl; L++) {
+            long n;
+            double f;
+            split_coord(o->pfrac, o->npfrac, o->kplane[L], &n, &f);
+            o->lplane[L] = n;
+            o->qplane[L] = f;
         }
     }
     /* azimuths */
@@ -891,7 +975,7 @@ void *orc_create(const orc_input *in, char *err, int errlen) {
 void orc_destroy(void *h) {
     orc_t *o = (orc_t *)h;
     if (!o) return;
-    void *ptrs[] = {o->lplane, o->has_pin, o->mat_in, o->mat_out, o->st, o->ss, o->nsf, o->chi, o->src,
+    void *ptrs[] = {o->lplane, o->kplane, o->qplane, o->pfrac, o->has_pin, o->mat_in, o->mat_out, o->st, o->ss, o->nsf, o->chi, o->src,
                     o->reg_base, o->fsr_mat, o->nx, o->ny, o->gg, o->Mcyc, o->phi_eff, o->span,
                     o->deff, o->lu, o->mu_gl, o->w_gl, o->cpol, o->cot, o->sinp, o->cosp,
                     o->a_off, o->t_azim, o->t_sface, o->t_sk, o->t_eface, o->t_ek, o->t_steps,
@@ -962,8 +1046,13 @@ int orc_stack_zeta(void *h, int t, int p, double *zeta) {
     orc_t *o = (orc_t *)h;
     if (t < 0 || t >= o->nt || p < 0 || p >= o->P) return -1;
     double cot, sn, cs;
-    int nb;
-    stack_geom(o, t, p, zeta, &nb, &cot, &sn, &cs);
+    int nb = (int)(o->soff[t + 1] - o->soff[t]);
+    long *zn = malloc(sizeof(long) * (size_t)(nb + 1));
+    double *zf = malloc(sizeof(double) * (size_t)(nb + 1));
+    stack_geom(o, t, p, zn, zf, &nb, &cot, &sn, &cs);
+    for (int j = 0; j <= nb; j++) zeta[j] = (double)zn[j] + zf[j];
+    free(zn);
+    free(zf);
     return nb;
 }
 

@@ -50,6 +50,17 @@ def lat3z(oracle_mod):
 
 
 @pytest.fixture(scope="module")
+def lat3o(oracle_mod):
+    """lat3 with layer planes off the axial lattice (0.6, 1.7 and 3.1 cm with
+    0.5 cm spacing: plane fractions 0.2, 0.4 and 0.2 of a spacing)."""
+    p = synth.lattice(3, n=3, G=3, height=4.0, n_layers=4, n_azim=8, n_polar=4,
+                      radial_spacing=0.15, axial_spacing=0.5, bc=(1, 1, 1, 1, 1, 1),
+                      n_gt=2, name="lat3o")
+    p = p.with_tracks(layer_z=np.array([0.0, 0.6, 1.7, 3.1, 4.0]))
+    return p, oracle_mod.Oracle(p, n_threads=2)
+
+
+@pytest.fixture(scope="module")
 def lat3(oracle_mod):
     p = synth.lattice(3, n=3, G=3, height=4.0, n_layers=4, n_azim=8, n_polar=4,
                       radial_spacing=0.15, axial_spacing=0.5, bc=(1, 1, 1, 1, 1, 1),
@@ -218,8 +229,12 @@ def _stack_checks(p, o, t, p_idx):
         l = ln[offs[k]:offs[k + 1]]
         ids, lens, h = bf.ray_fsrs_3d(p, x0, y0, dx, dy, tr["length"], (i + zeta[0]) * dz, cot,
                                       n_samples=100000)
-        a_i, a_l = bf.drop_short(f, l, 4 * h)
-        b_i, b_l = bf.drop_short(ids, lens, 4 * h)
+        # compare the pieces longer than a threshold that no exact piece lies
+        # near: a sampled run is within one sample length h of its piece
+        thr = next(T * h for T in (4, 8, 12, 16, 24, 32)
+                   if not np.any(np.abs(l - T * h) < 1.5 * h))
+        a_i, a_l = bf.drop_short(f, l, thr)
+        b_i, b_l = bf.drop_short(ids, lens, thr)
         np.testing.assert_array_equal(a_i, b_i)
         np.testing.assert_allclose(a_l, b_l, atol=8 * h)
         # total 3D length inside the box from the clipped line
@@ -229,8 +244,8 @@ def _stack_checks(p, o, t, p_idx):
         assert abs(l.sum() - (s_hi - s_lo) / sin) < 1e-9
 
 
-def test_3d_segments_bruteforce(pin, lat3, lat3r, lat3z):
-    for p, o in (pin, lat3, lat3r, lat3z):
+def test_3d_segments_bruteforce(pin, lat3, lat3r, lat3z, lat3o):
+    for p, o in (pin, lat3, lat3r, lat3z, lat3o):
         for t in range(0, o.n_tracks2d, max(1, o.n_tracks2d // 8)):
             for p_idx in range(p.n_polar):
                 _stack_checks(p, o, t, p_idx)
@@ -482,7 +497,101 @@ def test_unequal_layer_volumes_match_analytic(oracle_mod):
     assert abs(V.sum() - p.pitch ** 2 * p.height) < 1e-9 * p.pitch ** 2 * p.height
 
 
-def test_unequal_layers_off_the_lattice_rejected(oracle_mod):
-    p = synth.pin_cell(1, n_layers=3).with_tracks(layer_z=np.array([0.0, 0.6, 1.5, 2.0]))
-    with pytest.raises(ValueError):
-        oracle_mod.Oracle(p, n_threads=1)
+def test_layers_off_the_lattice_volumes_match_analytic(oracle_mod):
+    """Layer planes off the axial lattice (0.6 and 1.3 cm, Sec. 2.2's local
+    axial mesh): each FSR's tracked volume is its radial area times its
+    layer's height, within the sampling of the track layout, and closer as
+    the axial spacing is refined; the total volume stays exact."""
+    errs = []
+    for dz in (0.5, 0.1):
+        p = synth.pin_cell(1, radial_spacing=0.02, n_azim=32, n_layers=3,
+                           axial_spacing=dz).with_tracks(layer_z=np.array([0.0, 0.6, 1.3, 2.0]))
+        o = oracle_mod.Oracle(p, n_threads=4)
+        V = o.volumes().reshape(2, 3)
+        h = np.diff(p.layer_z)
+        fuel = math.pi * p.fuel_radius ** 2
+        ref = np.array([fuel * h, (p.pitch ** 2 - fuel) * h])
+        errs.append(np.abs(V / ref - 1).max())
+        assert abs(V.sum() - p.pitch ** 2 * p.height) < 1e-9 * p.pitch ** 2 * p.height
+    assert errs[0] < 0.01 and errs[1] < errs[0], errs
+
+
+def test_layers_off_the_lattice_infinite_medium_k(oracle_mod):
+    """An off-lattice axial mesh of the homogeneous, all-reflective pin cell
+    is still an infinite medium: k = nuSigma_f^T (Sigma_t - S^T)^-1 chi."""
+    p = synth.pin_cell(1, homogeneous=True, n_layers=3).with_tracks(
+        layer_z=np.array([0.0, 0.35, 1.45, 2.0]))
+    o = oracle_mod.Oracle(p, n_threads=2)
+    r = o.solve(tol_k=1e-12, tol_src=1e-11, max_iter=4000)
+    m = 0
+    A = np.diag(p.sigma_t[m]) - p.sigma_s[m].T
+    kinf = p.nu_sigma_f[m] @ np.linalg.solve(A, p.chi[m])
+    assert abs(r["k"] - kinf) < 1e-9, (r["k"], kinf)
+
+
+def test_layer_planes_must_rise_from_zero_to_the_height(oracle_mod):
+    for lz in ([0.1, 0.6, 1.5, 2.0], [0.0, 0.6, 1.5, 1.9], [0.0, 1.5, 0.6, 2.0]):
+        p = synth.pin_cell(1, n_layers=3).with_tracks(layer_z=np.array(lz))
+        with pytest.raises(ValueError):
+            oracle_mod.Oracle(p, n_threads=1)
+
+
+def test_equal_layers_off_the_lattice(oracle_mod):
+    """Three equal layers of 2/3 cm with a 0.5 cm axial spacing: their planes
+    lie 4/3 and 8/3 spacings up, off the lattice, and are taken as a plane
+    list L H / n_layers.  Volumes per layer match the analytic ones and the
+    3D segments the brute-force ray march."""
+    p = synth.pin_cell(1, radial_spacing=0.02, n_azim=32, n_layers=3, axial_spacing=0.5)
+    o = oracle_mod.Oracle(p, n_threads=4)
+    V = o.volumes().reshape(2, 3)
+    fuel = math.pi * p.fuel_radius ** 2
+    h = p.height / 3
+    ref = np.array([[fuel * h] * 3, [(p.pitch ** 2 - fuel) * h] * 3])
+    assert np.abs(V / ref - 1).max() < 0.01
+    assert abs(V.sum() - p.pitch ** 2 * p.height) < 1e-9 * p.pitch ** 2 * p.height
+    q = synth.pin_cell(1, n_layers=3, axial_spacing=0.5)
+    oq = oracle_mod.Oracle(q, n_threads=2)
+    for t in range(0, oq.n_tracks2d, max(1, oq.n_tracks2d // 6)):
+        for p_idx in range(q.n_polar):
+            _stack_checks(q, oq, t, p_idx)
+
+
+def _track_pieces(o, t, p_idx, i):
+    ti, ns, fs, ln = o.stack(t, p_idx)
+    k = int(np.flatnonzero(ti == i)[0])
+    a = int(ns[:k].sum())
+    return fs[a:a + ns[k]], ln[a:a + ns[k]]
+
+
+@pytest.mark.parametrize("down", [False, True])
+def test_plane_ties_are_exact(oracle_mod, down):
+    """A layer plane placed exactly at the height where a track starts (the
+    2D track's first boundary): an upward track that starts on the plane lies
+    above it from its first piece, a downward one below it.  Its pieces are
+    those of the same track with the plane moved by 1e-7 spacings to the
+    side the convention puts the track on (no piece of zero or rounding
+    length at the tie), and differ from the other side's (a short first
+    piece in the other layer)."""
+    base = synth.pin_cell(1, n_layers=3)
+    dz = 0.5
+    o0 = oracle_mod.Oracle(base.with_tracks(layer_z=np.array([0.0, 0.6, 1.3, 2.0])), n_threads=1)
+    p_idx = base.n_polar // 2 if down else 0
+    t = next(t for t in range(o0.n_tracks2d)
+             if 0.05 < o0.stack_zeta(t, p_idx)[0] % 1.0 < 0.95)
+    z0 = o0.stack_zeta(t, p_idx)[0]
+    f0 = z0 - math.floor(z0)
+    i = 1 - math.floor(z0)  # the track at u = i + z0 = 1 + f0 at its start
+
+    def pieces(eps):
+        mesh = np.array([0.0, (1.0 + f0 + eps) * dz, 1.3, 2.0])
+        o = oracle_mod.Oracle(base.with_tracks(layer_z=mesh), n_threads=1)
+        return _track_pieces(o, t, p_idx, i)
+
+    f_tie, l_tie = pieces(0.0)
+    f_lo, l_lo = pieces(-1e-7)   # the plane just below the start
+    f_hi, l_hi = pieces(1e-7)    # just above
+    assert l_tie.min() > 1e-6
+    same, other = (f_hi, f_lo) if down else (f_lo, f_hi)
+    np.testing.assert_array_equal(f_tie, same)
+    assert len(other) == len(f_tie) + 1
+    assert f_tie[0] % 3 == (0 if down else 1)
