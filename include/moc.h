@@ -87,9 +87,15 @@ typedef struct moc_tracks moc_tracks;
  * others mat_out.  With 1, 0, 1 a pin cell has two regions (circle, then
  * moderator).  Cells without a pin stay one region.
  *   layer_z       NULL (n_layers equal layers) or [n_layers + 1] layer planes
- *                 rising from 0 to height: unequal layers (a local axial
- *                 mesh); each plane must be a whole number of axial spacings
- *                 (moc_generate_tracks returns MOC_ERR_UNSUPPORTED otherwise). */
+ *                 rising from 0 to height: unequal layers (the local axial
+ *                 mesh of Sec. 2.2).  Planes may lie anywhere on the axial
+ *                 line: when every plane is a whole number of axial spacings
+ *                 the sweep uses segment templates and the shared tally;
+ *                 otherwise (also equal layers that are not whole spacings)
+ *                 each track direction is generated on its own against the
+ *                 planes (ties of a track end with a plane decided exactly,
+ *                 within 1e-10 of a spacing) and tallied into the FP64 FSR
+ *                 tally; a plane within 1e-9 of a spacing is on it. */
 typedef struct {
     int32_t ncx, ncy;
     double pitch, fuel_radius, height;
@@ -219,9 +225,10 @@ int moc_query_footprint(const moc_geometry *geom, const moc_track_params *params
  * tables (Sec. 3.2 Z-STACK), then on the device: per-track segment counts,
  * the preload plan (Sec. 4.2) and the stored segments, tracked FSR volumes,
  * and the initial state (phi = 1, boundary fluxes 0, k = 1).  Errors:
- * MOC_ERR_UNSUPPORTED when the layer height is not a whole number of axial
- * spacings or a problem with reflective faces has more than 2^29 3D tracks
- * (link destinations are 32-bit track-direction indices),
+ * MOC_ERR_UNSUPPORTED when a problem with reflective faces has more than
+ * 2^29 3D tracks (link destinations are 32-bit track-direction indices),
+ * more than 32 polar angles are asked for, or layer planes off the axial
+ * lattice have more than 4000 distinct fractions of a spacing,
  * MOC_ERR_OUT_OF_MEMORY when the device cannot hold the state, MOC_ERR_CUDA on
  * a CUDA failure. */
 int moc_generate_tracks(const moc_geometry *geom, const moc_track_params *params,
@@ -344,7 +351,8 @@ int moc_get_segments2d(const moc_tracks *tracks, int32_t t, int64_t cap, int32_t
  *   groups per lane, 22 2D segments per radial chunk (0: no unit is
  *   chunked), 23 tracks per synchronous block of the stored stacks (1: none,
  *   see moc_track_params.sync_block), 24 sweep slots (tracks plus the
- *   padding of synchronous blocks) */
+ *   padding of synchronous blocks), 25 1 when layer planes lie off the
+ *   axial lattice (11 is then 0) */
 int moc_tracks_info(const moc_tracks *tracks, int64_t *out, int32_t n);
 
 /* 3D segments of z-stack (t, p) as the device generator produces them
@@ -493,8 +501,8 @@ int moc_autotune(const moc_geometry *geom, const moc_track_params *base, int32_t
  * templates) fits next to the resident solves in the memory budget; a
  * request whose footprint alone exceeds the budget is not admitted and
  * finishes with MOC_ERR_OUT_OF_MEMORY.  A request that fails (track
- * generation, for example MOC_ERR_UNSUPPORTED for an axial mesh off the
- * lattice; an enqueue; a kernel) finishes with its own status while the other
+ * generation, for example MOC_ERR_UNSUPPORTED for more than 32 polar
+ * angles; an enqueue; a kernel) finishes with its own status while the other
  * resident solves go on.  Each resident solve
  * owns a stream and captured iteration graphs; a step enqueues a quantum of
  * outer iterations on every idle solve (their kernels overlap on the device),

@@ -242,7 +242,8 @@ INFO_KEYS = ["n_fsr", "groups", "tracks2d", "stacks", "tracks3d", "segments3d",
              "integrations_per_sweep", "stored_segments", "preloaded_stacks", "device_bytes",
              "n_z", "cells_per_layer", "sweep_blocks", "sweep_threads", "tally_mode", "precision",
              "sweep_smem_bytes", "tile_entries", "lanes_per_track", "max_segments_per_track",
-             "h2d_bytes", "groups_per_lane", "chunk_segments", "sync_block", "sweep_slots"]
+             "h2d_bytes", "groups_per_lane", "chunk_segments", "sync_block", "sweep_slots",
+             "off_lattice"]
 
 
 class Tracks:

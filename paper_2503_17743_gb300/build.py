@@ -22,7 +22,8 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["moc_kernels.cu", "moc_sweep.cu", "moc_sweep_f32g1.cu", "moc_sweep_f32g2.cu",
               "moc_sweep_f32g4.cu", "moc_sweep_f64.cu", "moc_api.cu", "moc_static.cu", "moc_peak.cu",
-              "moc_server.cu", "moc_tune.cu", "moc_trace.cu"]
+              "moc_server.cu", "moc_tune.cu", "moc_trace.cu",
+              "moc_sweep_ol.cu"]
 # per-file nvcc flags: the device 2D tracer must round like the host tracer
 CU_FLAGS = {"moc_trace.cu": ["-fmad=false"]}
 CPP_SOURCES = ["moc_host.cpp"]

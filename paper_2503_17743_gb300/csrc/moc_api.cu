@@ -44,6 +44,7 @@ struct moc_tracks {
     DevBuf d_desc, d_zn, d_zf, d_zf64, d_reg2d, d_len2d, d_len2d64, d_segs, d_fsr_mat, d_order;
     DevBuf d_tpl_off, d_tpl_loff, d_tpl_lmin, d_tpl_lidx;
     DevBuf d_dst, d_perm, d_win, d_chunk, d_hand, d_batch, d_lmap, d_reg_mat;
+    DevBuf d_zc0, d_zc1, d_zfd, d_zfd64, d_pl_n, d_pl_c, d_pl_f, d_pl_f64;  // planes off the lattice
     DevBuf d_phi, d_qr, d_tally, d_vol, d_psi[2], d_fiss, d_fiss_old, d_partial, d_scal, d_counter;
     DevBuf d_sigt, d_sigt64, d_sigs64, d_nsf64, d_chi64, d_src64, d_inv_st64, d_siga64, d_inv_vol;
     double *h_scal = nullptr;  // pinned mirror of the device scalars
@@ -169,6 +170,15 @@ void fill_views(moc_tracks *h) {
     dl.reg_mat = (const int32_t *)h->d_reg_mat.p;
     dl.hand_trk = (int32_t)h->hand_trk;
     dl.hand = h->d_hand.p;
+    dl.offlat = h->L.offlat;
+    dl.zc0 = (const int16_t *)h->d_zc0.p;
+    dl.zc1 = (const int16_t *)h->d_zc1.p;
+    dl.zfd = (const float *)h->d_zfd.p;
+    dl.zfd64 = (const double *)h->d_zfd64.p;
+    dl.pl_n = (const int32_t *)h->d_pl_n.p;
+    dl.pl_c = (const int32_t *)h->d_pl_c.p;
+    dl.pl_f = (const float *)h->d_pl_f.p;
+    dl.pl_f64 = (const double *)h->d_pl_f64.p;
     DevState &s = h->ds;
     s.phi = (double *)h->d_phi.p;
     s.qr = h->d_qr.p;
@@ -409,7 +419,8 @@ extern "C" int moc_query_footprint(const moc_geometry *g, const moc_track_params
     if (refl) b += 2 * L.n_gtrk * 4 * G * (int64_t)rs + L.n_gtrk * 4 * 4;  // boundary fluxes, links
     b += L.n_gtrk * (4 + 8);  // sweep order and record windows
     if (resident) *resident = b;
-    if (preload_all) {
+    if (preload_all && L.offlat) *preload_all = 0;  // planes off the lattice: nothing is stored
+    if (preload_all && !L.offlat) {
         // an upper estimate from the 2D segments: each 3D track crosses its 2D
         // segments plus the layer planes it passes
         double segs = 0;
@@ -477,6 +488,9 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
         // FP64 sweeps: a shared tile would add with compare-and-swap loops,
         // which measured slower than the native FP64 adds of the global tally
         if (mode == MOC_TALLY_AUTO) mode = h->precision == MOC_FP64 ? MOC_TALLY_GLOBAL : MOC_TALLY_SHARED;
+        // planes off the lattice: the frames' pieces differ, so the sweep of
+        // moc_sweep_ol.cu (FP64 global tally) takes every layout
+        if (L.offlat) mode = MOC_TALLY_GLOBAL;
         if (mode == MOC_TALLY_SHARED &&
             (prm->chunk_segments > 0 ||
              sweep_smem_bytes(h->precision, 1, 0, geo.M, G, h->gpl, h->tile_cap) > kWholeTile)) {
@@ -551,6 +565,17 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     TRY(upload(h.get(), h->d_zn, L.zn), "upload");
     TRY(upload(h.get(), h->d_zf, L.zf), "upload");
     if (!L.lmap.empty()) TRY(upload(h.get(), h->d_lmap, L.lmap), "upload");
+    if (L.offlat) {
+        TRY(upload(h.get(), h->d_zc0, L.zc[0]), "upload");
+        TRY(upload(h.get(), h->d_zc1, L.zc[1]), "upload");
+        TRY(upload(h.get(), h->d_zfd, L.zfd), "upload");
+        TRY(upload(h.get(), h->d_pl_n, L.pl_n), "upload");
+        TRY(upload(h.get(), h->d_pl_c, L.pl_c), "upload");
+        std::vector<float> pf(L.pl_f.begin(), L.pl_f.end());
+        TRY(upload(h.get(), h->d_pl_f, pf), "upload");
+        TRY(upload(h.get(), h->d_pl_f64, L.pl_f), "upload");
+        if (h->precision == MOC_FP64) TRY(upload(h.get(), h->d_zfd64, L.zfd64), "upload");
+    }
     TRY(upload(h.get(), h->d_reg2d, reg2d), "upload");
     TRY(upload(h.get(), h->d_len2d, len2d), "upload");
     TRY(upload(h.get(), h->d_fsr_mat, geo.fsr_mat), "upload");
@@ -592,7 +617,8 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     h->bytes -= d_nseg.n + d_max.n + d_tseg.n;
     int64_t segs_up = 0;
     for (auto v : h->stack_nseg) segs_up += v;
-    h->n_segments3d = 2 * segs_up;
+    // (the counts of layouts off the lattice hold both frames)
+    h->n_segments3d = L.offlat ? segs_up : 2 * segs_up;
     h->integrations = (double)h->n_segments3d * 2.0 * G;
     // Stored segments (EXP, Sec. 4.2).  What is stored is one template per
     // class r < cpl of a stack (the tracks r, r + cpl, ... are one-layer shifts
@@ -659,6 +685,7 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
             }
         }
         ok = ok && h->max_nseg < 65536;  // record windows hold the count in 16 bits
+        ok = ok && !L.offlat;            // no templates off the lattice
         if (!ok || (budget >= 0 && used + need > budget)) {
             for (int ph = 0; ph < Ph; ++ph) L.desc[(int64_t)t * Ph + ph].exp_base = -1;
             continue;
@@ -696,7 +723,7 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
             const int64_t o = d.trk_off;
             const int n = d.n_trk;
             d.slot_off = (int64_t)perm.size();
-            if (h->chunk_b > 0 && d.nb > h->chunk_b) {
+            if (L.offlat || (h->chunk_b > 0 && d.nb > h->chunk_b)) {
                 for (int k = 0; k < n; ++k) perm.push_back(k);
             } else if (B > 1 && d.exp_base >= 0) {
                 std::vector<std::pair<int32_t, std::vector<int32_t>>> blocks;
@@ -894,6 +921,11 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     if (bps < 1) { moc_set_error("sweep kernel does not fit on an SM"); return MOC_ERR_UNSUPPORTED; }
     if (prm->blocks_per_sm > 0) bps = std::min(bps, prm->blocks_per_sm);
     h->grid = std::max(1, std::min<int>(h->sms * bps, (int)std::min<int64_t>(ns, 1 << 30)));
+    if (L.offlat) {
+        // the off-lattice sweep: fixed blocks, eight per SM
+        h->block = sweep_ol_block();
+        h->grid = std::max(1, std::min(h->sms * 8, L.nt));
+    }
     if (h->chunk_b > 0) {
         // psi of the tracks between radial chunks: one region per block
         TRY(dalloc(h.get(), h->d_hand, (size_t)h->grid * h->hand_trk * 2 * G * real_size(h->precision)),
@@ -1015,6 +1047,9 @@ extern "C" int moc_state_create(const moc_tracks *t, const double *ext_source, m
     borrow(h->d_nsf64, base->d_nsf64); borrow(h->d_chi64, base->d_chi64);
     borrow(h->d_inv_st64, base->d_inv_st64); borrow(h->d_siga64, base->d_siga64);
     borrow(h->d_lmap, base->d_lmap); borrow(h->d_reg_mat, base->d_reg_mat);
+    borrow(h->d_zc0, base->d_zc0); borrow(h->d_zc1, base->d_zc1); borrow(h->d_zfd, base->d_zfd);
+    borrow(h->d_zfd64, base->d_zfd64); borrow(h->d_pl_n, base->d_pl_n); borrow(h->d_pl_c, base->d_pl_c);
+    borrow(h->d_pl_f, base->d_pl_f); borrow(h->d_pl_f64, base->d_pl_f64);
     // the solve state: its own
     TRY(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "stream");
     TRY(cudaMallocHost(&h->h_scal, SC_COUNT * sizeof(double)), "pinned scalars");
@@ -1286,14 +1321,14 @@ extern "C" int moc_get_volumes(moc_tracks *h, double *v) {
 
 extern "C" int moc_tracks_info(const moc_tracks *h, int64_t *out, int32_t n) {
     if (!h || !out) { moc_set_error("NULL argument"); return MOC_ERR_INVALID_ARG; }
-    const int64_t v[25] = {h->geom.nfsr, h->geom.G, h->L.nt, 2 * h->L.n_stacks, 2 * h->L.n_gtrk,
+    const int64_t v[26] = {h->geom.nfsr, h->geom.G, h->L.nt, 2 * h->L.n_stacks, 2 * h->L.n_gtrk,
                            h->n_segments3d, (int64_t)h->integrations, h->n_stored, h->n_exp_stacks,
                            (int64_t)h->bytes, h->L.Nz, h->L.cpl, h->grid, h->block,
                            h->tally_smem ? MOC_TALLY_SHARED : MOC_TALLY_GLOBAL, h->precision,
                            (int64_t)h->smem, h->tile_cap, sweep_lanes_per_track(h->geom.G, h->gpl),
                            h->max_nseg, (int64_t)h->h2d, h->gpl, h->chunk_b, h->sync_b > 1 ? h->sync_b : 1,
-                           h->n_slots};
-    for (int i = 0; i < n && i < 25; ++i) out[i] = v[i];
+                           h->n_slots, h->L.offlat};
+    for (int i = 0; i < n && i < 26; ++i) out[i] = v[i];
     return MOC_OK;
 }
 
@@ -1329,7 +1364,7 @@ extern "C" int moc_get_stack_segments(moc_tracks *h, int32_t t, int32_t p, int64
     DevBuf d_cnt;
     TRY(dalloc(h, d_cnt, (size_t)(d.n_trk + 1) * sizeof(int64_t)), "alloc");
     TRY(cudaMemsetAsync(d_cnt.p, 0, d_cnt.n, h->stream), "memset");
-    TRY(launch_track_counts(h->dl, s, (int64_t *)d_cnt.p, h->stream), "count");
+    TRY(launch_track_counts(h->dl, s, frame, (int64_t *)d_cnt.p, h->stream), "count");
     std::vector<int64_t> cnt(d.n_trk + 1, 0);
     TRY(cudaMemcpyAsync(cnt.data(), d_cnt.p, cnt.size() * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
     TRY(cudaStreamSynchronize(h->stream), "count");
@@ -1347,7 +1382,7 @@ extern "C" int moc_get_stack_segments(moc_tracks *h, int32_t t, int32_t p, int64
     TRY(upload(h, d_offs, offs), "upload");
     TRY(dalloc(h, d_f, (size_t)std::max<int64_t>(tot, 1) * 4), "alloc");
     TRY(dalloc(h, d_l, (size_t)std::max<int64_t>(tot, 1) * 8), "alloc");
-    TRY(launch_stack_segments(h->precision, h->dl, s, (const int64_t *)d_offs.p, (int32_t *)d_f.p,
+    TRY(launch_stack_segments(h->precision, h->dl, s, frame, (const int64_t *)d_offs.p, (int32_t *)d_f.p,
                               (double *)d_l.p, h->stream), "segments");
     std::vector<int32_t> f(tot);
     std::vector<double> l(tot);
@@ -1368,9 +1403,10 @@ extern "C" int moc_get_stack_segments(moc_tracks *h, int32_t t, int32_t p, int64
         n_seg[kk] = (int32_t)(offs[k + 1] - offs[k]);
         for (int64_t a = offs[k]; a < offs[k + 1]; ++a, ++q) {
             // the device lists (region, sweep layer) of the upward frame; the
-            // mirrored frame flips the layer, then the geometry's layer
+            // mirrored frame flips the layer, then the geometry's layer (planes
+            // off the lattice: the frame's own pieces, the geometry's layers)
             const int reg = f[a] / NL, Lv = f[a] % NL;
-            const int Lm = frame == 1 ? NL - 1 - Lv : Lv;
+            const int Lm = (frame == 1 && !L.offlat) ? NL - 1 - Lv : Lv;
             fsr[q] = reg * NLr + (L.lmap.empty() ? Lm : L.lmap[Lm]);
             length[q] = l[a];
         }

@@ -45,6 +45,17 @@ struct DevLayout {
     int32_t chunk_b;         // 2D segments per chunk (0: every unit is swept whole)
     int32_t hand_trk;        // tracks per block in the chunk hand-off buffer
     void *hand;              // [grid][hand_trk][2 frames][G] real: psi between chunks
+    // layer planes off the axial lattice (offlat = 1; cpl = 0): per frame f
+    // the rank of each boundary's fraction (zc[f]), the mirrored frame's own
+    // fractions (zfd, zfd64) and the NL + 1 planes of each frame (integer
+    // part, rank, fraction; frame-major)
+    int32_t offlat;
+    const int16_t *zc0, *zc1;
+    const float *zfd;
+    const double *zfd64;
+    const int32_t *pl_n, *pl_c;
+    const float *pl_f;
+    const double *pl_f64;
 };
 
 // State buffers of one solve.
@@ -224,6 +235,130 @@ __device__ __forceinline__ int count_otf(const DevLayout &dl, const StackDesc &d
     SegRange<float> r;
     for (int b = b0; b <= b1; ++b) {
         seg_range(dl, d, i, b, r);
+        n += r.Le - r.La + 1;
+    }
+    return n;
+}
+
+// ---------------------------------------------------------------------------
+// Layer planes off the axial lattice (Sec. 2.2's local axial mesh).  The
+// frames no longer share their pieces: each walks its own planes (frame 1 in
+// the mirrored coordinate, the same numbers as frame 0's lattice coordinate,
+// its layer L standing for the geometry's NL - 1 - L).  A point is the pair
+// (integer part, rank of its fraction in that frame); every decision is a
+// comparison of such pairs, the lengths use the fractions.
+
+struct OLPoint {
+    int32_t n, c;
+};
+__device__ __forceinline__ bool ol_le(int32_t an, int32_t ac, int32_t bn, int32_t bc) {
+    return an < bn || (an == bn && ac <= bc);
+}
+__device__ __forceinline__ bool ol_lt(int32_t an, int32_t ac, int32_t bn, int32_t bc) {
+    return an < bn || (an == bn && ac < bc);
+}
+
+template <typename real>
+__device__ __forceinline__ real ol_zf(const DevLayout &dl, int frame, int idx);
+template <>
+__device__ __forceinline__ float ol_zf<float>(const DevLayout &dl, int frame, int idx) {
+    return __ldg((frame ? dl.zfd : dl.zf) + idx);
+}
+template <>
+__device__ __forceinline__ double ol_zf<double>(const DevLayout &dl, int frame, int idx) {
+    return __ldg((frame ? dl.zfd64 : dl.zf64) + idx);
+}
+template <typename real>
+__device__ __forceinline__ real ol_pf(const DevLayout &dl, int k);
+template <>
+__device__ __forceinline__ float ol_pf<float>(const DevLayout &dl, int k) { return __ldg(dl.pl_f + k); }
+template <>
+__device__ __forceinline__ double ol_pf<double>(const DevLayout &dl, int k) { return __ldg(dl.pl_f64 + k); }
+
+// The layer of frame `frame` holding the point (n, c): the largest L < NL
+// whose lower plane lies at or below it (upper = false: the start of a piece,
+// a point on a plane belongs to the layer above) or strictly below it
+// (upper = true: the end of a piece, a point on a plane ends the layer below)
+__device__ __forceinline__ int ol_layer(const DevLayout &dl, int frame, int32_t n, int32_t c, bool upper) {
+    const int32_t *pn = dl.pl_n + frame * (dl.NL + 1), *pc = dl.pl_c + frame * (dl.NL + 1);
+    int lo = 0, hi = dl.NL - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int32_t mn = __ldg(pn + mid), mc = __ldg(pc + mid);
+        const bool below = upper ? ol_lt(mn, mc, n, c) : ol_le(mn, mc, n, c);
+        if (below) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename real>
+struct OLRange {
+    int32_t ua, ub;   // integer parts at the piece ends (clipped to [0, Nz])
+    real fa, fb;      // fractions at the ends (this frame's)
+    bool full;        // spans the whole 2D segment (Eq. 8 applies)
+    int32_t La, Le;   // first and last layer of this frame crossed
+};
+
+template <typename real>
+__device__ __forceinline__ void ol_range(const DevLayout &dl, const StackDesc &d, int i, int b, int frame,
+                                         OLRange<real> &r) {
+    const int z = d.zoff + b;
+    const int16_t *zc = frame ? dl.zc1 : dl.zc0;
+    int32_t ua = i + __ldg(dl.zn + z), ca = __ldg(zc + z);
+    int32_t ub = i + __ldg(dl.zn + z + 1), cb = __ldg(zc + z + 1);
+    real fa = ol_zf<real>(dl, frame, z), fb = ol_zf<real>(dl, frame, z + 1);
+    bool full = true;
+    // rank 1 is the fraction 0 in both frames
+    if (ua < 0) { ua = 0; ca = 1; fa = (real)0; full = false; }
+    if (ub > dl.Nz || (ub == dl.Nz && cb > 1)) { ub = dl.Nz; cb = 1; fb = (real)0; full = false; }
+    r.ua = ua; r.fa = fa; r.ub = ub; r.fb = fb; r.full = full;
+    r.La = ol_layer(dl, frame, ua, ca, false);
+    r.Le = ol_layer(dl, frame, ub, cb, true);
+}
+
+template <typename real>
+__device__ __forceinline__ real ol_len(const DevLayout &dl, const StackDesc &d, int b, int frame,
+                                       const OLRange<real> &r, int L) {
+    const real lam = lam_of(d, (real)0);
+    if (r.La == r.Le) {
+        if (r.full) return len_2d<real>(dl, d.seg2d_off + b) * isin_of(d, (real)0);   // Eq. 8
+        return ((real)(r.ub - r.ua) + (r.fb - r.fa)) * lam;
+    }
+    const int k = frame * (dl.NL + 1);
+    if (L == r.La)
+        return ((real)(__ldg(dl.pl_n + k + L + 1) - r.ua) + (ol_pf<real>(dl, k + L + 1) - r.fa)) * lam;
+    if (L == r.Le) return ((real)(r.ub - __ldg(dl.pl_n + k + L)) + (r.fb - ol_pf<real>(dl, k + L))) * lam;
+    return ((real)(__ldg(dl.pl_n + k + L + 1) - __ldg(dl.pl_n + k + L)) +                  // Eq. 11
+            (ol_pf<real>(dl, k + L + 1) - ol_pf<real>(dl, k + L))) * lam;
+}
+
+// the pieces of track i of frame `frame`, in the order of `sense`:
+// visit(b, the geometry's layer, length)
+template <typename real, class Visit>
+__device__ __forceinline__ void walk_ol(const DevLayout &dl, const StackDesc &d, int i, int frame,
+                                        int sense, Visit &visit) {
+    const int b0 = first_seg(dl, d, i), b1 = last_seg(dl, d, i);
+    const int NL = dl.NL;
+    OLRange<real> r;
+    if (sense == 0) {
+        for (int b = b0; b <= b1; ++b) {
+            ol_range(dl, d, i, b, frame, r);
+            for (int L = r.La; L <= r.Le; ++L) visit(b, frame ? NL - 1 - L : L, ol_len(dl, d, b, frame, r, L));
+        }
+    } else {
+        for (int b = b1; b >= b0; --b) {
+            ol_range(dl, d, i, b, frame, r);
+            for (int L = r.Le; L >= r.La; --L) visit(b, frame ? NL - 1 - L : L, ol_len(dl, d, b, frame, r, L));
+        }
+    }
+}
+
+__device__ __forceinline__ int count_ol(const DevLayout &dl, const StackDesc &d, int i, int frame) {
+    const int b0 = first_seg(dl, d, i), b1 = last_seg(dl, d, i);
+    int n = 0;
+    OLRange<float> r;
+    for (int b = b0; b <= b1; ++b) {
+        ol_range(dl, d, i, b, frame, r);
         n += r.Le - r.La + 1;
     }
     return n;

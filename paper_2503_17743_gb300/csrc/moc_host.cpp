@@ -23,6 +23,10 @@
 //    spacings; z_0 / dz = frac(1/2 + M_T c / Mcyc) (Eq. 5 lattice offset).
 //  * lattice coordinates zeta = (z_0 + s cot)/dz within 1e-10 of an integer
 //    are that integer (exact ties are decided by integer rules).
+//  * layer planes off the lattice (Sec. 2.2's local axial mesh; equal layers
+//    that are not whole spacings too): a fraction of zeta within 1e-10 of a
+//    plane's fraction is that fraction, per frame, and ties are decided on
+//    (integer part, rank of the fraction) pairs.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -179,6 +183,72 @@ void trace_2d(const moc_geometry &g, double x0, double y0, double dx, double dy,
 
 // ---------------------------------------------------------------------------
 
+// the fraction of frame `fr` that f ties with (within kTie), else f
+static double snap_frac(const Layout &L, int fr, double f) {
+    for (double x : L.pfr[fr])
+        if (std::fabs(f - x) <= kTie) return x;
+    return f;
+}
+
+// rank of a (snapped) fraction among frame fr's plane fractions
+static int16_t frac_rank(const Layout &L, int fr, double f) {
+    int below = 0, on = 0;
+    for (double x : L.pfr[fr]) {
+        below += x < f;
+        on |= x == f;
+    }
+    return (int16_t)(2 * below + on);
+}
+
+// Off-lattice planes u[0..nl] (lattice units): the fractions of each frame
+// and the planes per frame.  Frame 0's fractions are the distinct ones of the
+// interior planes in plane order (a fraction within kTie of an earlier one is
+// that one); frame 1's are 1 - those.
+static void offlat_planes(Layout &L, const std::vector<double> &u) {
+    const int nl = (int)u.size() - 1;
+    L.offlat = 1;
+    L.cpl = 0;
+    L.nlv = nl;
+    for (int fr = 0; fr < 2; ++fr) L.pfr[fr].assign(1, 0.0);
+    for (int l = 1; l < nl; ++l) {
+        const double f = u[l] - std::floor(u[l]);
+        if (f == 0.0) continue;
+        bool seen = false;
+        for (double x : L.pfr[0]) seen |= x != 0.0 && std::fabs(x - f) <= kTie;
+        if (!seen) L.pfr[0].push_back(f);
+    }
+    for (size_t q = 1; q < L.pfr[0].size(); ++q) {
+        const double m = 1.0 - L.pfr[0][q];
+        bool seen = false;
+        for (double x : L.pfr[1]) seen |= x != 0.0 && std::fabs(x - m) <= kTie;
+        if (!seen) L.pfr[1].push_back(m);
+    }
+    for (int fr = 0; fr < 2; ++fr) std::sort(L.pfr[fr].begin(), L.pfr[fr].end());
+    L.pl_n.assign(2 * (nl + 1), 0);
+    L.pl_c.assign(2 * (nl + 1), 0);
+    L.pl_f.assign(2 * (nl + 1), 0.0);
+    for (int l = 0; l <= nl; ++l) {
+        const double n = std::floor(u[l]);
+        const double f = snap_frac(L, 0, u[l] - n);
+        L.pl_n[l] = (int32_t)n;
+        L.pl_f[l] = f;
+        L.pl_c[l] = frac_rank(L, 0, f);
+        // mirrored: plane nl - l of frame 0 at Nz - u
+        const int m = nl - l;
+        const double nm = std::floor(u[m]);
+        const double fm = snap_frac(L, 0, u[m] - nm);
+        const int k = nl + 1 + l;
+        if (fm == 0.0) {
+            L.pl_n[k] = L.Nz - (int32_t)nm;
+            L.pl_f[k] = 0.0;
+        } else {
+            L.pl_n[k] = L.Nz - (int32_t)nm - 1;
+            L.pl_f[k] = snap_frac(L, 1, 1.0 - fm);
+        }
+        L.pl_c[k] = frac_rank(L, 1, L.pl_f[k]);
+    }
+}
+
 int moc_build_layout(const moc_geometry &g, const moc_track_params &prm, Layout &L,
                      std::string &err) {
     if (prm.n_azim < 4 || prm.n_azim % 4 || prm.n_polar < 2 || prm.n_polar % 2 ||
@@ -201,40 +271,45 @@ int moc_build_layout(const moc_geometry &g, const moc_track_params &prm, Layout 
     L.Nz = (int)Nz;
     L.dz = g.H / (double)Nz;
     L.lmap.clear();
-    if (g.layer_z.empty()) {
-        if (Nz % g.nl) {
-            err = "layer height is not a whole number of axial spacings";
-            return MOC_ERR_UNSUPPORTED;
-        }
+    L.offlat = 0;
+    if (g.layer_z.empty() && Nz % g.nl == 0) {
         L.cpl = (int)(Nz / g.nl);
         L.nlv = g.nl;
     } else {
-        // every plane on the axial lattice; the sweep's layers are the
-        // coarsest uniform grid that holds them all
-        std::vector<int64_t> P(g.nl + 1);
-        int64_t h = 0;
+        // the planes in lattice units (equal layers that are not whole
+        // spacings: the planes l H / nl); a plane within 1e-9 of a lattice
+        // index is that index
+        std::vector<double> u(g.nl + 1);
+        bool on = true;
         for (int l = 0; l <= g.nl; ++l) {
-            const double u = g.layer_z[l] / L.dz;
-            P[l] = (int64_t)std::nearbyint(u);
-            if (std::fabs(u - (double)P[l]) > 1e-9) {
-                err = "layer planes must lie on the axial lattice (whole numbers of axial spacings)";
+            const double zl = g.layer_z.empty() ? (double)l * g.H / (double)g.nl : g.layer_z[l];
+            u[l] = zl / L.dz;
+            const double k = std::nearbyint(u[l]);
+            if (std::fabs(u[l] - k) <= 1e-9) u[l] = k;
+            else on = false;
+            if ((l == 0 && u[l] != 0.0) || (l == g.nl && u[l] != (double)Nz) ||
+                (l > 0 && !(u[l] > u[l - 1] + 1e-6)) || !std::isfinite(u[l])) {
+                err = "layer planes must rise from 0 to the height";
                 return MOC_ERR_UNSUPPORTED;
             }
-            if (l > 0) h = gcd64(h, P[l] - P[l - 1]);
         }
-        if (P[0] != 0 || P[g.nl] != Nz || h < 1) {
-            err = "layer planes must rise from 0 to the height";
-            return MOC_ERR_UNSUPPORTED;
-        }
-        L.cpl = (int)h;
-        L.nlv = (int)(Nz / h);
-        if (L.nlv != g.nl) {
-            L.lmap.resize(L.nlv);
-            int l = 0;
-            for (int v = 0; v < L.nlv; ++v) {
-                while ((int64_t)v * h >= P[l + 1]) ++l;
-                L.lmap[v] = l;
+        if (on) {
+            // every plane on the axial lattice; the sweep's layers are the
+            // coarsest uniform grid that holds them all
+            int64_t h = 0;
+            for (int l = 1; l <= g.nl; ++l) h = gcd64(h, (int64_t)u[l] - (int64_t)u[l - 1]);
+            L.cpl = (int)h;
+            L.nlv = (int)(Nz / h);
+            if (L.nlv != g.nl) {
+                L.lmap.resize(L.nlv);
+                int l = 0;
+                for (int v = 0; v < L.nlv; ++v) {
+                    while ((double)((int64_t)v * h) >= u[l + 1]) ++l;
+                    L.lmap[v] = l;
+                }
             }
+        } else {
+            offlat_planes(L, u);
         }
     }
     // azimuth pairs
@@ -465,6 +540,15 @@ int moc_build_layout(const moc_geometry &g, const moc_track_params &prm, Layout 
     L.zn.resize(zt);
     L.zf.resize(zt);
     L.zf64.resize(zt);
+    if (L.offlat) {
+        if (L.pfr[0].size() + L.pfr[1].size() > 8000) {
+            err = "too many distinct layer-plane fractions";
+            return MOC_ERR_UNSUPPORTED;
+        }
+        for (int fr = 0; fr < 2; ++fr) L.zc[fr].resize(zt);
+        L.zfd.resize(zt);
+        L.zfd64.resize(zt);
+    }
     int64_t zpos = 0, gtrk = 0;
     for (int t = 0; t < nt; ++t) {
         const int a = L.t_azim[t];
@@ -481,9 +565,20 @@ int moc_build_layout(const moc_geometry &g, const moc_track_params &prm, Layout 
             for (int j = 0; j <= nb; ++j) {
                 double z = snap_tie(z0 + pos[j] * slope);
                 double fl = std::floor(z);
+                double fr = z - fl;
+                if (L.offlat) {
+                    // each frame's fraction, ties with its planes made exact
+                    const double fu = snap_frac(L, 0, fr), fd = snap_frac(L, 1, fr);
+                    L.zc[0][zpos + j] = frac_rank(L, 0, fu);
+                    L.zc[1][zpos + j] = frac_rank(L, 1, fd);
+                    L.zfd[zpos + j] = (float)fd;
+                    L.zfd64[zpos + j] = fd;
+                    fr = fu;
+                    z = fl + fr;
+                }
                 L.zn[zpos + j] = (int32_t)fl;
-                L.zf[zpos + j] = (float)(z - fl);
-                L.zf64[zpos + j] = z - fl;
+                L.zf[zpos + j] = (float)fr;
+                L.zf64[zpos + j] = fr;
                 if (j == 0) L.zeta0[s] = z;
                 if (j == nb) L.zetaL[s] = z;
             }

@@ -85,6 +85,24 @@ struct Layout {
     // geometry's layer of each (empty when they are the same layers)
     int nlv = 0;
     std::vector<int32_t> lmap;
+    // Layer planes off the axial lattice (the local axial mesh of Sec. 2.2;
+    // cpl = 0, nlv = the geometry's layers).  A lattice coordinate is its
+    // integer part (zn) and fraction.  Per frame (0: upward, 1: mirrored
+    // z -> H - z, whose planes sit at Nz minus the upward ones) a fraction
+    // within 1e-10 of one of that frame's plane fractions is that fraction
+    // (zf / zf64 for frame 0, zfd / zfd64 for frame 1), and zc ranks it among
+    // them (0 included): 2 x (the plane fractions below it) + 1 if it is one
+    // of them.  Comparing (integer part, rank) pairs then decides every
+    // "below / on / above a plane" exactly, as the host's FP64 comparisons
+    // do.  pl_*: per frame the nlv + 1 planes in that frame's lattice
+    // coordinate, ascending: integer part, rank, fraction.
+    int offlat = 0;
+    std::vector<double> pfr[2];            // per frame: 0 and the plane fractions, ascending
+    std::vector<int16_t> zc[2];            // per frame: rank of each boundary's fraction
+    std::vector<float> zfd;                // mirrored frame: the fraction snapped to its planes
+    std::vector<double> zfd64;
+    std::vector<int32_t> pl_n, pl_c;       // [2][nlv + 1]
+    std::vector<double> pl_f;
     // azimuth pairs m = 0..nq-1
     std::vector<int64_t> nx, ny, gg, Mcyc;
     std::vector<double> phi, span, deff, lu;

@@ -42,7 +42,10 @@ __global__ void k_count_stacks(DevLayout dl, int64_t n_stacks, int64_t *stack_ns
         double acc = 0;
         int mx = 0;
         for (int k = threadIdx.x; k < d.n_trk; k += blockDim.x) {
-            int n = count_otf(dl, d, d.i_lo + k);
+            // planes off the lattice: both frames' pieces (else the upward
+            // frame's, which the mirrored frame repeats)
+            const int n = dl.offlat ? count_ol(dl, d, d.i_lo + k, 0) + count_ol(dl, d, d.i_lo + k, 1)
+                                    : count_otf(dl, d, d.i_lo + k);
             trk_nseg[d.trk_off + k] = n;
             acc += n;
             mx = max(mx, n);
@@ -245,13 +248,34 @@ struct VolVisit {
     }
 };
 
+// planes off the lattice: each frame's pieces on their own
+template <typename real>
+struct VolVisitOL {
+    const DevLayout *dl;
+    const int32_t *reg2d;
+    unsigned long long *acc;
+    double c;
+    __device__ void operator()(int b, int L, real len) {
+        fix4_add(acc + 4 * fsr_of(*dl, __ldg(reg2d + b), L), c * (double)len);
+    }
+};
+
 template <typename real>
 __global__ void k_volumes(DevLayout dl, int64_t n_stacks, unsigned long long *acc) {
     for (int64_t s = blockIdx.x; s < n_stacks; s += gridDim.x) {
         const StackDesc d = dl.desc[s];
         // each stored track carries two directions of equal weight, in two frames
-        VolVisit<real> v{&dl, dl.reg2d + d.seg2d_off, dl.NL, acc, 2.0 * d.W / (4.0 * MOC_PI)};
-        for (int k = threadIdx.x; k < d.n_trk; k += blockDim.x) walk_otf<real>(dl, d, d.i_lo + k, 0, v);
+        const double c = 2.0 * d.W / (4.0 * MOC_PI);
+        if (dl.offlat) {
+            VolVisitOL<real> v{&dl, dl.reg2d + d.seg2d_off, acc, c};
+            for (int k = threadIdx.x; k < d.n_trk; k += blockDim.x) {
+                walk_ol<real>(dl, d, d.i_lo + k, 0, 0, v);
+                walk_ol<real>(dl, d, d.i_lo + k, 1, 0, v);
+            }
+        } else {
+            VolVisit<real> v{&dl, dl.reg2d + d.seg2d_off, dl.NL, acc, c};
+            for (int k = threadIdx.x; k < d.n_trk; k += blockDim.x) walk_otf<real>(dl, d, d.i_lo + k, 0, v);
+        }
     }
 }
 
@@ -285,13 +309,16 @@ struct ListVisit {
     }
 };
 
+// planes off the lattice: the pieces of the given frame, with the geometry's
+// layers
 template <typename real>
-__global__ void k_stack_segments(DevLayout dl, int64_t s, const int64_t *offs, int32_t *fsr_u,
+__global__ void k_stack_segments(DevLayout dl, int64_t s, int frame, const int64_t *offs, int32_t *fsr_u,
                                  double *len) {
     const StackDesc d = dl.desc[s];
     for (int k = threadIdx.x; k < d.n_trk; k += blockDim.x) {
         ListVisit<real> v{dl.reg2d + d.seg2d_off, dl.NL, fsr_u + offs[k], len + offs[k]};
-        walk_otf<real>(dl, d, d.i_lo + k, 0, v);
+        if (dl.offlat) walk_ol<real>(dl, d, d.i_lo + k, frame, 0, v);
+        else walk_otf<real>(dl, d, d.i_lo + k, 0, v);
     }
 }
 
@@ -532,14 +559,15 @@ size_t segrec_size(int precision) {
     return precision == MOC_FP64 ? sizeof(SegRec<double>) : sizeof(SegRec<float>);
 }
 
-// per-track segment counts of one stack (introspection)
-__global__ void k_track_counts(DevLayout dl, int64_t s, int64_t *cnt) {
+// per-track segment counts of one stack and frame (introspection)
+__global__ void k_track_counts(DevLayout dl, int64_t s, int frame, int64_t *cnt) {
     const StackDesc d = dl.desc[s];
-    for (int k = threadIdx.x; k < d.n_trk; k += blockDim.x) cnt[k + 1] = count_otf(dl, d, d.i_lo + k);
+    for (int k = threadIdx.x; k < d.n_trk; k += blockDim.x)
+        cnt[k + 1] = dl.offlat ? count_ol(dl, d, d.i_lo + k, frame) : count_otf(dl, d, d.i_lo + k);
 }
 
-cudaError_t launch_track_counts(const DevLayout &dl, int64_t stack, int64_t *cnt, cudaStream_t s) {
-    k_track_counts<<<1, 128, 0, s>>>(dl, stack, cnt);
+cudaError_t launch_track_counts(const DevLayout &dl, int64_t stack, int frame, int64_t *cnt, cudaStream_t s) {
+    k_track_counts<<<1, 128, 0, s>>>(dl, stack, frame, cnt);
     return cudaGetLastError();
 }
 
@@ -572,10 +600,10 @@ cudaError_t launch_volumes(int precision, const DevLayout &dl, int64_t n_stacks,
     return cudaGetLastError();
 }
 
-cudaError_t launch_stack_segments(int precision, const DevLayout &dl, int64_t stack,
+cudaError_t launch_stack_segments(int precision, const DevLayout &dl, int64_t stack, int frame,
                                   const int64_t *offs, int32_t *fsr, double *len, cudaStream_t s) {
-    if (precision == MOC_FP64) k_stack_segments<double><<<1, 128, 0, s>>>(dl, stack, offs, fsr, len);
-    else k_stack_segments<float><<<1, 128, 0, s>>>(dl, stack, offs, fsr, len);
+    if (precision == MOC_FP64) k_stack_segments<double><<<1, 128, 0, s>>>(dl, stack, frame, offs, fsr, len);
+    else k_stack_segments<float><<<1, 128, 0, s>>>(dl, stack, frame, offs, fsr, len);
     return cudaGetLastError();
 }
 

@@ -13,7 +13,7 @@ cudaError_t launch_tpl_count(const DevLayout &dl, const int32_t *exp_stacks, int
 cudaError_t launch_tpl_write(int precision, const DevLayout &dl, const int32_t *exp_stacks,
                              int64_t n_exp, void *recs, int32_t *lidx, int grid, cudaStream_t s);
 size_t segrec_size(int precision);
-cudaError_t launch_track_counts(const DevLayout &dl, int64_t stack, int64_t *cnt, cudaStream_t s);
+cudaError_t launch_track_counts(const DevLayout &dl, int64_t stack, int frame, int64_t *cnt, cudaStream_t s);
 // per track of the stored stacks, in sweep order: (record count << 48) | first record
 cudaError_t launch_windows(const DevLayout &dl, int64_t n_stacks, uint64_t *win, int grid,
                            cudaStream_t s);
@@ -26,7 +26,7 @@ cudaError_t launch_links(const DevLayout &dl, int64_t n_stacks, int32_t *dst, in
 // written to vol [nfsr]
 cudaError_t launch_volumes(int precision, const DevLayout &dl, int64_t n_stacks, int64_t nfsr,
                            unsigned long long *acc, double *vol, int grid, cudaStream_t s);
-cudaError_t launch_stack_segments(int precision, const DevLayout &dl, int64_t stack,
+cudaError_t launch_stack_segments(int precision, const DevLayout &dl, int64_t stack, int frame,
                                   const int64_t *offs, int32_t *fsr, double *len, cudaStream_t s);
 // the sweep (moc_sweep.cu); gpl = energy groups per lane (1 or 2, FP32 only)
 int sweep_default_gpl(int precision, int G);
@@ -49,6 +49,12 @@ cudaError_t launch_sweep(int precision, int tally_smem, int gpl, const DevLayout
                          const DevState &st, const int32_t *order, int32_t n_work, int32_t cap,
                          const void *psi_in, void *psi_out, int32_t *counter, int grid, int block,
                          size_t smem, cudaStream_t s);
+// The sweep of layouts with layer planes off the axial lattice
+// (moc_sweep_ol.cu): block sweep_ol_block() threads, no dynamic shared memory
+int sweep_ol_block();
+cudaError_t launch_sweep_ol(int precision, const DevLayout &dl, const DevState &st, const int32_t *order,
+                            int32_t n_work, const void *psi_in, void *psi_out, int32_t *counter, int grid,
+                            cudaStream_t s);
 // One sweep of n solves sharing the layout dl (shared tally, no radial
 // chunks): items[n] (device) hold their states; n_units = units in order.
 cudaError_t launch_sweep_batch(int precision, int gpl, const DevLayout &dl, const DevState &st,

@@ -86,6 +86,7 @@ cudaError_t launch_sweep(int precision, int tally_smem, int gpl, const DevLayout
                          const DevState &st, const int32_t *order, int32_t n_work, int32_t cap,
                          const void *psi_in, void *psi_out, int32_t *counter, int grid, int block,
                          size_t smem, cudaStream_t s) {
+    if (dl.offlat) return launch_sweep_ol(precision, dl, st, order, n_work, psi_in, psi_out, counter, grid, s);
     const void *f = sweep_fn(precision, tally_smem, tally_smem && dl.chunk_b > 0, dl.G, gpl, 0,
                              tally_smem && dl.sync_b > 0 ? 1 : 0);
     cudaError_t e = allow_dynamic_smem(f, smem);

@@ -324,6 +324,8 @@ def workload(name: str, seed: int = 1) -> Problem:
     * ``pin_cell_rings`` - the pin cell with 3 fuel rings, 2 moderator rings
                        and 4 sectors
     * ``lattice5_axial`` - lattice5 with unequal layers (0.5, 1, 1.5, 1 cm)
+    * ``lattice5_offaxial`` - lattice5 with layer planes off the axial lattice
+                       (0.7, 1.85, 3.15 cm)
     * ``asm1_absorber`` - one assembly + reflector on two sides, 8 cm, absorber
                        in the top layer of half the guide tubes
     * ``asm3x3``     - 3x3 assemblies + reflector on two sides, 64 cm
@@ -351,6 +353,13 @@ def workload(name: str, seed: int = 1) -> Problem:
         return replace(lattice(seed, n=5, n_azim=16, n_polar=4, radial_spacing=0.1,
                                axial_spacing=0.5, height=4.0, n_layers=4, name="lattice5_axial"),
                        layer_z=np.array([0.0, 0.5, 1.5, 3.0, 4.0]))
+    if name == "lattice5_offaxial":
+        # layer planes off the 0.5 cm axial lattice (Sec. 2.2's local axial
+        # mesh): 0.7, 1.85 and 3.15 cm, 0.4, 0.7 and 0.3 of a spacing above
+        # a lattice plane
+        return replace(lattice(seed, n=5, n_azim=16, n_polar=4, radial_spacing=0.1,
+                               axial_spacing=0.5, height=4.0, n_layers=4, name="lattice5_offaxial"),
+                       layer_z=np.array([0.0, 0.7, 1.85, 3.15, 4.0]))
     if name == "pin_cell_rings":
         return replace(pin_cell(seed), name="pin_cell_rings", fuel_rings=3, moderator_rings=2,
                        sectors=4)

@@ -454,11 +454,113 @@ def test_unequal_layers_power_iterations(name, prec, ktol, ftol):
     tr.close()
 
 
-def test_layer_planes_off_the_axial_lattice_rejected():
-    p = _lat3z().with_tracks(layer_z=np.array([0.0, 0.6, 1.5, 3.0, 4.0]))
-    from paper_2503_17743_gb300 import MocError
-    with pytest.raises(MocError):
-        Tracks(Geometry(p), track_params(p))
+# ------------------------------------------- layer planes off the axial lattice
+
+def _lat3o():
+    """Planes 0.6, 1.7 and 3.1 cm with 0.5 cm spacing (fractions 0.2, 0.4 and
+    0.2 of a spacing; the mirrored frame's 0.8 and 0.6), mixed faces."""
+    return _lat3(bc=(1, 0, 1, 1, 0, 1), seed=7).with_tracks(layer_z=np.array([0.0, 0.6, 1.7, 3.1, 4.0]),
+                                                            name="lat3o")
+
+
+def _lat3_eq3():
+    """Three equal layers of 4/3 cm with 0.5 cm spacing: planes 8/3 and 16/3
+    spacings up (equal layers that are not whole spacings)."""
+    return synth.lattice(8, n=3, G=3, height=4.0, n_layers=3, n_azim=8, n_polar=4,
+                         radial_spacing=0.15, axial_spacing=0.5, bc=(1, 1, 1, 1, 1, 1), n_gt=2,
+                         name="lat3_eq3")
+
+
+def _pin_ties():
+    """The pin cell with one plane where an upward track of a stack starts
+    and one where a downward track starts: tracks that touch a plane at
+    their first boundary (exact ties, decided from the FP64 layout)."""
+    base = synth.pin_cell(1, n_layers=3)
+    o0 = oracle.Oracle(base.with_tracks(layer_z=np.array([0.0, 0.6, 1.3, 2.0])), n_threads=1)
+
+    def start_frac(p_idx):
+        for t in range(o0.n_tracks2d):
+            z = o0.stack_zeta(t, p_idx)[0]
+            f = z - np.floor(z)
+            if 0.05 < f < 0.95:
+                return f
+        raise AssertionError("no track start off the lattice")
+
+    fu, fd = start_frac(0), start_frac(base.n_polar // 2)
+    mesh = np.array([0.0, (1.0 + fu) * 0.5, (2.0 + fd) * 0.5, 2.0])
+    return base.with_tracks(layer_z=mesh, name="pin_ties")
+
+
+OFFLAT = {"lat3o": _lat3o, "lat3_eq3": _lat3_eq3, "pin_ties": _pin_ties,
+          "lattice5_offaxial": lambda: synth.workload("lattice5_offaxial")}
+_offlat_cache = {}
+
+
+def get_offlat(name):
+    if name not in _offlat_cache:
+        p = OFFLAT[name]()
+        _offlat_cache[name] = (p, oracle.Oracle(p, n_threads=NTH), Geometry(p))
+    return _offlat_cache[name]
+
+
+@pytest.mark.parametrize("prec", [MOC_FP32, MOC_FP64])
+@pytest.mark.parametrize("name", list(OFFLAT))
+def test_off_lattice_segments_bit_exact_and_volumes(name, prec):
+    """Layer planes off the axial lattice (Sec. 2.2's local axial mesh):
+    every listed stack's track indices, segment counts and FSR-id sequences
+    equal the oracle's exactly, in both frames (upward and downward polar
+    stacks); lengths within 1e-6 (FP32) or 1e-12 (FP64); tracked volumes."""
+    p, o, g = get_offlat(name)
+    tr = Tracks(g, track_params(p, precision=prec))
+    assert tr.info["n_fsr"] == o.n_fsr and tr.info["tracks3d"] == o.n_tracks3d
+    lrel = 1e-6 if prec == MOC_FP32 else 1e-12
+    for t in range(0, o.n_tracks2d, max(1, o.n_tracks2d // 40)):
+        for pp in range(p.n_polar):
+            oi, on, of, ol = o.stack(t, pp)
+            gi, gn, gf, gl = tr.stack_segments(t, pp)
+            np.testing.assert_array_equal(gi, oi, err_msg=f"track indices t={t} p={pp}")
+            np.testing.assert_array_equal(gn, on, err_msg=f"segment counts t={t} p={pp}")
+            np.testing.assert_array_equal(gf, of, err_msg=f"fsr ids t={t} p={pp}")
+            assert np.all(np.abs(gl - ol) <= lrel * ol + lrel), (t, pp, np.abs(gl - ol).max())
+    np.testing.assert_allclose(tr.volumes(), o.volumes(), rtol=1e-6 if prec == MOC_FP32 else 1e-11)
+    tr.close()
+
+
+@pytest.mark.parametrize("prec", [MOC_FP64, MOC_FP32])
+@pytest.mark.parametrize("name", list(OFFLAT))
+def test_off_lattice_two_sweeps_from_source(name, prec):
+    """Two sweeps from a seeded source through the off-lattice sweep: tallies
+    element by element and the flux they give, as for the lattice meshes."""
+    p, o, g = get_offlat(name)
+    tr = Tracks(g, track_params(p, precision=prec))
+    rel, absb, frel = sweep_bars(prec, name)
+    Q = np.random.default_rng(13).uniform(0.2, 1.0, size=(o.n_fsr, p.num_groups))
+    sigt = p.sigma_t[o.fsr_materials()]
+    o.reset()
+    for sweep in range(2):
+        ot, ol = o.sweep_once(Q)
+        gt, gl = tr.sweep_from_source(Q)
+        check_flux(gt, ot, Q, o.volumes(), sigt, rel=frel, what=f"{name} sweep {sweep}")
+        check_tally(gt, ot, rel=rel, abs_frac=absb, what=f"{name} sweep {sweep}")
+        assert abs(gl - ol) <= absb * max(abs(ol), 1e-300) + 1e-300
+    o.reset()
+    tr.close()
+
+
+@pytest.mark.parametrize("prec,ktol,ftol", [(MOC_FP64, 1e-11, 1e-10), (MOC_FP32, 1e-5, 1e-4)])
+@pytest.mark.parametrize("name", list(OFFLAT))
+def test_off_lattice_power_iterations(name, prec, ktol, ftol):
+    p, o, g = get_offlat(name)
+    tr = Tracks(g, track_params(p, precision=prec))
+    o.reset()
+    ref = o.iterate(15)
+    res = tr.iterate(15, use_graph=True)
+    phi, k = tr.flux()
+    assert res["iterations"] == 15
+    assert abs(k - ref["k"]) < ktol, (k, ref["k"])
+    np.testing.assert_allclose(phi, o.flux(), rtol=ftol)
+    o.reset()
+    tr.close()
 
 
 # --------------------------------------------------------------- group counts

@@ -138,8 +138,12 @@ def test_failing_requests_do_not_disturb_neighbours():
     # a ringed, sectored lattice: its flux array is larger than 2 regions a pin
     rings = synth.workload("lattice5_rings")
     ref_rings = alone(rings)
-    # an axial mesh off the lattice (a plane at 0.6 cm with 0.5 cm spacing)
+    # an axial mesh off the lattice (a plane at 0.6 cm with 0.5 cm spacing):
+    # served like the others
     off = synth.pin_cell(1, n_layers=3).with_tracks(layer_z=np.array([0.0, 0.6, 1.5, 2.0]))
+    ref_off = alone(off)
+    # more than 32 polar angles: refused at track generation
+    bad = synth.pin_cell(1).with_tracks(n_polar=34)
     srv = Server(max_active=4, iterations_per_poll=8)
     geoms = {}
     tickets = {}
@@ -150,9 +154,9 @@ def test_failing_requests_do_not_disturb_neighbours():
     tickets["few"] = srv.submit(geoms["few"], track_params(good[0]), tol_k=1e-12, tol_src=1e-12,
                                 max_iter=3)
     geoms["off"] = Geometry(off)
-    with pytest.raises(_moc.MocError) as e:  # refused when it is queued
-        srv.submit(geoms["off"], track_params(off), **TOL)
-    assert e.value.code == _moc.MOC_ERR_UNSUPPORTED
+    tickets["off"] = srv.submit(geoms["off"], track_params(off), **TOL)
+    geoms["bad"] = Geometry(bad)
+    tickets["bad"] = srv.submit(geoms["bad"], track_params(bad), **TOL)
     geoms["rings"] = Geometry(rings)
     tickets["rings"] = srv.submit(geoms["rings"], track_params(rings), **TOL)
     out = {}
@@ -176,6 +180,13 @@ def test_failing_requests_do_not_disturb_neighbours():
     tr.close()
     assert out["rings"][4] == 0 and out["rings"][1].shape == (rings.n_fsr, rings.num_groups)
     check_same(out["rings"][0], out["rings"][1], *ref_rings)
+    # the off-lattice solve: its FSR tally is summed with FP64 atomics, so
+    # alone and in the mix agree to rounding rather than bit for bit
+    r, phi, _, _, rc = out["off"]
+    assert rc == 0 and abs(r["iterations"] - ref_off[0]["iterations"]) <= 1
+    assert abs(r["k"] - ref_off[0]["k"]) < 1e-9
+    np.testing.assert_allclose(phi, ref_off[1], rtol=1e-6)
+    assert out["bad"][4] == _moc.MOC_ERR_UNSUPPORTED
     for i in range(len(good)):
         r, phi, _, _, rc = out[f"good{i}"]
         assert rc == 0
