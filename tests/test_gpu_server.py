@@ -32,7 +32,8 @@ def alone(p):
 
 def check_same(r_mix, phi_mix, r_alone, phi_alone):
     """The same iterations on the same data give the same numbers: the FP32
-    sweep's FSR tallies are summed in 128-bit fixed point (exact, so the order
+    sweep's FSR tallies are summed in exact fixed point (three 64-bit words
+    per FSR-group; integer adds, so the order
     in which work units finish does not matter) and every reduction has a
     fixed order, so a solve in a mix repeats its solve alone bit for bit."""
     assert r_mix["iterations"] == r_alone["iterations"]
