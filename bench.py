@@ -400,7 +400,8 @@ def run_ours(args):
                         "integrations_per_step": integ, "segments3d": info["segments3d"],
                         "l2": "flushed between timed steps (256 MiB write outside the events)",
                         "k_after_steps": res["k"], "schedule": schedule,
-                        "sync_block": info.get("sync_block"), "unit_rates": rates},
+                        "sync_block": info.get("sync_block"), "tally_bits": info.get("tally_bits"),
+                        "unit_rates": rates},
             "roofline": roof, "clocks": clocks, "cpu_baseline": cpu, "e2e": e2e, "fp64": fp64,
             "large": large, "serving": serving, "ablation": ablation,
             "gpu_launches": 6 * args.steps}
@@ -487,6 +488,7 @@ def run_large(name, device, rates, iters=3, oracle_seconds=6.0):
             "ms_per_iteration": r["seconds"] / iters * 1e3, "iterations": iters,
             "generation_s": gen_s, "preloaded_stacks": info["preloaded_stacks"], "stacks": info["stacks"],
             "stored_segments": info["stored_segments"], "chunk_segments": info["chunk_segments"],
+            "tally_bits": info.get("tally_bits"),
             "device_bytes": info["device_bytes"], "clocks": clocks, "roofline": roof,
             "cpu_baseline": {"value": n_s / t_s, "unit": UNIT, "cores": os.cpu_count() or 1,
                              "kind": "oracle",

@@ -352,7 +352,8 @@ int moc_get_segments2d(const moc_tracks *tracks, int32_t t, int64_t cap, int32_t
  *   chunked), 23 tracks per synchronous block of the stored stacks (1: none,
  *   see moc_track_params.sync_block), 24 sweep slots (tracks plus the
  *   padding of synchronous blocks), 25 1 when layer planes lie off the
- *   axial lattice (11 is then 0) */
+ *   axial lattice (11 is then 0), 26 fixed-point bits of the FP32 shared
+ *   tally per unit bound (0: not used) */
 int moc_tracks_info(const moc_tracks *tracks, int64_t *out, int32_t n);
 
 /* 3D segments of z-stack (t, p) as the device generator produces them

@@ -243,7 +243,7 @@ INFO_KEYS = ["n_fsr", "groups", "tracks2d", "stacks", "tracks3d", "segments3d",
              "n_z", "cells_per_layer", "sweep_blocks", "sweep_threads", "tally_mode", "precision",
              "sweep_smem_bytes", "tile_entries", "lanes_per_track", "max_segments_per_track",
              "h2d_bytes", "groups_per_lane", "chunk_segments", "sync_block", "sweep_slots",
-             "off_lattice"]
+             "off_lattice", "tally_bits"]
 
 
 class Tracks:

@@ -1321,14 +1321,15 @@ extern "C" int moc_get_volumes(moc_tracks *h, double *v) {
 
 extern "C" int moc_tracks_info(const moc_tracks *h, int64_t *out, int32_t n) {
     if (!h || !out) { moc_set_error("NULL argument"); return MOC_ERR_INVALID_ARG; }
-    const int64_t v[26] = {h->geom.nfsr, h->geom.G, h->L.nt, 2 * h->L.n_stacks, 2 * h->L.n_gtrk,
+    const int64_t v[27] = {h->geom.nfsr, h->geom.G, h->L.nt, 2 * h->L.n_stacks, 2 * h->L.n_gtrk,
                            h->n_segments3d, (int64_t)h->integrations, h->n_stored, h->n_exp_stacks,
                            (int64_t)h->bytes, h->L.Nz, h->L.cpl, h->grid, h->block,
                            h->tally_smem ? MOC_TALLY_SHARED : MOC_TALLY_GLOBAL, h->precision,
                            (int64_t)h->smem, h->tile_cap, sweep_lanes_per_track(h->geom.G, h->gpl),
                            h->max_nseg, (int64_t)h->h2d, h->gpl, h->chunk_b, h->sync_b > 1 ? h->sync_b : 1,
-                           h->n_slots, h->L.offlat};
-    for (int i = 0; i < n && i < 26; ++i) out[i] = v[i];
+                           h->n_slots, h->L.offlat,
+                           (h->tally_smem && h->precision == MOC_FP32) ? h->tally_bits : 0};
+    for (int i = 0; i < n && i < 27; ++i) out[i] = v[i];
     return MOC_OK;
 }
 

@@ -622,6 +622,7 @@ int moc_build_layout(const moc_geometry &g, const moc_track_params &prm, Layout 
             d.lam64 = L.dz / L.cosp[k];
             d.inv_sin64 = 1.0 / L.sinp[k];
             d.W = L.W[k];
+            d.invW = 1.0 / L.W[k];
             d.chunk_base = -1;
             for (int v = 0; v < 4; ++v) {
                 const int frame = v >> 1, sense = v & 1;

@@ -51,6 +51,7 @@ struct StackDesc {
     float inv_sin;          // 1 / sin(theta)
     double lam64, inv_sin64;
     double W;               // track weight: azimuthal span x polar weight x dA
+    double invW;            // 1 / W
     // radial exits per variant: destination stack, variant, index map j = sign*i + shift
     int32_t rad_dst[4];
     int32_t rad_shift[4];

@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
     constexpr int GP = GL * GPL;     // groups per chunk (padded)
     constexpr int SLOTS = 32 / GL;   // tracks per warp task
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_work, s_next, s_ntask;
+    __shared__ int s_work, s_work_next, s_next, s_ntask;
     __shared__ UnitStack s_us[kMaxPh];
     __shared__ double s_leak[kMaxSweepBlock / 32];
     __shared__ float s_scl[32];      // FP32 fixed-point tally: scale of each group of the chunk
@@ -316,13 +316,18 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
     const real *sig_g = reinterpret_cast<const real *>(st.sig_t);
     const SegRec<real> *recs = reinterpret_cast<const SegRec<real> *>(dl.segs);
     real leak = (real)0;  // this lane's W psi leaving through vacuum faces
-    if (tid < 32) s_hmax[tid] = 0u;
+    if (tid < 32) {
+        s_hmax[tid] = 0u;
+        s_ubnd[tid] = 0u;
+    }
     if constexpr (sizeof(real) == 8)
         for (int i = tid; i < 64; i += blockDim.x) s_exp[i] = make_double2(moc_exp64::kTable[i].hi, moc_exp64::kTable[i].lo);
+    // the next unit is taken one unit ahead: thread 0 takes it from the
+    // counter when the unit's tasks start (its wait for the atomic then only
+    // delays its own warp's first task) and publishes it when the unit ends
+    if (tid == 0) s_work = atomicAdd(st.counter, 1);
 
     for (;;) {
-        __syncthreads();
-        if (tid == 0) s_work = atomicAdd(st.counter, 1);
         __syncthreads();
         const int w = s_work;
         if (w >= n_work) break;
@@ -332,7 +337,11 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                 reinterpret_cast<uint64_t *>(&s_item)[tid] =
                     reinterpret_cast<const uint64_t *>(items + w % n_items)[tid];
             __syncthreads();
-            if (s_item.scal[SC_CONV] != 0.0) continue;  // that solve has converged
+            if (s_item.scal[SC_CONV] != 0.0) {  // that solve has converged
+                __syncthreads();  // every thread has read s_work and s_item
+                if (tid == 0) s_work = atomicAdd(st.counter, 1);
+                continue;
+            }
         }
         // the unit's solve (one solve unless batched)
         const real *psi_in = BATCH ? reinterpret_cast<const real *>(s_item.psi_in) : psi_in_p;
@@ -342,35 +351,45 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
         const real *qr_g = reinterpret_cast<const real *>(BATCH ? s_item.qr : st.qr);
         double *tally_g = BATCH ? s_item.tally : st.tally;
         double *err = scal_u + SC_ERR;
-        if (tid == 0) {
-            int pre = 0;
-            for (int ph = 0; ph < Ph; ++ph) {
-                const StackDesc &e = dl.desc[(int64_t)T * Ph + ph];
-                UnitStack u;
+        if (warp == 0) {
+            // the unit's polar stacks, one lane each (Ph <= 16), stored field by
+            // field; task offsets by a prefix sum over the warp
+            int cnt = 0;
+            float wl = 0.0f;
+            if (lane < Ph) {
+                const StackDesc &e = dl.desc[(int64_t)T * Ph + lane];
+                UnitStack &u = s_us[lane];
                 u.trk_off = e.trk_off;
                 u.tpl_base = e.exp_base;
                 u.cbase = e.chunk_base;
                 u.slot_off = e.slot_off;
                 u.n_slot = e.n_slot;
                 u.W = e.W;
-                u.invW = 1.0 / e.W;
+                u.invW = e.invW;
                 u.Wf = (float)e.W;
-                u.invWf = (float)(1.0 / e.W);
+                u.invWf = (float)e.invW;
                 u.n_trk = e.n_trk;
                 u.i_lo = e.i_lo;
-                u.task_pre = pre;
-                s_us[ph] = u;
-                pre += 2 * ((e.n_slot + SLOTS - 1) / SLOTS);  // blocks of SLOTS slots, 2 senses
+                cnt = 2 * ((e.n_slot + SLOTS - 1) / SLOTS);  // blocks of SLOTS slots, 2 senses
+                wl = (float)e.W;
             }
-            s_ntask = pre;
-            float wm = 0.0f;
-            for (int ph = 0; ph < Ph; ++ph) wm = fmaxf(wm, (float)s_us[ph].W);
-            s_wmax = wm;
-            for (int qq = 0; qq < 32; ++qq) s_bmax[qq] = 0u;
+            int incl = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            for (int o = 16; o > 0; o >>= 1) wl = fmaxf(wl, __shfl_xor_sync(0xffffffffu, wl, o));
+            if (lane < Ph) s_us[lane].task_pre = incl - cnt;
+            if (lane == Ph - 1) s_ntask = incl;
+            if (lane == 0) s_wmax = wl;
+            s_bmax[lane] = 0u;
         }
         __syncthreads();
         const int ntask = s_ntask;
-        if (ntask == 0) continue;
+        if (ntask == 0) {
+            if (tid == 0) s_work = atomicAdd(st.counter, 1);
+            continue;
+        }
         const StackDesc &d0 = dl.desc[(int64_t)T * Ph];
         const int nb = d0.nb;
         const int32_t *reg2d = dl.reg2d + d0.seg2d_off;
@@ -414,22 +433,35 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
             }
             if (kFixed && SMEM && pass == 0 && ci == 0) {
                 // the unit's incoming fluxes psi_in[(gid 4 + v) G + g], its tracks
-                // gid one contiguous range: threads take a fixed group each
-                // (stride a multiple of G)
-                if (tid < 32) s_ubnd[tid] = 0u;
-                __syncthreads();
+                // gid one contiguous range of 4 G floats each: read as float4, a
+                // thread taking every S-th float4 with 4 S a multiple of G, so
+                // that its four elements always belong to the same four groups
+                // (4 tid + k) mod G; s_ubnd is zero here (cleared after its
+                // last use)
                 if (psi_in) {
                     const int S = (blockDim.x / G) * G;
                     const int64_t trk_end = s_us[Ph - 1].trk_off + s_us[Ph - 1].n_trk;
-                    const int64_t e0 = unit_trk0 * 4 * G, e1 = trk_end * 4 * G;
-                    const int gq = tid % G - g0;
-                    float um = 0.0f;
-                    if (tid < S && gq >= 0 && gq < gc)
-                        for (int64_t e = e0 + tid; e < e1; e += S) um = fmaxf(um, fabsf((float)psi_in[e]));
-                    if (um > 0.0f) atomicMax(&s_ubnd[gq], __float_as_uint(um));
+                    const int64_t n4 = (trk_end - unit_trk0) * G;
+                    const float4 *p4 = reinterpret_cast<const float4 *>(psi_in + unit_trk0 * 4 * G);
+                    float m4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                    if (tid < S) {
+#pragma unroll 4
+                        for (int64_t i = tid; i < n4; i += S) {
+                            const float4 v = __ldg(p4 + i);
+                            m4[0] = fmaxf(m4[0], fabsf(v.x));
+                            m4[1] = fmaxf(m4[1], fabsf(v.y));
+                            m4[2] = fmaxf(m4[2], fabsf(v.z));
+                            m4[3] = fmaxf(m4[3], fabsf(v.w));
+                        }
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int gq = (4 * tid + k) % G - g0;
+                            if (gq >= 0 && gq < gc && m4[k] > 0.0f) atomicMax(&s_ubnd[gq], __float_as_uint(m4[k]));
+                        }
+                    }
                 }
-                __syncthreads();
             }
+            __syncthreads();  // sig (below: Sigma_t from shared memory) and s_ubnd are complete
             if (SMEM) {
                 // rows of the (2D segment, layer) FSRs the unit (chunk) crosses
                 for (int bb = warp; bb < b1 - b0; bb += nwarps) {
@@ -442,9 +474,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                         const int et = tix(bb * NL + L, qq);
                         real q = (real)0, sg = (real)0;
                         if (qq < gc) {
-                            const int m = __ldg(dl.fsr_mat + f);
-                            sg = sig_g[m * G + g0 + qq];
-                            if (sizeof(real) == 4) sg = (real)((float)sg * kLog2e);
+                            sg = sig[__ldg(dl.fsr_mat + f) * GP + qq];  // FP32: times log2 e
                             q = qr_g[(size_t)f * G + g0 + qq];
                         }
                         if constexpr (SYNC) {
@@ -465,8 +495,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                         // Sigma_t once per 2D segment where its region has one material
                         const int rm = __ldg(dl.reg_mat + reg);
                         for (int qq = lane; qq < GP; qq += 32)
-                            sb_t[bb * GP + qq] = rm < 0 ? -1.0f
-                                                        : (qq < gc ? (float)sig_g[rm * G + g0 + qq] * kLog2e : 0.0f);
+                            sb_t[bb * GP + qq] = rm < 0 ? -1.0f : (qq < gc ? (float)sig[rm * GP + qq] : 0.0f);
                     }
                 }
                 if (kFixed) {
@@ -501,6 +530,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                 s_sh[tid] = B > 0.0f ? e - dl.tally_bits + 64 : 64;
             }
             __syncthreads();
+            if (tid == 0 && g0 == 0 && pass == 0 && ci == 0) s_work_next = atomicAdd(st.counter, 1);
 
             float hmx[GPL];  // this lane's max |psi| handed to the next chunk
 #pragma unroll
@@ -1035,6 +1065,9 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                     }
                 }
                 if (tid < 32) s_bmax[tid] = 0u;  // next chunk's bound (read only before its tasks)
+                // the unit's incoming-flux bound, read by every chunk's staging:
+                // cleared once the unit's last chunk is done
+                if (kFixed && tid < 32 && pass == (C > 1 ? 1 : 0) && ci == C - 1) s_ubnd[tid] = 0u;
             }
         }
         if constexpr (BATCH) {
@@ -1051,6 +1084,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                 if (v != 0.0) atomicAdd(scal_u + SC_LEAK, v);
             }
         }
+        if (tid == 0) s_work = s_work_next;  // read after the next loop-top barrier
     }
     if (BATCH) return;
     double leak64 = (double)leak;
