@@ -7,11 +7,12 @@
 // of a z-stack are no longer layer shifts of one another, so neither segment
 // templates nor the shared (Qr, Sigma_t) tile of the main sweep apply.  A
 // persistent grid takes work units (a 2D track with all its polar stacks)
-// from the same counter as the main sweep; a warp sweeps one direction
-// (track, frame, sense) at a time, its lanes over energy groups, every lane
-// generating the direction's pieces on the fly (walk_ol) from the integer
-// (lattice index, fraction rank) decisions, and adds each contribution
-// W (psi_in - psi_out) into the FP64 FSR tally with a native atomic.
+// from the same counter as the main sweep; a warp sweeps 32 / GLn directions
+// (track, frame, sense) side by side, GLn lanes each over energy groups, every
+// lane generating its direction's pieces on the fly (walk_ol) from the
+// integer (lattice index, fraction rank) decisions, and adds each
+// contribution W (psi_in - psi_out) into the FP64 FSR tally with a native
+// atomic.
 #include "moc_device.cuh"
 #include "moc_exp64.cuh"
 #include "moc_kernels.h"
@@ -45,6 +46,12 @@ __global__ void __launch_bounds__(kOLBlock) k_sweep_ol(DevLayout dl, DevState st
             s_exp[i] = make_double2(moc_exp64::kTable[i].hi, moc_exp64::kTable[i].lo);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int G = dl.G, Ph = dl.Ph;
+    // lanes per direction: the smallest power of two holding the groups (at
+    // most 32, in group chunks beyond); a warp sweeps 32 / GLn directions side
+    // by side, each walked by its own lanes
+    int GLn = 1;
+    while (GLn < G && GLn < 32) GLn <<= 1;
+    const int per = 32 / GLn, sub = lane / GLn, gl = lane - sub * GLn;
     const real scale = (real)st.scal[SC_SCALE];
     const real *qr = reinterpret_cast<const real *>(st.qr);
     const real *sig = reinterpret_cast<const real *>(st.sig_t);
@@ -58,15 +65,17 @@ __global__ void __launch_bounds__(kOLBlock) k_sweep_ol(DevLayout dl, DevState st
         const int T = order[w];
         for (int ph = 0; ph < Ph; ++ph) {
             const StackDesc &d = dl.desc[(int64_t)T * Ph + ph];
-            const int n_trk = d.n_trk;
+            const int n_dir = 4 * d.n_trk;
             const real W = (real)d.W;
             const int32_t *reg2d = dl.reg2d + d.seg2d_off;
-            for (int task = warp; task < 4 * n_trk; task += nwarps) {
+            for (int task0 = warp * per; task0 < n_dir; task0 += nwarps * per) {
+                const int task = task0 + sub;
+                if (task >= n_dir) continue;
                 const int k = task >> 2, v = task & 3;  // direction v = frame * 2 + sense
                 const int64_t gid = d.trk_off + k;
                 const int64_t dst = dl.dst ? (int64_t)__ldg(dl.dst + gid * 4 + v) : -1;
-                for (int g0 = 0; g0 < G; g0 += 32) {
-                    const int g = g0 + lane;
+                for (int g0 = 0; g0 < G; g0 += GLn) {
+                    const int g = g0 + gl;
                     const bool on = g < G;
                     real psi = (psi_in && on) ? psi_in[(gid * 4 + v) * G + g] * scale : (real)0;
                     auto visit = [&](int b, int L, real len) {
