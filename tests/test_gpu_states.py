@@ -130,3 +130,26 @@ def test_batch_step_rejects_mixed_layouts():
         batch_step([a, a])
     a.close()
     b.close()
+
+
+def test_states_and_batch_step_off_the_lattice():
+    """A layout with layer planes off the axial lattice: its solve states
+    share the off-lattice tables, and batched steps (one iteration per solve:
+    the off-lattice sweep tallies globally) equal the solves iterated alone
+    and the oracle."""
+    p = synth.workload("lattice5_offaxial")
+    g = Geometry(p)
+    owner = Tracks(g, track_params(p))
+    assert owner.info["off_lattice"] == 1
+    st = owner.state()
+    for _ in range(8):
+        batch_step([owner, st])
+    o = oracle.Oracle(p)
+    o.reset()
+    ref = o.iterate(8)
+    for t in (owner, st):
+        phi, k = t.flux()
+        assert abs(k - ref["k"]) < 1e-5
+        np.testing.assert_allclose(phi, o.flux(), rtol=1e-4)
+    st.close()
+    owner.close()
