@@ -412,6 +412,9 @@ extern "C" int moc_query_footprint(const moc_geometry *g, const moc_track_params
     const int64_t G = g->G;
     int64_t b = 0;
     b += (int64_t)L.desc.size() * sizeof(StackDesc) + (int64_t)L.zn.size() * 8;
+    // planes off the lattice: per boundary two 16-bit ranks and the mirrored
+    // frame's fraction (FP32, and FP64 for FP64 sweeps)
+    if (L.offlat) b += (int64_t)L.zn.size() * (rs == 8 ? 16 : 8);
     b += (int64_t)L.seg_reg.size() * 8 + (int64_t)g->nfsr * 4 + (int64_t)L.desc.size() * 4;
     b += (int64_t)g->nfsr * G * (8 + rs + 8) + (int64_t)g->nfsr * 8 * 3;
     bool refl = false;
