@@ -985,15 +985,42 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                         }
                     };
                     // two sets of four records: one set in flight while the other
-                    // is swept
+                    // is swept; in units swept whole the last nmax mod 4 steps go
+                    // one record at a time (the same arithmetic, so the same
+                    // bits), so that a warp does not sweep up to three steps of
+                    // zero-length pieces (radially chunked units keep the
+                    // rounded steps: the extra code costs their kernel spills)
+                    const int nq = CHUNK ? nmax : (nmax & ~3);
                     SegRec<real> ra[4], rb[4];
                     fetch4(ra, 0);
-                    for (int s = 0; s < nmax; s += 8) {
+                    for (int s = 0; s < nq; s += 8) {
                         fetch4(rb, s + 4);
                         sweep4(ra);
-                        if (s + 4 >= nmax) break;
+                        if (s + 4 >= nq) break;
                         fetch4(ra, s + 8);
                         sweep4(rb);
+                    }
+                    if constexpr (!CHUNK)
+                    for (int s = nq; s < nmax; ++s) {
+                        int ru, rd;
+                        real ln = (real)0;
+                        uint32_t key;
+                        if (n > 0) {
+                            const SegRec<real> c = pr[min(s, n - 1) * dir];
+                            key = c.key;
+                            if (s < n) ln = c.len;
+                        } else {
+                            key = CHUNK ? tpl_key_seg(b0, -m) : tpl_key(-m, m);
+                        }
+                        if constexpr (CHUNK) {
+                            const int bN = tpl_seg(key) * NL, Lt = tpl_layer(key);
+                            ru = bN + Lt + (m - rowoff);
+                            rd = bN - Lt + (NL - 1 - m - rowoff);
+                        } else {
+                            ru = tpl_row_up(key) + m;
+                            rd = tpl_row_down(key) - m;
+                        }
+                        visit(ru, rd, ln);
                     }
                 } else if (active) {
                     // generated on the fly: this track's own line, layers [0, NL),
