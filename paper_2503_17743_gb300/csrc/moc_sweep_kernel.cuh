@@ -275,6 +275,11 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
     // chunks, whose kernel is short of registers for the stride);
     // CS = words from group q to q + 1 of the same row
     constexpr bool kGM = kFixed && !CHUNK;
+    // units swept whole without synchronous blocks: a warp task takes SLOTS
+    // consecutive slots of the unit's stacks laid end to end (tracks of two
+    // polar stacks may share a warp), so that only the unit's last task per
+    // sense has idle slots instead of every stack's last
+    constexpr bool FLAT = !CHUNK && !SYNC;
     const int RS = kGM ? tally_rows(cap, GL, GPL) : 0;
     const int CS = kGM ? RS : 1;
     auto tix = [&](int row, int q) { return kGM ? q * RS + row : row * TS + q; };
@@ -370,7 +375,9 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                 u.invWf = (float)e.invW;
                 u.n_trk = e.n_trk;
                 u.i_lo = e.i_lo;
-                cnt = 2 * ((e.n_slot + SLOTS - 1) / SLOTS);  // blocks of SLOTS slots, 2 senses
+                // FLAT: slots counted across the stacks; else blocks of SLOTS
+                // slots per stack, 2 senses
+                cnt = FLAT ? e.n_slot : 2 * ((e.n_slot + SLOTS - 1) / SLOTS);
                 wl = (float)e.W;
             }
             int incl = cnt;
@@ -380,7 +387,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
             }
             for (int o = 16; o > 0; o >>= 1) wl = fmaxf(wl, __shfl_xor_sync(0xffffffffu, wl, o));
             if (lane < Ph) s_us[lane].task_pre = incl - cnt;
-            if (lane == Ph - 1) s_ntask = incl;
+            if (lane == Ph - 1) s_ntask = FLAT ? 2 * ((incl + SLOTS - 1) / SLOTS) : incl;
             if (lane == 0) s_wmax = wl;
             s_bmax[lane] = 0u;
         }
@@ -542,8 +549,11 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                 if (t >= ntask_c) break;
                 // warp task: polar stack ph, sense, block of SLOTS tracks taken in
                 // decreasing segment count
+                // FLAT: slot gs of the unit's slots across its stacks (each slot
+                // finds its own stack); else the stack of task t
+                const int gs = FLAT ? (t >> 1) * SLOTS + j : t;
                 int ph = 0;
-                while (ph + 1 < Ph && t >= s_us[ph + 1].task_pre) ++ph;
+                while (ph + 1 < Ph && gs >= s_us[ph + 1].task_pre) ++ph;
                 const UnitStack u = s_us[ph];
                 const int x = t - u.task_pre;
                 int sense, q, k, widx;
@@ -558,8 +568,8 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                     k = valid ? (int)(rng & 0xffffffff) + q : 0;
                     widx = k;
                 } else {
-                    sense = x & 1;
-                    q = (x >> 1) * SLOTS + j;
+                    sense = FLAT ? (t & 1) : (x & 1);
+                    q = FLAT ? gs - u.task_pre : (x >> 1) * SLOTS + j;
                     // the slot's track in the stack; a padding slot of a
                     // synchronous block holds -1 - (the track its block's
                     // sequence would continue with): idle, but with its m
