@@ -58,6 +58,17 @@ __device__ __forceinline__ double attenuation<double>(double x, const double2 *t
     return moc_exp64::exp_neg(x, tab);
 }
 
+// k / d for 0 <= k and 1 <= d, from the FP32 reciprocal rd ~ 1 / d: exact
+// below 2^24 after one correction step (the estimate is off by at most one
+// there); larger k take the integer division
+__device__ __forceinline__ int div_by(int k, int d, float rd) {
+    if (k >= (1 << 24)) return k / d;
+    int q = __float2int_rz((float)k * rd);
+    const int r = k - q * d;
+    q += (r >= d ? 1 : 0) - (r < 0 ? 1 : 0);
+    return q;
+}
+
 // per polar stack of the work unit, cached in shared memory
 // (the track weight and its inverse in both precisions: the sweep's hot path
 // does no FP64 arithmetic in FP32 mode)
@@ -263,6 +274,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
     __shared__ double2 s_exp[sizeof(real) == 8 ? 64 : 1];  // FP64: 2^{j/64} as hi, lo
     constexpr bool kFixed = sizeof(real) == 4;  // FP32 sweeps tally in fixed point
     const int G = dl.G, NL = dl.NL, M = dl.M, Ph = dl.Ph, cpl = dl.cpl;
+    const float rcpl = 1.0f / (float)max(cpl, 1);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int j = lane / GL;         // slot: track of the warp task
     const int ql = lane & (GL - 1);  // lane of the slot: groups ql * GPL + c, c < GPL
@@ -578,7 +590,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                     k = kk >= 0 ? kk : -1 - kk;
                     widx = q;
                 }
-                const int m = k / cpl;                       // shift of the track within its class
+                const int m = div_by(k, cpl, rcpl);          // shift of the track within its class
                 const int64_t gid = u.trk_off + k;
                 // the track's part in this chunk: records [p0, p0 + n) of its
                 // window (stored) or 2D segments [sb0, sb1] (on the fly), and
