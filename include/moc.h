@@ -49,6 +49,9 @@ extern "C" {
 /* moc_track_params.schedule flags (load balancing, Sec. 4.3; default 0 uses both) */
 #define MOC_SCHED_UNITS_NATURAL 1   /* work units (2D tracks) in index order, not largest first */
 #define MOC_SCHED_TRACKS_NATURAL 2  /* a stack's tracks in index order, not by segment count */
+/* the shared rows of the FP32 sweep carry Sigma_t beside Qr even where the
+ * stored segments could carry their material (see moc_tracks_info entry 27) */
+#define MOC_SCHED_ROWS_WITH_SIGMA 4
 
 /* arithmetic of the sweep */
 #define MOC_FP32 0
@@ -142,7 +145,7 @@ typedef struct {
  *   groups_per_lane    energy groups one thread carries along a track: 1, 2
  *                      or 4 (2 and 4 for FP32 sweeps only; 0 = tuned default)
  *   schedule           0, or MOC_SCHED_* flags that switch off a load-balancing
- *                      step (Sec. 4.3), for ablations
+ *                      step (Sec. 4.3) or the material-keyed rows, for ablations
  *   chunk_segments     shared tally only: sweep a unit (2D track) in radial
  *                      chunks of at most this many 2D segments; 0 = only the
  *                      units whose tile does not fit in shared memory, in the
@@ -353,7 +356,10 @@ int moc_get_segments2d(const moc_tracks *tracks, int32_t t, int64_t cap, int32_t
  *   see moc_track_params.sync_block), 24 sweep slots (tracks plus the
  *   padding of synchronous blocks), 25 1 when layer planes lie off the
  *   axial lattice (11 is then 0), 26 fixed-point bits of the FP32 shared
- *   tally per unit bound (0: not used) */
+ *   tally per unit bound (0: not used), 27 1 when the stored segments carry
+ *   their material and the shared rows hold Qr only (FP32, two groups per
+ *   lane, every unit stored and swept whole, one material per radial region,
+ *   at most 4 materials; Sigma_t then comes from the material table) */
 int moc_tracks_info(const moc_tracks *tracks, int64_t *out, int32_t n);
 
 /* 3D segments of z-stack (t, p) as the device generator produces them

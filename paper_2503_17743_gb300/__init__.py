@@ -6,7 +6,7 @@ the on-the-fly 3D segment generation, the preloaded/on-the-fly transport
 sweep, the source update and the FP64 reductions.  This package is the
 ctypes binding (argument marshalling only) plus the build script.
 """
-from ._moc import (MOC_FP32, MOC_FP64, MOC_SCHED_TRACKS_NATURAL, MOC_SCHED_UNITS_NATURAL,
+from ._moc import (MOC_FP32, MOC_FP64, MOC_SCHED_ROWS_WITH_SIGMA, MOC_SCHED_TRACKS_NATURAL, MOC_SCHED_UNITS_NATURAL,
                    MOC_TALLY_AUTO, MOC_TALLY_GLOBAL, MOC_TALLY_SHARED,
                    Geometry, MocError, Server, Tracks, autotune, batch_step, load,
                    measure_ex2_rate, measure_unit_rates, eval_attenuation_f64, eval_attenuation_f32, track_params)
@@ -14,4 +14,4 @@ from ._moc import (MOC_FP32, MOC_FP64, MOC_SCHED_TRACKS_NATURAL, MOC_SCHED_UNITS
 __all__ = ["Geometry", "Tracks", "Server", "MocError", "autotune", "batch_step", "load",
            "track_params", "measure_ex2_rate", "measure_unit_rates", "eval_attenuation_f64", "eval_attenuation_f32",
            "MOC_FP32", "MOC_FP64", "MOC_TALLY_AUTO", "MOC_TALLY_SHARED", "MOC_TALLY_GLOBAL",
-           "MOC_SCHED_UNITS_NATURAL", "MOC_SCHED_TRACKS_NATURAL"]
+           "MOC_SCHED_UNITS_NATURAL", "MOC_SCHED_TRACKS_NATURAL", "MOC_SCHED_ROWS_WITH_SIGMA"]

@@ -26,6 +26,7 @@ MOC_FP32 = 0
 MOC_FP64 = 1
 MOC_SCHED_UNITS_NATURAL = 1
 MOC_SCHED_TRACKS_NATURAL = 2
+MOC_SCHED_ROWS_WITH_SIGMA = 4
 MOC_TALLY_AUTO = 0
 MOC_TALLY_SHARED = 1
 MOC_TALLY_GLOBAL = 2
@@ -243,7 +244,7 @@ INFO_KEYS = ["n_fsr", "groups", "tracks2d", "stacks", "tracks3d", "segments3d",
              "n_z", "cells_per_layer", "sweep_blocks", "sweep_threads", "tally_mode", "precision",
              "sweep_smem_bytes", "tile_entries", "lanes_per_track", "max_segments_per_track",
              "h2d_bytes", "groups_per_lane", "chunk_segments", "sync_block", "sweep_slots",
-             "off_lattice", "tally_bits"]
+             "off_lattice", "tally_bits", "material_keys"]
 
 
 class Tracks:

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["moc_kernels.cu", "moc_sweep.cu", "moc_sweep_f32g1.cu", "moc_sweep_f32g2.cu",
+CU_SOURCES = ["moc_kernels.cu", "moc_sweep.cu", "moc_sweep_f32g1.cu", "moc_sweep_f32g2.cu", "moc_sweep_f32g2m.cu",
               "moc_sweep_f32g4.cu", "moc_sweep_f64.cu", "moc_api.cu", "moc_static.cu", "moc_peak.cu",
               "moc_server.cu", "moc_tune.cu", "moc_trace.cu",
               "moc_sweep_ol.cu"]

@@ -68,6 +68,7 @@ struct moc_tracks {
     int tile_cap = 0;
     int chunk_b = 0;            // 2D segments per radial chunk (0: units swept whole)
     int sync_b = 0;             // tracks per synchronous block of the stored stacks (0: none)
+    int matk = 0;               // stored records carry materials, rows hold Qr only (DevLayout::matk)
     int64_t n_slots = 0;        // sweep slots of all stacks (perm / win entries)
     int64_t hand_trk = 0;       // tracks of the largest chunked unit
     int block = 256;
@@ -167,6 +168,7 @@ void fill_views(moc_tracks *h) {
     dl.chunk_tab = (const int64_t *)h->d_chunk.p;
     dl.chunk_b = h->chunk_b;
     dl.sync_b = h->sync_b;
+    dl.matk = h->matk;
     dl.reg_mat = (const int32_t *)h->d_reg_mat.p;
     dl.hand_trk = (int32_t)h->hand_trk;
     dl.hand = h->d_hand.p;
@@ -582,7 +584,13 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     TRY(upload(h.get(), h->d_reg2d, reg2d), "upload");
     TRY(upload(h.get(), h->d_len2d, len2d), "upload");
     TRY(upload(h.get(), h->d_fsr_mat, geo.fsr_mat), "upload");
-    if (h->sync_b) {
+    // material keys (DevLayout::matk): FP32, two groups per lane, shared tally,
+    // units swept whole without synchronous blocks, at most 4 materials and
+    // one material per radial region; the stored templates must cover every
+    // unit (checked once they are planned)
+    bool matk_cand = h->precision == MOC_FP32 && h->gpl == 2 && h->tally_smem && h->chunk_b == 0 &&
+                     h->sync_b == 0 && !L.offlat && geo.M <= 4 && !(prm->schedule & MOC_SCHED_ROWS_WITH_SIGMA);
+    if (h->sync_b || matk_cand) {
         // per radial region: its material when every layer has the same one
         // (then Sigma_t is one value per 2D segment of a unit), else -1
         std::vector<int32_t> reg_mat(geo.nreg);
@@ -591,6 +599,7 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
             for (int l = 1; l < geo.nl && m >= 0; ++l)
                 if (geo.fsr_mat[(size_t)r * geo.nl + l] != m) m = -1;
             reg_mat[r] = m;
+            if (m < 0) matk_cand = false;
         }
         TRY(upload(h.get(), h->d_reg_mat, reg_mat), "upload");
     }
@@ -760,6 +769,20 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
         fill_views(h.get());
     }
     TRY(cudaMemcpyAsync(h->d_desc.p, L.desc.data(), ns * sizeof(StackDesc), cudaMemcpyHostToDevice, h->stream), "upload");
+    if (matk_cand) {
+        // every unit stored, and the mirrored tile rows b NL + NL-1-L_t of the
+        // keys within 14 signed bits
+        for (int64_t s = 0; s < ns && matk_cand; ++s) {
+            const StackDesc &d = L.desc[s];
+            if (d.exp_base < 0) { matk_cand = false; break; }
+            for (int r = 0; r < std::min(cpl, d.n_trk); ++r) {
+                const int64_t q = tpl_first[s] + r;
+                if ((int64_t)d.nb * L.nlv - tlmin[q] >= 8000 || tlmin[q] + tnlay[q] >= 8000) matk_cand = false;
+            }
+        }
+        h->matk = matk_cand ? 1 : 0;
+        fill_views(h.get());
+    }
     if (!exp_stacks.empty()) {
         DevBuf d_exp_stacks;
         TRY(upload(h.get(), d_exp_stacks, exp_stacks), "upload");
@@ -912,14 +935,14 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     fill_views(h.get());
     // sweep launch shape (tally mode chosen above)
     h->smem = sweep_smem_bytes(h->precision, h->tally_smem, h->chunk_b > 0, geo.M, G, h->gpl, h->tile_cap,
-                               h->sync_b, L.nlv);
+                               h->sync_b, L.nlv, h->matk);
     {
         const int bmax = sweep_block_threads(h->precision, h->gpl);
         h->block = prm->block_threads > 0 ? std::max(32, std::min(prm->block_threads, bmax) / 32 * 32) : bmax;
     }
     int bps = 0;
     TRY(sweep_occupancy(h->precision, h->tally_smem, h->chunk_b > 0, G, h->gpl, h->block, h->smem, &bps,
-                        h->sync_b > 0),
+                        h->sync_b > 0, h->matk != 0),
         "occupancy");
     if (bps < 1) { moc_set_error("sweep kernel does not fit on an SM"); return MOC_ERR_UNSUPPORTED; }
     if (prm->blocks_per_sm > 0) bps = std::min(bps, prm->blocks_per_sm);
@@ -1030,6 +1053,7 @@ extern "C" int moc_state_create(const moc_tracks *t, const double *ext_source, m
     h->tile_cap = base->tile_cap;
     h->chunk_b = base->chunk_b;
     h->sync_b = base->sync_b;
+    h->matk = base->matk;
     h->n_slots = base->n_slots;
     h->hand_trk = base->hand_trk;
     h->block = base->block;
@@ -1324,15 +1348,15 @@ extern "C" int moc_get_volumes(moc_tracks *h, double *v) {
 
 extern "C" int moc_tracks_info(const moc_tracks *h, int64_t *out, int32_t n) {
     if (!h || !out) { moc_set_error("NULL argument"); return MOC_ERR_INVALID_ARG; }
-    const int64_t v[27] = {h->geom.nfsr, h->geom.G, h->L.nt, 2 * h->L.n_stacks, 2 * h->L.n_gtrk,
+    const int64_t v[28] = {h->geom.nfsr, h->geom.G, h->L.nt, 2 * h->L.n_stacks, 2 * h->L.n_gtrk,
                            h->n_segments3d, (int64_t)h->integrations, h->n_stored, h->n_exp_stacks,
                            (int64_t)h->bytes, h->L.Nz, h->L.cpl, h->grid, h->block,
                            h->tally_smem ? MOC_TALLY_SHARED : MOC_TALLY_GLOBAL, h->precision,
                            (int64_t)h->smem, h->tile_cap, sweep_lanes_per_track(h->geom.G, h->gpl),
                            h->max_nseg, (int64_t)h->h2d, h->gpl, h->chunk_b, h->sync_b > 1 ? h->sync_b : 1,
                            h->n_slots, h->L.offlat,
-                           (h->tally_smem && h->precision == MOC_FP32) ? h->tally_bits : 0};
-    for (int i = 0; i < n && i < 27; ++i) out[i] = v[i];
+                           (h->tally_smem && h->precision == MOC_FP32) ? h->tally_bits : 0, h->matk};
+    for (int i = 0; i < n && i < 28; ++i) out[i] = v[i];
     return MOC_OK;
 }
 

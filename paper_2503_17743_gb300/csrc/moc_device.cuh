@@ -31,6 +31,9 @@ struct DevLayout {
                              // consecutive tracks r + m cpl of one class, padding entries
                              // -1 - (r + m cpl) continuing the block's sequence
     int32_t sync_b;          // tracks per synchronous block (0: none)
+    int32_t matk;            // 1: every radial region has one material in all layers, the
+                             // stored records carry it (tpl_key_mat) and the shared rows of
+                             // units swept whole hold Qr only (Sigma_t from the material table)
     int32_t tally3;          // 1: the FSR tally is three 64-bit fixed-point words per
                              // FSR-group (FP32 sweeps with the shared tally), else FP64
     const int32_t *reg_mat;  // per radial region: its material if the same in every layer, else -1
@@ -495,6 +498,14 @@ __host__ __device__ __forceinline__ uint32_t tpl_key(int A, int B) {
 }
 __device__ __forceinline__ int tpl_row_up(uint32_t key) { return (int)(int16_t)(key & 0xffffu); }
 __device__ __forceinline__ int tpl_row_down(uint32_t key) { return (int)key >> 16; }
+// Layouts with one material per radial region (DevLayout::matk): the upward
+// row in bits 0-15 as above, the mirrored row in bits 16-29 (signed, |B| <
+// 2^13) and the piece's material in bits 30-31 (M <= 4)
+__host__ __device__ __forceinline__ uint32_t tpl_key_mat(int A, int B, int mat) {
+    return (uint32_t)(uint16_t)(int16_t)A | (((uint32_t)B & 0x3fffu) << 16) | ((uint32_t)mat << 30);
+}
+__device__ __forceinline__ int tpl_row_down_mat(uint32_t key) { return (int)(key << 2) >> 18; }
+__device__ __forceinline__ int tpl_mat(uint32_t key) { return (int)(key >> 30); }
 __host__ __device__ __forceinline__ uint32_t tpl_key_seg(int b, int L) {
     return ((uint32_t)b << 16) | (uint32_t)(uint16_t)(int16_t)L;
 }

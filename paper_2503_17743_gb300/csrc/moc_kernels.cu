@@ -105,7 +105,9 @@ __global__ void k_tpl_write(DevLayout dl, const int32_t *exp_stacks, int64_t n_e
                     SegRec<real> rec{};
                     rec.key = (dl.chunk_b > 0 || dl.sync_b > 1)
                                   ? tpl_key_seg(b, L)
-                                  : tpl_key(b * dl.NL + L, b * dl.NL + dl.NL - 1 - L);
+                                  : dl.matk ? tpl_key_mat(b * dl.NL + L, b * dl.NL + dl.NL - 1 - L,
+                                                          dl.reg_mat[dl.reg2d[d.seg2d_off + b]])
+                                            : tpl_key(b * dl.NL + L, b * dl.NL + dl.NL - 1 - L);
                     rec.len = tpl_len(dl, d, b, tr, L);
                     out[pos++] = rec;
                 }

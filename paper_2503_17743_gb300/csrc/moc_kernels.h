@@ -34,8 +34,9 @@ int sweep_lanes_per_track(int G, int gpl);
 // threads per sweep block the kernel is compiled for (its launch bound)
 int sweep_block_threads(int precision, int gpl);
 // sync: tracks per synchronous block (0: none; the split tile), NL: sweep layers
+// matk: rows of Qr only (layouts whose records carry materials)
 size_t sweep_smem_bytes(int precision, int tally_smem, int chunk, int M, int G, int gpl, int cap,
-                        int sync = 0, int NL = 1);
+                        int sync = 0, int NL = 1, int matk = 0);
 // The state of one solve of a batched sweep (pointers into device memory)
 struct BatchItem {
     const void *qr;             // Q / Sigma_t, real
@@ -68,9 +69,12 @@ const void *sweep_kernel_f32_gpl1(int tally_smem, int chunk, int batch, int gl);
 // sync: the synchronous-block variant (layouts with dl.sync_b > 0)
 const void *sweep_kernel_f32_gpl2(int tally_smem, int chunk, int batch, int gl, int sync);
 const void *sweep_kernel_f32_gpl4(int tally_smem, int chunk, int batch, int gl);
+// the variant for layouts whose records carry materials (moc_sweep_f32g2m.cu:
+// two groups per lane, shared tally, units swept whole)
+const void *sweep_kernel_f32_gpl2_matk(int batch, int gl);
 const void *sweep_kernel_f64(int tally_smem, int chunk, int batch, int gl);
 cudaError_t sweep_occupancy(int precision, int tally_smem, int chunk, int G, int gpl, int block,
-                            size_t smem, int *blocks_per_sm, bool sync = false);
+                            size_t smem, int *blocks_per_sm, bool sync = false, bool matk = false);
 // threads per block of the per-FSR kernels (source, finalize, residual, init):
 // small blocks spread a few thousand FSRs over many SMs
 constexpr int kSmallBlock = 64;

@@ -15,9 +15,12 @@ int lanes_for_groups(int G, int gpl) {
 }
 
 // chunk: some units are swept in radial chunks (shared tally only)
-const void *sweep_fn(int precision, int tally_smem, int chunk, int G, int gpl, int batch = 0, int sync = 0) {
+// matk: the layout's records carry materials (DevLayout::matk)
+const void *sweep_fn(int precision, int tally_smem, int chunk, int G, int gpl, int batch = 0, int sync = 0,
+                     int matk = 0) {
     const int gl = lanes_for_groups(G, gpl);
     if (precision == MOC_FP64) return sweep_kernel_f64(tally_smem, chunk, batch, gl);
+    if (matk) return sweep_kernel_f32_gpl2_matk(batch, gl);
     if (gpl == 4) return sweep_kernel_f32_gpl4(tally_smem, chunk, batch, gl);
     if (gpl == 2) return sweep_kernel_f32_gpl2(tally_smem, chunk, batch, gl, sync);
     return sweep_kernel_f32_gpl1(tally_smem, chunk, batch, gl);
@@ -54,7 +57,7 @@ int sweep_lanes_per_track(int G, int gpl) { return lanes_for_groups(G, gpl); }
 int sweep_block_threads(int precision, int gpl) { return sweep_block(precision != MOC_FP64, gpl); }
 
 size_t sweep_smem_bytes(int precision, int tally_smem, int chunk, int M, int G, int gpl, int cap,
-                        int sync, int NL) {
+                        int sync, int NL, int matk) {
     const size_t rs = precision == MOC_FP64 ? 8 : 4;
     const size_t gp = (size_t)lanes_for_groups(G, gpl) * gpl;
     size_t b = ((size_t)M * gp * rs + 15) & ~(size_t)15;
@@ -67,16 +70,16 @@ size_t sweep_smem_bytes(int precision, int tally_smem, int chunk, int M, int G, 
         b += ((size_t)tally_rows(cap, (int)(gp / gpl), gpl) * gp + kSyncGuard) * 4;
         return b;
     }
-    // (Qr, Sigma_t) rows + tally rows
-    b += (size_t)cap * gp * rs * 2 +
+    // (Qr, Sigma_t) rows (Qr only with material keys) + tally rows
+    b += (size_t)cap * gp * rs * (matk ? 1 : 2) +
          (precision == MOC_FP64 || chunk ? (size_t)cap * tally_stride((int)(gp / gpl), gpl)
                                          : (size_t)tally_rows(cap, (int)(gp / gpl), gpl) * gp) * rs;
     return b;
 }
 
 cudaError_t sweep_occupancy(int precision, int tally_smem, int chunk, int G, int gpl, int block,
-                            size_t smem, int *blocks_per_sm, bool sync) {
-    const void *f = sweep_fn(precision, tally_smem, chunk, G, gpl, 0, sync ? 1 : 0);
+                            size_t smem, int *blocks_per_sm, bool sync, bool matk) {
+    const void *f = sweep_fn(precision, tally_smem, chunk, G, gpl, 0, sync ? 1 : 0, matk ? 1 : 0);
     cudaError_t e = allow_dynamic_smem(f, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, block, smem);
@@ -88,7 +91,7 @@ cudaError_t launch_sweep(int precision, int tally_smem, int gpl, const DevLayout
                          size_t smem, cudaStream_t s) {
     if (dl.offlat) return launch_sweep_ol(precision, dl, st, order, n_work, psi_in, psi_out, counter, grid, s);
     const void *f = sweep_fn(precision, tally_smem, tally_smem && dl.chunk_b > 0, dl.G, gpl, 0,
-                             tally_smem && dl.sync_b > 0 ? 1 : 0);
+                             tally_smem && dl.sync_b > 0 ? 1 : 0, tally_smem ? dl.matk : 0);
     cudaError_t e = allow_dynamic_smem(f, smem);
     if (e != cudaSuccess) return e;
     DevLayout a0 = dl;
@@ -108,7 +111,7 @@ cudaError_t launch_sweep_batch(int precision, int gpl, const DevLayout &dl, cons
                                const int32_t *order, int32_t n_units, int32_t cap, int32_t *counter,
                                const BatchItem *items, int32_t n, int grid, int block, size_t smem,
                                cudaStream_t s) {
-    const void *f = sweep_fn(precision, 1, 0, dl.G, gpl, 1, dl.sync_b > 0 ? 1 : 0);
+    const void *f = sweep_fn(precision, 1, 0, dl.G, gpl, 1, dl.sync_b > 0 ? 1 : 0, dl.matk);
     cudaError_t e = allow_dynamic_smem(f, smem);
     if (e != cudaSuccess) return e;
     DevLayout a0 = dl;

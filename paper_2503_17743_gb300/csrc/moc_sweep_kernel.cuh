@@ -253,7 +253,13 @@ constexpr int kSyncGuard = 8;
 // conflicts, and the record is read once per block.  The tile keeps Qr and
 // Sigma_t in separate arrays, with Sigma_t also once per 2D segment when the
 // segment's region has one material in every layer.
-template <typename real, int GL, int GPL, bool SMEM, bool CHUNK, bool BATCH, bool SYNC = false>
+// MATK (layouts with DevLayout::matk; FP32, two groups per lane, units swept
+// whole, no synchronous blocks): the shared rows hold Qr only and a piece's
+// Sigma_t log2 e comes from the material table, the material read from the
+// record's key (one 8-byte table load serves both frames: a 2D segment lies
+// in one region, and the region has one material in every layer).
+template <typename real, int GL, int GPL, bool SMEM, bool CHUNK, bool BATCH, bool SYNC = false,
+          bool MATK = false>
 __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(real) == 4 ? 3 : 2)
     k_sweep(DevLayout dl, DevState st, const int32_t *order, int32_t n_work, int32_t cap,
             const real *psi_in_p, real *psi_out_p, const BatchItem *items, int32_t n_items) {
@@ -296,6 +302,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
     const int CS = kGM ? RS : 1;
     auto tix = [&](int row, int q) { return kGM ? q * RS + row : row * TS + q; };
     static_assert(!SYNC || (sizeof(real) == 4 && GPL == 2 && SMEM && !CHUNK), "synchronous blocks: FP32 pairs");
+    static_assert(!MATK || (sizeof(real) == 4 && GPL == 2 && SMEM && !CHUNK && !SYNC), "material keys: FP32 pairs");
     if (!BATCH && st.scal[SC_CONV] != 0.0) return;  // converged: later iterations are no-ops
     real *sig = reinterpret_cast<real *>(smem);
     size_t off = ((size_t)M * GP * sizeof(real) + 15) & ~(size_t)15;
@@ -312,11 +319,12 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
         sb_t = reinterpret_cast<float *>(smem + off);
         off += ((size_t)(cap / NL) * GP * 4 + 15) & ~(size_t)15;
     } else {
-        off += (size_t)cap * GP * 2 * sizeof(real);
+        off += (size_t)cap * GP * (MATK ? 1 : 2) * sizeof(real);
     }
     real *tl_s = reinterpret_cast<real *>(smem + off);
     int *tl_i = reinterpret_cast<int *>(smem + off);  // the same tally rows in fixed point
     const unsigned rows_sa = (unsigned)__cvta_generic_to_shared(rows);
+    const unsigned sig_sa = (unsigned)__cvta_generic_to_shared(sig);
     const unsigned tl_sa = (unsigned)__cvta_generic_to_shared(tl_s);
     const unsigned qr_sa = SYNC ? (unsigned)__cvta_generic_to_shared(qr_t) : 0u;
     const unsigned sg_sa = SYNC ? (unsigned)__cvta_generic_to_shared(sg_t) : 0u;
@@ -481,7 +489,47 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                 }
             }
             __syncthreads();  // sig (below: Sigma_t from shared memory) and s_ubnd are complete
-            if (SMEM) {
+            if (SMEM && kFixed && !SYNC && GPL >= 2) {
+                // rows of the (2D segment, layer) FSRs the unit (chunk) crosses:
+                // one thread per (row, pair of groups), so that a row's FSR and
+                // material are found once for two groups; the pair's Qr (and
+                // Sigma_t log2 e) go out in one vector store and its two tally
+                // words are cleared (the block size is a multiple of the pairs
+                // per row, so a thread keeps its pair)
+                constexpr int NP = GP / 2;
+                const int nrow = (b1 - b0) * NL, q0 = 2 * (tid % NP);
+                const float rNL = 1.0f / (float)NL;
+                float bm0 = 0.0f, bm1 = 0.0f;
+                for (int rr = tid / NP; rr < nrow; rr += (int)blockDim.x / NP) {
+                    const int bb = div_by(rr, NL, rNL), L = rr - bb * NL;
+                    const int64_t f = fsr_of(dl, __ldg(reg2d + b0 + bb), L);
+                    const float *qs = reinterpret_cast<const float *>(qr_g) + (size_t)f * G + g0 + q0;
+                    const float qa = q0 < gc ? qs[0] : 0.0f, qb = q0 + 1 < gc ? qs[1] : 0.0f;
+                    const int e = rr * GP + q0;
+                    if constexpr (MATK) {
+                        *reinterpret_cast<float2 *>(reinterpret_cast<float *>(rows) + e) = make_float2(qa, qb);
+                    } else {
+                        const int mt = __ldg(dl.fsr_mat + f);
+                        const float2 sg = *reinterpret_cast<const float2 *>(reinterpret_cast<const float *>(sig) + mt * GP + q0);
+                        *reinterpret_cast<float4 *>(reinterpret_cast<float *>(rows) + 2 * e) =
+                            make_float4(qa, qb, sg.x, sg.y);
+                    }
+                    tl_i[tix(rr, q0)] = 0;
+                    tl_i[tix(rr, q0 + 1)] = 0;
+                    bm0 = fmaxf(bm0, fabsf(qa));
+                    bm1 = fmaxf(bm1, fabsf(qb));
+                }
+                if (bm0 > 0.0f) atomicMax(&s_bmax[q0], __float_as_uint(bm0));
+                if (bm1 > 0.0f) atomicMax(&s_bmax[q0 + 1], __float_as_uint(bm1));
+                if (tid < GP) {
+                    // incoming fluxes and psi handed over from the previous chunk
+                    // enter the bound too (see below)
+                    float v = 0.0f;
+                    if (psi_in && tid < gc) v = __uint_as_float(s_ubnd[tid]) * fabsf((float)scale);
+                    if (C > 1 && ci > 0) v = fmaxf(v, __uint_as_float(s_hmax[tid]));
+                    if (v > 0.0f) atomicMax(&s_bmax[tid], __float_as_uint(v));
+                }
+            } else if (SMEM) {
                 // rows of the (2D segment, layer) FSRs the unit (chunk) crosses
                 for (int bb = warp; bb < b1 - b0; bb += nwarps) {
                     const int b = b0 + bb;
@@ -676,13 +724,21 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                 }
                 // one segment of this slot's track, in tile rows rU (upward frame,
                 // row b * NL + L) and rD (mirrored frame, row b * NL + NL-1-L)
-                auto visit = [&](int rU, int rD, real len) {
+                auto visit = [&](int rU, int rD, real len, int mat) {
                     real tU[GPL], tD[GPL];
                     if (SMEM) {
                         const int eU = rU * GP + qlo, eD = rD * GP + qlo;
                         const int tU_ = tix(rU, qlo), tD_ = tix(rD, qlo);
                         real qU[GPL], sU[GPL], qD[GPL], sD[GPL];
-                        if constexpr (SYNC) {
+                        if constexpr (MATK) {
+                            float2 a, sg;
+                            lds_f2(rows_sa + (unsigned)eU * 4u, a);
+                            qU[0] = a.x; qU[1] = a.y;
+                            lds_f2(rows_sa + (unsigned)eD * 4u, a);
+                            qD[0] = a.x; qD[1] = a.y;
+                            lds_f2(sig_sa + (unsigned)(mat * GP + qlo) * 4u, sg);
+                            sU[0] = sg.x; sU[1] = sg.y; sD[0] = sg.x; sD[1] = sg.y;
+                        } else if constexpr (SYNC) {
                             float2 a, b;
                             lds_f2(qr_sa + eU * 4u, a);
                             lds_f2(sg_sa + eU * 4u, b);
@@ -799,7 +855,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                                   const int (&bs)[4]) {
                     if constexpr (!SMEM) {
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) visit(rU[i], rD[i], len[i]);
+                        for (int i = 0; i < 4; ++i) visit(rU[i], rD[i], len[i], 0);
                     } else {
                         int eU[4], eD[4], fU[4], fD[4];
                         if constexpr (kFixed && GPL == 2) {
@@ -829,6 +885,13 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                                         SU[i] = sb;
                                         SD[i] = sb;
                                     }
+                                } else if constexpr (MATK) {
+                                    // Qr of both frames; Sigma_t of the piece's material
+                                    // (bs: the material from the record's key)
+                                    lds_f2(rows_sa + (unsigned)eU[i] * 4u, QU[i]);
+                                    lds_f2(rows_sa + (unsigned)eD[i] * 4u, QD[i]);
+                                    lds_f2(sig_sa + (unsigned)(bs[i] * GP + qlo) * 4u, SU[i]);
+                                    SD[i] = SU[i];
                                 } else {
                                     row_load_f2(rows_sa + eU[i] * 8u, QU[i], SU[i]);
                                     row_load_f2(rows_sa + eD[i] * 8u, QD[i], SD[i]);
@@ -993,16 +1056,18 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                                 rd[i] = bN - Lt + (NL - 1 - m - rowoff);
                             } else {
                                 ru[i] = tpl_row_up(c[i].key) + m;
-                                rd[i] = tpl_row_down(c[i].key) - m;
+                                rd[i] = (MATK ? tpl_row_down_mat(c[i].key) : tpl_row_down(c[i].key)) - m;
                             }
                             ln[i] = c[i].len;
                         }
                         if constexpr (GPL >= 4) {
                             // eight recurrences per segment already: no batching
 #pragma unroll
-                            for (int i = 0; i < 4; ++i) visit(ru[i], rd[i], ln[i]);
+                            for (int i = 0; i < 4; ++i) visit(ru[i], rd[i], ln[i], 0);
                         } else {
-                            const int bs[4] = {0, 0, 0, 0};
+                            int bs[4];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) bs[i] = MATK ? tpl_mat(c[i].key) : 0;
                             visit4(ru, rd, ln, bs);
                         }
                     };
@@ -1040,9 +1105,9 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                             rd = bN - Lt + (NL - 1 - m - rowoff);
                         } else {
                             ru = tpl_row_up(key) + m;
-                            rd = tpl_row_down(key) - m;
+                            rd = (MATK ? tpl_row_down_mat(key) : tpl_row_down(key)) - m;
                         }
-                        visit(ru, rd, ln);
+                        visit(ru, rd, ln, MATK ? tpl_mat(key) : 0);
                     }
                 } else if (active) {
                     // generated on the fly: this track's own line, layers [0, NL),
@@ -1057,7 +1122,8 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                         int b, L;
                         real len;
                         it.next(dl, dsk, b, L, len);
-                        visit((b - b0) * NL + L, (b - b0) * NL + NL - 1 - L, len);
+                        visit((b - b0) * NL + L, (b - b0) * NL + NL - 1 - L, len,
+                              MATK ? __ldg(dl.reg_mat + __ldg(reg2d + b)) : 0);
                     }
                 }
                 if (active && !last_out) {
@@ -1093,7 +1159,25 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
                 }
             }
             __syncthreads();
+            if (SMEM && kFixed && GPL >= 2) {
+                // one thread per (row, pair of groups), as in the staging
+                constexpr int NP = GP / 2;
+                const int nrow = (b1 - b0) * NL, q0 = 2 * (tid % NP);
+                const int sh0 = s_sh[q0], sh1 = s_sh[q0 + 1];
+                const float rNL = 1.0f / (float)NL;
+                for (int rr = tid / NP; rr < nrow; rr += (int)blockDim.x / NP) {
+                    const int bb = div_by(rr, NL, rNL), L = rr - bb * NL;
+                    const size_t gi = (size_t)fsr_of(dl, __ldg(reg2d + b0 + bb), L) * G + g0 + q0;
+                    const int iv0 = tl_i[tix(rr, q0)], iv1 = tl_i[tix(rr, q0 + 1)];
+                    // into the three-word fixed-point tally: exact, so the order of
+                    // the units does not matter
+                    long long *t3 = reinterpret_cast<long long *>(tally_g) + 3 * gi;
+                    if (iv0 != 0 && q0 < gc && !tally3_add(t3, iv0, sh0)) *err = 2.0;
+                    if (iv1 != 0 && q0 + 1 < gc && !tally3_add(t3 + 3, iv1, sh1)) *err = 2.0;
+                }
+            }
             if (SMEM) {
+                if (!(kFixed && GPL >= 2))
                 for (int bb = warp; bb < b1 - b0; bb += nwarps) {
                     const int reg = __ldg(reg2d + b0 + bb);
                     for (int x = lane; x < NL * GP; x += 32) {
@@ -1149,12 +1233,13 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL), sizeof(re
 
 // the kernel for gl lanes per track; only shapes with gl * GPL <= 32 exist
 // (each translation unit of the sweep instantiates its share)
-template <typename real, int GPL, bool SMEM, bool CHUNK, bool BATCH, int GL = 32 / GPL, bool SYNC = false>
+template <typename real, int GPL, bool SMEM, bool CHUNK, bool BATCH, int GL = 32 / GPL, bool SYNC = false,
+          bool MATK = false>
 const void *pick(int gl) {
     if constexpr (GL > 1) {
-        if (gl < GL) return pick<real, GPL, SMEM, CHUNK, BATCH, GL / 2, SYNC>(gl);
+        if (gl < GL) return pick<real, GPL, SMEM, CHUNK, BATCH, GL / 2, SYNC, MATK>(gl);
     }
-    return (const void *)k_sweep<real, GL, GPL, SMEM, CHUNK, BATCH, SYNC>;
+    return (const void *)k_sweep<real, GL, GPL, SMEM, CHUNK, BATCH, SYNC, MATK>;
 }
 
 template <typename real, int GPL>

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import synth
-from paper_2503_17743_gb300 import MOC_FP32, Geometry, Tracks, track_params
+from paper_2503_17743_gb300 import MOC_FP32, MOC_SCHED_ROWS_WITH_SIGMA, Geometry, Tracks, track_params
 
 pytestmark = pytest.mark.gpu
 
@@ -39,3 +39,40 @@ def test_solve_repeats_bit_for_bit(name):
     assert res[0][0] == res[1][0]
     assert res[0][1] == res[1][1]
     np.testing.assert_array_equal(res[0][2], res[1][2])
+
+
+@pytest.mark.parametrize("name", ["lattice5", "lattice5_rings", "lattice17_small"])
+def test_material_keyed_rows_give_the_same_bits(name):
+    """Where every radial region has one material in all layers, the stored
+    segments carry it and the shared rows hold Qr only, Sigma_t coming from
+    the material table: the same values enter Eq. 3, so a sweep's tallies and
+    an iterated solve's k and flux are the same bits as with rows that carry
+    Sigma_t."""
+    p = synth.workload(name)
+    g = Geometry(p)
+    Q = np.random.default_rng(5).uniform(0.2, 1.0, size=(p.n_fsr, p.num_groups))
+    outs = []
+    for sched, keyed in ((0, 1), (MOC_SCHED_ROWS_WITH_SIGMA, 0)):
+        tr = Tracks(g, track_params(p, precision=MOC_FP32, groups_per_lane=2, schedule=sched))
+        assert tr.info["material_keys"] == keyed
+        t, lk = tr.sweep_from_source(Q)
+        tr.reset()
+        tr.iterate(12)
+        phi, k = tr.flux()
+        outs.append((t, lk, k, phi))
+        tr.close()
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    # (the leakage is summed per lane in the order a lane takes its tracks,
+    # which changes from run to run: equal to rounding)
+    assert outs[0][1] == pytest.approx(outs[1][1], rel=1e-9)
+    assert outs[0][2] == outs[1][2]
+    np.testing.assert_array_equal(outs[0][3], outs[1][3])
+
+
+def test_material_keys_need_one_material_per_region():
+    """asm1_absorber puts an absorber in the top layer of some guide tubes: a
+    region whose material changes with the layer keeps Sigma_t in the rows."""
+    p = synth.workload("asm1_absorber")
+    tr = Tracks(Geometry(p), track_params(p, precision=MOC_FP32, groups_per_lane=2))
+    assert tr.info["material_keys"] == 0
+    tr.close()
