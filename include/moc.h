@@ -358,8 +358,9 @@ int moc_get_segments2d(const moc_tracks *tracks, int32_t t, int64_t cap, int32_t
  *   axial lattice (11 is then 0), 26 fixed-point bits of the FP32 shared
  *   tally per unit bound (0: not used), 27 1 when the stored segments carry
  *   their material and the shared rows hold Qr only (FP32, two groups per
- *   lane, every unit stored and swept whole, one material per radial region,
- *   at most 4 materials; Sigma_t then comes from the material table) */
+ *   lane, shared tally, every unit stored, no synchronous blocks, one
+ *   material per radial region, at most 4 materials; Sigma_t then comes from
+ *   the material table) */
 int moc_tracks_info(const moc_tracks *tracks, int64_t *out, int32_t n);
 
 /* 3D segments of z-stack (t, p) as the device generator produces them

@@ -584,12 +584,12 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     TRY(upload(h.get(), h->d_reg2d, reg2d), "upload");
     TRY(upload(h.get(), h->d_len2d, len2d), "upload");
     TRY(upload(h.get(), h->d_fsr_mat, geo.fsr_mat), "upload");
-    // material keys (DevLayout::matk): FP32, two groups per lane, shared tally,
-    // units swept whole without synchronous blocks, at most 4 materials and
-    // one material per radial region; the stored templates must cover every
-    // unit (checked once they are planned)
-    bool matk_cand = h->precision == MOC_FP32 && h->gpl == 2 && h->tally_smem && h->chunk_b == 0 &&
-                     h->sync_b == 0 && !L.offlat && geo.M <= 4 && !(prm->schedule & MOC_SCHED_ROWS_WITH_SIGMA);
+    // material keys (DevLayout::matk): FP32, two groups per lane, shared tally
+    // (units swept whole or in radial chunks), no synchronous blocks, at most
+    // 4 materials and one material per radial region; the stored templates
+    // must cover every unit (checked once they are planned)
+    bool matk_cand = h->precision == MOC_FP32 && h->gpl == 2 && h->tally_smem && h->sync_b == 0 &&
+                     !L.offlat && geo.M <= 4 && !(prm->schedule & MOC_SCHED_ROWS_WITH_SIGMA);
     if (h->sync_b || matk_cand) {
         // per radial region: its material when every layer has the same one
         // (then Sigma_t is one value per 2D segment of a unit), else -1
@@ -771,16 +771,33 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     TRY(cudaMemcpyAsync(h->d_desc.p, L.desc.data(), ns * sizeof(StackDesc), cudaMemcpyHostToDevice, h->stream), "upload");
     if (matk_cand) {
         // every unit stored, and the mirrored tile rows b NL + NL-1-L_t of the
-        // keys within 14 signed bits
+        // keys within 14 signed bits (radially chunked layouts: the 2D
+        // segment index within 14 unsigned bits)
         for (int64_t s = 0; s < ns && matk_cand; ++s) {
             const StackDesc &d = L.desc[s];
             if (d.exp_base < 0) { matk_cand = false; break; }
+            if (h->chunk_b > 0) {
+                if (d.nb >= 16000) matk_cand = false;
+                continue;
+            }
             for (int r = 0; r < std::min(cpl, d.n_trk); ++r) {
                 const int64_t q = tpl_first[s] + r;
                 if ((int64_t)d.nb * L.nlv - tlmin[q] >= 8000 || tlmin[q] + tnlay[q] >= 8000) matk_cand = false;
             }
         }
         h->matk = matk_cand ? 1 : 0;
+        if (h->matk && h->chunk_b > 0) {
+            // rows of Qr only: wider radial chunks in the same shared memory
+            // (the keys name 2D segments, so the stored records do not change)
+            constexpr size_t kChunkTile = 72 * 1024;
+            int cb = h->chunk_b;
+            while (cb < h->nb_max &&
+                   sweep_smem_bytes(h->precision, 1, 1, geo.M, G, h->gpl, (cb + 1) * L.nlv, 0, 1, 1) <= kChunkTile)
+                ++cb;
+            if (prm->chunk_segments > 0) cb = std::min(cb, (int)prm->chunk_segments);
+            h->chunk_b = cb;
+            h->tile_cap = cb * L.nlv;
+        }
         fill_views(h.get());
     }
     if (!exp_stacks.empty()) {
@@ -937,7 +954,7 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     h->smem = sweep_smem_bytes(h->precision, h->tally_smem, h->chunk_b > 0, geo.M, G, h->gpl, h->tile_cap,
                                h->sync_b, L.nlv, h->matk);
     {
-        const int bmax = sweep_block_threads(h->precision, h->gpl, h->matk);
+        const int bmax = sweep_block_threads(h->precision, h->gpl, h->matk && h->chunk_b == 0);
         h->block = prm->block_threads > 0 ? std::max(32, std::min(prm->block_threads, bmax) / 32 * 32) : bmax;
     }
     int bps = 0;

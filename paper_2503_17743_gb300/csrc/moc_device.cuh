@@ -32,8 +32,8 @@ struct DevLayout {
                              // -1 - (r + m cpl) continuing the block's sequence
     int32_t sync_b;          // tracks per synchronous block (0: none)
     int32_t matk;            // 1: every radial region has one material in all layers, the
-                             // stored records carry it (tpl_key_mat) and the shared rows of
-                             // units swept whole hold Qr only (Sigma_t from the material table)
+                             // stored records carry it (tpl_key_mat, tpl_key_seg_mat) and the
+                             // shared rows hold Qr only (Sigma_t from the material table)
     int32_t tally3;          // 1: the FSR tally is three 64-bit fixed-point words per
                              // FSR-group (FP32 sweeps with the shared tally), else FP64
     const int32_t *reg_mat;  // per radial region: its material if the same in every layer, else -1
@@ -506,6 +506,12 @@ __host__ __device__ __forceinline__ uint32_t tpl_key_mat(int A, int B, int mat) 
 }
 __device__ __forceinline__ int tpl_row_down_mat(uint32_t key) { return (int)(key << 2) >> 18; }
 __device__ __forceinline__ int tpl_mat(uint32_t key) { return (int)(key >> 30); }
+// the same for the keys of radially chunked layouts: 2D segment b < 2^14 in
+// bits 16-29, the template layer in bits 0-15, the material in bits 30-31
+__host__ __device__ __forceinline__ uint32_t tpl_key_seg_mat(int b, int L, int mat) {
+    return (((uint32_t)b & 0x3fffu) << 16) | (uint32_t)(uint16_t)(int16_t)L | ((uint32_t)mat << 30);
+}
+__device__ __forceinline__ int tpl_seg_mat(uint32_t key) { return (int)((key >> 16) & 0x3fffu); }
 __host__ __device__ __forceinline__ uint32_t tpl_key_seg(int b, int L) {
     return ((uint32_t)b << 16) | (uint32_t)(uint16_t)(int16_t)L;
 }

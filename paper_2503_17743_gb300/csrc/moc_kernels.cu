@@ -104,7 +104,8 @@ __global__ void k_tpl_write(DevLayout dl, const int32_t *exp_stacks, int64_t n_e
                     while (x <= L - Lmin && x <= nL) lidx[lb + x++] = pos;
                     SegRec<real> rec{};
                     rec.key = (dl.chunk_b > 0 || dl.sync_b > 1)
-                                  ? tpl_key_seg(b, L)
+                                  ? (dl.matk ? tpl_key_seg_mat(b, L, dl.reg_mat[dl.reg2d[d.seg2d_off + b]])
+                                             : tpl_key_seg(b, L))
                                   : dl.matk ? tpl_key_mat(b * dl.NL + L, b * dl.NL + dl.NL - 1 - L,
                                                           dl.reg_mat[dl.reg2d[d.seg2d_off + b]])
                                             : tpl_key(b * dl.NL + L, b * dl.NL + dl.NL - 1 - L);
@@ -187,7 +188,7 @@ __global__ void k_chunk_tables(DevLayout dl, const int32_t *stacks, int64_t n, i
                 while (lo < hi) {  // first record with b >= c * cb
                     const int64_t mid = (lo + hi) >> 1;
                     const uint32_t key = recs[mid].key;
-                    const int b = tpl_seg(key);
+                    const int b = dl.matk ? tpl_seg_mat(key) : tpl_seg(key);
                     if (b >= bb) hi = mid; else lo = mid + 1;
                 }
                 t[e] = lo;

@@ -70,8 +70,8 @@ const void *sweep_kernel_f32_gpl1(int tally_smem, int chunk, int batch, int gl);
 const void *sweep_kernel_f32_gpl2(int tally_smem, int chunk, int batch, int gl, int sync);
 const void *sweep_kernel_f32_gpl4(int tally_smem, int chunk, int batch, int gl);
 // the variant for layouts whose records carry materials (moc_sweep_f32g2m.cu:
-// two groups per lane, shared tally, units swept whole)
-const void *sweep_kernel_f32_gpl2_matk(int batch, int gl);
+// two groups per lane, shared tally; chunk: some units in radial chunks)
+const void *sweep_kernel_f32_gpl2_matk(int chunk, int batch, int gl);
 const void *sweep_kernel_f64(int tally_smem, int chunk, int batch, int gl);
 cudaError_t sweep_occupancy(int precision, int tally_smem, int chunk, int G, int gpl, int block,
                             size_t smem, int *blocks_per_sm, bool sync = false, bool matk = false);

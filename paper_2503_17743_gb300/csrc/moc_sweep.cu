@@ -20,7 +20,7 @@ const void *sweep_fn(int precision, int tally_smem, int chunk, int G, int gpl, i
                      int matk = 0) {
     const int gl = lanes_for_groups(G, gpl);
     if (precision == MOC_FP64) return sweep_kernel_f64(tally_smem, chunk, batch, gl);
-    if (matk) return sweep_kernel_f32_gpl2_matk(batch, gl);
+    if (matk) return sweep_kernel_f32_gpl2_matk(chunk, batch, gl);
     if (gpl == 4) return sweep_kernel_f32_gpl4(tally_smem, chunk, batch, gl);
     if (gpl == 2) return sweep_kernel_f32_gpl2(tally_smem, chunk, batch, gl, sync);
     return sweep_kernel_f32_gpl1(tally_smem, chunk, batch, gl);

@@ -256,14 +256,15 @@ constexpr int kSyncGuard = 8;
 // conflicts, and the record is read once per block.  The tile keeps Qr and
 // Sigma_t in separate arrays, with Sigma_t also once per 2D segment when the
 // segment's region has one material in every layer.
-// MATK (layouts with DevLayout::matk; FP32, two groups per lane, units swept
-// whole, no synchronous blocks): the shared rows hold Qr only and a piece's
+// MATK (layouts with DevLayout::matk; FP32, two groups per lane, no
+// synchronous blocks): the shared rows hold Qr only and a piece's
 // Sigma_t log2 e comes from the material table, the material read from the
 // record's key (one 8-byte table load serves both frames: a 2D segment lies
 // in one region, and the region has one material in every layer).
 template <typename real, int GL, int GPL, bool SMEM, bool CHUNK, bool BATCH, bool SYNC = false,
           bool MATK = false>
-__global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL, MATK), sweep_min_blocks(sizeof(real) == 4, MATK))
+__global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL, MATK && !CHUNK),
+                                  sweep_min_blocks(sizeof(real) == 4, MATK && !CHUNK))
     k_sweep(DevLayout dl, DevState st, const int32_t *order, int32_t n_work, int32_t cap,
             const real *psi_in_p, real *psi_out_p, const BatchItem *items, int32_t n_items) {
     constexpr int GP = GL * GPL;     // groups per chunk (padded)
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL, MATK), swe
     const int CS = kGM ? RS : 1;
     auto tix = [&](int row, int q) { return kGM ? q * RS + row : row * TS + q; };
     static_assert(!SYNC || (sizeof(real) == 4 && GPL == 2 && SMEM && !CHUNK), "synchronous blocks: FP32 pairs");
-    static_assert(!MATK || (sizeof(real) == 4 && GPL == 2 && SMEM && !CHUNK && !SYNC), "material keys: FP32 pairs");
+    static_assert(!MATK || (sizeof(real) == 4 && GPL == 2 && SMEM && !SYNC), "material keys: FP32 pairs");
     if (!BATCH && st.scal[SC_CONV] != 0.0) return;  // converged: later iterations are no-ops
     real *sig = reinterpret_cast<real *>(smem);
     size_t off = ((size_t)M * GP * sizeof(real) + 15) & ~(size_t)15;
@@ -1054,7 +1055,8 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL, MATK), swe
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             if constexpr (CHUNK) {
-                                const int bN = tpl_seg(c[i].key) * NL, Lt = tpl_layer(c[i].key);
+                                const int bN = (MATK ? tpl_seg_mat(c[i].key) : tpl_seg(c[i].key)) * NL,
+                                          Lt = tpl_layer(c[i].key);
                                 ru[i] = bN + Lt + (m - rowoff);
                                 rd[i] = bN - Lt + (NL - 1 - m - rowoff);
                             } else {
@@ -1103,7 +1105,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL, MATK), swe
                             key = CHUNK ? tpl_key_seg(b0, -m) : tpl_key(-m, m);
                         }
                         if constexpr (CHUNK) {
-                            const int bN = tpl_seg(key) * NL, Lt = tpl_layer(key);
+                            const int bN = (MATK ? tpl_seg_mat(key) : tpl_seg(key)) * NL, Lt = tpl_layer(key);
                             ru = bN + Lt + (m - rowoff);
                             rd = bN - Lt + (NL - 1 - m - rowoff);
                         } else {
