@@ -169,6 +169,7 @@ void fill_views(moc_tracks *h) {
     dl.chunk_b = h->chunk_b;
     dl.sync_b = h->sync_b;
     dl.matk = h->matk;
+    dl.rcpl = dl.cpl > 0 ? 1.0f / (float)dl.cpl : 0.0f;
     dl.reg_mat = (const int32_t *)h->d_reg_mat.p;
     dl.hand_trk = (int32_t)h->hand_trk;
     dl.hand = h->d_hand.p;

@@ -38,6 +38,7 @@ struct DevLayout {
                              // FSR-group (FP32 sweeps with the shared tally), else FP64
     const int32_t *reg_mat;  // per radial region: its material if the same in every layer, else -1
     int32_t Nz, cpl, NL, G, M, Ph;  // NL: the sweep's (uniform) layers
+    float rcpl;              // 1 / cpl rounded to FP32 (0 when cpl = 0)
     int32_t NLr;             // the geometry's layers (FSR = region * NLr + layer)
     const int32_t *lmap;     // the geometry's layer of each sweep layer, or null (the same)
     int32_t bc_zmin, bc_zmax;
@@ -453,6 +454,16 @@ __device__ __forceinline__ float fast_exp2(float x) {
 // so clipping a track to the domain never cuts a template piece.
 
 __device__ __forceinline__ int floor_div(int a, int c) { return a >= 0 ? a / c : -((-a + c - 1) / c); }
+// the same from rc = 1 / c rounded to FP32: for |a| < 2^22 the estimate
+// floor(a rc) is off by at most one, and one correction step makes it exact;
+// larger |a| take the integer division
+__device__ __forceinline__ int floor_div_rc(int a, int c, float rc) {
+    if (a >= (1 << 22) || a <= -(1 << 22)) return floor_div(a, c);
+    int q = __float2int_rd((float)a * rc);
+    const int r = a - q * c;
+    q += (r >= c ? 1 : 0) - (r < 0 ? 1 : 0);
+    return q;
+}
 
 // pieces of the unclipped line u = i0 + zeta(s) inside 2D segment b
 template <typename real>
@@ -470,8 +481,8 @@ __device__ __forceinline__ void tpl_range(const DevLayout &dl, const StackDesc &
     r.ub = i0 + __ldg(dl.zn + d.zoff + b + 1);
     r.fb = lat_frac<real>(dl, d.zoff + b + 1);
     const bool fb_pos = __ldg(dl.zf + d.zoff + b + 1) > 0.0f;
-    r.La = floor_div(r.ua, dl.cpl);
-    r.Le = floor_div(fb_pos ? r.ub : r.ub - 1, dl.cpl);
+    r.La = floor_div_rc(r.ua, dl.cpl, dl.rcpl);
+    r.Le = floor_div_rc(fb_pos ? r.ub : r.ub - 1, dl.cpl, dl.rcpl);
 }
 
 template <typename real>

@@ -1114,6 +1114,9 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL, MATK && !C
                         }
                         visit(ru, rd, ln, MATK ? tpl_mat(key) : 0);
                     }
+                } else if constexpr (MATK) {
+                    // (no unit of a material-keyed layout is generated on the fly:
+                    // the mode needs every unit stored)
                 } else if (active) {
                     // generated on the fly: this track's own line, layers [0, NL),
                     // 2D segments [sb0, sb1]
@@ -1127,8 +1130,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL, MATK && !C
                         int b, L;
                         real len;
                         it.next(dl, dsk, b, L, len);
-                        visit((b - b0) * NL + L, (b - b0) * NL + NL - 1 - L, len,
-                              MATK ? __ldg(dl.reg_mat + __ldg(reg2d + b)) : 0);
+                        visit((b - b0) * NL + L, (b - b0) * NL + NL - 1 - L, len, 0);
                     }
                 }
                 if (active && !last_out) {
