@@ -80,30 +80,63 @@ struct UnitStack {
 };
 constexpr int kMaxPh = 16;
 
-// Template pieces generated on the fly, in the order of one sense, limited to
-// the layers [lo, hi) of the unclipped line i0.
+// Template pieces generated on the fly (Eqs. 8-11 on the integer lattice), in
+// the order of one sense, layers [0, NL) of the unclipped line i0.  The
+// iterator keeps the stack's constants and the lattice coordinates of the
+// current 2D segment's two boundaries (integer part, fraction, fraction > 0
+// in the FP32 table); moving to the next 2D segment reuses the boundary the
+// two share, so each step loads one boundary.  Pieces, lengths and layer
+// ranges are those of tpl_range / tpl_len (the stored templates).
 template <typename real>
 struct TplIter {
-    int i0, b, bend, L, Lend, lo, hi, dir;
-    TplRange<real> r;
+    int i0, b, bend, L, Lend, dir;
+    int zoff, soff;    // the stack's first boundary entry and first 2D segment
+    real lam, isin;    // 3D length per lattice unit; 1 / sin(theta)
+    int ua, ub, La, Le;
+    real fa, fb;
+    bool pa, pb;
     bool done;
 
-    __device__ __forceinline__ void init(const DevLayout &dl, const StackDesc &d, int i0_, int b0,
-                                         int b1, int lo_, int hi_, int dir_) {
+    __device__ __forceinline__ void bound(const DevLayout &dl, int k, int &u, real &f, bool &p) {
+        u = i0 + __ldg(dl.zn + zoff + k);
+        f = lat_frac<real>(dl, zoff + k);
+        p = __ldg(dl.zf + zoff + k) > 0.0f;
+    }
+    __device__ __forceinline__ void init(const DevLayout &dl, const StackDesc &d, int i0_, int b0, int b1,
+                                         int dir_) {
         i0 = i0_;
-        lo = lo_;
-        hi = hi_;
         dir = dir_;
+        zoff = d.zoff;
+        soff = d.seg2d_off;
+        lam = lam_of(d, (real)0);
+        isin = isin_of(d, (real)0);
         b = dir > 0 ? b0 : b1;
         bend = dir > 0 ? b1 : b0;
         done = b0 > b1;
-        if (!done) load_b(dl, d);
+        if (!done) {
+            bound(dl, b, ua, fa, pa);
+            bound(dl, b + 1, ub, fb, pb);
+            settle(dl);
+        }
     }
-    // load 2D segment b, moving on while its layer range is empty
-    __device__ __forceinline__ void load_b(const DevLayout &dl, const StackDesc &d) {
+    // to 2D segment b + dir, reusing the boundary the two segments share
+    __device__ __forceinline__ void step(const DevLayout &dl) {
+        if (dir > 0) {
+            ua = ub; fa = fb; pa = pb;
+            ++b;
+            bound(dl, b + 1, ub, fb, pb);
+        } else {
+            ub = ua; fb = fa; pb = pa;
+            --b;
+            bound(dl, b, ua, fa, pa);
+        }
+    }
+    // the layer range of 2D segment b; moving on while it holds no layer in [0, NL)
+    __device__ __forceinline__ void settle(const DevLayout &dl) {
         for (;;) {
-            tpl_range(dl, d, i0, b, r);
-            const int a = max(r.La, lo), e = min(r.Le, hi - 1);
+            La = floor_div_rc(ua, dl.cpl, dl.rcpl);
+            Le = floor_div_rc(pb ? ub : ub - 1, dl.cpl, dl.rcpl);
+            const int a = max(La, 0), e = min(Le, dl.NL - 1);
             if (a <= e) {
                 L = dir > 0 ? a : e;
                 Lend = dir > 0 ? e : a;
@@ -113,19 +146,21 @@ struct TplIter {
                 done = true;
                 return;
             }
-            b += dir;
+            step(dl);
         }
     }
-    __device__ __forceinline__ void next(const DevLayout &dl, const StackDesc &d, int &ob, int &oL,
-                                         real &len) {
+    __device__ __forceinline__ void next(const DevLayout &dl, int &ob, int &oL, real &len) {
         ob = b;
         oL = L;
-        len = tpl_len(dl, d, b, r, L);
+        if (La == Le) len = len_2d<real>(dl, soff + b) * isin;                          // Eq. 8
+        else if (L == La) len = ((real)((La + 1) * dl.cpl - ua) - fa) * lam;
+        else if (L == Le) len = ((real)(ub - Le * dl.cpl) + fb) * lam;
+        else len = (real)dl.cpl * lam;                                                   // Eq. 11
         if (L != Lend) {
             L += dir;
         } else if (b != bend) {
-            b += dir;
-            load_b(dl, d);
+            step(dl);
+            settle(dl);
         } else {
             done = true;
         }
@@ -493,7 +528,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL, MATK && !C
                 }
             }
             __syncthreads();  // sig (below: Sigma_t from shared memory) and s_ubnd are complete
-            if (SMEM && kFixed && !SYNC && GPL >= 2) {
+            if constexpr (SMEM && kFixed && !SYNC && GPL >= 2) {
                 // rows of the (2D segment, layer) FSRs the unit (chunk) crosses:
                 // one thread per (row, pair of groups), so that a row's FSR and
                 // material are found once for two groups; the pair's Qr (and
@@ -1123,13 +1158,13 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL, MATK && !C
                     const StackDesc &dsk = dl.desc[(int64_t)T * Ph + ph];
                     const int i_trk = u.i_lo + k;
                     TplIter<real> it;
-                    if (CHUNK && C > 1) it.init(dl, dsk, i_trk, sb0, sb1, 0, NL, sense == 0 ? 1 : -1);
-                    else it.init(dl, dsk, i_trk, first_seg(dl, dsk, i_trk), last_seg(dl, dsk, i_trk), 0, NL,
+                    if (CHUNK && C > 1) it.init(dl, dsk, i_trk, sb0, sb1, sense == 0 ? 1 : -1);
+                    else it.init(dl, dsk, i_trk, first_seg(dl, dsk, i_trk), last_seg(dl, dsk, i_trk),
                                  sense == 0 ? 1 : -1);
                     while (!it.done) {
                         int b, L;
                         real len;
-                        it.next(dl, dsk, b, L, len);
+                        it.next(dl, b, L, len);
                         visit((b - b0) * NL + L, (b - b0) * NL + NL - 1 - L, len, 0);
                     }
                 }
@@ -1166,7 +1201,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL, MATK && !C
                 }
             }
             __syncthreads();
-            if (SMEM && kFixed && GPL >= 2) {
+            if constexpr (SMEM && kFixed && GPL >= 2) {
                 // one thread per (row, pair of groups), as in the staging
                 constexpr int NP = GP / 2;
                 const int nrow = (b1 - b0) * NL, q0 = 2 * (tid % NP);
