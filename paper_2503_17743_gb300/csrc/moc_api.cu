@@ -424,6 +424,7 @@ extern "C" int moc_query_footprint(const moc_geometry *g, const moc_track_params
     for (int f = 0; f < 6; ++f) refl |= g->bc[f] != 0;
     if (refl) b += 2 * L.n_gtrk * 4 * G * (int64_t)rs + L.n_gtrk * 4 * 4;  // boundary fluxes, links
     b += L.n_gtrk * (4 + 8);  // sweep order and record windows
+    b += (int64_t)g->nreg * 4;  // the material of each radial region (material-keyed records)
     if (resident) *resident = b;
     if (preload_all && L.offlat) *preload_all = 0;  // planes off the lattice: nothing is stored
     if (preload_all && !L.offlat) {
