@@ -956,7 +956,8 @@ extern "C" int moc_generate_tracks(const moc_geometry *g, const moc_track_params
     h->smem = sweep_smem_bytes(h->precision, h->tally_smem, h->chunk_b > 0, geo.M, G, h->gpl, h->tile_cap,
                                h->sync_b, L.nlv, h->matk);
     {
-        const int bmax = sweep_block_threads(h->precision, h->gpl, h->matk && h->chunk_b == 0);
+        const int bmax = sweep_block_threads(h->precision, h->gpl, h->matk && h->chunk_b == 0,
+                                             h->chunk_b > 0 && !h->matk);
         h->block = prm->block_threads > 0 ? std::max(32, std::min(prm->block_threads, bmax) / 32 * 32) : bmax;
     }
     int bps = 0;

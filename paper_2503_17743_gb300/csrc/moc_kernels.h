@@ -32,7 +32,7 @@ cudaError_t launch_stack_segments(int precision, const DevLayout &dl, int64_t st
 int sweep_default_gpl(int precision, int G);
 int sweep_lanes_per_track(int G, int gpl);
 // threads per sweep block the kernel is compiled for (its launch bound)
-int sweep_block_threads(int precision, int gpl, int matk = 0);
+int sweep_block_threads(int precision, int gpl, int matk = 0, int chunk = 0);
 // sync: tracks per synchronous block (0: none; the split tile), NL: sweep layers
 // matk: rows of Qr only (layouts whose records carry materials)
 size_t sweep_smem_bytes(int precision, int tally_smem, int chunk, int M, int G, int gpl, int cap,

@@ -54,7 +54,9 @@ int sweep_default_gpl(int precision, int G) {
 
 int sweep_lanes_per_track(int G, int gpl) { return lanes_for_groups(G, gpl); }
 
-int sweep_block_threads(int precision, int gpl, int matk) { return sweep_block(precision != MOC_FP64, gpl, matk != 0); }
+int sweep_block_threads(int precision, int gpl, int matk, int chunk) {
+    return sweep_block(precision != MOC_FP64, gpl, matk != 0, chunk != 0);
+}
 
 size_t sweep_smem_bytes(int precision, int tally_smem, int chunk, int M, int G, int gpl, int cap,
                         int sync, int NL, int matk) {

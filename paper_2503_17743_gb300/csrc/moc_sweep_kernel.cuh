@@ -255,8 +255,8 @@ struct TallyAdd<double, 1> {
 // group per lane, nine with more (their extra registers), eight in FP64; the
 // material-keyed kernel (rows of Qr only: a smaller tile) runs four blocks of
 // eight warps (64 registers)
-__host__ __device__ constexpr int sweep_block(bool fp32, int GPL, bool matk = false) {
-    return fp32 ? (GPL == 1 ? 320 : matk ? 256 : 288) : 256;
+__host__ __device__ constexpr int sweep_block(bool fp32, int GPL, bool matk = false, bool chunk = false) {
+    return fp32 ? (GPL == 1 ? 320 : (matk || chunk) ? 256 : 288) : 256;
 }
 __host__ __device__ constexpr int sweep_min_blocks(bool fp32, bool matk) { return fp32 ? (matk ? 4 : 3) : 2; }
 constexpr int kMaxSweepBlock = 320;
@@ -298,7 +298,7 @@ constexpr int kSyncGuard = 8;
 // in one region, and the region has one material in every layer).
 template <typename real, int GL, int GPL, bool SMEM, bool CHUNK, bool BATCH, bool SYNC = false,
           bool MATK = false>
-__global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL, MATK && !CHUNK),
+__global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL, MATK && !CHUNK, CHUNK && !MATK),
                                   sweep_min_blocks(sizeof(real) == 4, MATK && !CHUNK))
     k_sweep(DevLayout dl, DevState st, const int32_t *order, int32_t n_work, int32_t cap,
             const real *psi_in_p, real *psi_out_p, const BatchItem *items, int32_t n_items) {
