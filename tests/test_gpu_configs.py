@@ -40,6 +40,11 @@ def test_large_configuration_samples(name, budget, n_stacks):
     if budget > 0:
         # part stored, part generated on the fly (Sec. 4.2)
         assert 0 < info["preloaded_stacks"] < info["stacks"] // 2
+    # both sweep in radial chunks; the core's records carry their material
+    # (one material per radial region), the assemblies' rows carry Sigma_t
+    # (the absorber changes a guide tube's material with the layer)
+    assert info["chunk_segments"] > 0
+    assert info["material_keys"] == (1 if name == "core7x7" else 0)
     rng = np.random.default_rng(31)
     for _ in range(n_stacks):
         t = int(rng.integers(o.n_tracks2d))
