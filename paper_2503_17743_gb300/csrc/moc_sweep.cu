@@ -74,8 +74,8 @@ size_t sweep_smem_bytes(int precision, int tally_smem, int chunk, int M, int G, 
     }
     // (Qr, Sigma_t) rows (Qr only with material keys) + tally rows
     b += (size_t)cap * gp * rs * (matk ? 1 : 2) +
-         (precision == MOC_FP64 || chunk ? (size_t)cap * tally_stride((int)(gp / gpl), gpl)
-                                         : (size_t)tally_rows(cap, (int)(gp / gpl), gpl) * gp) * rs;
+         (precision == MOC_FP64 || (chunk && !matk) ? (size_t)cap * tally_stride((int)(gp / gpl), gpl)
+                                                    : (size_t)tally_rows(cap, (int)(gp / gpl), gpl) * gp) * rs;
     return b;
 }
 

@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(sweep_block(sizeof(real) == 4, GPL, MATK && !C
     // tile of units swept whole, row-major otherwise (FP64; and radial
     // chunks, whose kernel is short of registers for the stride);
     // CS = words from group q to q + 1 of the same row
-    constexpr bool kGM = kFixed && !CHUNK;
+    constexpr bool kGM = kFixed && (!CHUNK || MATK);
     // units swept whole without synchronous blocks: a warp task takes SLOTS
     // consecutive slots of the unit's stacks laid end to end (tracks of two
     // polar stacks may share a warp), so that only the unit's last task per
